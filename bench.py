@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark of the SSP2(222) IMEX step for resistive SRMHD on GB300.
+
+Workload: 2-D resistive SRMHD Kelvin-Helmholtz shear layer, 1024 x 1024 cells,
+periodic, Gamma = 4/3, sigma = 1e3, seeded synthetic data (the shape of the
+paper's KHI test, Sec. 4.4). One "step" = one full SSP2(222) IMEX step (two
+implicit per-cell stage solves, two WENO3/LF flux passes, stage combine and
+recovery) over all cells. Metric: cell-updates/s.
+
+Printed JSON line: the FP64 form is `value`; the mixed form (FP32 flux
+arithmetic, FP64 source solve) is under "mixed" with its error against the
+FP64 result; "e2e" is the same metric through the C ABI with host buffers
+(prims uploaded and read back every step); "roofline" is for the dominant
+kernel, timed with CUDA events inside the timed region; "cpu_baseline" is the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling); the
+time is the max over ranks.
+
+`--impl reference` times the CPU oracle instead (the reference arm of this
+repository: there is no reference implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per IMEX step, FP64 vs mixed, % HBM roofline; adjoint/fwd cost"
+UNIT = "cell-updates/s"
+WORKLOAD = "khi-2d-1024x1024 (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=4/3, sigma=1e3, SSP2(222), WENO3+LF)"
+
+# Algorithmic FP64 operations per interior cell for each kernel of the FP64
+# form on a 2-D grid (counted from the kernels' arithmetic; each FP64 pipe
+# instruction -- add, mul, fma, approximate reciprocal/rsqrt, conversion --
+# counts as one op). See DESIGN.md "Roofline".
+FP64_OPS_PER_CELL = {"stage": 210.0, "flux1": 960.0, "flux2": 1010.0}
+# Algorithmic HBM bytes per cell for each kernel (read once + written once).
+BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured", float(d.get("sm_max_mhz", 2070.0))
+    return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def natural_scale(model, want, mu_ref=1.0):
+    """Per-variable scale used for errors (vector components share one; the
+    charge/cleaning fields are scaled by the field magnitude)."""
+    import numpy as np
+    m = np.abs(want).reshape(want.shape[0], -1).max(axis=1)
+    s = m.copy()
+    for a, b in ((1, 4), (5, 8), (8, 11)):
+        s[a:b] = m[a:b].max()
+    s[11:14] = np.maximum(m[11:14], max(s[5], s[8]))
+    return np.maximum(s, 1e-300)
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """FP64 CPU oracle on the host cores: KHI recipe at 128 x 128 (a bounded
+    sample of the benchmark workload), as many steps as fit in ~`seconds`."""
+    import oracle as O
+    from paper_1808_09721_gb300 import workloads as WL
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    wl = WL.khi(n=128, seed=0)
+    s = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
+    s.set_prims(wl.prims)
+    t0 = time.perf_counter()
+    s.step(wl.dt, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(200, int(seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(wl.dt, steps)
+    el = time.perf_counter() - t0
+    value = steps * wl.cells / el
+    # one-core figure (the paper's CPU baseline is a single core), short sample
+    O.set_threads(1)
+    s1 = O.Sim(wl.model, 32, 32, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
+    s1.set_prims(WL.khi(n=32, seed=0).prims)
+    t0 = time.perf_counter()
+    s1.step(wl.dt, 2)
+    one = 2 * 32 * 32 / (time.perf_counter() - t0)
+    O.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"KHI recipe 128x128 periodic, {steps} SSP2(222) steps ({el:.1f} s), all host cores",
+            "single_core_value": one}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle, each step a bounded sample (one
+    SSP2(222) step of the KHI recipe at 96 x 96)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1808_09721_gb300 import workloads as WL
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    wl = WL.khi(n=96, seed=0)
+    s = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
+    s.set_prims(wl.prims)
+    s.step(wl.dt, args.warmup)
+    t0 = time.perf_counter()
+    s.step(wl.dt, args.steps)
+    el = time.perf_counter() - t0
+    value = args.steps * wl.cells / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "96x96 window of the same recipe per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+                             "sample": f"KHI recipe 96x96 periodic, one SSP2(222) step per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--n", type=int, default=1024, help="grid side (default: the 1024^2 workload)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1808_09721_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+    from paper_1808_09721_gb300 import FP64, MIXED, HOST
+    from paper_1808_09721_gb300 import workloads as WL
+    from paper_1808_09721_gb300.sim import Sim
+
+    wl = WL.khi(n=args.n, seed=0)
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_run(precision, profile):
+        sim = Sim.from_workload(wl, precision=precision, device=f"cuda:{local}")
+        sim.step(wl.dt, W)
+        sim.check()
+        sim.set_profiling(profile)
+        st = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        sim.step(wl.dt, K)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kt = sim.kernel_times() if profile else None
+        sim.set_profiling(False)
+        sim.check()
+        return sim, max_over_ranks(ms), kt
+
+    with ClockSampler(local) as clk:
+        sim64, ms64, kt64 = timed_run(FP64, True)
+    clocks = clk.summary()
+    simmx, msmx, ktmx = timed_run(MIXED, True)
+    q64, qmx = sim64.cons(), simmx.cons()
+    rel_l1_mixed = float(np.max(np.abs(qmx - q64).reshape(14, -1).mean(axis=1) / natural_scale(0, q64)))
+    del simmx
+
+    total_cells = world * wl.cells
+    value = total_cells * K / (ms64 * 1e-3)
+    value_mx = total_cells * K / (msmx * 1e-3)
+
+    # e2e through the C ABI with host buffers: upload prims, one step, read prims back
+    pin = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)
+    pin[...] = wl.prims
+    out = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)
+    e2e_sim = sim64
+    for _ in range(2):
+        e2e_sim.set_prims(pin)
+        e2e_sim.step(wl.dt, 1)
+        e2e_sim.prims(out=out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_sim.set_prims(pin)
+        e2e_sim.step(wl.dt, 1)
+        e2e_sim.prims(out=out)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = total_cells * K / e2e_s
+    io_bytes = wl.prims.size * 8
+
+    # roofline of the dominant kernel (FP64 form)
+    hbm_gbs, peak_src, smax = _peaks()
+    dom = max(kt64, key=lambda k: kt64[k][0])
+    dom_ms, dom_n = kt64[dom]
+    per_launch_ms = dom_ms / dom_n
+    fp64_peak = 2.0 * 152 * smax * 1e6 / 1e12  # TOP/s: 2 FP64 lanes/clk/SM x 152 SMs x max clock
+    achieved = FP64_OPS_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3) / 1e12
+    hbm_achieved = BYTES_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None, "kernel": dom,
+                "kernel_ms_per_launch": per_launch_ms,
+                "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
+                "hbm_gbs": hbm_achieved, "hbm_frac": hbm_achieved / hbm_gbs,
+                "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": peak_src}
+    step_bytes = 1056.0  # algorithmic HBM bytes per cell-update of the whole step
+    kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt64.items()}
+    kernels_mx = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in ktmx.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms64 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells_per_gpu": wl.cells, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2: state+workspace %.2f GB > 129 MB" %
+                                 (sim64.workspace.numel() / 1e9)},
+                "mixed": {"value": value_mx, "ms_per_step": msmx / K, "dtype": "f32 flux / f64 source",
+                          "rel_l1_vs_fp64": rel_l1_mixed, "speedup_vs_fp64": value_mx / value, "kernels": kernels_mx},
+                "hbm_roofline_step": {"bytes_per_cell_update": step_bytes,
+                                      "achieved_gbs": step_bytes * value / world / 1e9,
+                                      "frac": step_bytes * value / world / 1e9 / hbm_gbs},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                        "d2h_bytes_per_step": io_bytes},
+                "gpu_launches": 4 * K,
+                "roofline": roofline,
+                "kernels": kernels,
+                "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

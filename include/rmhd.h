@@ -1,0 +1,150 @@
+/*
+ * rmhd.h -- C ABI of the GB300 (sm_103a) library for one SSP2(222) IMEX time
+ * step of resistive special-relativistic MHD, single-fluid and two-fluid,
+ * after Wright & Hawke, "Resistive and multi-fluid RMHD on graphics
+ * processing units" (arXiv:1808.09721).
+ *
+ * Conventions
+ *   - Every call returns an int status: RMHD_OK (0) or a negative RMHD_ERR_*.
+ *     rmhd_last_error() gives a message owned by the context, valid until the
+ *     next call on that context.
+ *   - Arrays are structure-of-arrays FP64, variable-major, x fastest:
+ *     a[v][j][i] at a[(v * ny + j) * nx + i], interior cells only (no ghosts).
+ *   - `where` selects RMHD_HOST (pageable or pinned host memory) or
+ *     RMHD_DEVICE (memory of the context's GPU). The caller keeps ownership of
+ *     every array it passes; the library copies and never keeps the pointer.
+ *   - All device work is issued on the CUDA stream given to rmhd_create. Calls
+ *     marked "async" return after enqueueing; the calls that read results back
+ *     synchronise that stream first.
+ *
+ * Variables (Sec. 2.1.1 and Sec. 2.1.2 of the paper)
+ *   one fluid, 14 conserved: D, S_x, S_y, S_z, tau, B_x, B_y, B_z, E_x, E_y, E_z, varrho, psi, phi
+ *   one fluid, 11 primitives: rho, v_x, v_y, v_z, p, B_x, B_y, B_z, E_x, E_y, E_z
+ *   two fluids, 18 conserved: D, S_xyz, tau, Dbar, Sbar_xyz, taubar, B_xyz, E_xyz, psi, phi
+ *   two fluids, 16 primitives: rho_e, v_e(3), p_e, rho_p, v_p(3), p_p, B(3), E(3)
+ */
+#ifndef RMHD_H
+#define RMHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RMHD_OK 0
+#define RMHD_ERR_INVALID (-1)  /* bad argument, or inadmissible primitive state (v >= 1, rho <= 0, p <= 0, NaN) */
+#define RMHD_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define RMHD_ERR_NEWTON (-3)   /* an implicit-stage solve did not converge in some cell */
+#define RMHD_ERR_C2P (-4)      /* primitive recovery failed in some cell */
+#define RMHD_ERR_STATE (-5)    /* call out of order (e.g. step before set_prims) */
+#define RMHD_ERR_NOMEM (-6)    /* workspace too small or allocation failed */
+
+/* models */
+#define RMHD_RESISTIVE 0 /* single-fluid resistive SRMHD, Eq. (resistive RMHD), N_c = 14 */
+#define RMHD_TWO_FLUID 1 /* two-fluid resistive SRMHD, Eq. (twoFluid cons) + Appendix A, N_c = 18 */
+
+/* boundary conditions */
+#define RMHD_OUTFLOW 0  /* ghost cells copy the nearest interior cell */
+#define RMHD_PERIODIC 1 /* ghost cells wrap around */
+
+/* flux arithmetic */
+#define RMHD_FP64 0  /* everything in FP64 */
+#define RMHD_MIXED 1 /* WENO3/flux arithmetic in FP32 with FP64 accumulation of the update;
+                        the implicit source solve, primitive recovery and current J stay FP64 */
+
+/* memory kinds for `where` */
+#define RMHD_HOST 0
+#define RMHD_DEVICE 1
+
+typedef struct rmhd_config {
+    int model;        /* RMHD_RESISTIVE or RMHD_TWO_FLUID */
+    int nx, ny;       /* interior cells; ny = 1 is a 1-D run along x */
+    double xmin, xmax, ymin, ymax;
+    double gamma;     /* Gamma-law EOS p = rho e (Gamma - 1), Sec. 2.1; 1 < Gamma <= 2 */
+    double sigma;     /* conductivity (one fluid, Ohm's law of Sec. 2.1.1); eta = 1/sigma for two fluids */
+    double mu_e, mu_p;/* charge-to-mass ratios (two fluids only), mu_e != mu_p */
+    double kappa;     /* divergence-cleaning rate, 1 in the paper (Sec. 2.1.1) */
+    double cfl;       /* dt = cfl * min(dx, dy) when rmhd_imex_step gets dt <= 0 */
+    int bc_x, bc_y;   /* RMHD_OUTFLOW or RMHD_PERIODIC */
+    int precision;    /* RMHD_FP64 or RMHD_MIXED */
+    int reserved[5];  /* set to 0 */
+} rmhd_config;
+
+typedef struct rmhd_ctx rmhd_ctx;
+
+/* Bytes of device workspace a context with this configuration needs.
+ * Errors: RMHD_ERR_INVALID for a bad configuration. */
+int rmhd_workspace_bytes(const rmhd_config *cfg, size_t *bytes);
+
+/* Create a context on the device of `cuda_stream` (a cudaStream_t; NULL means
+ * the legacy default stream of the current device). If `workspace` is not
+ * NULL it must be device memory of at least rmhd_workspace_bytes() bytes,
+ * 256-byte aligned, owned by the caller and kept alive until rmhd_destroy;
+ * otherwise the library allocates (and later frees) its own.
+ * Errors: RMHD_ERR_INVALID, RMHD_ERR_NOMEM, RMHD_ERR_CUDA. On error *out is NULL. */
+int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream,
+                void *workspace, size_t workspace_bytes);
+
+/* Release the context (synchronises its stream). NULL is accepted. */
+void rmhd_destroy(rmhd_ctx *ctx);
+
+/* Message for the last failing call on this context (never NULL). */
+const char *rmhd_last_error(const rmhd_ctx *ctx);
+
+/* Set the state from primitives [n_prim][ny][nx] (11 or 16 variables, see
+ * above). psi = phi = 0 (Sec. 2.1.1). For one fluid the charge density is
+ * initialised from Gauss's law varrho = div E by second-order central
+ * differences with the boundary conditions (Sec. 2.1.1). Conserved variables
+ * follow Eq. (resistive prims) / Eq. (twoFluid cons). Synchronous.
+ * Errors: RMHD_ERR_INVALID (inadmissible state; message names the first cell). */
+int rmhd_set_prims(rmhd_ctx *ctx, const double *prims, int where);
+
+/* Primitives of the current state in the same layout. Synchronous. */
+int rmhd_get_prims(rmhd_ctx *ctx, double *prims, int where);
+
+/* Conserved state [N_c][ny][nx]; set_cons recovers the primitives
+ * (Sec. 2.1.3) and fails with RMHD_ERR_C2P if some cell has none. Synchronous. */
+int rmhd_get_cons(rmhd_ctx *ctx, double *cons, int where);
+int rmhd_set_cons(rmhd_ctx *ctx, const double *cons, int where);
+
+/* Advance `nsteps` SSP2(222) IMEX steps (Sec. 2.2.1, Table 1) with fluxes from
+ * Lax-Friedrichs splitting + WENO3 (Sec. 2.2.2). dt <= 0 selects
+ * dt = cfl * min(dx, dy). Async: enqueued on the context's stream. A failed
+ * implicit solve or recovery is recorded on the device and reported by the
+ * next synchronous call (or rmhd_check). If t_out is not NULL it receives the
+ * simulation time after the steps (host bookkeeping, no synchronisation). */
+int rmhd_imex_step(rmhd_ctx *ctx, double dt, int nsteps, double *t_out);
+
+/* Synchronise the stream and report any failure recorded on the device since
+ * the last check: RMHD_ERR_NEWTON or RMHD_ERR_C2P with the first failing cell
+ * in rmhd_last_error. */
+int rmhd_check(rmhd_ctx *ctx);
+
+/* Diagnostics of the current state (Sec. 2.1 invariants), written to out[8]:
+ * sum D, sum tau, sum S_x, sum B_x, sum varrho (Dbar for two fluids)
+ * (cell sums times dx dy), max |v|, number of non-finite conserved values,
+ * and the CFL time step cfl * min(dx, dy). Synchronous. */
+int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
+
+/* Per-kernel timing for roofline measurements (no counterpart in the paper,
+ * which times whole main-loop iterations). While enabled, rmhd_imex_step
+ * launches its kernels without a CUDA graph and brackets each launch with
+ * CUDA events on the context's stream. rmhd_kernel_times synchronises the
+ * stream, writes the summed milliseconds and launch counts per kernel kind
+ * (RMHD_K_STAGE, RMHD_K_FLUX1, RMHD_K_FLUX2) into ms[3] and counts[3], and
+ * clears the record. Enabling twice or disabling while off is harmless. */
+#define RMHD_K_STAGE 0 /* implicit-stage solve (both stages) */
+#define RMHD_K_FLUX1 1 /* flux pass after stage 1 (+ stage-2 right-hand side) */
+#define RMHD_K_FLUX2 2 /* flux pass after stage 2 (+ combine + recovery) */
+int rmhd_set_profiling(rmhd_ctx *ctx, int enable);
+int rmhd_kernel_times(rmhd_ctx *ctx, double *ms, int *counts);
+
+/* Library version string. */
+const char *rmhd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMHD_H */

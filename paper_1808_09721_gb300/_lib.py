@@ -1,0 +1,75 @@
+"""ctypes declarations of the C ABI in include/rmhd.h (librmhd.so).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of librmhd.so. If the library is missing or cannot be loaded the import fails
+loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librmhd.so")
+
+RMHD_OK = 0
+ERRORS = {-1: "RMHD_ERR_INVALID", -2: "RMHD_ERR_CUDA", -3: "RMHD_ERR_NEWTON", -4: "RMHD_ERR_C2P",
+          -5: "RMHD_ERR_STATE", -6: "RMHD_ERR_NOMEM"}
+RESISTIVE, TWO_FLUID = 0, 1
+OUTFLOW, PERIODIC = 0, 1
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+
+# every symbol include/rmhd.h declares
+EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_error", "rmhd_set_prims",
+           "rmhd_get_prims", "rmhd_get_cons", "rmhd_set_cons", "rmhd_imex_step", "rmhd_check",
+           "rmhd_diagnostics", "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_version")
+
+
+class Config(C.Structure):
+    _fields_ = [("model", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
+                ("gamma", C.c_double), ("sigma", C.c_double), ("mu_e", C.c_double), ("mu_p", C.c_double),
+                ("kappa", C.c_double), ("cfl", C.c_double),
+                ("bc_x", C.c_int), ("bc_y", C.c_int), ("precision", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class RmhdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def load(path: str | None = None):
+    """Load librmhd.so (build it first with paper_1808_09721_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"librmhd.so not found at {p}: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(p)
+    for name in EXPORTS:
+        if not hasattr(L, name):
+            raise ImportError(f"librmhd.so lacks {name}")
+    L.rmhd_workspace_bytes.argtypes = [C.POINTER(Config), C.POINTER(C.c_size_t)]
+    L.rmhd_create.argtypes = [C.POINTER(_P), C.POINTER(Config), _P, _P, C.c_size_t]
+    L.rmhd_destroy.argtypes = [_P]
+    L.rmhd_destroy.restype = None
+    L.rmhd_last_error.argtypes = [_P]
+    L.rmhd_last_error.restype = C.c_char_p
+    for name in ("rmhd_set_prims", "rmhd_get_prims", "rmhd_get_cons", "rmhd_set_cons"):
+        getattr(L, name).argtypes = [_P, _P, C.c_int]
+    L.rmhd_imex_step.argtypes = [_P, C.c_double, C.c_int, _D]
+    L.rmhd_check.argtypes = [_P]
+    L.rmhd_diagnostics.argtypes = [_P, _D]
+    L.rmhd_set_profiling.argtypes = [_P, C.c_int]
+    L.rmhd_kernel_times.argtypes = [_P, _D, C.POINTER(C.c_int)]
+    L.rmhd_version.restype = C.c_char_p
+    _lib = L
+    return L

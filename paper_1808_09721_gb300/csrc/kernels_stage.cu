@@ -1,0 +1,334 @@
+// kernels_stage.cu -- per-cell kernels: the implicit IMEX stage solve (Eq.
+// implicit stage of Wright & Hawke, arXiv:1808.09721), primitive <-> conserved
+// maps (Eq. resistive prims, Eq. twoFluid cons), primitive recovery
+// (Sec. 2.1.3), layout packing and the diagnostics reduction.
+#include "rmhd_internal.h"
+#include "physics_sf.cuh"
+#include "physics_tf.cuh"
+
+namespace rmhd {
+
+static constexpr int kStageThreads = 128;
+static constexpr int kNRef = 2;  // FP64 refinement passes per stage solve
+
+__device__ __forceinline__ void record(int *status, int st, long long cell) {
+    if (st != 0) {
+        atomicCAS(status, 0, st);
+        atomicMin(status + 1, (int)cell);
+    }
+}
+
+__device__ __forceinline__ int wrap(int i, int n, int bc) {
+    if (bc == 1) {
+        i %= n;
+        return i < 0 ? i + n : i;
+    }
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// ---------------------------------------------------------------- stage
+__global__ void __launch_bounds__(kStageThreads) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
+    using namespace sf;
+    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma};
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        double r[NC], q[NC], w[NW];
+#pragma unroll
+        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
+        double pw = a.wwarm[P * g.plane + cell];
+        int st = stage_solve<kNRef>(r, pw, k, q, w);
+        record(a.status, st, cell);
+#pragma unroll
+        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
+#pragma unroll
+        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
+    }
+}
+
+__global__ void __launch_bounds__(kStageThreads) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
+    using namespace tf;
+    tf::StageConst k{a.adt, cpsi};
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        double r[NC], q[NC], w[NW], ww[NW];
+#pragma unroll
+        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
+#pragma unroll
+        for (int v = 0; v < NW; ++v) ww[v] = a.wwarm[v * g.plane + cell];
+        int st = stage_solve<kNRef>(r, ww, k, ph, q, w);
+        record(a.status, st, cell);
+#pragma unroll
+        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
+#pragma unroll
+        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
+    }
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > (1 << 30) ? (1 << 30) : b));
+}
+
+cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s) {
+    double cpsi = 1.0 / (1.0 + a.adt * ph.kappa);
+    int blocks = grid_for(g.ncell, kStageThreads);
+    if (model == 0) k_stage_sf<<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+    else k_stage_tf<<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- prims -> cons
+// user primitives are dense [np][ny][nx]; the state uses padded planes.
+__global__ void k_set_prims_sf(Grid g, Phys ph, const double *U, double *q, double *w, int *status) {
+    using namespace sf;
+    const long long n = g.ncell;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+         cell += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(cell / g.nx), i = (int)(cell - (long long)j * g.nx);
+        double rho = U[0 * n + cell], v[3] = {U[1 * n + cell], U[2 * n + cell], U[3 * n + cell]}, p = U[4 * n + cell];
+        double B[3] = {U[5 * n + cell], U[6 * n + cell], U[7 * n + cell]};
+        double E[3] = {U[8 * n + cell], U[9 * n + cell], U[10 * n + cell]};
+        double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        bool ok = rho > 0.0 && p > 0.0 && v2 < 1.0 && isfinite(rho + p + v2 + B[0] + B[1] + B[2] + E[0] + E[1] + E[2]);
+        if (!ok) { record(status, -1, cell); continue; }
+        // Gauss's law varrho = div E, central differences with the boundary map
+        int il = wrap(i - 1, g.nx, g.bcx), ir = wrap(i + 1, g.nx, g.bcx);
+        double divE = (U[8 * n + (long long)j * g.nx + ir] - U[8 * n + (long long)j * g.nx + il]) / (2.0 * g.dx);
+        if (g.ny > 1) {
+            int jl = wrap(j - 1, g.ny, g.bcy), jr = wrap(j + 1, g.ny, g.bcy);
+            divE += (U[9 * n + (long long)jr * g.nx + i] - U[9 * n + (long long)jl * g.nx + i]) / (2.0 * g.dy);
+        }
+        double W = 1.0 / sqrt(1.0 - v2);
+        double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
+        double Z = rho * h * W * W;
+        double ExB[3];
+        cross(E, B, ExB);
+        double qc[NC];
+        qc[D] = rho * W;
+        for (int k = 0; k < 3; ++k) {
+            qc[SX + k] = Z * v[k] + ExB[k];
+            qc[BX + k] = B[k];
+            qc[EX + k] = E[k];
+        }
+        qc[TAU] = Z - p + 0.5 * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) - rho * W;
+        qc[RHOE] = divE;
+        qc[PSI] = 0.0;
+        qc[PHI] = 0.0;
+        for (int k = 0; k < NC; ++k) q[k * g.plane + cell] = qc[k];
+        w[VX * g.plane + cell] = v[0];
+        w[VY * g.plane + cell] = v[1];
+        w[VZ * g.plane + cell] = v[2];
+        w[P * g.plane + cell] = p;
+        w[LOR * g.plane + cell] = W;
+    }
+}
+
+__global__ void k_set_prims_tf(Grid g, Phys ph, const double *U, double *q, double *w, int *status) {
+    using namespace tf;
+    const long long n = g.ncell;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+         cell += (long long)gridDim.x * blockDim.x) {
+        double qc[NC];
+        for (int k = 0; k < NC; ++k) qc[k] = 0.0;
+        const double mu[2] = {ph.mu_e, ph.mu_p};
+        double B[3] = {U[10 * n + cell], U[11 * n + cell], U[12 * n + cell]};
+        double E[3] = {U[13 * n + cell], U[14 * n + cell], U[15 * n + cell]};
+        bool ok = isfinite(B[0] + B[1] + B[2] + E[0] + E[1] + E[2]);
+        for (int s = 0; s < 2; ++s) {
+            double rho = U[(5 * s) * n + cell], p = U[(5 * s + 4) * n + cell];
+            double v[3] = {U[(5 * s + 1) * n + cell], U[(5 * s + 2) * n + cell], U[(5 * s + 3) * n + cell]};
+            double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            ok = ok && rho > 0.0 && p > 0.0 && v2 < 1.0 && isfinite(rho + p + v2);
+            double W = 1.0 / sqrt(1.0 - v2);
+            double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
+            double Z = rho * h * W * W;
+            qc[D] += rho * W;
+            qc[DB] += mu[s] * rho * W;
+            for (int k = 0; k < 3; ++k) {
+                qc[SX + k] += Z * v[k];
+                qc[SBX + k] += mu[s] * Z * v[k];
+            }
+            qc[TAU] += Z - p - rho * W;
+            qc[TAUB] += mu[s] * (Z - p - rho * W);
+            for (int k = 0; k < 3; ++k) w[(5 * s + k) * g.plane + cell] = v[k];
+            w[(5 * s + P) * g.plane + cell] = p;
+            w[(5 * s + ZZ) * g.plane + cell] = Z;
+        }
+        if (!ok) { record(status, -1, cell); continue; }
+        double ExB[3];
+        cross(E, B, ExB);
+        for (int k = 0; k < 3; ++k) {
+            qc[SX + k] += ExB[k];
+            qc[BX + k] = B[k];
+            qc[EX + k] = E[k];
+        }
+        qc[TAU] += 0.5 * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        for (int k = 0; k < NC; ++k) q[k * g.plane + cell] = qc[k];
+    }
+}
+
+cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const double *prims, double *q, double *w,
+                             int *status, cudaStream_t s) {
+    int blocks = grid_for(g.ncell, 256);
+    if (model == 0) k_set_prims_sf<<<blocks, 256, 0, s>>>(g, ph, prims, q, w, status);
+    else k_set_prims_tf<<<blocks, 256, 0, s>>>(g, ph, prims, q, w, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- state -> user primitives
+__global__ void k_get_prims_sf(Grid g, const double *q, const double *w, double *U) {
+    using namespace sf;
+    const long long n = g.ncell;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+         cell += (long long)gridDim.x * blockDim.x) {
+        U[0 * n + cell] = q[D * g.plane + cell] / w[LOR * g.plane + cell];
+        U[1 * n + cell] = w[VX * g.plane + cell];
+        U[2 * n + cell] = w[VY * g.plane + cell];
+        U[3 * n + cell] = w[VZ * g.plane + cell];
+        U[4 * n + cell] = w[P * g.plane + cell];
+        for (int k = 0; k < 6; ++k) U[(5 + k) * n + cell] = q[(BX + k) * g.plane + cell];
+    }
+}
+
+__global__ void k_get_prims_tf(Grid g, Phys ph, const double *q, const double *w, double *U) {
+    using namespace tf;
+    const long long n = g.ncell;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+         cell += (long long)gridDim.x * blockDim.x) {
+        double Dt = q[D * g.plane + cell], Db = q[DB * g.plane + cell];
+        double Ds[2] = {(Db - ph.mu_p * Dt) / (ph.mu_e - ph.mu_p), (ph.mu_e * Dt - Db) / (ph.mu_e - ph.mu_p)};
+        for (int s = 0; s < 2; ++s) {
+            double v[3] = {w[(5 * s) * g.plane + cell], w[(5 * s + 1) * g.plane + cell], w[(5 * s + 2) * g.plane + cell]};
+            double W = 1.0 / sqrt(1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+            U[(5 * s) * n + cell] = Ds[s] / W;
+            for (int k = 0; k < 3; ++k) U[(5 * s + 1 + k) * n + cell] = v[k];
+            U[(5 * s + 4) * n + cell] = w[(5 * s + P) * g.plane + cell];
+        }
+        for (int k = 0; k < 6; ++k) U[(10 + k) * n + cell] = q[(BX + k) * g.plane + cell];
+    }
+}
+
+cudaError_t launch_get_prims(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
+                             double *prims, cudaStream_t s) {
+    int blocks = grid_for(g.ncell, 256);
+    if (model == 0) k_get_prims_sf<<<blocks, 256, 0, s>>>(g, q, w, prims);
+    else k_get_prims_tf<<<blocks, 256, 0, s>>>(g, ph, q, w, prims);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- recovery
+__global__ void k_recover(int model, Grid g, Phys ph, const double *q, double *w, int *status) {
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        if (model == 0) {
+            double qc[sf::NC], wc[sf::NW];
+            for (int v = 0; v < sf::NC; ++v) qc[v] = q[v * g.plane + cell];
+            // cold start: the recovery brackets the root itself
+            int st = sf::recover(qc, -1.0, ph.gamma, wc);
+            record(status, st, cell);
+            for (int v = 0; v < sf::NW; ++v) w[v * g.plane + cell] = wc[v];
+        } else {
+            double qc[tf::NC], wc[tf::NW], wo[tf::NW];
+            for (int v = 0; v < tf::NC; ++v) qc[v] = q[v * g.plane + cell];
+            for (int v = 0; v < tf::NW; ++v) wo[v] = -1.0;
+            int st = tf::recover(qc, wo, ph, wc);
+            record(status, st, cell);
+            for (int v = 0; v < tf::NW; ++v) w[v * g.plane + cell] = wc[v];
+        }
+    }
+}
+
+cudaError_t launch_recover(int model, const Grid &g, const Phys &ph, const double *q, double *w, int *status,
+                           cudaStream_t s) {
+    k_recover<<<grid_for(g.ncell, 128), 128, 0, s>>>(model, g, ph, q, w, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- layout
+__global__ void k_pack(Grid g, int nvar, const double *user, double *dev) {
+    long long total = (long long)nvar * g.ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long v = e / g.ncell, c = e - v * g.ncell;
+        dev[v * g.plane + c] = user[e];
+    }
+}
+__global__ void k_unpack(Grid g, int nvar, const double *dev, double *user) {
+    long long total = (long long)nvar * g.ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long v = e / g.ncell, c = e - v * g.ncell;
+        user[e] = dev[v * g.plane + c];
+    }
+}
+cudaError_t launch_pack(const Grid &g, int nvar, const double *user, double *dev, cudaStream_t s) {
+    k_pack<<<grid_for((long long)nvar * g.ncell, 256), 256, 0, s>>>(g, nvar, user, dev);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpack(const Grid &g, int nvar, const double *dev, double *user, cudaStream_t s) {
+    k_unpack<<<grid_for((long long)nvar * g.ncell, 256), 256, 0, s>>>(g, nvar, dev, user);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics
+// Two-level deterministic reduction: each of kDiagBlocks blocks reduces a
+// strided share of the cells into 8 partials in `scratch`; one block then
+// combines the partials in a fixed order.
+static constexpr int kDiagBlocks = 304, kDiagThreads = 256;
+
+size_t reduce_scratch_doubles() { return (size_t)kDiagBlocks * 8; }
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(int model, Grid g, const double *q, const double *w,
+                                                               double *scratch) {
+    const int NC = model == 0 ? 14 : 18;
+    const int iS = 1, iT = 4, iB = model == 0 ? 5 : 10, iR = model == 0 ? 11 : 5;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        acc[0] += q[0 * g.plane + cell];
+        acc[1] += q[iT * g.plane + cell];
+        acc[2] += q[iS * g.plane + cell];
+        acc[3] += q[iB * g.plane + cell];
+        acc[4] += q[iR * g.plane + cell];
+        for (int s = 0; s < (model == 0 ? 1 : 2); ++s) {
+            double vx = w[(5 * s) * g.plane + cell], vy = w[(5 * s + 1) * g.plane + cell], vz = w[(5 * s + 2) * g.plane + cell];
+            acc[5] = fmax(acc[5], sqrt(vx * vx + vy * vy + vz * vz));
+        }
+        double bad = 0.0;
+        for (int v = 0; v < NC; ++v) bad += isfinite(q[v * g.plane + cell]) ? 0.0 : 1.0;
+        acc[6] += bad;
+    }
+    __shared__ double red[8][kDiagThreads];
+    for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int off = kDiagThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int k = 0; k < 8; ++k)
+                red[k][threadIdx.x] = (k == 5) ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + off])
+                                               : red[k][threadIdx.x] + red[k][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) scratch[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(Grid g, double cfl, const double *scratch, int nblocks, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int k = 0; k < 8; ++k) r[k] = (k == 5) ? fmax(r[k], scratch[b * 8 + k]) : r[k] + scratch[b * 8 + k];
+    double vol = g.dx * (g.ny > 1 ? g.dy : 1.0);
+    for (int k = 0; k < 5; ++k) out[k] = r[k] * vol;
+    out[5] = r[5];
+    out[6] = r[6];
+    out[7] = cfl * (g.ny > 1 ? fmin(g.dx, g.dy) : g.dx);
+}
+
+cudaError_t launch_diagnostics(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
+                               double *scratch, double *out, cudaStream_t s) {
+    (void)ph;
+    k_diag_partial<<<kDiagBlocks, kDiagThreads, 0, s>>>(model, g, q, w, scratch);
+    k_diag_final<<<1, 32, 0, s>>>(g, 0.0, scratch, kDiagBlocks, out);
+    return cudaGetLastError();
+}
+
+} // namespace rmhd

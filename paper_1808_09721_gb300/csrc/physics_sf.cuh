@@ -1,0 +1,326 @@
+// physics_sf.cuh -- single-fluid resistive SRMHD on the device (Sec. 2.1.1 of
+// Wright & Hawke, arXiv:1808.09721): primitive recovery (Sec. 2.1.3), Ohm's-law
+// current, flux along x or y, and the per-cell implicit stage of the IMEX
+// scheme (Eq. implicit stage).
+//
+// Implicit stage q = r + a dt Psi(q): D, S, tau, B and varrho have no source
+// and equal r; psi and phi are linear in themselves and solved in closed form;
+// E (3 unknowns) solves G(E) = E - r_E + a dt J(E) = 0, where J needs the
+// primitives of q(E) and hence a pressure root per evaluation.
+//
+// Precision strategy (GB300: FP64 is ~1/67 of FP32 throughput):
+//   1. Newton on G in FP32 until the FP32 residual stalls (~1e-7 relative).
+//      Jacobian columns come from forward-mode duals through the same code,
+//      the pressure root's derivative by the implicit-function theorem.
+//   2. A fixed number of FP64 refinement passes: evaluate G in FP64 (one FP64
+//      Newton step of the pressure root per pass, started from a first-order
+//      prediction) and correct E with the FP32 inverse Jacobian. Each pass
+//      gains ~6-7 digits, so two passes reach the FP64 root to ~1e-13.
+//   3. One more FP64 pressure step at the final E gives consistent primitives.
+#pragma once
+#include "device_math.cuh"
+
+namespace rmhd {
+namespace sf {
+
+enum { D = 0, SX = 1, SY = 2, SZ = 3, TAU = 4, BX = 5, BY = 6, BZ = 7, EX = 8, EY = 9, EZ = 10, RHOE = 11, PSI = 12, PHI = 13, NC = 14 };
+// internal primitives kept per cell: velocity, pressure and Lorentz factor
+enum { VX = 0, VY = 1, VZ = 2, P = 3, LOR = 4, NW = 5 };
+
+template <class A, class B, class C>
+__device__ __forceinline__ void cross(const A a[3], const B b[3], C c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Pressure-root residual for one species with hydrodynamic data:
+// a = tau~ + D, S2 = |S~|^2. With Z = a + p = rho h W^2 and v^2 = S2/Z^2,
+//   f(p) = (Gamma-1) [Z - S2/Z - D sqrt(1 - v^2)] - Gamma p,
+// which vanishes exactly when p = (Gamma-1) rho eps (Sec. 2.1 EOS).
+template <class T, class S>
+__device__ __forceinline__ T pres_resid(T p, T a, T S2, S Dd, S gm1, S gam) {
+    T Z = a + p;
+    T rZ = s_rcp(Z);
+    T v2 = S2 * rZ * rZ;
+    T om = S(1) - v2;
+    T sq = om * s_rsqrt(om);
+    return gm1 * (Z - S2 * rZ - Dd * sq) - gam * p;
+}
+
+// FP32 Newton-bisection solve of the pressure root from the guess p.
+// Returns false if the data admit no root (|S~| >= tau~ + D or D <= 0).
+// On return p is converged (to ~1e-6 relative) and dfdp the slope there.
+__device__ __forceinline__ bool pres_solve_f32(float &p, float a, float S2, float Dd, float gm1, float gam, float &dfdp) {
+    if (!(Dd > 0.f) || !(a * a > S2) || !(a > 0.f)) return false;
+    float lo = 0.f, hi = gm1 * a;
+    if (!(p > lo && p < hi)) p = 0.5f * hi;
+    for (int it = 0; it < 60; ++it) {
+        float Z = a + p;
+        float rZ = s_rcp(Z);
+        float v2 = S2 * rZ * rZ;
+        float om = 1.f - v2;
+        float W = s_rsqrt(om);
+        float sq = om * W;
+        float f = gm1 * (Z - S2 * rZ - Dd * sq) - gam * p;
+        float df = gm1 * (1.f + v2 - Dd * v2 * rZ * W) - gam;
+        dfdp = df;
+        if (f > 0.f) lo = p; else hi = p;
+        float pn = p - f / df;
+        if (!(pn > lo && pn < hi)) pn = 0.5f * (lo + hi);
+        float dp = fabsf(pn - p);
+        p = pn;
+        if (dp <= 2e-7f * p || hi - lo <= 2e-7f * hi) return true;
+    }
+    return true;
+}
+
+// EM split of Sec. 2.1.3: S~ = S - E x B, tau~ = tau - (E^2 + B^2)/2.
+// tauB = tau - B^2/2 is precomputed; a = tau~ + D; S2 = |S~|^2.
+template <class T, class S>
+__device__ __forceinline__ void em_split(const T E[3], const S Sv[3], const S B[3], S tauB, S Dd, T St[3], T &a, T &S2) {
+    T ExB[3];
+    cross(E, B, ExB);
+    St[0] = Sv[0] - ExB[0];
+    St[1] = Sv[1] - ExB[1];
+    St[2] = Sv[2] - ExB[2];
+    T E2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+    a = (tauB + Dd) - S(0.5) * E2;
+    S2 = St[0] * St[0] + St[1] * St[1] + St[2] * St[2];
+}
+
+// Stage residual at E given a converged pressure p:
+//   v = S~/(a + p), W = (1 - v^2)^(-1/2),
+//   J = varrho v + W sigma [E + v x B - (v.E) v]   (Ohm's law, Sec. 2.1.1),
+//   G = E - r_E + a dt J.
+template <class T, class S>
+__device__ __forceinline__ void stage_resid(const T E[3], T p, const T St[3], T a, const S B[3], const S rE[3], S rhoe,
+                                            S adt, S sig, T G[3], T v[3], T &W) {
+    T rZ = s_rcp(a + p);
+    v[0] = St[0] * rZ;
+    v[1] = St[1] * rZ;
+    v[2] = St[2] * rZ;
+    T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    W = s_rsqrt(S(1) - v2);
+    T vxB[3];
+    cross(v, B, vxB);
+    T vE = v[0] * E[0] + v[1] * E[1] + v[2] * E[2];
+    T Ws = W * sig;
+    for (int i = 0; i < 3; ++i) {
+        T u = E[i] + vxB[i] - vE * v[i];
+        T J = rhoe * v[i] + Ws * u;
+        G[i] = (E[i] - rE[i]) + adt * J;
+    }
+}
+
+// 3x3 inverse by cofactors (FP32). Returns false if singular.
+__device__ __forceinline__ bool inv3(const float m[9], float inv[9]) {
+    float c0 = m[4] * m[8] - m[5] * m[7];
+    float c1 = m[5] * m[6] - m[3] * m[8];
+    float c2 = m[3] * m[7] - m[4] * m[6];
+    float det = m[0] * c0 + m[1] * c1 + m[2] * c2;
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
+    float id = 1.f / det;
+    inv[0] = c0 * id;
+    inv[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    inv[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    inv[3] = c1 * id;
+    inv[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    inv[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    inv[6] = c2 * id;
+    inv[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    inv[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+    return true;
+}
+
+// Status codes recorded per cell (match the library's error codes).
+enum { ST_OK = 0, ST_NEWTON = -3, ST_C2P = -4 };
+
+struct StageConst {
+    double adt;   // a_ii dt
+    double cpsi;  // 1 / (1 + adt kappa)
+    double sigma, gamma;
+};
+
+// Solve one implicit stage for one cell. r: explicit part (14, FP64);
+// p_warm: pressure guess. Outputs q (14) and w = (v, p, W). NREF FP64 passes.
+template <int NREF>
+__device__ int stage_solve(const double r[NC], double p_warm, const StageConst &k, double q[NC], double w[NW]) {
+    const double gm1 = k.gamma - 1.0, gam = k.gamma;
+    for (int i = 0; i < NC; ++i) q[i] = r[i];
+    q[PSI] = (r[PSI] + k.adt * r[RHOE]) * k.cpsi;
+    q[PHI] = r[PHI] * k.cpsi;
+
+    const double B[3] = {r[BX], r[BY], r[BZ]};
+    const double Sv[3] = {r[SX], r[SY], r[SZ]};
+    const double rE[3] = {r[EX], r[EY], r[EZ]};
+    const double tauB = r[TAU] - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+
+    // ---- FP32 Newton
+    const float Bf[3] = {(float)B[0], (float)B[1], (float)B[2]};
+    const float Sf[3] = {(float)Sv[0], (float)Sv[1], (float)Sv[2]};
+    const float rEf[3] = {(float)rE[0], (float)rE[1], (float)rE[2]};
+    const float tauBf = (float)tauB, Df = (float)r[D], rhoef = (float)r[RHOE];
+    const float adtf = (float)k.adt, sigf = (float)k.sigma, gm1f = (float)gm1, gamf = (float)gam;
+    const float scale = fmaxf(fmaxf(fabsf(rEf[0]), fabsf(rEf[1])), fmaxf(fabsf(rEf[2]), 1e-30f));
+
+    float E[3] = {rEf[0], rEf[1], rEf[2]};
+    float p = (float)p_warm, dfdp = -1.f;
+    float G[3], v[3], W, St[3], a, S2;
+    em_split(E, Sf, Bf, tauBf, Df, St, a, S2);
+    if (!pres_solve_f32(p, a, S2, Df, gm1f, gamf, dfdp)) return ST_C2P;
+    stage_resid(E, p, St, a, Bf, rEf, rhoef, adtf, sigf, G, v, W);
+    float gn = fmaxf(fmaxf(fabsf(G[0]), fabsf(G[1])), fabsf(G[2]));
+
+    float Minv[9], dpdE[3];
+    bool have_jac = false;
+    for (int it = 0; it < 24; ++it) {
+        // Jacobian columns dG/dE_k with duals; dp/dE_k by the implicit-function theorem
+        float Jm[9];
+        for (int kc = 0; kc < 3; ++kc) {
+            Dual<float> Ed[3] = {Dual<float>(E[0], kc == 0), Dual<float>(E[1], kc == 1), Dual<float>(E[2], kc == 2)};
+            Dual<float> Std[3], ad, S2d;
+            em_split(Ed, Sf, Bf, tauBf, Df, Std, ad, S2d);
+            Dual<float> pd(p);
+            Dual<float> fd = pres_resid(pd, ad, S2d, Df, gm1f, gamf);
+            pd = Dual<float>(p, -fd.d / dfdp);
+            dpdE[kc] = pd.d;
+            Dual<float> Gd[3], vd[3], Wd;
+            stage_resid(Ed, pd, Std, ad, Bf, rEf, rhoef, adtf, sigf, Gd, vd, Wd);
+            Jm[0 + kc] = Gd[0].d;
+            Jm[3 + kc] = Gd[1].d;
+            Jm[6 + kc] = Gd[2].d;
+        }
+        if (!inv3(Jm, Minv)) return ST_NEWTON;
+        have_jac = true;
+        float dE[3];
+        for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * G[0] + Minv[3 * i + 1] * G[1] + Minv[3 * i + 2] * G[2];
+        float dn = fmaxf(fmaxf(fabsf(dE[0]), fabsf(dE[1])), fabsf(dE[2]));
+        if (dn <= 2e-7f * fmaxf(scale, fmaxf(fmaxf(fabsf(E[0]), fabsf(E[1])), fabsf(E[2])))) break;
+        // backtracking on |G|_inf
+        float t = 1.f;
+        bool accepted = false;
+        for (int ls = 0; ls < 8; ++ls) {
+            float Et[3] = {E[0] - t * dE[0], E[1] - t * dE[1], E[2] - t * dE[2]};
+            float pt = p, dft = dfdp, Gt[3], vt[3], Wt, Stt[3], at, S2t;
+            em_split(Et, Sf, Bf, tauBf, Df, Stt, at, S2t);
+            if (pres_solve_f32(pt, at, S2t, Df, gm1f, gamf, dft)) {
+                stage_resid(Et, pt, Stt, at, Bf, rEf, rhoef, adtf, sigf, Gt, vt, Wt);
+                float gt = fmaxf(fmaxf(fabsf(Gt[0]), fabsf(Gt[1])), fabsf(Gt[2]));
+                if (gt < gn || t < 0.02f) {
+                    E[0] = Et[0]; E[1] = Et[1]; E[2] = Et[2];
+                    p = pt; dfdp = dft; G[0] = Gt[0]; G[1] = Gt[1]; G[2] = Gt[2];
+                    gn = gt;
+                    accepted = true;
+                    break;
+                }
+            }
+            t *= 0.5f;
+        }
+        if (!accepted) break;  // FP32 noise floor: hand over to the FP64 passes
+    }
+    if (!have_jac) return ST_NEWTON;
+
+    // ---- FP64 refinement passes
+    double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
+    double pdd = (double)p;
+    const double rdf = (double)(1.f / dfdp);
+    double St64[3], a64, S264, G64[3], v64[3], W64;
+    double last = 0.0;
+    for (int pass = 0; pass < NREF; ++pass) {
+        em_split(Ed, Sv, B, tauB, r[D], St64, a64, S264);
+        pdd -= pres_resid(pdd, a64, S264, r[D], gm1, gam) * rdf;
+        stage_resid(Ed, pdd, St64, a64, B, rE, r[RHOE], k.adt, k.sigma, G64, v64, W64);
+        float Gf[3] = {(float)G64[0], (float)G64[1], (float)G64[2]};
+        float dE[3];
+        for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
+        // first-order prediction of the pressure at the corrected E
+        pdd -= (double)(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
+        Ed[0] -= (double)dE[0];
+        Ed[1] -= (double)dE[1];
+        Ed[2] -= (double)dE[2];
+        last = fmax(fmax(fabs((double)dE[0]), fabs((double)dE[1])), fabs((double)dE[2]));
+    }
+    // consistent primitives at the final E
+    em_split(Ed, Sv, B, tauB, r[D], St64, a64, S264);
+    pdd -= pres_resid(pdd, a64, S264, r[D], gm1, gam) * rdf;
+    double rZ = s_rcp(a64 + pdd);
+    w[VX] = St64[0] * rZ;
+    w[VY] = St64[1] * rZ;
+    w[VZ] = St64[2] * rZ;
+    w[P] = pdd;
+    w[LOR] = s_rsqrt(1.0 - (w[VX] * w[VX] + w[VY] * w[VY] + w[VZ] * w[VZ]));
+    q[EX] = Ed[0];
+    q[EY] = Ed[1];
+    q[EZ] = Ed[2];
+    double sc = fmax((double)scale, fmax(fmax(fabs(Ed[0]), fabs(Ed[1])), fabs(Ed[2])));
+    if (!(pdd > 0.0) || !(last <= 1e-9 * sc) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
+    return ST_OK;
+}
+
+// Primitive recovery of a conserved state (no source solve): FP32 root, then
+// two FP64 Newton steps with the FP32 slope. Returns status; w = (v, p, W).
+__device__ __forceinline__ int recover(const double q[NC], double p_warm, double gamma, double w[NW]) {
+    const double gm1 = gamma - 1.0;
+    const double B[3] = {q[BX], q[BY], q[BZ]}, E[3] = {q[EX], q[EY], q[EZ]}, Sv[3] = {q[SX], q[SY], q[SZ]};
+    const double tauB = q[TAU] - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    double St[3], a, S2;
+    em_split(E, Sv, B, tauB, q[D], St, a, S2);
+    float p = (float)p_warm, df = -1.f;
+    if (!pres_solve_f32(p, (float)a, (float)S2, (float)q[D], (float)gm1, (float)gamma, df)) return ST_C2P;
+    double pd = (double)p, rdf = (double)(1.f / df);
+    pd -= pres_resid(pd, a, S2, q[D], gm1, gamma) * rdf;
+    pd -= pres_resid(pd, a, S2, q[D], gm1, gamma) * rdf;
+    double rZ = s_rcp(a + pd);
+    w[VX] = St[0] * rZ;
+    w[VY] = St[1] * rZ;
+    w[VZ] = St[2] * rZ;
+    w[P] = pd;
+    w[LOR] = s_rsqrt(1.0 - (w[VX] * w[VX] + w[VY] * w[VY] + w[VZ] * w[VZ]));
+    if (!(pd > 0.0) || !isfinite(w[LOR])) return ST_C2P;
+    return ST_OK;
+}
+
+// Ohm's-law current J = varrho v + W sigma [E + v x B - (v.E) v] (FP64).
+__device__ __forceinline__ void current(const double *q, const double *w, double sigma, double J[3]) {
+    const double v[3] = {w[VX], w[VY], w[VZ]};
+    const double B[3] = {q[BX], q[BY], q[BZ]}, E[3] = {q[EX], q[EY], q[EZ]};
+    double vxB[3];
+    cross(v, B, vxB);
+    double vE = v[0] * E[0] + v[1] * E[1] + v[2] * E[2];
+    double Ws = w[LOR] * sigma;
+    for (int i = 0; i < 3; ++i) J[i] = q[RHOE] * v[i] + Ws * (E[i] + vxB[i] - vE * v[i]);
+}
+
+// Flux along direction `dir` (0 = x, 1 = y) of Eq. (resistive RMHD):
+//   D v_d; Z v_i v_d + [p + (E^2+B^2)/2] delta_id - E_i E_d - B_i B_d; S_d - D v_d;
+//   B: -eps_ijd E_j + delta_id phi; E: eps_ijd B_j + delta_id psi; J_d; E_d; B_d,
+// with Z = rho h W^2 = tau - (E^2+B^2)/2 + D + p (no division needed).
+// T is the flux arithmetic type; J is passed in (computed in FP64).
+template <class T>
+__device__ __forceinline__ void flux(const T q[NC], const T w[NW], const T J[3], int dir, T f[NC]) {
+    const T E2B2 = q[EX] * q[EX] + q[EY] * q[EY] + q[EZ] * q[EZ] + q[BX] * q[BX] + q[BY] * q[BY] + q[BZ] * q[BZ];
+    const T pem = w[P] + T(0.5) * E2B2;
+    const T Z = (q[TAU] - T(0.5) * E2B2) + q[D] + w[P];
+    const T vd = w[VX + dir], Ed = q[EX + dir], Bd = q[BX + dir];
+    const T Zv = Z * vd;
+    f[D] = q[D] * vd;
+    f[SX] = Zv * w[VX] - q[EX] * Ed - q[BX] * Bd;
+    f[SY] = Zv * w[VY] - q[EY] * Ed - q[BY] * Bd;
+    f[SZ] = Zv * w[VZ] - q[EZ] * Ed - q[BZ] * Bd;
+    f[SX + dir] += pem;
+    f[TAU] = q[SX + dir] - q[D] * vd;
+    if (dir == 0) {
+        f[BX] = q[PHI]; f[BY] = -q[EZ]; f[BZ] = q[EY];
+        f[EX] = q[PSI]; f[EY] = q[BZ]; f[EZ] = -q[BY];
+    } else {
+        f[BX] = q[EZ]; f[BY] = q[PHI]; f[BZ] = -q[EX];
+        f[EX] = -q[BZ]; f[EY] = q[PSI]; f[EZ] = q[BX];
+    }
+    f[RHOE] = J[dir];
+    f[PSI] = Ed;
+    f[PHI] = Bd;
+}
+
+} // namespace sf
+} // namespace rmhd

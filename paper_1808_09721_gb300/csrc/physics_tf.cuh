@@ -1,0 +1,415 @@
+// physics_tf.cuh -- two-fluid resistive SRMHD on the device (Sec. 2.1.2 and
+// Appendix A of Wright & Hawke, arXiv:1808.09721).
+//
+// Conserved: D, S_i, tau (species totals), Dbar, Sbar_i, taubar (charge-to-
+// mass weighted, hydrodynamic parts only), B, E, psi, phi.
+// Internal primitives per species s in {e, p}: v_s (3), p_s, Z_s = rho_s h_s W_s^2.
+// D_s follows from (D, Dbar) by the species split, so the flux needs no division.
+//
+// Implicit stage: Sbar, taubar and E (7 unknowns) have stiff sources; D, S,
+// tau, Dbar, B have none; psi and phi are linear. The unknowns are scaled
+// (Sbar, taubar divided by mu_ref = max |mu_s|) so that the FP32 Jacobian is
+// balanced. Same precision strategy as the single fluid: FP32 Newton with
+// dual-number Jacobian columns, then FP64 refinement passes with the FP32
+// inverse Jacobian, then consistent FP64 primitives.
+#pragma once
+#include "device_math.cuh"
+#include "physics_sf.cuh"
+#include "rmhd_internal.h"
+
+namespace rmhd {
+namespace tf {
+
+enum { D = 0, SX = 1, SY = 2, SZ = 3, TAU = 4, DB = 5, SBX = 6, SBY = 7, SBZ = 8, TAUB = 9,
+       BX = 10, BY = 11, BZ = 12, EX = 13, EY = 14, EZ = 15, PSI = 16, PHI = 17, NC = 18 };
+// per species s (offset 5 s): v (3), p, Z
+enum { VX = 0, VY = 1, VZ = 2, P = 3, ZZ = 4, NW = 10 };
+
+using sf::cross;
+
+// Species split of Sec. 2.1.3 for a pair (total, mu-weighted):
+//   X_e = (Xbar - mu_p X) / (mu_e - mu_p),  X_p = (mu_e X - Xbar) / (mu_e - mu_p).
+struct Split {
+    double ce_bar, ce_tot, cp_bar, cp_tot;  // X_e = ce_bar Xbar + ce_tot X ; X_p = cp_bar Xbar + cp_tot X
+    __device__ __forceinline__ Split(double mu_e, double mu_p, double inv) {
+        ce_bar = inv;
+        ce_tot = -mu_p * inv;
+        cp_bar = -inv;
+        cp_tot = mu_e * inv;
+    }
+};
+
+// Two-fluid flux along dir (Appendix A, Eq. twoFluid flux), T = flux arithmetic.
+template <class T>
+__device__ __forceinline__ void flux(const T q[NC], const T w[NW], T mu_e, T mu_p, T inv, int dir, T f[NC]) {
+    const T Ds[2] = {(q[DB] - mu_p * q[D]) * inv, (mu_e * q[D] - q[DB]) * inv};
+    const T mu[2] = {mu_e, mu_p};
+#pragma unroll
+    for (int v = 0; v < 10; ++v) f[v] = T(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const T *ws = w + 5 * s;
+        const T vd = ws[VX + dir];
+        const T Dv = Ds[s] * vd;
+        const T Zv = ws[ZZ] * vd;
+        f[D] += Dv;
+        f[DB] += mu[s] * Dv;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T Sij = Zv * ws[VX + i];
+            if (i == dir) Sij += ws[P];
+            f[SX + i] += Sij;
+            f[SBX + i] += mu[s] * Sij;
+        }
+        f[TAUB] += mu[s] * (Zv - Dv);
+    }
+    const T E2B2 = q[EX] * q[EX] + q[EY] * q[EY] + q[EZ] * q[EZ] + q[BX] * q[BX] + q[BY] * q[BY] + q[BZ] * q[BZ];
+    const T Ed = q[EX + dir], Bd = q[BX + dir];
+    f[SX] -= q[EX] * Ed + q[BX] * Bd;
+    f[SY] -= q[EY] * Ed + q[BY] * Bd;
+    f[SZ] -= q[EZ] * Ed + q[BZ] * Bd;
+    f[SX + dir] += T(0.5) * E2B2;
+    f[TAU] = q[SX + dir] - f[D];
+    if (dir == 0) {
+        f[BX] = q[PHI]; f[BY] = -q[EZ]; f[BZ] = q[EY];
+        f[EX] = q[PSI]; f[EY] = q[BZ]; f[EZ] = -q[BY];
+    } else {
+        f[BX] = q[EZ]; f[BY] = q[PHI]; f[BZ] = -q[EX];
+        f[EX] = -q[BZ]; f[EY] = q[PSI]; f[EZ] = q[BX];
+    }
+    f[PSI] = Ed;
+    f[PHI] = Bd;
+}
+
+// Source of Appendix A, written with M0 = sum mu_s^2 D_s, M1 = sum mu_s^2 D_s v_s,
+// wp2 = omega_p^2 = sum mu_s^2 D_s / W_s, varrho = sum mu_s D_s, J = sum mu_s D_s v_s:
+//   omega_p^2 W = M0, omega_p^2 u = M1, varrho_0 = (M0 varrho - J.M1)/wp2,
+//   Sbar: M0 E + M1 x B - eta (wp2 J - varrho M1)
+//   taubar: M1.E - eta (wp2 varrho - M0 varrho_0)
+//   E: -J;  psi: varrho - kappa psi;  phi: -kappa phi.
+template <class T, class S>
+__device__ __forceinline__ void source_terms(const T Ds[2], const T v[2][3], const T sq[2], const T E[3], const S B[3],
+                                             S mu_e, S mu_p, S eta, T Sb[3], T &tb, T J[3], T &varrho) {
+    const S mu[2] = {mu_e, mu_p};
+    T M0 = mu[0] * mu[0] * Ds[0] + mu[1] * mu[1] * Ds[1];
+    T M1[3], Jv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        M1[i] = (mu[0] * mu[0]) * (Ds[0] * v[0][i]) + (mu[1] * mu[1]) * (Ds[1] * v[1][i]);
+        Jv[i] = mu[0] * (Ds[0] * v[0][i]) + mu[1] * (Ds[1] * v[1][i]);
+        J[i] = Jv[i];
+    }
+    T wp2 = (mu[0] * mu[0]) * (Ds[0] * sq[0]) + (mu[1] * mu[1]) * (Ds[1] * sq[1]);
+    varrho = mu[0] * Ds[0] + mu[1] * Ds[1];
+    T M1xB[3];
+    cross(M1, B, M1xB);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Sb[i] = M0 * E[i] + M1xB[i] - eta * (wp2 * Jv[i] - varrho * M1[i]);
+    T JM1 = Jv[0] * M1[0] + Jv[1] * M1[1] + Jv[2] * M1[2];
+    T r0 = (M0 * varrho - JM1) * s_rcp(wp2);
+    tb = (M1[0] * E[0] + M1[1] * E[1] + M1[2] * E[2]) - eta * (wp2 * varrho - M0 * r0);
+}
+
+// Recovery of the primitives of a conserved state (FP64 result).
+__device__ __forceinline__ int recover(const double q[NC], const double wold[NW], const Phys &ph, double w[NW]) {
+    const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
+    const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
+    const double B[3] = {q[BX], q[BY], q[BZ]}, E[3] = {q[EX], q[EY], q[EZ]};
+    double ExB[3];
+    cross(E, B, ExB);
+    double St[3] = {q[SX] - ExB[0], q[SY] - ExB[1], q[SZ] - ExB[2]};
+    double taut = q[TAU] - 0.5 * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    double Ds[2] = {sp.ce_bar * q[DB] + sp.ce_tot * q[D], sp.cp_bar * q[DB] + sp.cp_tot * q[D]};
+    double Ss[2][3], ts[2];
+    for (int i = 0; i < 3; ++i) {
+        Ss[0][i] = sp.ce_bar * q[SBX + i] + sp.ce_tot * St[i];
+        Ss[1][i] = sp.cp_bar * q[SBX + i] + sp.cp_tot * St[i];
+    }
+    ts[0] = sp.ce_bar * q[TAUB] + sp.ce_tot * taut;
+    ts[1] = sp.cp_bar * q[TAUB] + sp.cp_tot * taut;
+    for (int s = 0; s < 2; ++s) {
+        double a = ts[s] + Ds[s];
+        double S2 = Ss[s][0] * Ss[s][0] + Ss[s][1] * Ss[s][1] + Ss[s][2] * Ss[s][2];
+        float p = (float)wold[5 * s + P], df = -1.f;
+        if (!sf::pres_solve_f32(p, (float)a, (float)S2, (float)Ds[s], (float)gm1, (float)gam, df)) return sf::ST_C2P;
+        double pd = (double)p, rdf = (double)(1.f / df);
+        pd -= sf::pres_resid(pd, a, S2, Ds[s], gm1, gam) * rdf;
+        pd -= sf::pres_resid(pd, a, S2, Ds[s], gm1, gam) * rdf;
+        double Z = a + pd, rZ = s_rcp(Z);
+        w[5 * s + VX] = Ss[s][0] * rZ;
+        w[5 * s + VY] = Ss[s][1] * rZ;
+        w[5 * s + VZ] = Ss[s][2] * rZ;
+        w[5 * s + P] = pd;
+        w[5 * s + ZZ] = Z;
+        double v2 = w[5 * s] * w[5 * s] + w[5 * s + 1] * w[5 * s + 1] + w[5 * s + 2] * w[5 * s + 2];
+        if (!(pd > 0.0) || !(v2 < 1.0)) return sf::ST_C2P;
+    }
+    return sf::ST_OK;
+}
+
+// Source of a state with known primitives (FP64), full N_c vector.
+__device__ __forceinline__ void source(const double q[NC], const double w[NW], const Phys &ph, double s[NC]) {
+    const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
+    double Ds[2] = {sp.ce_bar * q[DB] + sp.ce_tot * q[D], sp.cp_bar * q[DB] + sp.cp_tot * q[D]};
+    double v[2][3], sq[2];
+    for (int k = 0; k < 2; ++k) {
+        for (int i = 0; i < 3; ++i) v[k][i] = w[5 * k + i];
+        double om = 1.0 - (v[k][0] * v[k][0] + v[k][1] * v[k][1] + v[k][2] * v[k][2]);
+        sq[k] = om * s_rsqrt(om);
+    }
+    const double E[3] = {q[EX], q[EY], q[EZ]}, B[3] = {q[BX], q[BY], q[BZ]};
+    double Sb[3], tb, J[3], varrho;
+    source_terms(Ds, v, sq, E, B, ph.mu_e, ph.mu_p, ph.eta, Sb, tb, J, varrho);
+    for (int i = 0; i < NC; ++i) s[i] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        s[SBX + i] = Sb[i];
+        s[EX + i] = -J[i];
+    }
+    s[TAUB] = tb;
+    s[PSI] = varrho - ph.kappa * q[PSI];
+    s[PHI] = -ph.kappa * q[PHI];
+}
+
+// Constant (unknown-independent) data of one stage solve, in scalar type S.
+template <class S>
+struct Cell {
+    S D, Ds[2], Sv[3], B[3], tauB, rx[7];  // rx: scaled explicit part of the unknowns
+    S mu_e, mu_p, inv, mur, imur, eta, adt, gm1, gam;
+};
+
+// Stage residual in scaled unknowns x = (Sbar/mur, taubar/mur, E). Pressures
+// p[2] must be converged for value(x) (or be one Newton step in type T).
+// Outputs G (scaled), per-species S~, a, S2 are recomputed inside.
+template <class T, class S>
+__device__ __forceinline__ void split_x(const Cell<S> &c, const T x[7], T St2[2][3], T a[2], T S2[2]) {
+    T E[3] = {x[4], x[5], x[6]};
+    T ExB[3];
+    cross(E, c.B, ExB);
+    T St[3] = {c.Sv[0] - ExB[0], c.Sv[1] - ExB[1], c.Sv[2] - ExB[2]};
+    T taut = c.tauB - S(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+    T Sb[3] = {c.mur * x[0], c.mur * x[1], c.mur * x[2]};
+    T tb = c.mur * x[3];
+    // X_e = (Xbar - mu_p X) inv ; X_p = (mu_e X - Xbar) inv
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        St2[0][i] = (Sb[i] - c.mu_p * St[i]) * c.inv;
+        St2[1][i] = (c.mu_e * St[i] - Sb[i]) * c.inv;
+    }
+    a[0] = (tb - c.mu_p * taut) * c.inv + c.Ds[0];
+    a[1] = (c.mu_e * taut - tb) * c.inv + c.Ds[1];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) S2[k] = St2[k][0] * St2[k][0] + St2[k][1] * St2[k][1] + St2[k][2] * St2[k][2];
+}
+
+template <class T, class S>
+__device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], const T St2[2][3], const T a[2],
+                                            const T p[2], T G[7], T v[2][3], T Z[2]) {
+    T sq[2], Dsv[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        Z[k] = a[k] + p[k];
+        T rZ = s_rcp(Z[k]);
+        v[k][0] = St2[k][0] * rZ;
+        v[k][1] = St2[k][1] * rZ;
+        v[k][2] = St2[k][2] * rZ;
+        T om = S(1) - (v[k][0] * v[k][0] + v[k][1] * v[k][1] + v[k][2] * v[k][2]);
+        sq[k] = om * s_rsqrt(om);
+        Dsv[k] = T(c.Ds[k]);
+    }
+    T E[3] = {x[4], x[5], x[6]};
+    T Sb[3], tb, J[3], varrho;
+    source_terms(Dsv, v, sq, E, c.B, c.mu_e, c.mu_p, c.eta, Sb, tb, J, varrho);
+    const S k1 = c.adt * c.imur;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        G[i] = (x[i] - c.rx[i]) - k1 * Sb[i];
+        G[4 + i] = (x[4 + i] - c.rx[4 + i]) + c.adt * J[i];
+    }
+    G[3] = (x[3] - c.rx[3]) - k1 * tb;
+}
+
+// In-place inverse of an n x n FP32 matrix (Gauss-Jordan, partial pivoting).
+template <int N>
+__device__ __forceinline__ bool invert(float m[N * N], float inv[N * N]) {
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) inv[i] = (i % (N + 1) == 0) ? 1.f : 0.f;
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        float best = fabsf(m[c * N + c]);
+        for (int r = c + 1; r < N; ++r)
+            if (fabsf(m[r * N + c]) > best) { best = fabsf(m[r * N + c]); piv = r; }
+        if (!(best > 0.f) || !isfinite(best)) return false;
+        if (piv != c)
+            for (int k = 0; k < N; ++k) {
+                float t = m[c * N + k]; m[c * N + k] = m[piv * N + k]; m[piv * N + k] = t;
+                t = inv[c * N + k]; inv[c * N + k] = inv[piv * N + k]; inv[piv * N + k] = t;
+            }
+        float id = 1.f / m[c * N + c];
+        for (int k = 0; k < N; ++k) { m[c * N + k] *= id; inv[c * N + k] *= id; }
+        for (int r = 0; r < N; ++r) {
+            if (r == c) continue;
+            float f = m[r * N + c];
+            for (int k = 0; k < N; ++k) { m[r * N + k] -= f * m[c * N + k]; inv[r * N + k] -= f * inv[c * N + k]; }
+        }
+    }
+    return true;
+}
+
+struct StageConst {
+    double adt, cpsi;
+};
+
+template <int NREF>
+__device__ int stage_solve(const double r[NC], const double wwarm[NW], const StageConst &k, const Phys &ph,
+                           double q[NC], double w[NW]) {
+    const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
+    const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
+    for (int i = 0; i < NC; ++i) q[i] = r[i];
+    q[PSI] = (r[PSI] + k.adt * r[DB]) * k.cpsi;  // varrho = Dbar has no source
+    q[PHI] = r[PHI] * k.cpsi;
+
+    Cell<double> c;
+    c.D = r[D];
+    c.Ds[0] = sp.ce_bar * r[DB] + sp.ce_tot * r[D];
+    c.Ds[1] = sp.cp_bar * r[DB] + sp.cp_tot * r[D];
+    for (int i = 0; i < 3; ++i) { c.Sv[i] = r[SX + i]; c.B[i] = r[BX + i]; }
+    c.tauB = r[TAU] - 0.5 * (c.B[0] * c.B[0] + c.B[1] * c.B[1] + c.B[2] * c.B[2]);
+    c.mu_e = ph.mu_e; c.mu_p = ph.mu_p; c.inv = ph.inv_dmu;
+    c.mur = ph.mur;
+    c.imur = ph.imur;
+    c.eta = ph.eta;
+    c.adt = k.adt; c.gm1 = gm1; c.gam = gam;
+    for (int i = 0; i < 3; ++i) { c.rx[i] = r[SBX + i] * c.imur; c.rx[4 + i] = r[EX + i]; }
+    c.rx[3] = r[TAUB] * c.imur;
+
+    Cell<float> cf;
+    cf.D = (float)c.D; cf.Ds[0] = (float)c.Ds[0]; cf.Ds[1] = (float)c.Ds[1];
+    for (int i = 0; i < 3; ++i) { cf.Sv[i] = (float)c.Sv[i]; cf.B[i] = (float)c.B[i]; }
+    cf.tauB = (float)c.tauB;
+    for (int i = 0; i < 7; ++i) cf.rx[i] = (float)c.rx[i];
+    cf.mu_e = (float)c.mu_e; cf.mu_p = (float)c.mu_p; cf.inv = (float)c.inv; cf.mur = (float)c.mur;
+    cf.imur = (float)c.imur; cf.eta = (float)c.eta; cf.adt = (float)c.adt; cf.gm1 = (float)gm1; cf.gam = (float)gam;
+
+    float scale = 1e-30f;
+    for (int i = 0; i < 7; ++i) scale = fmaxf(scale, fabsf(cf.rx[i]));
+
+    // ---- FP32 Newton
+    float x[7], p[2] = {(float)wwarm[P], (float)wwarm[5 + P]}, dfdp[2] = {-1.f, -1.f};
+    for (int i = 0; i < 7; ++i) x[i] = cf.rx[i];
+    float St2[2][3], a[2], S2[2], G[7], v[2][3], Z[2];
+    split_x(cf, x, St2, a, S2);
+    for (int s = 0; s < 2; ++s)
+        if (!sf::pres_solve_f32(p[s], a[s], S2[s], cf.Ds[s], cf.gm1, cf.gam, dfdp[s])) return sf::ST_C2P;
+    stage_resid(cf, x, St2, a, p, G, v, Z);
+    float gn = 0.f;
+    for (int i = 0; i < 7; ++i) gn = fmaxf(gn, fabsf(G[i]));
+
+    float Minv[49], dpdx[2][7];
+    bool have_jac = false;
+    for (int it = 0; it < 30; ++it) {
+        float Jm[49];
+        for (int kc = 0; kc < 7; ++kc) {
+            Dual<float> xd[7];
+            for (int i = 0; i < 7; ++i) xd[i] = Dual<float>(x[i], i == kc ? 1.f : 0.f);
+            Dual<float> Std[2][3], ad[2], S2d[2], pd[2], Gd[7], vd[2][3], Zd[2];
+            split_x(cf, xd, Std, ad, S2d);
+            for (int s = 0; s < 2; ++s) {
+                Dual<float> ps(p[s]);
+                Dual<float> fs = sf::pres_resid(ps, ad[s], S2d[s], cf.Ds[s], cf.gm1, cf.gam);
+                pd[s] = Dual<float>(p[s], -fs.d / dfdp[s]);
+                dpdx[s][kc] = pd[s].d;
+            }
+            stage_resid(cf, xd, Std, ad, pd, Gd, vd, Zd);
+            for (int i = 0; i < 7; ++i) Jm[i * 7 + kc] = Gd[i].d;
+        }
+        if (!invert<7>(Jm, Minv)) return sf::ST_NEWTON;
+        have_jac = true;
+        float dx[7], dn = 0.f, xn = scale;
+        for (int i = 0; i < 7; ++i) {
+            float s = 0.f;
+            for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * G[j];
+            dx[i] = s;
+            dn = fmaxf(dn, fabsf(s));
+            xn = fmaxf(xn, fabsf(x[i]));
+        }
+        if (dn <= 2e-7f * xn) break;
+        float t = 1.f;
+        bool accepted = false;
+        for (int ls = 0; ls < 8; ++ls) {
+            float xt[7], pt[2] = {p[0], p[1]}, dft[2] = {dfdp[0], dfdp[1]}, Gt[7], vt[2][3], Zt[2];
+            float St2t[2][3], at[2], S2t[2];
+            for (int i = 0; i < 7; ++i) xt[i] = x[i] - t * dx[i];
+            split_x(cf, xt, St2t, at, S2t);
+            bool ok = sf::pres_solve_f32(pt[0], at[0], S2t[0], cf.Ds[0], cf.gm1, cf.gam, dft[0]) &&
+                      sf::pres_solve_f32(pt[1], at[1], S2t[1], cf.Ds[1], cf.gm1, cf.gam, dft[1]);
+            if (ok) {
+                stage_resid(cf, xt, St2t, at, pt, Gt, vt, Zt);
+                float gt = 0.f;
+                for (int i = 0; i < 7; ++i) gt = fmaxf(gt, fabsf(Gt[i]));
+                if (gt < gn || t < 0.02f) {
+                    for (int i = 0; i < 7; ++i) { x[i] = xt[i]; G[i] = Gt[i]; }
+                    p[0] = pt[0]; p[1] = pt[1]; dfdp[0] = dft[0]; dfdp[1] = dft[1];
+                    gn = gt;
+                    accepted = true;
+                    break;
+                }
+            }
+            t *= 0.5f;
+        }
+        if (!accepted) break;
+    }
+    if (!have_jac) return sf::ST_NEWTON;
+
+    // ---- FP64 refinement passes
+    double xd[7], pdd[2] = {(double)p[0], (double)p[1]};
+    const double rdf[2] = {(double)(1.f / dfdp[0]), (double)(1.f / dfdp[1])};
+    for (int i = 0; i < 7; ++i) xd[i] = (double)x[i];
+    double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
+    double last = 0.0;
+    for (int pass = 0; pass < NREF; ++pass) {
+        split_x(c, xd, St64, a64, S264);
+        for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
+        stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
+        float Gf[7], dx[7];
+        for (int i = 0; i < 7; ++i) Gf[i] = (float)G64[i];
+        last = 0.0;
+        for (int i = 0; i < 7; ++i) {
+            float s = 0.f;
+            for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * Gf[j];
+            dx[i] = s;
+        }
+        for (int s = 0; s < 2; ++s) {
+            float dp = 0.f;
+            for (int i = 0; i < 7; ++i) dp += dpdx[s][i] * dx[i];
+            pdd[s] -= (double)dp;
+        }
+        for (int i = 0; i < 7; ++i) {
+            xd[i] -= (double)dx[i];
+            last = fmax(last, fabs((double)dx[i]));
+        }
+    }
+    split_x(c, xd, St64, a64, S264);
+    bool ok = true;
+    for (int s = 0; s < 2; ++s) {
+        pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
+        double Zs = a64[s] + pdd[s], rZ = s_rcp(Zs);
+        w[5 * s + VX] = St64[s][0] * rZ;
+        w[5 * s + VY] = St64[s][1] * rZ;
+        w[5 * s + VZ] = St64[s][2] * rZ;
+        w[5 * s + P] = pdd[s];
+        w[5 * s + ZZ] = Zs;
+        ok = ok && pdd[s] > 0.0 && isfinite(Zs);
+    }
+    for (int i = 0; i < 3; ++i) {
+        q[SBX + i] = xd[i] * c.mur;
+        q[EX + i] = xd[4 + i];
+    }
+    q[TAUB] = xd[3] * c.mur;
+    double sc = (double)scale;
+    for (int i = 0; i < 7; ++i) sc = fmax(sc, fabs(xd[i]));
+    if (!ok || !(last <= 1e-9 * sc)) return sf::ST_NEWTON;
+    return sf::ST_OK;
+}
+
+} // namespace tf
+} // namespace rmhd

@@ -1,0 +1,412 @@
+// rmhd_api.cu -- C ABI of the library (declared in include/rmhd.h): context
+// and workspace management, host <-> device transfers, and the SSP2(222)
+// IMEX step sequence (Sec. 2.2.1 and Table 1 of Wright & Hawke,
+// arXiv:1808.09721):
+//
+//   stage 1:  q1 = q^n + g dt Psi(q1)                         (per-cell solve)
+//   flux 1:   r2 = q^n + dt L(q1) + (1 - 2g) dt Psi(q1),
+//             acc = q^n + dt/2 (L(q1) + Psi(q1))               (fused)
+//   stage 2:  q2 = r2 + g dt Psi(q2)                           (per-cell solve)
+//   flux 2:   q^{n+1} = acc + dt/2 (L(q2) + Psi(q2)), w^{n+1} = recovery   (fused)
+//
+// with g = 1 - 1/sqrt(2). One step is captured once in a CUDA graph per time
+// step size and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdint>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rmhd.h"
+#include "rmhd_internal.h"
+
+using namespace rmhd;
+
+struct rmhd_ctx {
+    rmhd_config cfg;
+    Grid g;
+    Phys ph;
+    cudaStream_t stream;
+    int device;
+    bool own_ws;
+    char *ws;
+    size_t ws_bytes;
+    double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
+    int *status;       // device [2]
+    int *h_status;     // pinned host [2]
+    double *h_diag;    // pinned host [8]
+    bool has_state;
+    double t;
+    cudaGraphExec_t graph;
+    double graph_dt;
+    bool profiling;
+    struct Timed { int kind; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::string err;
+};
+
+static const double kGamma = 1.0 - 0.70710678118654752440;  // 1 - 1/sqrt(2)
+
+static int fail(rmhd_ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+static int fail(rmhd_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CK(c, call)                                                                                  \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail((c), RMHD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int validate(const rmhd_config *cfg) {
+    if (!cfg) return RMHD_ERR_INVALID;
+    if (cfg->model != RMHD_RESISTIVE && cfg->model != RMHD_TWO_FLUID) return RMHD_ERR_INVALID;
+    if (cfg->nx < 1 || cfg->ny < 1 || (long long)cfg->nx * cfg->ny > (1LL << 31) - 1) return RMHD_ERR_INVALID;
+    if (!(cfg->xmax > cfg->xmin) || (cfg->ny > 1 && !(cfg->ymax > cfg->ymin))) return RMHD_ERR_INVALID;
+    if (!(cfg->gamma > 1.0 && cfg->gamma <= 2.0)) return RMHD_ERR_INVALID;
+    if (!(cfg->sigma > 0.0) || !std::isfinite(cfg->sigma)) return RMHD_ERR_INVALID;
+    if (!(cfg->kappa >= 0.0)) return RMHD_ERR_INVALID;
+    if (cfg->model == RMHD_TWO_FLUID && !(cfg->mu_e != cfg->mu_p)) return RMHD_ERR_INVALID;
+    if ((cfg->bc_x != RMHD_OUTFLOW && cfg->bc_x != RMHD_PERIODIC) || (cfg->bc_y != RMHD_OUTFLOW && cfg->bc_y != RMHD_PERIODIC))
+        return RMHD_ERR_INVALID;
+    if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED) return RMHD_ERR_INVALID;
+    return RMHD_OK;
+}
+
+static Grid make_grid(const rmhd_config *cfg) {
+    Grid g;
+    g.nx = cfg->nx;
+    g.ny = cfg->ny;
+    g.bcx = cfg->bc_x;
+    g.bcy = cfg->bc_y;
+    g.ncell = (long long)cfg->nx * cfg->ny;
+    g.plane = (g.ncell + 63) / 64 * 64;
+    g.dx = (cfg->xmax - cfg->xmin) / cfg->nx;
+    g.dy = cfg->ny > 1 ? (cfg->ymax - cfg->ymin) / cfg->ny : 1.0;
+    return g;
+}
+
+struct Layout {
+    size_t Q, W, Q1, W1, R, ACC, stage, scratch, diag, status, total;
+};
+
+static Layout layout(const rmhd_config *cfg) {
+    Grid g = make_grid(cfg);
+    int nc = model_nc(cfg->model), nw = model_nw(cfg->model), np = model_np(cfg->model);
+    size_t pl = (size_t)g.plane * sizeof(double);
+    Layout L;
+    size_t o = 0;
+    L.Q = o; o += align256(nc * pl);
+    L.W = o; o += align256(nw * pl);
+    L.Q1 = o; o += align256(nc * pl);
+    L.W1 = o; o += align256(nw * pl);
+    L.R = o; o += align256(nc * pl);
+    L.ACC = o; o += align256(nc * pl);
+    L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
+    L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
+    L.diag = o; o += align256(8 * sizeof(double));
+    L.status = o; o += align256(2 * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+extern "C" {
+
+const char *rmhd_version(void) { return "rmhd-gb300 0.1 (sm_103a)"; }
+
+int rmhd_workspace_bytes(const rmhd_config *cfg, size_t *bytes) {
+    if (!bytes) return RMHD_ERR_INVALID;
+    int v = validate(cfg);
+    if (v) return v;
+    *bytes = layout(cfg).total;
+    return RMHD_OK;
+}
+
+const char *rmhd_last_error(const rmhd_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+static int reset_status(rmhd_ctx *c) {
+    int init[2] = {0, INT_MAX};
+    CK(c, cudaMemcpyAsync(c->status, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    return RMHD_OK;
+}
+
+// synchronise and decode the device status word
+static int read_status(rmhd_ctx *c, const char *what) {
+    CK(c, cudaMemcpyAsync(c->h_status, c->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    int code = c->h_status[0], cell = c->h_status[1];
+    if (code == 0) return RMHD_OK;
+    int st = reset_status(c);
+    if (st) return st;
+    int i = cell % c->cfg.nx, j = cell / c->cfg.nx;
+    const char *kind = code == RMHD_ERR_NEWTON ? "implicit-stage solve did not converge"
+                       : code == RMHD_ERR_C2P  ? "primitive recovery failed"
+                                               : "inadmissible primitive state";
+    return fail(c, code, "%s: %s in cell (i=%d, j=%d)", what, kind, i, j);
+}
+
+int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void *workspace, size_t workspace_bytes) {
+    if (!out) return RMHD_ERR_INVALID;
+    *out = nullptr;
+    int v = validate(cfg);
+    if (v) return v;
+    rmhd_ctx *c = new rmhd_ctx();
+    c->cfg = *cfg;
+    c->g = make_grid(cfg);
+    c->ph.gamma = cfg->gamma;
+    c->ph.sigma = cfg->sigma;
+    c->ph.kappa = cfg->kappa;
+    c->ph.mu_e = cfg->mu_e;
+    c->ph.mu_p = cfg->mu_p;
+    c->ph.inv_dmu = cfg->model == RMHD_TWO_FLUID ? 1.0 / (cfg->mu_e - cfg->mu_p) : 0.0;
+    c->ph.eta = 1.0 / cfg->sigma;
+    c->ph.mur = std::max(std::fabs(cfg->mu_e), std::fabs(cfg->mu_p));
+    if (!(c->ph.mur > 0.0)) c->ph.mur = 1.0;
+    c->ph.imur = 1.0 / c->ph.mur;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->graph = nullptr;
+    c->graph_dt = 0.0;
+    c->profiling = false;
+    c->t = 0.0;
+    c->has_state = false;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return RMHD_ERR_CUDA; }
+    Layout L = layout(cfg);
+    if (workspace) {
+        if (workspace_bytes < L.total || ((uintptr_t)workspace & 255)) { delete c; return RMHD_ERR_NOMEM; }
+        c->ws = (char *)workspace;
+        c->own_ws = false;
+    } else {
+        if (cudaMalloc(&c->ws, L.total) != cudaSuccess) { delete c; return RMHD_ERR_NOMEM; }
+        c->own_ws = true;
+    }
+    c->ws_bytes = L.total;
+    c->Q = (double *)(c->ws + L.Q);
+    c->W = (double *)(c->ws + L.W);
+    c->Q1 = (double *)(c->ws + L.Q1);
+    c->W1 = (double *)(c->ws + L.W1);
+    c->R = (double *)(c->ws + L.R);
+    c->ACC = (double *)(c->ws + L.ACC);
+    c->stage_buf = (double *)(c->ws + L.stage);
+    c->scratch = (double *)(c->ws + L.scratch);
+    c->diag = (double *)(c->ws + L.diag);
+    c->status = (int *)(c->ws + L.status);
+    if (cudaMallocHost(&c->h_status, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_diag, 8 * sizeof(double)) != cudaSuccess) {
+        if (c->own_ws) cudaFree(c->ws);
+        delete c;
+        return RMHD_ERR_NOMEM;
+    }
+    if (reset_status(c)) { rmhd_destroy(c); return RMHD_ERR_CUDA; }
+    *out = c;
+    return RMHD_OK;
+}
+
+void rmhd_destroy(rmhd_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto &t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    if (c->own_ws) cudaFree(c->ws);
+    cudaFreeHost(c->h_status);
+    cudaFreeHost(c->h_diag);
+    delete c;
+}
+
+// Bring user data [nvar][ny][nx] to the device staging buffer (dense layout).
+static int stage_in(rmhd_ctx *c, const double *src, int nvar, int where) {
+    size_t bytes = (size_t)nvar * c->g.ncell * sizeof(double);
+    CK(c, cudaMemcpyAsync(c->stage_buf, src, bytes, where == RMHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          c->stream));
+    return RMHD_OK;
+}
+static int stage_out(rmhd_ctx *c, double *dst, int nvar, int where) {
+    size_t bytes = (size_t)nvar * c->g.ncell * sizeof(double);
+    CK(c, cudaMemcpyAsync(dst, c->stage_buf, bytes, where == RMHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return RMHD_OK;
+}
+
+int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
+    if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_prims: bad argument");
+    int np = model_np(c->cfg.model);
+    int st = stage_in(c, prims, np, where);
+    if (st) return st;
+    CK(c, launch_set_prims(c->cfg.model, c->g, c->ph, c->stage_buf, c->Q, c->W, c->status, c->stream));
+    st = read_status(c, "set_prims");
+    if (st) return st;
+    c->has_state = true;
+    c->t = 0.0;
+    return RMHD_OK;
+}
+
+int rmhd_get_prims(rmhd_ctx *c, double *prims, int where) {
+    if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_prims: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_prims: no state (call rmhd_set_prims first)");
+    CK(c, launch_get_prims(c->cfg.model, c->g, c->ph, c->Q, c->W, c->stage_buf, c->stream));
+    return stage_out(c, prims, model_np(c->cfg.model), where);
+}
+
+int rmhd_get_cons(rmhd_ctx *c, double *cons, int where) {
+    if (!c || !cons || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_cons: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_cons: no state (call rmhd_set_prims first)");
+    int nc = model_nc(c->cfg.model);
+    CK(c, launch_unpack(c->g, nc, c->Q, c->stage_buf, c->stream));
+    return stage_out(c, cons, nc, where);
+}
+
+int rmhd_set_cons(rmhd_ctx *c, const double *cons, int where) {
+    if (!c || !cons || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_cons: bad argument");
+    int nc = model_nc(c->cfg.model);
+    int st = stage_in(c, cons, nc, where);
+    if (st) return st;
+    CK(c, launch_pack(c->g, nc, c->stage_buf, c->Q, c->stream));
+    CK(c, launch_recover(c->cfg.model, c->g, c->ph, c->Q, c->W, c->status, c->stream));
+    st = read_status(c, "set_cons");
+    if (st) return st;
+    c->has_state = true;
+    return RMHD_OK;
+}
+
+// Event bracket around one launch when profiling (no-op otherwise).
+static int tic(rmhd_ctx *c, int kind) {
+    if (!c->profiling) return RMHD_OK;
+    rmhd_ctx::Timed t{kind, nullptr, nullptr};
+    CK(c, cudaEventCreate(&t.a));
+    CK(c, cudaEventCreate(&t.b));
+    CK(c, cudaEventRecord(t.a, c->stream));
+    c->timed.push_back(t);
+    return RMHD_OK;
+}
+static int toc(rmhd_ctx *c) {
+    if (!c->profiling) return RMHD_OK;
+    CK(c, cudaEventRecord(c->timed.back().b, c->stream));
+    return RMHD_OK;
+}
+
+#define LAUNCH(c, kind, call)           \
+    do {                                \
+        int st_ = tic((c), (kind));     \
+        if (st_) return st_;            \
+        CK((c), (call));                \
+        st_ = toc(c);                   \
+        if (st_) return st_;            \
+    } while (0)
+
+// Enqueue one SSP2(222) step with time step dt.
+static int enqueue_step(rmhd_ctx *c, double dt) {
+    const int m = c->cfg.model;
+    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
+    FluxArgs f1{c->Q1, c->W1, c->Q, c->R, c->ACC, c->status, dt, 1.0 - 2.0 * kGamma};
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, c->cfg.precision, 1, c->g, c->ph, f1, c->stream));
+    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
+    FluxArgs f2{c->Q1, c->W1, c->ACC, c->Q, c->W, c->status, dt, 0.0};
+    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, c->cfg.precision, 2, c->g, c->ph, f2, c->stream));
+    return RMHD_OK;
+}
+
+int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
+    if (!c || nsteps < 0) return fail(c, RMHD_ERR_INVALID, "imex_step: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "imex_step: no state (call rmhd_set_prims first)");
+    if (!(dt > 0.0)) dt = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt must be positive (set cfl)");
+    if (nsteps == 0) { if (t_out) *t_out = c->t; return RMHD_OK; }
+    // Legacy default stream (no graph capture there) or profiling: launch directly.
+    if (c->profiling || c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread) {
+        for (int n = 0; n < nsteps; ++n) {
+            int st = enqueue_step(c, dt);
+            if (st) return st;
+            c->t += dt;
+        }
+        if (t_out) *t_out = c->t;
+        return RMHD_OK;
+    }
+    // one step as a CUDA graph, re-captured when dt changes
+    if (!c->graph || c->graph_dt != dt) {
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        // first launch outside capture also sets the kernels' shared-memory attributes
+        int st = enqueue_step(c, dt);
+        if (st) return st;
+        nsteps -= 1;
+        c->t += dt;
+        cudaGraph_t gr;
+        CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_step(c, dt);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+        if (st) return st;
+        if (e != cudaSuccess) return fail(c, RMHD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) { c->graph = nullptr; return fail(c, RMHD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        c->graph_dt = dt;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        CK(c, cudaGraphLaunch(c->graph, c->stream));
+        c->t += dt;
+    }
+    if (t_out) *t_out = c->t;
+    return RMHD_OK;
+}
+
+int rmhd_set_profiling(rmhd_ctx *c, int enable) {
+    if (!c) return RMHD_ERR_INVALID;
+    c->profiling = enable != 0;
+    return RMHD_OK;
+}
+
+int rmhd_kernel_times(rmhd_ctx *c, double *ms, int *counts) {
+    if (!c || !ms || !counts) return fail(c, RMHD_ERR_INVALID, "kernel_times: bad argument");
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) { ms[k] = 0.0; counts[k] = 0; }
+    int st = RMHD_OK;
+    for (auto &t : c->timed) {
+        float e = 0.f;
+        if (st == RMHD_OK && cudaEventElapsedTime(&e, t.a, t.b) != cudaSuccess)
+            st = fail(c, RMHD_ERR_CUDA, "kernel_times: cudaEventElapsedTime failed");
+        ms[t.kind] += e;
+        counts[t.kind] += 1;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->timed.clear();
+    return st;
+}
+
+int rmhd_check(rmhd_ctx *c) {
+    if (!c) return RMHD_ERR_INVALID;
+    return read_status(c, "imex_step");
+}
+
+int rmhd_diagnostics(rmhd_ctx *c, double *out) {
+    if (!c || !out) return fail(c, RMHD_ERR_INVALID, "diagnostics: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "diagnostics: no state");
+    CK(c, launch_diagnostics(c->cfg.model, c->g, c->ph, c->Q, c->W, c->scratch, c->diag, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_diag, c->diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 7; ++k) out[k] = c->h_diag[k];
+    out[7] = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
+    return RMHD_OK;
+}
+
+} // extern "C"

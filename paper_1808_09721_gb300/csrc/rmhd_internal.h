@@ -1,0 +1,80 @@
+// rmhd_internal.h -- declarations shared by the translation units of the CUDA
+// library (kernel launchers and plain-data parameter blocks). Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rmhd {
+
+// Device layout of one field: variable planes of `plane` doubles each; cell
+// (i, j) of variable v at base[v * plane + j * nx + i]. plane is nx * ny
+// rounded up to 64 elements so every plane starts 512-byte aligned.
+struct Grid {
+    int nx, ny;
+    int bcx, bcy;      // 0 outflow, 1 periodic
+    long long ncell;   // nx * ny
+    long long plane;
+    double dx, dy;
+};
+
+// Physical constants of a run plus host-precomputed reciprocals (the device
+// avoids IEEE FP64 divisions, which cost ~7.5 FP64 ops each on GB300).
+struct Phys {
+    double gamma, sigma, kappa, mu_e, mu_p;
+    double inv_dmu;  // 1 / (mu_e - mu_p)
+    double eta;      // 1 / sigma
+    double mur;      // max(|mu_e|, |mu_p|), scale of the two-fluid weighted unknowns
+    double imur;     // 1 / mur
+};
+
+// Coefficients of one flux pass.
+//  mode 1 (after stage 1):  out1 = base + dt L + c_src dt Psi      (stage-2 explicit part)
+//                           out2 = base + dt/2 (L + Psi)           (carried accumulator)
+//  mode 2 (after stage 2):  out1 = base + dt/2 (L + Psi)           (q^{n+1})
+//                           out2 = primitives of out1               (recovery)
+struct FluxArgs {
+    const double *q;     // stage state, NC planes
+    const double *w;     // stage primitives, NW planes
+    const double *base;  // q^n (mode 1) or the accumulator (mode 2), NC planes
+    double *out1;
+    double *out2;
+    int *status;         // [0] first error code, [1] smallest failing cell
+    double dt;
+    double c_src;        // (1 - 2 gamma_ssp) for mode 1
+};
+
+struct StageArgs {
+    const double *r;     // explicit part, NC planes
+    const double *wwarm; // primitives used as the starting guess, NW planes
+    double *q;           // stage solution, NC planes
+    double *w;           // its primitives, NW planes
+    int *status;
+    double adt;          // a_ii dt
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s);
+cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+                        cudaStream_t s);
+// primitives (user layout, device) -> conserved + internal primitives
+cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const double *prims, double *q, double *w,
+                             int *status, cudaStream_t s);
+// internal state -> primitives in the user layout
+cudaError_t launch_get_prims(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
+                             double *prims, cudaStream_t s);
+// conserved -> internal primitives (recovery), warm-started from w
+cudaError_t launch_recover(int model, const Grid &g, const Phys &ph, const double *q, double *w, int *status,
+                           cudaStream_t s);
+// copy between the user layout [v][ny][nx] and the padded device layout
+cudaError_t launch_pack(const Grid &g, int nvar, const double *user, double *dev, cudaStream_t s);
+cudaError_t launch_unpack(const Grid &g, int nvar, const double *dev, double *user, cudaStream_t s);
+// diagnostics: out[8] (see rmhd.h); partial sums in `scratch` (>= reduce_scratch_doubles())
+size_t reduce_scratch_doubles();
+cudaError_t launch_diagnostics(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
+                               double *scratch, double *out, cudaStream_t s);
+
+inline int model_nc(int model) { return model == 0 ? 14 : 18; }
+inline int model_nw(int model) { return model == 0 ? 5 : 10; }
+inline int model_np(int model) { return model == 0 ? 11 : 16; }
+
+} // namespace rmhd

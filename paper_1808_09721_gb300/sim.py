@@ -1,0 +1,134 @@
+"""Python handle over the C ABI: one simulation context on one GPU.
+
+PyTorch provides the device memory (one workspace tensor from its caching
+allocator) and the CUDA stream; librmhd.so does all the work. Arrays are
+structure-of-arrays float64 [n_var][ny][nx].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Sim:
+    """One resistive (N_c = 14) or two-fluid (N_c = 18) SRMHD run."""
+
+    def __init__(self, model: int, nx: int, ny: int, xlim, ylim, gamma: float, sigma: float,
+                 bc_x: int, bc_y: int, cfl: float = 0.4, mu_e: float = -1.0, mu_p: float = 1.0,
+                 kappa: float = 1.0, precision: int = L.FP64, device=None):
+        torch = _torch()
+        self.lib = L.load()
+        self.device = torch.device("cuda" if device is None else device)
+        self.cfg = L.Config(model, nx, ny, xlim[0], xlim[1], ylim[0], ylim[1], gamma, sigma, mu_e, mu_p,
+                            kappa, cfl, bc_x, bc_y, precision)
+        self.model, self.nx, self.ny = model, nx, ny
+        nbytes = C.c_size_t()
+        self._check(self.lib.rmhd_workspace_bytes(C.byref(self.cfg), C.byref(nbytes)), None)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            # a stream of its own: the library captures its step in a CUDA graph,
+            # which the legacy default stream does not allow
+            self.stream = torch.cuda.Stream(self.device)
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.h = C.c_void_p()
+        self._check(self.lib.rmhd_create(C.byref(self.h), C.byref(self.cfg), C.c_void_p(self.stream.cuda_stream),
+                                         C.c_void_p(self.workspace.data_ptr()), nbytes.value), None)
+
+    @classmethod
+    def from_workload(cls, wl, precision: int = L.FP64, device=None):
+        s = cls(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl,
+                wl.mu_e, wl.mu_p, wl.kappa, precision, device)
+        s.set_prims(wl.prims)
+        return s
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, code, what):
+        if code != L.RMHD_OK:
+            msg = self.lib.rmhd_last_error(self.h).decode() if what is not None and self.h else ""
+            raise L.RmhdError(code, msg or str(what))
+
+    @property
+    def nc(self):
+        return 14 if self.model == L.RESISTIVE else 18
+
+    @property
+    def np(self):
+        return 11 if self.model == L.RESISTIVE else 16
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.rmhd_destroy(h)
+            self.h = None
+
+    def _ptr(self, a, nvar, writable):
+        """(pointer, where, keepalive) for a numpy array or a CUDA tensor."""
+        torch = _torch()
+        n = nvar * self.nx * self.ny
+        if isinstance(a, torch.Tensor):
+            assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+            # order the library's stream after the producer of `a` on torch's stream
+            self.stream.wait_stream(torch.cuda.current_stream(a.device))
+            return C.c_void_p(a.data_ptr()), L.DEVICE, a
+        assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n
+        if writable:
+            assert a.flags.writeable
+        return C.c_void_p(a.ctypes.data), L.HOST, a
+
+    # -------------------------------------------------------------- API
+    def set_prims(self, prims):
+        if isinstance(prims, np.ndarray):
+            prims = np.ascontiguousarray(prims, dtype=np.float64)
+        p, where, _keep = self._ptr(prims, self.np, False)
+        self._check(self.lib.rmhd_set_prims(self.h, p, where), "set_prims")
+
+    def set_cons(self, cons):
+        if isinstance(cons, np.ndarray):
+            cons = np.ascontiguousarray(cons, dtype=np.float64)
+        p, where, _keep = self._ptr(cons, self.nc, False)
+        self._check(self.lib.rmhd_set_cons(self.h, p, where), "set_cons")
+
+    def prims(self, out=None):
+        if out is None:
+            out = np.empty((self.np, self.ny, self.nx))
+        p, where, _keep = self._ptr(out, self.np, True)
+        self._check(self.lib.rmhd_get_prims(self.h, p, where), "get_prims")
+        return out
+
+    def cons(self, out=None):
+        if out is None:
+            out = np.empty((self.nc, self.ny, self.nx))
+        p, where, _keep = self._ptr(out, self.nc, True)
+        self._check(self.lib.rmhd_get_cons(self.h, p, where), "get_cons")
+        return out
+
+    def step(self, dt: float = 0.0, nsteps: int = 1) -> float:
+        t = C.c_double()
+        self._check(self.lib.rmhd_imex_step(self.h, float(dt), int(nsteps), C.byref(t)), "imex_step")
+        return t.value
+
+    def check(self):
+        self._check(self.lib.rmhd_check(self.h), "check")
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.rmhd_set_profiling(self.h, int(bool(on))), "set_profiling")
+
+    def kernel_times(self) -> dict:
+        """{kind: (total ms, launches)} since profiling was enabled (synchronises)."""
+        ms, n = (C.c_double * 3)(), (C.c_int * 3)()
+        self._check(self.lib.rmhd_kernel_times(self.h, ms, n), "kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("stage", "flux1", "flux2"))}
+
+    def diagnostics(self) -> dict:
+        out = (C.c_double * 8)()
+        self._check(self.lib.rmhd_diagnostics(self.h, out), "diagnostics")
+        keys = ("sum_D", "sum_tau", "sum_Sx", "sum_Bx", "sum_charge", "max_v", "nonfinite", "dt_cfl")
+        return dict(zip(keys, list(out)))

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded primitive inputs. Bar: relative L-infinity <= 1e-9 per
+conserved variable, relative to the variable's natural scale (conftest.parity_scale:
+its own max |q|, shared by vector components; mu-weighted two-fluid variables
+and the charge/cleaning fields scaled by the terms that make them up)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import parity_errors
+from paper_1808_09721_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_09721_gb300 import _lib
+    from paper_1808_09721_gb300 import build as B
+    B.build()
+    _lib.load()
+    from paper_1808_09721_gb300.sim import Sim as S
+    return S
+
+
+def oracle_for(wl):
+    s = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y,
+              mu_e=wl.mu_e, mu_p=wl.mu_p, kappa=wl.kappa)
+    s.set_prims(wl.prims)
+    return s
+
+
+def rel_linf(got, want, mu_ref=1.0):
+    model = 0 if want.shape[0] == 14 else 1
+    return parity_errors(model, got, want, mu_ref)
+
+
+def run_pair(Sim, wl, nsteps, precision=0):
+    g = Sim.from_workload(wl, precision=precision)
+    o = oracle_for(wl)
+    g.step(wl.dt, nsteps)
+    g.check()
+    o.step(wl.dt, nsteps)
+    return g, o
+
+
+def test_set_prims_matches_oracle(Sim):
+    for wl in (WL.khi(n=24, seed=3), WL.tf_sheet(n=16, seed=4)):
+        g = Sim.from_workload(wl)
+        o = oracle_for(wl)
+        err = rel_linf(g.cons(), o.cons(), max(abs(wl.mu_e), abs(wl.mu_p)))
+        assert np.all(err <= 1e-14), err
+        np.testing.assert_allclose(g.prims(), wl.prims, rtol=1e-13, atol=1e-14)
+
+
+def test_brio_wu_full_run(Sim):
+    """Config: 1-D Brio-Wu, N = 400, sigma = 100, Gamma = 2, 400 steps to t = 0.4."""
+    wl = WL.brio_wu()
+    g, o = run_pair(Sim, wl, wl.nsteps)
+    err = rel_linf(g.cons(), o.cons())
+    assert np.all(err <= TOL), err
+
+
+@pytest.mark.parametrize("n,ny,steps", [(64, 64, 6), (70, 45, 4)])
+def test_khi_parity(Sim, n, ny, steps):
+    """2-D KHI shear layer (sigma = 1e3, periodic), incl. a ragged grid that does
+    not fill the 32 x 8 tiles."""
+    wl = WL.khi(n=n, ny=ny, seed=1)
+    g, o = run_pair(Sim, wl, steps)
+    err = rel_linf(g.cons(), o.cons())
+    assert np.all(err <= TOL), err
+    gp, op = g.prims(), o.prims()
+    assert np.max(np.abs(gp - op)) <= 1e-9 * np.max(np.abs(op))
+
+
+def test_two_fluid_sheet_parity(Sim):
+    wl = WL.tf_sheet(n=40, seed=2)
+    g, o = run_pair(Sim, wl, 4)
+    err = rel_linf(g.cons(), o.cons(), 1e3)
+    assert np.all(err <= TOL), err
+
+
+def test_field_loop_parity(Sim):
+    wl = WL.field_loop(n=32)
+    g, o = run_pair(Sim, wl, 5)
+    err = rel_linf(g.cons(), o.cons())
+    assert np.all(err <= TOL), err
+
+
+def test_stiff_tubes_parity(Sim):
+    """1-D tubes with sigma up to 1e6 (stiff implicit stage) and Gamma = 4/3."""
+    for wl in WL.batch_tubes(count=4, seed=5, nmin=100, nmax=300)[:4]:
+        g, o = run_pair(Sim, wl, 20)
+        err = rel_linf(g.cons(), o.cons())
+        assert np.all(err <= TOL), (wl.name, wl.sigma, err)
+
+
+def test_outflow_2d_and_tiny_grids(Sim):
+    """Outflow in both directions; degenerate grids smaller than the stencil."""
+    wl = WL.khi(n=20, ny=12, seed=7)
+    wl = wl.with_prims(wl.prims, bc_x=WL.OUTFLOW, bc_y=WL.OUTFLOW)
+    g, o = run_pair(Sim, wl, 3)
+    assert np.all(rel_linf(g.cons(), o.cons()) <= TOL)
+    for nx in (1, 2, 3):
+        wl = WL.brio_wu(nx=nx)
+        g, o = run_pair(Sim, wl, 3)
+        assert np.all(rel_linf(g.cons(), o.cons()) <= TOL)
+
+
+def rel_l1(got, want, mu_ref=1.0):
+    """Mean |error| over the cells divided by the variable's natural scale."""
+    from conftest import parity_scale
+    model = 0 if want.shape[0] == 14 else 1
+    d = np.abs(got - want).reshape(want.shape[0], -1).mean(axis=1)
+    return d / parity_scale(model, want, mu_ref)
+
+
+def test_mixed_precision_error(Sim):
+    """Mixed form: FP32 flux arithmetic, FP64 source solve; relative L1 <= 1e-4."""
+    wl = WL.khi(n=64, seed=1)
+    g, o = run_pair(Sim, wl, 6, precision=1)
+    l1 = rel_l1(g.cons(), o.cons())
+    assert np.all(l1 <= 1e-4), l1
+    wl = WL.tf_sheet(n=40, seed=2)
+    g, o = run_pair(Sim, wl, 4, precision=1)
+    l1 = rel_l1(g.cons(), o.cons(), 1e3)
+    assert np.all(l1 <= 1e-4), l1
+
+
+def test_error_reporting_keeps_context_usable(Sim):
+    """An inadmissible state is rejected with the first bad cell; the context stays usable."""
+    from paper_1808_09721_gb300 import RmhdError
+    wl = WL.khi(n=16, seed=0)
+    bad = wl.prims.copy()
+    bad[1, 3, 5] = 1.2  # v_x > 1
+    g = Sim.from_workload(wl)
+    with pytest.raises(RmhdError) as ei:
+        g.set_prims(bad)
+    assert ei.value.code == -1 and "i=5, j=3" in str(ei.value)
+    g.set_prims(wl.prims)
+    g.step(wl.dt, 1)
+    g.check()
+    assert np.all(np.isfinite(g.cons()))
+
+
+def test_diagnostics_conservation(Sim):
+    wl = WL.khi(n=64, seed=2)
+    g = Sim.from_workload(wl)
+    d0 = g.diagnostics()
+    g.step(wl.dt, 5)
+    d1 = g.diagnostics()
+    assert d1["nonfinite"] == 0
+    for k in ("sum_D", "sum_tau", "sum_Sx", "sum_Bx"):
+        assert abs(d1[k] - d0[k]) <= 1e-12 * max(abs(d0[k]), 1e-3), k
+    assert abs(d1["dt_cfl"] - wl.dt) < 1e-15
+
+
+def test_full_size_khi_sampled_cells(Sim):
+    """Full 1024^2 KHI in the bench's launch configuration: one step on the GPU;
+    sampled cells checked against the oracle on 16 x 16 periodic windows (a cell
+    after one step depends only on cells within 4 of it)."""
+    wl = WL.khi(n=1024, seed=0)
+    g = Sim.from_workload(wl)
+    g.step(wl.dt, 1)
+    g.check()
+    got = g.cons()
+    rng = np.random.default_rng(9)
+    h = 8
+    for _ in range(6):
+        j0, i0 = (int(x) for x in rng.integers(0, 1024, size=2))
+        jj = (np.arange(j0 - h, j0 + h) % 1024)
+        ii = (np.arange(i0 - h, i0 + h) % 1024)
+        win = np.ascontiguousarray(wl.prims[:, jj][:, :, ii])
+        sub = wl.with_prims(win, nx=2 * h, ny=2 * h, bc_x=WL.OUTFLOW, bc_y=WL.OUTFLOW,
+                            xlim=(0.0, 2 * h * wl.dx), ylim=(0.0, 2 * h * wl.dy))
+        o = oracle_for(sub)
+        o.step(wl.dt, 1)
+        want = o.cons()[:, h, h]
+        from conftest import parity_scale
+        scale = parity_scale(0, got)
+        assert np.all(np.abs(got[:, j0, i0] - want) <= TOL * scale), (j0, i0)
