@@ -141,6 +141,24 @@ int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 int rmhd_set_profiling(rmhd_ctx *ctx, int enable);
 int rmhd_kernel_times(rmhd_ctx *ctx, double *ms, int *counts);
 
+/* Diagnostics without any allocation (the paper has no counterpart). For
+ * callers that cannot call cudaMalloc -- e.g. code running while a memory
+ * pool or arena owns the device, or a framework that forbids allocation after
+ * start-up -- this computes the same 7 numbers as out[0..6] of
+ * rmhd_diagnostics from caller-owned device arrays, with no context:
+ *   cons  [N_c][ny][nx] and prims [n_prim][ny][nx] (dense, device, FP64),
+ *   out   7 doubles in device memory (written asynchronously on cuda_stream).
+ * Partial sums live in a file-scope device array of 512 KiB that every GPU
+ * loading the library keeps until exit; it limits inputs to 16,777,216 cells.
+ * The first call on a device looks up that array's address with
+ * cudaGetSymbolAddress (once per device, that device current); make that
+ * first call before any stream capture. Calls share the array: two calls
+ * whose kernels overlap on the GPU race. Calls no cudaMalloc/cudaFree.
+ * Errors: RMHD_ERR_INVALID (bad argument), RMHD_ERR_NOMEM (more cells than
+ * the static array holds), RMHD_ERR_CUDA. */
+int rmhd_diagnostics_noalloc(int model, int nx, int ny, double dx, double dy, const double *cons,
+                             const double *prims, double *out, void *cuda_stream);
+
 /* Library version string. */
 const char *rmhd_version(void);
 

@@ -23,7 +23,8 @@ HOST, DEVICE = 0, 1
 # every symbol include/rmhd.h declares
 EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_error", "rmhd_set_prims",
            "rmhd_get_prims", "rmhd_get_cons", "rmhd_set_cons", "rmhd_imex_step", "rmhd_check",
-           "rmhd_diagnostics", "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_version")
+           "rmhd_diagnostics", "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc",
+           "rmhd_version")
 
 
 class Config(C.Structure):
@@ -70,6 +71,7 @@ def load(path: str | None = None):
     L.rmhd_diagnostics.argtypes = [_P, _D]
     L.rmhd_set_profiling.argtypes = [_P, C.c_int]
     L.rmhd_kernel_times.argtypes = [_P, _D, C.POINTER(C.c_int)]
+    L.rmhd_diagnostics_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, _P, _P]
     L.rmhd_version.restype = C.c_char_p
     _lib = L
     return L
