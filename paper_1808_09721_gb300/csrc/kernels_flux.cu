@@ -45,37 +45,69 @@ __device__ __forceinline__ void record_status(int *status, int st, long long cel
 }
 
 // ---- model adaptors ------------------------------------------------------
+// Per-cell quantities staged once per tile (aux), the flux of one cell from
+// shared memory, the nonzero source entries of an interior cell, and the
+// recovery of the updated state.
 struct SFModel {
     static constexpr int NC = sf::NC, NW = sf::NW;
-    // physical flux of the cell whose state sits at st[v * stride + idx]
-    template <class FT>
-    static __device__ __forceinline__ void cell_flux(const double *st, int stride, int idx, int dir, const Phys &ph,
-                                                     FT f[NC]) {
+    static constexpr int NAUX = 5;  // J (3), Z = rho h W^2, p + (E^2 + B^2)/2
+    static constexpr int NS = 5;    // source slots: E (3), psi, phi
+    static constexpr int G_FP64 = 4, G_FP32 = 4;
+    static __device__ __forceinline__ int src_slot(int c) {
+        return c >= sf::EX && c <= sf::EZ ? c - sf::EX : (c == sf::PSI ? 3 : (c == sf::PHI ? 4 : -1));
+    }
+    static __device__ __forceinline__ void prep(const double *st, int SN, int idx, const Phys &ph, double *aux) {
         double q[NC], w[NW], J[3];
 #pragma unroll
-        for (int v = 0; v < NC; ++v) q[v] = st[v * stride + idx];
+        for (int v = 0; v < NC; ++v) q[v] = st[v * SN + idx];
 #pragma unroll
-        for (int v = 0; v < NW; ++v) w[v] = st[(NC + v) * stride + idx];
+        for (int v = 0; v < NW; ++v) w[v] = st[(NC + v) * SN + idx];
         sf::current(q, w, ph.sigma, J);
-        FT qf[NC], wf[NW], Jf[3];
-#pragma unroll
-        for (int v = 0; v < NC; ++v) qf[v] = (FT)q[v];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) wf[v] = (FT)w[v];
-        Jf[0] = (FT)J[0]; Jf[1] = (FT)J[1]; Jf[2] = (FT)J[2];
-        sf::flux(qf, wf, Jf, dir, f);
+        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
+                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
+        aux[0 * SN + idx] = J[0];
+        aux[1 * SN + idx] = J[1];
+        aux[2 * SN + idx] = J[2];
+        aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
+        aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
     }
-    // source Psi of Eq. (resistive RMHD), nonzero only for E, psi, phi
-    static __device__ __forceinline__ void source(const double q[NC], const double w[NW], const Phys &ph, double s[NC]) {
-        double J[3];
-        sf::current(q, w, ph.sigma, J);
+    template <class FT>
+    static __device__ __forceinline__ void cell_flux(const double *st, const double *aux, int SN, int idx, int dir,
+                                                     const Phys &ph, FT f[NC]) {
+        (void)ph;
+        const FT vd = (FT)st[(NC + sf::VX + dir) * SN + idx];
+        const FT Ed = (FT)st[(sf::EX + dir) * SN + idx], Bd = (FT)st[(sf::BX + dir) * SN + idx];
+        const FT Zv = (FT)aux[3 * SN + idx] * vd;
+        const FT D = (FT)st[sf::D * SN + idx];
+        f[sf::D] = D * vd;
 #pragma unroll
-        for (int v = 0; v < NC; ++v) s[v] = 0.0;
-        s[sf::EX] = -J[0];
-        s[sf::EY] = -J[1];
-        s[sf::EZ] = -J[2];
-        s[sf::PSI] = q[sf::RHOE] - ph.kappa * q[sf::PSI];
-        s[sf::PHI] = -ph.kappa * q[sf::PHI];
+        for (int i = 0; i < 3; ++i)
+            f[sf::SX + i] = Zv * (FT)st[(NC + sf::VX + i) * SN + idx] - (FT)st[(sf::EX + i) * SN + idx] * Ed -
+                            (FT)st[(sf::BX + i) * SN + idx] * Bd;
+        f[sf::SX + dir] += (FT)aux[4 * SN + idx];
+        f[sf::TAU] = (FT)st[(sf::SX + dir) * SN + idx] - f[sf::D];
+        const FT EX = (FT)st[sf::EX * SN + idx], EY = (FT)st[sf::EY * SN + idx], EZ = (FT)st[sf::EZ * SN + idx];
+        const FT BX = (FT)st[sf::BX * SN + idx], BY = (FT)st[sf::BY * SN + idx], BZ = (FT)st[sf::BZ * SN + idx];
+        const FT psi = (FT)st[sf::PSI * SN + idx], phi = (FT)st[sf::PHI * SN + idx];
+        if (dir == 0) {
+            f[sf::BX] = phi; f[sf::BY] = -EZ; f[sf::BZ] = EY;
+            f[sf::EX] = psi; f[sf::EY] = BZ; f[sf::EZ] = -BY;
+        } else {
+            f[sf::BX] = EZ; f[sf::BY] = phi; f[sf::BZ] = -EX;
+            f[sf::EX] = -BZ; f[sf::EY] = psi; f[sf::EZ] = BX;
+        }
+        f[sf::RHOE] = (FT)aux[dir * SN + idx];
+        f[sf::PSI] = Ed;
+        f[sf::PHI] = Bd;
+    }
+    // nonzero source entries of Eq. (resistive RMHD): E: -J, psi: varrho - kappa psi, phi: -kappa phi
+    static __device__ __forceinline__ void source(const double *st, const double *aux, int SN, int idx,
+                                                  const Phys &ph, double s[NS]) {
+        s[0] = -aux[0 * SN + idx];
+        s[1] = -aux[1 * SN + idx];
+        s[2] = -aux[2 * SN + idx];
+        s[3] = fma(-ph.kappa, st[sf::PSI * SN + idx], st[sf::RHOE * SN + idx]);
+        s[4] = -ph.kappa * st[sf::PHI * SN + idx];
     }
     static __device__ __forceinline__ int recover(const double q[NC], const double wold[NW], const Phys &ph,
                                                   double w[NW]) {
@@ -85,18 +117,36 @@ struct SFModel {
 
 struct TFModel {
     static constexpr int NC = tf::NC, NW = tf::NW;
+    static constexpr int NAUX = 0;
+    static constexpr int NS = 9;  // Sbar (3), taubar, E (3), psi, phi
+    static constexpr int G_FP64 = 2, G_FP32 = 4;
+    static __device__ __forceinline__ int src_slot(int c) {
+        return c >= tf::SBX && c <= tf::TAUB ? c - tf::SBX
+               : (c >= tf::EX && c <= tf::EZ ? 4 + c - tf::EX : (c == tf::PSI ? 7 : (c == tf::PHI ? 8 : -1)));
+    }
+    static __device__ __forceinline__ void prep(const double *, int, int, const Phys &, double *) {}
     template <class FT>
-    static __device__ __forceinline__ void cell_flux(const double *st, int stride, int idx, int dir, const Phys &ph,
-                                                     FT f[NC]) {
+    static __device__ __forceinline__ void cell_flux(const double *st, const double *aux, int SN, int idx, int dir,
+                                                     const Phys &ph, FT f[NC]) {
+        (void)aux;
         FT qf[NC], wf[NW];
 #pragma unroll
-        for (int v = 0; v < NC; ++v) qf[v] = (FT)st[v * stride + idx];
+        for (int v = 0; v < NC; ++v) qf[v] = (FT)st[v * SN + idx];
 #pragma unroll
-        for (int v = 0; v < NW; ++v) wf[v] = (FT)st[(NC + v) * stride + idx];
+        for (int v = 0; v < NW; ++v) wf[v] = (FT)st[(NC + v) * SN + idx];
         tf::flux(qf, wf, (FT)ph.mu_e, (FT)ph.mu_p, (FT)ph.inv_dmu, dir, f);
     }
-    static __device__ __forceinline__ void source(const double q[NC], const double w[NW], const Phys &ph, double s[NC]) {
-        tf::source(q, w, ph, s);
+    static __device__ __forceinline__ void source(const double *st, const double *aux, int SN, int idx,
+                                                  const Phys &ph, double s[NS]) {
+        (void)aux;
+        double q[NC], w[NW], full[NC];
+#pragma unroll
+        for (int v = 0; v < NC; ++v) q[v] = st[v * SN + idx];
+#pragma unroll
+        for (int v = 0; v < NW; ++v) w[v] = st[(NC + v) * SN + idx];
+        tf::source(q, w, ph, full);
+        s[0] = full[tf::SBX]; s[1] = full[tf::SBY]; s[2] = full[tf::SBZ]; s[3] = full[tf::TAUB];
+        s[4] = full[tf::EX]; s[5] = full[tf::EY]; s[6] = full[tf::EZ]; s[7] = full[tf::PSI]; s[8] = full[tf::PHI];
     }
     static __device__ __forceinline__ int recover(const double q[NC], const double wold[NW], const Phys &ph,
                                                   double w[NW]) {
@@ -105,21 +155,43 @@ struct TFModel {
 };
 
 // ---- the fused flux kernel -----------------------------------------------
-template <class M, int TX, int TY, class FT, int MODE>
-__global__ void __launch_bounds__(TX *TY, 1) k_flux(Grid g, Phys ph, FluxArgs a) {
+// G component groups of TX*TY threads each: thread (g, l) owns interior cell l
+// and components c = g, g + G, g + 2G, ...; one round of the reconstruction
+// handles G components at once (one per group).
+template <class M, int TX, int TY, int G, class FT, int MODE>
+struct FluxSmem {
+    static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
+    static constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH, NL = TX * TY;
+    // byte offsets
+    static constexpr size_t st = 0;
+    static constexpr size_t aux = st + sizeof(double) * NV * SN;
+    static constexpr size_t src = aux + sizeof(double) * M::NAUX * SN;
+    static constexpr size_t fl = src + sizeof(double) * M::NS * NL;
+    static constexpr size_t hp = fl + sizeof(FT) * NC * SN;
+    static constexpr size_t fc = hp + sizeof(FT) * 4 * G * SN;
+    static constexpr size_t total = fc + sizeof(FT) * G * SN;
+};
+
+template <class M, int TX, int TY, int G, class FT, int MODE>
+__global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs a) {
+    using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
     constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     constexpr bool TWO_D = TY > 1;
-    constexpr int SW = TX + 4, SH = TWO_D ? TY + 4 : 1, SN = SW * SH;
-    constexpr int NT = TX * TY;
-    constexpr int OY = TWO_D ? 2 : 0;  // SMEM row of the first interior row
+    constexpr int SW = L_::SW, SH = L_::SH, SN = L_::SN, NL = L_::NL;
+    constexpr int NT = NL * G;
+    constexpr int OY = TWO_D ? 2 : 0;   // SMEM row of the first interior row
+    constexpr int NR = (NC + G - 1) / G; // component rounds
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *st = reinterpret_cast<double *>(smem_raw);            // [NV][SH][SW]
-    FT *fl = reinterpret_cast<FT *>(st + NV * SN);                 // [NC][SH][SW]
-    FT *hp = fl + NC * SN;                                         // [4][SH][SW]: e+, e-, A+, A-
-    FT *fc = hp + 4 * SN;                                          // [SH][SW]: 4 F at the face right of the cell
+    double *st = reinterpret_cast<double *>(smem_raw + L_::st);   // [NV][SH][SW]
+    double *aux = reinterpret_cast<double *>(smem_raw + L_::aux); // [NAUX][SH][SW]
+    double *src = reinterpret_cast<double *>(smem_raw + L_::src); // [NS][NL] (interior cells)
+    FT *fl = reinterpret_cast<FT *>(smem_raw + L_::fl);           // [NC][SH][SW]
+    FT *hp = reinterpret_cast<FT *>(smem_raw + L_::hp);           // [G][4][SH][SW]: e+, e-, A+, A-
+    FT *fc = reinterpret_cast<FT *>(smem_raw + L_::fc);           // [G][SH][SW]: 4 F at the face after the cell
 
     const int tid = threadIdx.x;
+    const int grp = tid / NL, lid = tid - grp * NL;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
 
     // 1. stage the tile + halo (boundary conditions by index map)
@@ -128,136 +200,160 @@ __global__ void __launch_bounds__(TX *TY, 1) k_flux(Grid g, Phys ph, FluxArgs a)
         int sy = r / SW, sx = r - sy * SW;
         int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
         int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
-        const double *src = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-        st[e] = src[(long long)gj * g.nx + gi];
+        const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
+        st[e] = srcp[(long long)gj * g.nx + gi];
     }
     __syncthreads();
-
-    const int tx = tid % TX, ty = tid / TX;
-    const int ox = tx + 2, oy = ty + OY;  // owner cell in SMEM coordinates
-    FT L[NC];
+    // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
+    if (M::NAUX > 0)
+        for (int e = tid; e < SN; e += NT) M::prep(st, SN, e, ph, aux);
+    __syncthreads();
+    for (int e = tid; e < NL; e += NT) {
+        int ty = e / TX, tx = e - ty * TX;
+        double s[M::NS];
+        M::source(st, aux, SN, (ty + OY) * SW + tx + 2, ph, s);
 #pragma unroll
-    for (int v = 0; v < NC; ++v) L[v] = FT(0);
+        for (int k = 0; k < M::NS; ++k) src[k * NL + e] = s[k];
+    }
+
+    const int tx = lid % TX, ty = lid / TX;
+    const int ox = tx + 2, oy = ty + OY;  // owned cell in SMEM coordinates
+    FT L[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) L[r] = FT(0);
 
     const FT eps4 = FT(4e-6);
+    FT *hpg = hp + grp * 4 * SN;
+    FT *fcg = fc + grp * SN;
 #pragma unroll 1
     for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
-        const int sstep = dir == 0 ? 1 : SW;  // SMEM offset of the next cell along dir
+        const int sstep = dir == 0 ? 1 : SW;
         const FT inv4h = FT(0.25 / (dir == 0 ? g.dx : g.dy));
-        // 2a. physical flux of every cell the reconstruction needs
+        // 3a. physical flux of every cell the reconstruction needs
         const int ncx = dir == 0 ? SW : TX, ncy = dir == 0 ? TY : SH;
         const int cx0 = dir == 0 ? 0 : 2, cy0 = dir == 0 ? OY : 0;
         for (int e = tid; e < ncx * ncy; e += NT) {
             int cy = e / ncx, cx = e - cy * ncx;
             int idx = (cy0 + cy) * SW + cx0 + cx;
             FT f[NC];
-            M::template cell_flux<FT>(st, SN, idx, dir, ph, f);
+            M::template cell_flux<FT>(st, aux, SN, idx, dir, ph, f);
 #pragma unroll
             for (int v = 0; v < NC; ++v) fl[v * SN + idx] = f[v];
         }
         __syncthreads();
-        // half points between cell c and c + sstep: along dir, from the first
-        // halo cell to the last-but-one
         const int nhx = dir == 0 ? SW - 1 : TX, nhy = dir == 0 ? TY : SH - 1;
         const int hx0 = dir == 0 ? 0 : 2, hy0 = dir == 0 ? OY : 0;
-        // faces right of cells 1 .. T+1 (SMEM coordinate along dir)
         const int nfx = dir == 0 ? TX + 1 : TX, nfy = dir == 0 ? TY : TY + 1;
         const int fx0 = dir == 0 ? 1 : 2, fy0 = dir == 0 ? OY : 1;
-#pragma unroll 1
-        for (int c = 0; c < NC; ++c) {
-            const FT *fv = fl + c * SN;
-            const double *qv = st + c * SN;
-            for (int e = tid; e < nhx * nhy; e += NT) {
-                int hy = e / nhx, hx = e - hy * nhx;
-                int idx = (hy0 + hy) * SW + hx0 + hx;
-                FT df = fv[idx + sstep] - fv[idx];
-                FT dq = FT(qv[idx + sstep] - qv[idx]);
-                FT ep = df + dq, em = df - dq;
-                FT ap = eps4 + ep * ep, am = eps4 + em * em;
-                hp[idx] = ep;
-                hp[SN + idx] = em;
-                hp[2 * SN + idx] = ap * ap;
-                hp[3 * SN + idx] = am * am;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int c = r * G + grp;
+            const bool active = c < NC;
+            // 3b. half points of component c (group grp)
+            if (active) {
+                const FT *fv = fl + c * SN;
+                const double *qv = st + c * SN;
+                for (int e = lid; e < nhx * nhy; e += NL) {
+                    int hy = e / nhx, hx = e - hy * nhx;
+                    int idx = (hy0 + hy) * SW + hx0 + hx;
+                    FT df = fv[idx + sstep] - fv[idx];
+                    FT dq = FT(qv[idx + sstep] - qv[idx]);
+                    FT ep = df + dq, em = df - dq;
+                    FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
+                    hpg[idx] = ep;
+                    hpg[SN + idx] = em;
+                    hpg[2 * SN + idx] = ap * ap;
+                    hpg[3 * SN + idx] = am * am;
+                }
             }
             __syncthreads();
-            for (int e = tid; e < nfx * nfy; e += NT) {
-                int fy = e / nfx, fx = e - fy * nfx;
-                int idx = (fy0 + fy) * SW + fx0 + fx;
-                int il = idx - sstep, ir = idx + sstep;
-                FT Ap = hp[2 * SN + idx], Am = hp[3 * SN + idx];
-                FT wp = Ap * s_rcp1(Ap + FT(2) * hp[2 * SN + il]);
-                FT wm = Am * s_rcp1(Am + FT(2) * hp[3 * SN + ir]);
-                FT Xp = hp[il] - hp[idx];
-                FT Xm = hp[SN + idx] - hp[SN + ir];
-                fc[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+            // 3c. face values of component c
+            if (active) {
+                const FT *fv = fl + c * SN;
+                for (int e = lid; e < nfx * nfy; e += NL) {
+                    int fy = e / nfx, fx = e - fy * nfx;
+                    int idx = (fy0 + fy) * SW + fx0 + fx;
+                    int il = idx - sstep, ir = idx + sstep;
+                    FT Ap = hpg[2 * SN + idx], Am = hpg[3 * SN + idx];
+                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpg[2 * SN + il], Ap));
+                    FT wm = Am * s_rcp1(s_fma(FT(2), hpg[3 * SN + ir], Am));
+                    FT Xp = hpg[il] - hpg[idx];
+                    FT Xm = hpg[SN + idx] - hpg[SN + ir];
+                    fcg[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+                }
             }
             __syncthreads();
-            L[c] = s_fma(fc[oy * SW + ox - sstep] - fc[oy * SW + ox], inv4h, L[c]);
+            // 3d. flux difference into the owned cell's accumulator
+            if (active) L[r] = s_fma(fcg[oy * SW + ox - sstep] - fcg[oy * SW + ox], inv4h, L[r]);
         }
         __syncthreads();
     }
 
-    // 3. epilogue for the owner cell
+    // 4. epilogue: each thread updates its own components of its cell
     const int gi = i0 + tx, gj = j0 + ty;
-    if (gi >= g.nx || gj >= g.ny) return;
+    const bool inside = gi < g.nx && gj < g.ny;
     const long long cell = (long long)gj * g.nx + gi;
-    const int oidx = oy * SW + ox;
-    double q[NC], w[NW], s[NC];
-#pragma unroll
-    for (int v = 0; v < NC; ++v) q[v] = st[v * SN + oidx];
-#pragma unroll
-    for (int v = 0; v < NW; ++v) w[v] = st[(NC + v) * SN + oidx];
-    M::source(q, w, ph, s);
     const double dt = a.dt, hdt = 0.5 * a.dt;
-    if (MODE == 1) {
-        const double cs = a.c_src * a.dt;
+    // [NC][NL] staging of q^{n+1} for the recovery (mode 2): reuses the q planes
+    // of the staged state, which are dead here (only the primitive planes are read)
+    double *qn_sm = st;
 #pragma unroll
-        for (int v = 0; v < NC; ++v) {
-            double b = a.base[v * g.plane + cell];
-            double Lv = (double)L[v];
-            a.out1[v * g.plane + cell] = fma(cs, s[v], fma(dt, Lv, b));
-            a.out2[v * g.plane + cell] = fma(hdt, Lv + s[v], b);
+    for (int r = 0; r < NR; ++r) {
+        const int c = r * G + grp;
+        if (c >= NC) continue;
+        const int slot = M::src_slot(c);
+        const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
+        const double Lv = (double)L[r];
+        if (MODE == 1) {
+            if (inside) {
+                const double b = a.base[c * g.plane + cell];
+                a.out1[c * g.plane + cell] = fma(a.c_src * dt, s, fma(dt, Lv, b));
+                a.out2[c * g.plane + cell] = fma(hdt, Lv + s, b);
+            }
+        } else {
+            const double qn = inside ? fma(hdt, Lv + s, a.base[c * g.plane + cell]) : 0.0;
+            if (inside) a.out1[c * g.plane + cell] = qn;
+            qn_sm[c * NL + lid] = qn;
         }
-    } else {
-        double qn[NC], wn[NW];
+    }
+    if (MODE == 2) {
+        __syncthreads();
+        if (grp == 0 && inside) {
+            double qn[NC], wold[NW], wn[NW];
 #pragma unroll
-        for (int v = 0; v < NC; ++v) {
-            qn[v] = fma(hdt, (double)L[v] + s[v], a.base[v * g.plane + cell]);
-            a.out1[v * g.plane + cell] = qn[v];
+            for (int v = 0; v < NC; ++v) qn[v] = qn_sm[v * NL + lid];
+#pragma unroll
+            for (int v = 0; v < NW; ++v) wold[v] = st[(NC + v) * SN + oy * SW + ox];
+            int stc = M::recover(qn, wold, ph, wn);
+            record_status(a.status, stc, cell);
+#pragma unroll
+            for (int v = 0; v < NW; ++v) a.out2[v * g.plane + cell] = wn[v];
         }
-        int stc = M::recover(qn, w, ph, wn);
-        record_status(a.status, stc, cell);
-#pragma unroll
-        for (int v = 0; v < NW; ++v) a.out2[v * g.plane + cell] = wn[v];
     }
 }
 
-template <class M, int TX, int TY, class FT>
-static size_t flux_smem() {
-    constexpr int NC = M::NC, NW = M::NW;
-    constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH;
-    return (size_t)(NC + NW) * SN * sizeof(double) + (size_t)(NC + 5) * SN * sizeof(FT);
-}
-
-template <class M, int TX, int TY, class FT, int MODE>
+template <class M, int TX, int TY, int G, class FT, int MODE>
 static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
-    size_t smem = flux_smem<M, TX, TY, FT>();
+    using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
+    static_assert(L_::total <= 227 * 1024, "shared memory budget");
+    const size_t smem = L_::total;
     static bool configured = false;  // attribute is per device function; set once
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, FT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, G, FT, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((g.nx + TX - 1) / TX, TY > 1 ? (g.ny + TY - 1) / TY : g.ny);
-    k_flux<M, TX, TY, FT, MODE><<<grid, TX * TY, smem, s>>>(g, ph, a);
+    k_flux<M, TX, TY, G, FT, MODE><<<grid, TX * TY * G, smem, s>>>(g, ph, a);
     return cudaGetLastError();
 }
 
 template <class M, class FT, int MODE>
 static cudaError_t launch_flux_m(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
-    if (g.ny == 1) return launch_flux_t<M, 128, 1, FT, MODE>(g, ph, a, s);
-    return launch_flux_t<M, 32, 8, FT, MODE>(g, ph, a, s);
+    constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
+    if (g.ny == 1) return launch_flux_t<M, 128, 1, G, FT, MODE>(g, ph, a, s);
+    return launch_flux_t<M, 32, 8, G, FT, MODE>(g, ph, a, s);
 }
 
 cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
