@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--n", type=int, default=1024, help="grid side (default: the 1024^2 workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-ensemble workload")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -263,6 +264,43 @@ def main():
     value = total_cells * K / (ms64 * 1e-3)
     value_mx = total_cells * K / (msmx * 1e-3)
 
+    # batched ensemble: 512 independent 1-D shock tubes, N ~ U{100..4096},
+    # sigma log-uniform in [1, 1e6], own CFL dt, mixed form, one graph per step
+    batch = None
+    if args.batch:
+        runs = WL.batch_tubes(count=512, seed=2)
+        bsim = Sim.batch(runs, precision=MIXED, device=f"cuda:{local}")
+        choice = bsim.autotune()
+        bsim.step(0.0, W)
+        bsim.check()
+        bst = bsim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(bst)
+        bsim.step(0.0, K)
+        e1.record(bst)
+        torch.cuda.synchronize()
+        barrier()
+        bms = max_over_ranks(e0.elapsed_time(e1))
+        bsim.check()
+        bcells = int(bsim.nx)
+        # the configuration's whole run: 400 steps of every tube from its initial state
+        bsim.set_prims(bsim.pack([w.prims for w in runs]))
+        torch.cuda.synchronize()
+        e0.record(bst)
+        bsim.step(0.0, 400)
+        e1.record(bst)
+        torch.cuda.synchronize()
+        bsim.check()
+        full_ms = e0.elapsed_time(e1)
+        batch = {"value": world * bcells * K / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms / K,
+                 "runs": len(runs), "cells": bcells, "dtype": "f32 flux / f64 source",
+                 "full_run_400_steps_s": full_ms * 1e-3, "autotune": choice,
+                 "workload": "512 1-D resistive shock tubes, N~U{100..4096}, sigma log-uniform [1,1e6], "
+                             "Gamma=4/3, own CFL dt, one CUDA graph per step"}
+        del bsim
+
     # e2e through the C ABI with host buffers: upload prims, one step, read prims back
     pin = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)
     pin[...] = wl.prims
@@ -318,6 +356,7 @@ def main():
                 "hbm_roofline_step": {"bytes_per_cell_update": step_bytes,
                                       "achieved_gbs": step_bytes * value / world / 1e9,
                                       "frac": step_bytes * value / world / 1e9 / hbm_gbs},
+                "batch": batch,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                         "d2h_bytes_per_step": io_bytes},
                 "gpu_launches": 4 * K,

@@ -128,6 +128,28 @@ int rmhd_check(rmhd_ctx *ctx);
  * and the CFL time step cfl * min(dx, dy). Synchronous. */
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
+/* Batched ensemble of independent 1-D runs (many tests of Sec. 4.1 at once).
+ * All runs share `base` (model, x-range, Gamma, kappa, cfl, boundary
+ * conditions, precision; base->ny is ignored and taken as 1); run r has
+ * nx[r] cells and conductivity sigma[r] (sigma == NULL: base->sigma for all).
+ * The runs are packed one after another: every array of the other calls
+ * (prims, cons) has the layout [n_var][sum_r nx[r]] with run r at offset
+ * sum_{s<r} nx[s]. rmhd_imex_step with dt <= 0 advances every run by its own
+ * dt_r = cfl * dx_r (t_out reports run 0's time); dt > 0 uses dt for all.
+ * The step runs as one CUDA graph of persistent kernels walking a work list of
+ * (run, tile) pairs. rmhd_diagnostics on a batch sums over all cells without
+ * a cell-volume factor. Errors as for rmhd_create. */
+int rmhd_batch_workspace_bytes(const rmhd_config *base, int nruns, const int *nx, size_t *bytes);
+int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const int *nx, const double *sigma,
+                      void *cuda_stream, void *workspace, size_t workspace_bytes);
+
+/* Autotuner for a batched context (needs a state): times the flux tile width
+ * (64, 128, 256 cells), the number of persistent CTAs and the stage-kernel
+ * block size on the current state -- which it saves and restores -- keeps
+ * the fastest, and writes (tile width, CTAs, stage threads) to choice[3].
+ * Synchronous. Errors: RMHD_ERR_STATE for a single-grid context. */
+int rmhd_autotune(rmhd_ctx *ctx, int *choice);
+
 /* Per-kernel timing for roofline measurements (no counterpart in the paper,
  * which times whole main-loop iterations). While enabled, rmhd_imex_step
  * launches its kernels without a CUDA graph and brackets each launch with

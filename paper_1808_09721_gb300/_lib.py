@@ -23,8 +23,8 @@ HOST, DEVICE = 0, 1
 # every symbol include/rmhd.h declares
 EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_error", "rmhd_set_prims",
            "rmhd_get_prims", "rmhd_get_cons", "rmhd_set_cons", "rmhd_imex_step", "rmhd_check",
-           "rmhd_diagnostics", "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc",
-           "rmhd_version")
+           "rmhd_diagnostics", "rmhd_batch_workspace_bytes", "rmhd_create_batch", "rmhd_autotune",
+           "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc", "rmhd_version")
 
 
 class Config(C.Structure):
@@ -69,6 +69,10 @@ def load(path: str | None = None):
     L.rmhd_imex_step.argtypes = [_P, C.c_double, C.c_int, _D]
     L.rmhd_check.argtypes = [_P]
     L.rmhd_diagnostics.argtypes = [_P, _D]
+    _I = C.POINTER(C.c_int)
+    L.rmhd_batch_workspace_bytes.argtypes = [C.POINTER(Config), C.c_int, _I, C.POINTER(C.c_size_t)]
+    L.rmhd_create_batch.argtypes = [C.POINTER(_P), C.POINTER(Config), C.c_int, _I, _D, _P, _P, C.c_size_t]
+    L.rmhd_autotune.argtypes = [_P, _I]
     L.rmhd_set_profiling.argtypes = [_P, C.c_int]
     L.rmhd_kernel_times.argtypes = [_P, _D, C.POINTER(C.c_int)]
     L.rmhd_diagnostics_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, _P, _P]

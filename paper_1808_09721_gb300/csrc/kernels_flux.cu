@@ -172,8 +172,13 @@ struct FluxSmem {
     static constexpr size_t total = fc + sizeof(FT) * G * SN;
 };
 
+// One tile: interior cells [i0, i0 + TX) x [j0, j0 + TY) of the grid g whose
+// cell (i, j) lives at base + j * nx + i in every variable plane. All threads
+// of the CTA call it; it starts with a barrier so that a persistent CTA can
+// process tiles back to back.
 template <class M, int TX, int TY, int G, class FT, int MODE>
-__global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs a) {
+__device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const FluxArgs &a, int i0, int j0,
+                                          long long base, unsigned char *smem_raw) {
     using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
     constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     constexpr bool TWO_D = TY > 1;
@@ -182,7 +187,6 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
     constexpr int OY = TWO_D ? 2 : 0;   // SMEM row of the first interior row
     constexpr int NR = (NC + G - 1) / G; // component rounds
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     double *st = reinterpret_cast<double *>(smem_raw + L_::st);   // [NV][SH][SW]
     double *aux = reinterpret_cast<double *>(smem_raw + L_::aux); // [NAUX][SH][SW]
     double *src = reinterpret_cast<double *>(smem_raw + L_::src); // [NS][NL] (interior cells)
@@ -192,8 +196,8 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
 
     const int tid = threadIdx.x;
     const int grp = tid / NL, lid = tid - grp * NL;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
 
+    __syncthreads();  // the previous tile of a persistent CTA is done with shared memory
     // 1. stage the tile + halo (boundary conditions by index map)
     for (int e = tid; e < NV * SN; e += NT) {
         int v = e / SN, r = e - v * SN;
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
         int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
         int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
         const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-        st[e] = srcp[(long long)gj * g.nx + gi];
+        st[e] = srcp[base + (long long)gj * g.nx + gi];
     }
     __syncthreads();
     // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
     // 4. epilogue: each thread updates its own components of its cell
     const int gi = i0 + tx, gj = j0 + ty;
     const bool inside = gi < g.nx && gj < g.ny;
-    const long long cell = (long long)gj * g.nx + gi;
+    const long long cell = base + (long long)gj * g.nx + gi;
     const double dt = a.dt, hdt = 0.5 * a.dt;
     // [NC][NL] staging of q^{n+1} for the recovery (mode 2): reuses the q planes
     // of the staged state, which are dead here (only the primitive planes are read)
@@ -333,6 +337,34 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
 }
 
 template <class M, int TX, int TY, int G, class FT, int MODE>
+__global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    flux_tile<M, TX, TY, G, FT, MODE>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY, 0, smem_raw);
+}
+
+// Batched ensemble of 1-D runs packed one after another in every variable
+// plane: persistent CTAs walk the work list of (run, first cell) tiles; each
+// run has its own size, cell width, time step and conductivity.
+template <class M, int TX, int G, class FT, int MODE>
+__global__ void __launch_bounds__(TX *G, 1) k_flux_batch(Grid g, Phys ph, FluxArgs a, BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int w = blockIdx.x; w < b.nwork; w += gridDim.x) {
+        const int2 item = b.work[w];  // (run, first cell)
+        const int run = item.x;
+        Grid gt = g;
+        gt.nx = b.nx[run];
+        gt.ny = 1;
+        gt.dx = b.dx[run];
+        Phys pt = ph;
+        pt.sigma = b.sigma[run];
+        pt.eta = b.eta[run];
+        FluxArgs at = a;
+        at.dt = b.dt[run];
+        flux_tile<M, TX, 1, G, FT, MODE>(gt, pt, at, item.y, 0, b.offset[run], smem_raw);
+    }
+}
+
+template <class M, int TX, int TY, int G, class FT, int MODE>
 static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
     using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
     static_assert(L_::total <= 227 * 1024, "shared memory budget");
@@ -366,6 +398,69 @@ cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const
     if (precision == 0)
         return mode == 1 ? launch_flux_m<TFModel, double, 1>(g, ph, a, s) : launch_flux_m<TFModel, double, 2>(g, ph, a, s);
     return mode == 1 ? launch_flux_m<TFModel, float, 1>(g, ph, a, s) : launch_flux_m<TFModel, float, 2>(g, ph, a, s);
+}
+
+// ---- batched ensemble ------------------------------------------------------
+template <class M, int TX, class FT, int MODE>
+static cudaError_t launch_fb_t(const Grid &g, const Phys &ph, const FluxArgs &a, const BatchArgs &b, int blocks,
+                               cudaStream_t s) {
+    constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
+    using L_ = FluxSmem<M, TX, 1, G, FT, MODE>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_flux_batch<M, TX, G, FT, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L_::total);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_flux_batch<M, TX, G, FT, MODE><<<blocks, TX * G, L_::total, s>>>(g, ph, a, b);
+    return cudaGetLastError();
+}
+
+template <class M, class FT, int MODE>
+static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a, const BatchArgs &b, int tile_x,
+                               int blocks, cudaStream_t s) {
+    if (tile_x == 64) return launch_fb_t<M, 64, FT, MODE>(g, ph, a, b, blocks, s);
+    if (tile_x == 256) return launch_fb_t<M, 256, FT, MODE>(g, ph, a, b, blocks, s);
+    return launch_fb_t<M, 128, FT, MODE>(g, ph, a, b, blocks, s);
+}
+
+cudaError_t launch_flux_batch(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+                              const BatchArgs &b, int tile_x, int blocks, cudaStream_t s) {
+    if (model == 0) {
+        if (precision == 0)
+            return mode == 1 ? launch_fb_m<SFModel, double, 1>(g, ph, a, b, tile_x, blocks, s)
+                             : launch_fb_m<SFModel, double, 2>(g, ph, a, b, tile_x, blocks, s);
+        return mode == 1 ? launch_fb_m<SFModel, float, 1>(g, ph, a, b, tile_x, blocks, s)
+                         : launch_fb_m<SFModel, float, 2>(g, ph, a, b, tile_x, blocks, s);
+    }
+    if (precision == 0)
+        return mode == 1 ? launch_fb_m<TFModel, double, 1>(g, ph, a, b, tile_x, blocks, s)
+                         : launch_fb_m<TFModel, double, 2>(g, ph, a, b, tile_x, blocks, s);
+    return mode == 1 ? launch_fb_m<TFModel, float, 1>(g, ph, a, b, tile_x, blocks, s)
+                     : launch_fb_m<TFModel, float, 2>(g, ph, a, b, tile_x, blocks, s);
+}
+
+template <class M, int TX, class FT>
+static int occ_t() {
+    constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
+    using L_ = FluxSmem<M, TX, 1, G, FT, 2>;
+    cudaFuncSetAttribute(k_flux_batch<M, TX, G, FT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L_::total);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_flux_batch<M, TX, G, FT, 2>, TX * G, L_::total) != cudaSuccess)
+        return 0;
+    return n;
+}
+template <class M, class FT>
+static int occ_m(int tile_x) {
+    if (tile_x == 64) return occ_t<M, 64, FT>();
+    if (tile_x == 256) return occ_t<M, 256, FT>();
+    if (tile_x == 128) return occ_t<M, 128, FT>();
+    return 0;
+}
+int flux_batch_occupancy(int model, int precision, int tile_x) {
+    if (model == 0) return precision == 0 ? occ_m<SFModel, double>(tile_x) : occ_m<SFModel, float>(tile_x);
+    return precision == 0 ? occ_m<TFModel, double>(tile_x) : occ_m<TFModel, float>(tile_x);
 }
 
 } // namespace rmhd

@@ -15,8 +15,9 @@
 //   2. A fixed number of FP64 refinement passes: evaluate G in FP64 (one FP64
 //      Newton step of the pressure root per pass, started from a first-order
 //      prediction) and correct E with the FP32 inverse Jacobian. Each pass
-//      gains ~6-7 digits, so two passes reach the FP64 root to ~1e-13.
-//   3. One more FP64 pressure step at the final E gives consistent primitives.
+//      gains ~6-7 digits. The evaluation point of the last pass (~1e-13 from
+//      the FP64 root) is returned with its own primitives, so E and v are
+//      consistent; the last correction only checks convergence.
 #pragma once
 #include "device_math.cuh"
 
@@ -221,7 +222,12 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
     }
     if (!have_jac) return ST_NEWTON;
 
-    // ---- FP64 refinement passes
+    // ---- FP64 refinement passes. Pass k evaluates G in FP64 at E_k (one FP64
+    // pressure step, started from a first-order prediction) and forms the
+    // correction dE_k with the FP32 inverse Jacobian. The last pass's
+    // evaluation point is the result: its primitives are exactly those of the
+    // returned E (J amplifies any E/v mismatch by sigma), and its correction,
+    // ~1e-13 relative after the first pass, only gates convergence.
     double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
     double pdd = (double)p;
     const double rdf = (double)(1.f / dfdp);
@@ -234,27 +240,24 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
         float Gf[3] = {(float)G64[0], (float)G64[1], (float)G64[2]};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
+        last = fmax(fmax(fabs((double)dE[0]), fabs((double)dE[1])), fabs((double)dE[2]));
+        if (pass == NREF - 1) break;
         // first-order prediction of the pressure at the corrected E
         pdd -= (double)(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
         Ed[0] -= (double)dE[0];
         Ed[1] -= (double)dE[1];
         Ed[2] -= (double)dE[2];
-        last = fmax(fmax(fabs((double)dE[0]), fabs((double)dE[1])), fabs((double)dE[2]));
     }
-    // consistent primitives at the final E
-    em_split(Ed, Sv, B, tauB, r[D], St64, a64, S264);
-    pdd -= pres_resid(pdd, a64, S264, r[D], gm1, gam) * rdf;
-    double rZ = s_rcp(a64 + pdd);
-    w[VX] = St64[0] * rZ;
-    w[VY] = St64[1] * rZ;
-    w[VZ] = St64[2] * rZ;
+    w[VX] = v64[0];
+    w[VY] = v64[1];
+    w[VZ] = v64[2];
     w[P] = pdd;
-    w[LOR] = s_rsqrt(1.0 - (w[VX] * w[VX] + w[VY] * w[VY] + w[VZ] * w[VZ]));
+    w[LOR] = W64;
     q[EX] = Ed[0];
     q[EY] = Ed[1];
     q[EZ] = Ed[2];
     double sc = fmax((double)scale, fmax(fmax(fabs(Ed[0]), fabs(Ed[1])), fabs(Ed[2])));
-    if (!(pdd > 0.0) || !(last <= 1e-9 * sc) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
+    if (!(pdd > 0.0) || !(last <= 1e-10 * sc) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
     return ST_OK;
 }
 

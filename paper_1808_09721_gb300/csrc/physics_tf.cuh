@@ -360,7 +360,8 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     }
     if (!have_jac) return sf::ST_NEWTON;
 
-    // ---- FP64 refinement passes
+    // ---- FP64 refinement passes (as for one fluid: the last evaluation point
+    // is the result, with its own primitives; its correction gates convergence)
     double xd[7], pdd[2] = {(double)p[0], (double)p[1]};
     const double rdf[2] = {(double)(1.f / dfdp[0]), (double)(1.f / dfdp[1])};
     for (int i = 0; i < 7; ++i) xd[i] = (double)x[i];
@@ -377,28 +378,24 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
             float s = 0.f;
             for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * Gf[j];
             dx[i] = s;
+            last = fmax(last, fabs((double)s));
         }
+        if (pass == NREF - 1) break;
         for (int s = 0; s < 2; ++s) {
             float dp = 0.f;
             for (int i = 0; i < 7; ++i) dp += dpdx[s][i] * dx[i];
             pdd[s] -= (double)dp;
         }
-        for (int i = 0; i < 7; ++i) {
-            xd[i] -= (double)dx[i];
-            last = fmax(last, fabs((double)dx[i]));
-        }
+        for (int i = 0; i < 7; ++i) xd[i] -= (double)dx[i];
     }
-    split_x(c, xd, St64, a64, S264);
     bool ok = true;
     for (int s = 0; s < 2; ++s) {
-        pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
-        double Zs = a64[s] + pdd[s], rZ = s_rcp(Zs);
-        w[5 * s + VX] = St64[s][0] * rZ;
-        w[5 * s + VY] = St64[s][1] * rZ;
-        w[5 * s + VZ] = St64[s][2] * rZ;
+        w[5 * s + VX] = v64[s][0];
+        w[5 * s + VY] = v64[s][1];
+        w[5 * s + VZ] = v64[s][2];
         w[5 * s + P] = pdd[s];
-        w[5 * s + ZZ] = Zs;
-        ok = ok && pdd[s] > 0.0 && isfinite(Zs);
+        w[5 * s + ZZ] = Z64[s];
+        ok = ok && pdd[s] > 0.0 && isfinite(Z64[s]);
     }
     for (int i = 0; i < 3; ++i) {
         q[SBX + i] = xd[i] * c.mur;
@@ -407,7 +404,7 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     q[TAUB] = xd[3] * c.mur;
     double sc = (double)scale;
     for (int i = 0; i < 7; ++i) sc = fmax(sc, fabs(xd[i]));
-    if (!ok || !(last <= 1e-9 * sc)) return sf::ST_NEWTON;
+    if (!ok || !(last <= 1e-10 * sc)) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
 

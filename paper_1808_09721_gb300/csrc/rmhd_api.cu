@@ -46,6 +46,21 @@ struct rmhd_ctx {
     cudaGraphExec_t graph;
     double graph_dt;
     bool profiling;
+    // batched ensemble of 1-D runs (batch == true)
+    bool batch;
+    int nruns, nwork;
+    std::vector<int> run_nx;
+    std::vector<long long> run_off;
+    std::vector<double> run_dx, run_sigma;
+    BatchArgs bargs;
+    int *d_nx, *d_run_of;
+    int2 *d_work;
+    long long *d_off;
+    double *d_dx, *d_dt, *d_sigma, *d_eta, *d_adt, *d_cpsi;
+    double *h_tab;       // pinned host staging for the per-run time-step tables
+    double *Qsave, *Wsave;
+    int tile_x, flux_blocks, stage_threads;
+    double tab_dt;       // dt the tables were built for (<= 0: per-run CFL)
     struct Timed { int kind; cudaEvent_t a, b; };
     std::vector<Timed> timed;
     std::string err;
@@ -103,11 +118,30 @@ static Grid make_grid(const rmhd_config *cfg) {
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, stage, scratch, diag, status, total;
+    size_t Q, W, Q1, W1, R, ACC, stage, scratch, diag, status;
+    size_t nx, off, dx, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
+    size_t total;
 };
 
-static Layout layout(const rmhd_config *cfg) {
-    Grid g = make_grid(cfg);
+// Grid of a context; a batch is one packed 1-D "grid" of all runs' cells.
+static Grid make_grid_n(const rmhd_config *cfg, long long ncell) {
+    Grid g = {};
+    g.nx = (int)ncell;
+    g.ny = 1;
+    g.bcx = cfg->bc_x;
+    g.bcy = cfg->bc_y;
+    g.ncell = ncell;
+    g.plane = (ncell + 63) / 64 * 64;
+    g.dx = 1.0;
+    g.dy = 1.0;
+    return g;
+}
+
+static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork);
+
+static Layout layout(const rmhd_config *cfg) { return layout_g(cfg, make_grid(cfg), 0, 0); }
+
+static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork) {
     int nc = model_nc(cfg->model), nw = model_nw(cfg->model), np = model_np(cfg->model);
     size_t pl = (size_t)g.plane * sizeof(double);
     Layout L;
@@ -122,8 +156,29 @@ static Layout layout(const rmhd_config *cfg) {
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
+    L.nx = L.off = L.dx = L.dt = L.sigma = L.eta = L.adt = L.cpsi = L.work = L.run_of = L.Qsave = L.Wsave = 0;
+    if (nruns > 0) {
+        L.nx = o; o += align256((size_t)nruns * sizeof(int));
+        L.off = o; o += align256((size_t)nruns * sizeof(long long));
+        L.dx = o; o += align256((size_t)nruns * sizeof(double));
+        L.dt = o; o += align256((size_t)nruns * sizeof(double));
+        L.sigma = o; o += align256((size_t)nruns * sizeof(double));
+        L.eta = o; o += align256((size_t)nruns * sizeof(double));
+        L.adt = o; o += align256((size_t)nruns * sizeof(double));
+        L.cpsi = o; o += align256((size_t)nruns * sizeof(double));
+        L.work = o; o += align256((size_t)maxwork * sizeof(int2));
+        L.run_of = o; o += align256((size_t)g.ncell * sizeof(int));
+        L.Qsave = o; o += align256(nc * pl);
+        L.Wsave = o; o += align256(nw * pl);
+    }
     L.total = o;
     return L;
+}
+
+static long long batch_maxwork(int nruns, const int *nx) {
+    long long w = 0;
+    for (int r = 0; r < nruns; ++r) w += (nx[r] + 63) / 64;  // the narrowest tile width
+    return w;
 }
 
 extern "C" {
@@ -186,6 +241,14 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->graph = nullptr;
     c->graph_dt = 0.0;
     c->profiling = false;
+    c->batch = false;
+    c->nruns = 0;
+    c->nwork = 0;
+    c->h_tab = nullptr;
+    c->tile_x = 128;
+    c->flux_blocks = 0;
+    c->stage_threads = 128;
+    c->tab_dt = -1.0;
     c->t = 0.0;
     c->has_state = false;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return RMHD_ERR_CUDA; }
@@ -228,6 +291,7 @@ void rmhd_destroy(rmhd_ctx *c) {
     if (c->own_ws) cudaFree(c->ws);
     cudaFreeHost(c->h_status);
     cudaFreeHost(c->h_diag);
+    if (c->h_tab) cudaFreeHost(c->h_tab);
     delete c;
 }
 
@@ -251,7 +315,10 @@ int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     int np = model_np(c->cfg.model);
     int st = stage_in(c, prims, np, where);
     if (st) return st;
-    CK(c, launch_set_prims(c->cfg.model, c->g, c->ph, c->stage_buf, c->Q, c->W, c->status, c->stream));
+    if (c->batch)
+        CK(c, launch_set_prims_batch(c->cfg.model, c->g, c->ph, c->bargs, c->stage_buf, c->Q, c->W, c->status, c->stream));
+    else
+        CK(c, launch_set_prims(c->cfg.model, c->g, c->ph, c->stage_buf, c->Q, c->W, c->status, c->stream));
     st = read_status(c, "set_prims");
     if (st) return st;
     c->has_state = true;
@@ -312,8 +379,46 @@ static int toc(rmhd_ctx *c) {
         if (st_) return st_;            \
     } while (0)
 
+// One SSP2(222) step of a batch: per-run dt, a_ii dt and 1/(1 + a_ii dt kappa)
+// come from the device tables (uploaded by upload_dt_tables).
+static int enqueue_step_batch(rmhd_ctx *c) {
+    const int m = c->cfg.model;
+    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, 0.0};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s1, c->bargs, c->stage_threads, c->stream));
+    FluxArgs f1{c->Q1, c->W1, c->Q, c->R, c->ACC, c->status, 0.0, 1.0 - 2.0 * kGamma};
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux_batch(m, c->cfg.precision, 1, c->g, c->ph, f1, c->bargs, c->tile_x,
+                                              c->flux_blocks, c->stream));
+    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, 0.0};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s2, c->bargs, c->stage_threads, c->stream));
+    FluxArgs f2{c->Q1, c->W1, c->ACC, c->Q, c->W, c->status, 0.0, 0.0};
+    LAUNCH(c, RMHD_K_FLUX2, launch_flux_batch(m, c->cfg.precision, 2, c->g, c->ph, f2, c->bargs, c->tile_x,
+                                              c->flux_blocks, c->stream));
+    return RMHD_OK;
+}
+
+// Per-run time-step tables: dt <= 0 selects each run's own CFL step.
+static int upload_dt_tables(rmhd_ctx *c, double dt) {
+    if (c->tab_dt == dt) return RMHD_OK;
+    const int n = c->nruns;
+    double *h = c->h_tab;
+    for (int r = 0; r < n; ++r) {
+        double d = dt > 0.0 ? dt : c->cfg.cfl * c->run_dx[r];
+        h[r] = d;
+        h[n + r] = kGamma * d;
+        h[2 * n + r] = 1.0 / (1.0 + kGamma * d * c->cfg.kappa);
+    }
+    CK(c, cudaMemcpyAsync(c->d_dt, h, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_adt, h + n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_cpsi, h + 2 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the pinned staging must not be rewritten before these copies run
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->tab_dt = dt;
+    return RMHD_OK;
+}
+
 // Enqueue one SSP2(222) step with time step dt.
 static int enqueue_step(rmhd_ctx *c, double dt) {
+    if (c->batch) return enqueue_step_batch(c);
     const int m = c->cfg.model;
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
@@ -329,6 +434,12 @@ static int enqueue_step(rmhd_ctx *c, double dt) {
 int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
     if (!c || nsteps < 0) return fail(c, RMHD_ERR_INVALID, "imex_step: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "imex_step: no state (call rmhd_set_prims first)");
+    if (c->batch) {
+        if (!(c->cfg.cfl > 0.0) && !(dt > 0.0)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt <= 0 needs cfl > 0");
+        int st = upload_dt_tables(c, dt > 0.0 ? dt : 0.0);
+        if (st) return st;
+        dt = dt > 0.0 ? dt : c->cfg.cfl * c->run_dx[0];  // time of run 0 is reported
+    }
     if (!(dt > 0.0)) dt = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt must be positive (set cfl)");
     if (nsteps == 0) { if (t_out) *t_out = c->t; return RMHD_OK; }
@@ -366,6 +477,226 @@ int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
         c->t += dt;
     }
     if (t_out) *t_out = c->t;
+    return RMHD_OK;
+}
+
+// ---------------------------------------------------------------- batched ensemble
+static int validate_batch(const rmhd_config *base, int nruns, const int *nx, const double *sigma) {
+    if (!base || nruns < 1 || !nx) return RMHD_ERR_INVALID;
+    rmhd_config one = *base;
+    one.ny = 1;
+    long long tot = 0;
+    for (int r = 0; r < nruns; ++r) {
+        if (nx[r] < 1) return RMHD_ERR_INVALID;
+        tot += nx[r];
+        if (sigma && !(sigma[r] > 0.0 && std::isfinite(sigma[r]))) return RMHD_ERR_INVALID;
+    }
+    if (tot > (1LL << 31) - 1) return RMHD_ERR_INVALID;
+    one.nx = (int)std::min<long long>(tot, 1 << 30);
+    return validate(&one);
+}
+
+static long long batch_cells(int nruns, const int *nx) {
+    long long t = 0;
+    for (int r = 0; r < nruns; ++r) t += nx[r];
+    return t;
+}
+
+int rmhd_batch_workspace_bytes(const rmhd_config *base, int nruns, const int *nx, size_t *bytes) {
+    if (!bytes) return RMHD_ERR_INVALID;
+    int v = validate_batch(base, nruns, nx, nullptr);
+    if (v) return v;
+    Grid g = make_grid_n(base, batch_cells(nruns, nx));
+    *bytes = layout_g(base, g, nruns, batch_maxwork(nruns, nx)).total;
+    return RMHD_OK;
+}
+
+// Work list of (run, first cell) tiles of width tile_x.
+static int upload_work(rmhd_ctx *c, int tile_x) {
+    std::vector<int2> w;
+    for (int r = 0; r < c->nruns; ++r)
+        for (int i0 = 0; i0 < c->run_nx[r]; i0 += tile_x) w.push_back(make_int2(r, i0));
+    CK(c, cudaMemcpy(c->d_work, w.data(), w.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    c->nwork = (int)w.size();
+    c->bargs.nwork = c->nwork;
+    c->tile_x = tile_x;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return RMHD_OK;
+}
+
+static int default_blocks(rmhd_ctx *c, int tile_x) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    int occ = flux_batch_occupancy(c->cfg.model, c->cfg.precision, tile_x);
+    return std::max(1, sms * std::max(1, occ));
+}
+
+int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const int *nx, const double *sigma,
+                      void *cuda_stream, void *workspace, size_t workspace_bytes) {
+    if (!out) return RMHD_ERR_INVALID;
+    *out = nullptr;
+    int v = validate_batch(base, nruns, nx, sigma);
+    if (v) return v;
+    rmhd_config cfg = *base;
+    cfg.ny = 1;
+    cfg.nx = 1;  // placeholder; the packed grid is built below
+    rmhd_ctx *c = nullptr;
+    // create a single-run context for the bookkeeping, then re-lay it out as a batch
+    Grid g = make_grid_n(&cfg, batch_cells(nruns, nx));
+    Layout L = layout_g(&cfg, g, nruns, batch_maxwork(nruns, nx));
+    if (workspace && workspace_bytes < L.total) return RMHD_ERR_NOMEM;
+    cfg.nx = 1;
+    int st = rmhd_create(&c, &cfg, cuda_stream, nullptr, 0);
+    if (st) return st;
+    // replace the single-run workspace with the batch one
+    if (c->own_ws) cudaFree(c->ws);
+    if (workspace) {
+        if ((uintptr_t)workspace & 255) { c->own_ws = false; rmhd_destroy(c); return RMHD_ERR_NOMEM; }
+        c->ws = (char *)workspace;
+        c->own_ws = false;
+    } else {
+        if (cudaMalloc(&c->ws, L.total) != cudaSuccess) { c->own_ws = false; rmhd_destroy(c); return RMHD_ERR_NOMEM; }
+        c->own_ws = true;
+    }
+    c->ws_bytes = L.total;
+    c->g = g;
+    c->cfg.nx = (int)g.ncell;  // messages name the packed cell index
+    c->batch = true;
+    c->nruns = nruns;
+    c->Q = (double *)(c->ws + L.Q);
+    c->W = (double *)(c->ws + L.W);
+    c->Q1 = (double *)(c->ws + L.Q1);
+    c->W1 = (double *)(c->ws + L.W1);
+    c->R = (double *)(c->ws + L.R);
+    c->ACC = (double *)(c->ws + L.ACC);
+    c->stage_buf = (double *)(c->ws + L.stage);
+    c->scratch = (double *)(c->ws + L.scratch);
+    c->diag = (double *)(c->ws + L.diag);
+    c->status = (int *)(c->ws + L.status);
+    c->d_nx = (int *)(c->ws + L.nx);
+    c->d_off = (long long *)(c->ws + L.off);
+    c->d_dx = (double *)(c->ws + L.dx);
+    c->d_dt = (double *)(c->ws + L.dt);
+    c->d_sigma = (double *)(c->ws + L.sigma);
+    c->d_eta = (double *)(c->ws + L.eta);
+    c->d_adt = (double *)(c->ws + L.adt);
+    c->d_cpsi = (double *)(c->ws + L.cpsi);
+    c->d_work = (int2 *)(c->ws + L.work);
+    c->d_run_of = (int *)(c->ws + L.run_of);
+    c->Qsave = (double *)(c->ws + L.Qsave);
+    c->Wsave = (double *)(c->ws + L.Wsave);
+    c->run_nx.assign(nx, nx + nruns);
+    c->run_off.resize(nruns);
+    c->run_dx.resize(nruns);
+    c->run_sigma.resize(nruns);
+    std::vector<int> run_of(g.ncell);
+    std::vector<double> eta(nruns);
+    long long o = 0;
+    for (int r = 0; r < nruns; ++r) {
+        c->run_off[r] = o;
+        c->run_dx[r] = (base->xmax - base->xmin) / nx[r];
+        c->run_sigma[r] = sigma ? sigma[r] : base->sigma;
+        eta[r] = 1.0 / c->run_sigma[r];
+        for (int i = 0; i < nx[r]; ++i) run_of[o + i] = r;
+        o += nx[r];
+    }
+    if (cudaMallocHost(&c->h_tab, 3 * (size_t)nruns * sizeof(double)) != cudaSuccess) { rmhd_destroy(c); return RMHD_ERR_NOMEM; }
+    bool ok = cudaMemcpy(c->d_nx, nx, nruns * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_off, c->run_off.data(), nruns * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_dx, c->run_dx.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_sigma, c->run_sigma.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_eta, eta.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_run_of, run_of.data(), g.ncell * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok || reset_status(c)) { rmhd_destroy(c); return RMHD_ERR_CUDA; }
+    BatchArgs &b = c->bargs;
+    b.nruns = nruns;
+    b.work = c->d_work;
+    b.nx = c->d_nx;
+    b.offset = c->d_off;
+    b.dx = c->d_dx;
+    b.dt = c->d_dt;
+    b.sigma = c->d_sigma;
+    b.eta = c->d_eta;
+    b.adt = c->d_adt;
+    b.cpsi = c->d_cpsi;
+    b.run_of = c->d_run_of;
+    if (upload_work(c, 128)) { rmhd_destroy(c); return RMHD_ERR_CUDA; }
+    c->flux_blocks = default_blocks(c, 128);
+    *out = c;
+    return RMHD_OK;
+}
+
+// Time `reps` steps of the current configuration (state restored by the caller).
+static int time_steps(rmhd_ctx *c, int reps, float *ms) {
+    cudaEvent_t a, b;
+    CK(c, cudaEventCreate(&a));
+    CK(c, cudaEventCreate(&b));
+    int st = enqueue_step(c, 0.0);  // warm-up (and per-kernel attribute set-up)
+    if (!st) {
+        cudaEventRecord(a, c->stream);
+        for (int k = 0; k < reps && !st; ++k) st = enqueue_step(c, 0.0);
+        cudaEventRecord(b, c->stream);
+        if (!st) st = cudaEventSynchronize(b) == cudaSuccess ? RMHD_OK : RMHD_ERR_CUDA;
+        if (!st) cudaEventElapsedTime(ms, a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+int rmhd_autotune(rmhd_ctx *c, int *choice) {
+    if (!c || !choice) return fail(c, RMHD_ERR_INVALID, "autotune: bad argument");
+    if (!c->batch) return fail(c, RMHD_ERR_STATE, "autotune: only batched contexts are tuned");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "autotune: no state (call rmhd_set_prims first)");
+    int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    size_t qb = (size_t)nc * c->g.plane * sizeof(double), wb = (size_t)nw * c->g.plane * sizeof(double);
+    CK(c, cudaMemcpyAsync(c->Qsave, c->Q, qb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->Wsave, c->W, wb, cudaMemcpyDeviceToDevice, c->stream));
+    int st = upload_dt_tables(c, c->tab_dt > 0.0 ? c->tab_dt : 0.0);
+    if (st) return st;
+    bool prof = c->profiling;
+    c->profiling = false;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    float best = 1e30f;
+    int bt = 128, bb = default_blocks(c, 128), bs = 128;
+    const int tiles[3] = {64, 128, 256};
+    for (int ti = 0; ti < 3 && !st; ++ti) {
+        int occ = flux_batch_occupancy(c->cfg.model, c->cfg.precision, tiles[ti]);
+        if (occ < 1) continue;
+        st = upload_work(c, tiles[ti]);
+        for (int k = 1; k <= occ && !st; k *= 2) {
+            c->flux_blocks = sms * k;
+            float ms = 0.f;
+            st = time_steps(c, 2, &ms);
+            if (!st && ms < best) { best = ms; bt = tiles[ti]; bb = c->flux_blocks; }
+            CK(c, cudaMemcpyAsync(c->Q, c->Qsave, qb, cudaMemcpyDeviceToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(c->W, c->Wsave, wb, cudaMemcpyDeviceToDevice, c->stream));
+        }
+    }
+    if (!st) st = upload_work(c, bt);
+    c->flux_blocks = bb;
+    const int threads[3] = {64, 128, 256};
+    best = 1e30f;
+    for (int k = 0; k < 3 && !st; ++k) {
+        c->stage_threads = threads[k];
+        float ms = 0.f;
+        st = time_steps(c, 2, &ms);
+        if (!st && ms < best) { best = ms; bs = threads[k]; }
+        CK(c, cudaMemcpyAsync(c->Q, c->Qsave, qb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->W, c->Wsave, wb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    c->stage_threads = bs;
+    c->profiling = prof;
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (st) return st;
+    // the timing steps may have recorded failures of their own; the restored state is what counts
+    st = reset_status(c);
+    if (st) return st;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    choice[0] = c->tile_x;
+    choice[1] = c->flux_blocks;
+    choice[2] = c->stage_threads;
     return RMHD_OK;
 }
 

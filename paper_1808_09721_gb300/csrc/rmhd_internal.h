@@ -52,6 +52,19 @@ struct StageArgs {
     double adt;          // a_ii dt
 };
 
+// Batched ensemble of independent 1-D runs packed one after another in every
+// variable plane (run r occupies cells [offset[r], offset[r] + nx[r])).
+struct BatchArgs {
+    int nruns, nwork;
+    const int2 *work;          // flux tiles: (run, first cell of the tile)
+    const int *nx;             // cells per run
+    const long long *offset;   // first packed cell of each run
+    const double *dx, *dt;     // cell width and time step per run
+    const double *sigma, *eta; // conductivity and 1/sigma per run
+    const double *adt, *cpsi;  // a_ii dt and 1/(1 + a_ii dt kappa) per run
+    const int *run_of;         // run of every packed cell
+};
+
 // launchers (return cudaGetLastError())
 cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s);
 cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
@@ -72,6 +85,17 @@ cudaError_t launch_unpack(const Grid &g, int nvar, const double *dev, double *us
 size_t reduce_scratch_doubles();
 cudaError_t launch_diagnostics(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
                                double *scratch, double *out, cudaStream_t s);
+
+// batched ensemble: stage solve per packed cell; flux tiles of width tile_x
+// (64, 128 or 256) on `blocks` persistent CTAs; Gauss's law within each run
+cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const StageArgs &a, const BatchArgs &b,
+                               int threads, cudaStream_t s);
+cudaError_t launch_flux_batch(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+                              const BatchArgs &b, int tile_x, int blocks, cudaStream_t s);
+cudaError_t launch_set_prims_batch(int model, const Grid &g, const Phys &ph, const BatchArgs &b, const double *prims,
+                                   double *q, double *w, int *status, cudaStream_t s);
+// resident CTAs per SM of the batch flux kernel for a tile width (0 if unsupported)
+int flux_batch_occupancy(int model, int precision, int tile_x);
 
 inline int model_nc(int model) { return model == 0 ? 14 : 18; }
 inline int model_nw(int model) { return model == 0 ? 5 : 10; }

@@ -43,6 +43,12 @@ class Sim:
                                          C.c_void_p(self.workspace.data_ptr()), nbytes.value), None)
 
     @classmethod
+    def batch(cls, workloads, precision: int = L.FP64, device=None):
+        """One context for many independent 1-D runs (same model, x-range,
+        Gamma, boundaries; own size and sigma), packed along x."""
+        return BatchSim(workloads, precision, device)
+
+    @classmethod
     def from_workload(cls, wl, precision: int = L.FP64, device=None):
         s = cls(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl,
                 wl.mu_e, wl.mu_p, wl.kappa, precision, device)
@@ -132,3 +138,48 @@ class Sim:
         self._check(self.lib.rmhd_diagnostics(self.h, out), "diagnostics")
         keys = ("sum_D", "sum_tau", "sum_Sx", "sum_Bx", "sum_charge", "max_v", "nonfinite", "dt_cfl")
         return dict(zip(keys, list(out)))
+
+
+class BatchSim(Sim):
+    """Batched ensemble of 1-D runs in one context (rmhd_create_batch)."""
+
+    def __init__(self, workloads, precision: int = L.FP64, device=None):
+        torch = _torch()
+        self.lib = L.load()
+        w0 = workloads[0]
+        for w in workloads:
+            assert w.ny == 1 and w.model == w0.model and w.gamma == w0.gamma and w.xlim == w0.xlim
+            assert (w.bc_x, w.cfl, w.kappa, w.mu_e, w.mu_p) == (w0.bc_x, w0.cfl, w0.kappa, w0.mu_e, w0.mu_p)
+        self.device = torch.device("cuda" if device is None else device)
+        self.runs = list(workloads)
+        self.run_nx = np.array([w.nx for w in workloads], dtype=np.int32)
+        self.offsets = np.concatenate([[0], np.cumsum(self.run_nx)])
+        self.model, self.nx, self.ny = w0.model, int(self.run_nx.sum()), 1
+        self.cfg = L.Config(w0.model, 1, 1, w0.xlim[0], w0.xlim[1], 0.0, 1.0, w0.gamma, w0.sigma, w0.mu_e, w0.mu_p,
+                            w0.kappa, w0.cfl, w0.bc_x, w0.bc_y, precision)
+        nx_c = (C.c_int * len(workloads))(*self.run_nx.tolist())
+        sig_c = (C.c_double * len(workloads))(*[w.sigma for w in workloads])
+        nbytes = C.c_size_t()
+        self.h = C.c_void_p()
+        self._check(self.lib.rmhd_batch_workspace_bytes(C.byref(self.cfg), len(workloads), nx_c, C.byref(nbytes)), None)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.Stream(self.device)
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._check(self.lib.rmhd_create_batch(C.byref(self.h), C.byref(self.cfg), len(workloads), nx_c, sig_c,
+                                               C.c_void_p(self.stream.cuda_stream),
+                                               C.c_void_p(self.workspace.data_ptr()), nbytes.value), None)
+        self.set_prims(self.pack([w.prims for w in workloads]))
+
+    def pack(self, arrays):
+        """Concatenate per-run [n_var][1][nx_r] arrays along x."""
+        return np.ascontiguousarray(np.concatenate([a.reshape(a.shape[0], 1, -1) for a in arrays], axis=2))
+
+    def unpack(self, packed):
+        """Split a packed [n_var][1][sum nx] array into per-run arrays."""
+        return [packed[:, :, self.offsets[r]:self.offsets[r + 1]] for r in range(len(self.runs))]
+
+    def autotune(self):
+        ch = (C.c_int * 3)()
+        self._check(self.lib.rmhd_autotune(self.h, ch), "autotune")
+        return {"tile_x": ch[0], "flux_ctas": ch[1], "stage_threads": ch[2]}

@@ -65,3 +65,15 @@ def test_null_arguments_are_rejected(lib):
     assert not h.value
     assert lib.rmhd_last_error(None) == b"null context"
     lib.rmhd_destroy(None)
+
+
+def test_batch_workspace_bytes(lib):
+    nx = (C.c_int * 3)(100, 4096, 7)
+    n = C.c_size_t()
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 3, nx, C.byref(n)) == 0
+    total = 100 + 4096 + 7
+    plane = (total + 63) // 64 * 64 * 8
+    assert n.value >= (4 * 14 + 2 * 5) * plane + total * 4 and n.value % 256 == 0
+    bad = (C.c_int * 2)(10, 0)
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 2, bad, C.byref(n)) == -1
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 0, nx, C.byref(n)) == -1
