@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--n", type=int, default=1024, help="grid side (default: the 1024^2 workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-ensemble workload")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint-cost workload")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -301,6 +302,47 @@ def main():
                              "Gamma=4/3, own CFL dt, one CUDA graph per step"}
         del bsim
 
+    # discrete adjoint: field loop 256^2, 50 FP64 steps, checkpoints every 10;
+    # gradient of sum (B_x^2 + B_y^2 + 2 B_z^2) dV w.r.t. initial prims and sigma
+    adjoint = None
+    if args.adjoint:
+        fl = WL.field_loop(n=256, seed=3, nsteps=50)
+        fs = Sim.from_workload(fl, device=f"cuda:{local}")
+        fs.step(fl.dt, 3)
+        fs.set_prims(fl.prims)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs.step(fl.dt, 50)
+        fs.check()
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        fs.set_prims(fl.prims)
+        fs.record(50, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs.step(fl.dt, 50)
+        fs.check()
+        torch.cuda.synchronize()
+        t_rec = time.perf_counter() - t0
+        qN = fs.cons()
+        dv = fl.dx * fl.dy
+        lam = np.zeros_like(qN)
+        lam[5] = 2.0 * qN[5] * dv
+        lam[6] = 2.0 * qN[6] * dv
+        lam[7] = 4.0 * qN[7] * dv
+        fs.adjoint(lam)  # warm-up (kernel set-up)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gp, gsig = fs.adjoint(lam)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        adjoint = {"fwd_s": t_fwd, "recorded_fwd_s": t_rec, "adjoint_s": t_adj,
+                   "adjoint_over_fwd": t_adj / t_fwd, "total_over_fwd": (t_rec + t_adj) / t_fwd,
+                   "dJ_dsigma": gsig, "sigma": fl.sigma,
+                   "workload": "field loop 256x256 periodic, 50 SSP2(222) steps FP64, checkpoints every 10, "
+                               "J = sum(Bx^2 + By^2 + 2 Bz^2) dV"}
+        del fs
+
     # e2e through the C ABI with host buffers: upload prims, one step, read prims back
     pin = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)
     pin[...] = wl.prims
@@ -357,6 +399,7 @@ def main():
                                       "achieved_gbs": step_bytes * value / world / 1e9,
                                       "frac": step_bytes * value / world / 1e9 / hbm_gbs},
                 "batch": batch,
+                "adjoint": adjoint,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                         "d2h_bytes_per_step": io_bytes},
                 "gpu_launches": 4 * K,

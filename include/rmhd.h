@@ -128,6 +128,31 @@ int rmhd_check(rmhd_ctx *ctx);
  * and the CFL time step cfl * min(dx, dy). Synchronous. */
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
+/* Discrete adjoint of the SSP2(222) step (single fluid, FP64, single grid with
+ * at least 3 cells per direction): gradients of a functional of the final
+ * conserved state with respect to the initial primitives and sigma.
+ *   rmhd_record arms recording of the next `nsteps` steps; it must follow
+ *   rmhd_set_prims directly (the gradient is w.r.t. those primitives, with
+ *   varrho = div E and psi = phi = 0 as rmhd_set_prims builds them). While
+ *   armed, rmhd_imex_step stores a checkpoint every `ckpt_every` steps and
+ *   all recorded steps must use one dt. `workspace` (device, 256-byte
+ *   aligned, >= rmhd_recording_bytes) may be NULL: the library allocates.
+ *   rmhd_adjoint_step reverses every recorded step: from dJ/dq at the final
+ *   state ([14][ny][nx]) it writes dJ/d(prims) ([11][ny][nx], may be NULL) and
+ *   dJ/dsigma (may be NULL). Each segment of ckpt_every steps is recomputed from its
+ *   checkpoint (same kernels, same results), the implicit stage solves and
+ *   the primitive recovery are differentiated by the implicit-function
+ *   theorem, and the WENO3/LF flux divergence is transposed face by face.
+ *   The final state is restored afterwards; the recording stays valid for
+ *   further adjoint calls. Synchronous.
+ * (The paper has no adjoint; this serves gradient-based use of the method.)
+ * Errors: RMHD_ERR_STATE (unsupported context, not armed, too many steps),
+ * RMHD_ERR_INVALID, RMHD_ERR_NOMEM, RMHD_ERR_CUDA. */
+int rmhd_recording_bytes(rmhd_ctx *ctx, int nsteps, int ckpt_every, size_t *bytes);
+int rmhd_record(rmhd_ctx *ctx, int nsteps, int ckpt_every, void *workspace, size_t workspace_bytes);
+int rmhd_adjoint_step(rmhd_ctx *ctx, const double *dJ_dcons, int where_in, double *dJ_dprims0, int where_out,
+                      double *dJ_dsigma);
+
 /* Batched ensemble of independent 1-D runs (many tests of Sec. 4.1 at once).
  * All runs share `base` (model, x-range, Gamma, kappa, cfl, boundary
  * conditions, precision; base->ny is ignored and taken as 1); run r has

@@ -23,7 +23,8 @@ HOST, DEVICE = 0, 1
 # every symbol include/rmhd.h declares
 EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_error", "rmhd_set_prims",
            "rmhd_get_prims", "rmhd_get_cons", "rmhd_set_cons", "rmhd_imex_step", "rmhd_check",
-           "rmhd_diagnostics", "rmhd_batch_workspace_bytes", "rmhd_create_batch", "rmhd_autotune",
+           "rmhd_diagnostics", "rmhd_recording_bytes", "rmhd_record", "rmhd_adjoint_step",
+           "rmhd_batch_workspace_bytes", "rmhd_create_batch", "rmhd_autotune",
            "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc", "rmhd_version")
 
 
@@ -70,6 +71,9 @@ def load(path: str | None = None):
     L.rmhd_check.argtypes = [_P]
     L.rmhd_diagnostics.argtypes = [_P, _D]
     _I = C.POINTER(C.c_int)
+    L.rmhd_recording_bytes.argtypes = [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+    L.rmhd_record.argtypes = [_P, C.c_int, C.c_int, _P, C.c_size_t]
+    L.rmhd_adjoint_step.argtypes = [_P, _P, C.c_int, _P, C.c_int, _D]
     L.rmhd_batch_workspace_bytes.argtypes = [C.POINTER(Config), C.c_int, _I, C.POINTER(C.c_size_t)]
     L.rmhd_create_batch.argtypes = [C.POINTER(_P), C.POINTER(Config), C.c_int, _I, _D, _P, _P, C.c_size_t]
     L.rmhd_autotune.argtypes = [_P, _I]

@@ -1,0 +1,311 @@
+// kernels_adjoint.cu -- discrete adjoint of the SSP2(222) IMEX step (single
+// fluid, FP64) of Wright & Hawke, arXiv:1808.09721 (Sec. 2.2.1, Table 1;
+// Sec. 2.2.2 fluxes; Sec. 2.1.1 model).
+//
+// Reverse of one step, with lambda the adjoint of q^{n+1}, (q_i, w_i) the
+// stored stage states and g = 1 - 1/sqrt(2):
+//   lambda_q2 = (dL/dq)^T (dt/2 lambda) + (dPsi/dq)^T (dt/2 lambda)    at q2
+//   lambda_r2 = (I - g dt dPsi/dq)^{-T} lambda_q2                       at q2
+//   lambda_q1 = (dL/dq)^T (dt lambda_r2 + dt/2 lambda)
+//             + (dPsi/dq)^T ((1 - 2g) dt lambda_r2 + dt/2 lambda)       at q1
+//   lambda^n  = (I - g dt dPsi/dq)^{-T} lambda_q1 + lambda_r2 + lambda  at q1
+// The stage solves are differentiated by the implicit-function theorem, the
+// primitive recovery inside every map likewise (adjoint_sf.cuh). The flux
+// divergence is transposed face by face: each face's WENO3/LF value depends on
+// four stencil cells (mapped through the boundary conditions); its reverse
+// scatters into their flux- and state-adjoints with FP64 atomics.
+//
+// Intermediates live in global memory (one plane per variable): the sweep is
+// bound by FP64 arithmetic, not by HBM, so simple per-cell and per-face
+// kernels are used instead of a fused tile.
+#include "rmhd_internal.h"
+#include "adjoint_sf.cuh"
+
+namespace rmhd {
+
+namespace {
+
+__device__ __forceinline__ int amap(int i, int n, int bc) {
+    if (bc == 1) {
+        i %= n;
+        return i < 0 ? i + n : i;
+    }
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Physical fluxes f_x, f_y (14 each) of every cell of a stage state.
+__global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, double *fx, double *fy) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double qc[sf::NC], wc[sf::NW], J[3], f[sf::NC];
+        for (int v = 0; v < sf::NC; ++v) qc[v] = q[v * g.plane + c];
+        for (int v = 0; v < sf::NW; ++v) wc[v] = w[v * g.plane + c];
+        sf::current(qc, wc, ph.sigma, J);
+        sf::flux(qc, wc, J, 0, f);
+        for (int v = 0; v < sf::NC; ++v) fx[v * g.plane + c] = f[v];
+        if (g.ny > 1) {
+            sf::flux(qc, wc, J, 1, f);
+            for (int v = 0; v < sf::NC; ++v) fy[v * g.plane + c] = f[v];
+        }
+    }
+}
+
+// Reverse of the face values along `dir`. One thread per (face, component):
+// faces k = -1 .. n-1 along dir (the face after cell k) for every line.
+// lambda_L of a cell = aL * LA + bL * LB (LB may be null).
+__global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, const double *LA, double aL,
+                           const double *LB, double bL, double *fbar, double *qbar) {
+    const int n = dir == 0 ? g.nx : g.ny, m = dir == 0 ? g.ny : g.nx, bc = dir == 0 ? g.bcx : g.bcy;
+    const double h4 = 0.25 / (dir == 0 ? g.dx : g.dy);
+    const long long nf = (long long)(n + 1) * m * sf::NC;
+    const double eps4 = 4e-6;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t % sf::NC);
+        const long long r = t / sf::NC;
+        const int k = (int)(r % (n + 1)) - 1;  // face after cell k
+        const int line = (int)(r / (n + 1));
+        auto cell = [&](int i) -> long long {
+            int im = amap(i, n, bc);
+            return dir == 0 ? (long long)line * g.nx + im : (long long)im * g.nx + line;
+        };
+        auto lamL = [&](long long cc) -> double {
+            double l = aL * LA[c * g.plane + cc];
+            if (LB) l += bL * LB[c * g.plane + cc];
+            return l;
+        };
+        // 4F at this face enters L of cell k (- 1/(4h)) and of cell k+1 (+ 1/(4h)), real cells only
+        double Fb = 0.0;
+        if (k >= 0) Fb -= h4 * lamL(cell(k));
+        if (k + 1 < n) Fb += h4 * lamL(cell(k + 1));
+        if (Fb == 0.0) continue;
+        long long cs[4];
+        double fs[4], qs[4];
+        for (int s = 0; s < 4; ++s) {
+            cs[s] = cell(k - 1 + s);
+            fs[s] = f[c * g.plane + cs[s]];
+            qs[s] = q[c * g.plane + cs[s]];
+        }
+        // half points j = 0, 1, 2 between stencil cells (j, j+1)
+        double ep[3], em[3], Ap[3], Am[3], sp[3], sm[3];
+        for (int j = 0; j < 3; ++j) {
+            double df = fs[j + 1] - fs[j], dq = qs[j + 1] - qs[j];
+            ep[j] = df + dq;
+            em[j] = df - dq;
+            sp[j] = eps4 + ep[j] * ep[j];
+            sm[j] = eps4 + em[j] * em[j];
+            Ap[j] = sp[j] * sp[j];
+            Am[j] = sm[j] * sm[j];
+        }
+        const double denp = Ap[1] + 2.0 * Ap[0], denm = Am[1] + 2.0 * Am[2];
+        const double rdp = s_rcp(denp), rdm = s_rcp(denm);
+        const double wp = Ap[1] * rdp, wm = Am[1] * rdm;
+        const double Xp = ep[0] - ep[1], Xm = em[1] - em[2];
+        // reverse
+        double fb[4] = {0, 2.0 * Fb, 2.0 * Fb, 0}, qb[4] = {0, 0, 0, 0};
+        double epb[3] = {0, 0, 0}, emb[3] = {0, 0, 0}, Apb[3] = {0, 0, 0}, Amb[3] = {0, 0, 0};
+        const double wpb = Fb * Xp, Xpb = Fb * wp, wmb = Fb * Xm, Xmb = Fb * wm;
+        epb[0] += Xpb;
+        epb[1] -= Xpb;
+        emb[1] += Xmb;
+        emb[2] -= Xmb;
+        Apb[1] += wpb * 2.0 * Ap[0] * rdp * rdp;
+        Apb[0] -= wpb * 2.0 * Ap[1] * rdp * rdp;
+        Amb[1] += wmb * 2.0 * Am[2] * rdm * rdm;
+        Amb[2] -= wmb * 2.0 * Am[1] * rdm * rdm;
+        for (int j = 0; j < 3; ++j) {
+            epb[j] += Apb[j] * 4.0 * ep[j] * sp[j];
+            emb[j] += Amb[j] * 4.0 * em[j] * sm[j];
+            const double dfb = epb[j] + emb[j], dqb = epb[j] - emb[j];
+            fb[j + 1] += dfb;
+            fb[j] -= dfb;
+            qb[j + 1] += dqb;
+            qb[j] -= dqb;
+        }
+        for (int s = 0; s < 4; ++s) {
+            atomicAdd(&fbar[c * g.plane + cs[s]], fb[s]);
+            atomicAdd(&qbar[c * g.plane + cs[s]], qb[s]);
+        }
+    }
+}
+
+// Per cell: lambda_q = qbar (direct, from the splitting) + cell_vjp(fbar_x, fbar_y, sbar),
+// sbar = aP * LA[src] + bP * LB[src]. Adds the sigma adjoint into sig[cell].
+__global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, const double *fbx, const double *fby,
+                           const double *qbd, const double *LA, double aP, const double *LB, double bP,
+                           double *lamq, double *sig) {
+    const int src[5] = {sf::EX, sf::EY, sf::EZ, sf::PSI, sf::PHI};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double qc[sf::NC], qb[sf::NC], fb[2][sf::NC], sb[5];
+        for (int v = 0; v < sf::NC; ++v) {
+            qc[v] = q[v * g.plane + c];
+            qb[v] = qbd[v * g.plane + c];
+            fb[0][v] = fbx[v * g.plane + c];
+            fb[1][v] = g.ny > 1 ? fby[v * g.plane + c] : 0.0;
+        }
+        for (int k = 0; k < 5; ++k) {
+            double s = aP * LA[src[k] * g.plane + c];
+            if (LB) s += bP * LB[src[k] * g.plane + c];
+            sb[k] = s;
+        }
+        double sigb = 0.0;
+        sf::cell_vjp(qc, w[sf::P * g.plane + c], ph.gamma, ph.sigma, ph.kappa, g.ny > 1 ? 2 : 1, fb, sb, qb, &sigb);
+        for (int v = 0; v < sf::NC; ++v) lamq[v * g.plane + c] = qb[v];
+        sig[c] += sigb;
+    }
+}
+
+// Implicit-stage adjoint at the stage state q: mu = (I - adt dPsi/dq)^{-T} lambda.
+// Psi has nonzero rows only for (E, psi, phi): the E block (3x3) is solved
+// exactly, psi and phi scale by 1/(1 + adt kappa), the other components are
+// mu_n = lambda_n + adt [(dPsi/dq)^T mu_src]_n. out = mu (+ P1 + P2 if given).
+__global__ void k_stage_adj(Grid g, Phys ph, double adt, const double *q, const double *w, const double *lam,
+                            const double *P1, const double *P2, double *out, double *sig) {
+    const double nofb[2][sf::NC] = {};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double qc[sf::NC], la[sf::NC];
+        for (int v = 0; v < sf::NC; ++v) {
+            qc[v] = q[v * g.plane + c];
+            la[v] = lam[v * g.plane + c];
+        }
+        const double p = w[sf::P * g.plane + c];
+        // rows of dPsi_E/dE by three reverse products
+        double A[3][3];
+        for (int i = 0; i < 3; ++i) {
+            double sb[5] = {0, 0, 0, 0, 0}, qb[sf::NC] = {}, sgd = 0.0;
+            sb[i] = 1.0;
+            sf::cell_vjp(qc, p, ph.gamma, ph.sigma, ph.kappa, 0, nofb, sb, qb, &sgd);
+            for (int j = 0; j < 3; ++j) A[i][j] = qb[sf::EX + j];
+        }
+        // (I - adt A)^T mu_E = lambda_E  ->  M mu = lambda_E with M_ji = delta_ji - adt A_ij
+        double M[9];
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) M[3 * j + i] = (i == j ? 1.0 : 0.0) - adt * A[i][j];
+        const double c0 = M[4] * M[8] - M[5] * M[7], c1 = M[5] * M[6] - M[3] * M[8], c2 = M[3] * M[7] - M[4] * M[6];
+        const double det = M[0] * c0 + M[1] * c1 + M[2] * c2, id = 1.0 / det;
+        const double b0 = la[sf::EX], b1 = la[sf::EY], b2 = la[sf::EZ];
+        double mu[5];
+        mu[0] = (b0 * c0 + b1 * (M[2] * M[7] - M[1] * M[8]) + b2 * (M[1] * M[5] - M[2] * M[4])) * id;
+        mu[1] = (b0 * c1 + b1 * (M[0] * M[8] - M[2] * M[6]) + b2 * (M[2] * M[3] - M[0] * M[5])) * id;
+        mu[2] = (b0 * c2 + b1 * (M[1] * M[6] - M[0] * M[7]) + b2 * (M[0] * M[4] - M[1] * M[3])) * id;
+        const double ck = 1.0 / (1.0 + adt * ph.kappa);
+        mu[3] = la[sf::PSI] * ck;
+        mu[4] = la[sf::PHI] * ck;
+        double qb[sf::NC] = {}, sgb = 0.0;
+        sf::cell_vjp(qc, p, ph.gamma, ph.sigma, ph.kappa, 0, nofb, mu, qb, &sgb);
+        double o[sf::NC];
+        for (int v = 0; v < sf::NC; ++v) o[v] = la[v] + adt * qb[v];
+        o[sf::EX] = mu[0];
+        o[sf::EY] = mu[1];
+        o[sf::EZ] = mu[2];
+        o[sf::PSI] = mu[3];
+        o[sf::PHI] = mu[4];
+        for (int v = 0; v < sf::NC; ++v) {
+            double x = o[v];
+            if (P1) x += P1[v * g.plane + c];
+            if (P2) x += P2[v * g.plane + c];
+            out[v * g.plane + c] = x;
+        }
+        sig[c] += adt * sgb;
+    }
+}
+
+// Adjoint of the initial map (user primitives -> conserved state, Gauss's
+// law varrho = div E by central differences with the boundary map; psi = phi
+// = 0 are constants). pbar: 11 planes, E planes accumulated atomically.
+__global__ void k_prims_adj(Grid g, Phys ph, const double *q, const double *w, const double *lam, double *pbar) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        double qb[sf::NC], prim[11], pb[11];
+        for (int v = 0; v < sf::NC; ++v) qb[v] = lam[v * g.plane + c];
+        const double W = w[sf::LOR * g.plane + c];
+        prim[0] = q[sf::D * g.plane + c] / W;
+        for (int i = 0; i < 3; ++i) prim[1 + i] = w[(sf::VX + i) * g.plane + c];
+        prim[4] = w[sf::P * g.plane + c];
+        for (int i = 0; i < 6; ++i) prim[5 + i] = q[(sf::BX + i) * g.plane + c];
+        sf::p2c_vjp(prim, ph.gamma, qb, pb);
+        for (int k = 0; k < 11; ++k) atomicAdd(&pbar[k * g.plane + c], pb[k]);
+        // varrho_c = (E_x[i+1] - E_x[i-1]) / (2 dx) + (E_y[j+1] - E_y[j-1]) / (2 dy)
+        const double lr = qb[sf::RHOE];
+        const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
+        const double hx = lr / (2.0 * g.dx);
+        atomicAdd(&pbar[8 * g.plane + (long long)j * g.nx + amap(i + 1, g.nx, g.bcx)], hx);
+        atomicAdd(&pbar[8 * g.plane + (long long)j * g.nx + amap(i - 1, g.nx, g.bcx)], -hx);
+        if (g.ny > 1) {
+            const double hy = lr / (2.0 * g.dy);
+            atomicAdd(&pbar[9 * g.plane + (long long)amap(j + 1, g.ny, g.bcy) * g.nx + i], hy);
+            atomicAdd(&pbar[9 * g.plane + (long long)amap(j - 1, g.ny, g.bcy) * g.nx + i], -hy);
+        }
+    }
+}
+
+// Deterministic single-block sum of a plane.
+__global__ void k_sum(const double *x, long long n, double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+int blocks_for(long long n, int t) {
+    long long b = (n + t - 1) / t;
+    return (int)(b < 1 ? 1 : (b > (1 << 20) ? (1 << 20) : b));
+}
+
+} // namespace
+
+// One reverse step; see the file comment. Buffers: lam (in), out (lambda^n),
+// S1q/S1w, S2q/S2w the stage states, scratch planes fx, fy, fbx, fby, qbd, lq, lr2,
+// sig (per-cell sigma adjoint, accumulated).
+cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, double dt, const double *lam, double *out,
+                                const double *S1q, const double *S1w, const double *S2q, const double *S2w,
+                                double *fx, double *fy, double *fbx, double *fby, double *qbd, double *lq,
+                                double *lr2, double *sig, cudaStream_t s) {
+    const double gam = 1.0 - 0.70710678118654752440;
+    const size_t pb = (size_t)g.plane * sf::NC * sizeof(double);
+    const int T = 256;
+    const int cb = blocks_for(g.ncell, T);
+    const int ndir = g.ny > 1 ? 2 : 1;
+    for (int stage = 2; stage >= 1; --stage) {
+        const double *q = stage == 2 ? S2q : S1q, *w = stage == 2 ? S2w : S1w;
+        cudaMemsetAsync(fbx, 0, pb, s);
+        if (ndir > 1) cudaMemsetAsync(fby, 0, pb, s);
+        cudaMemsetAsync(qbd, 0, pb, s);
+        k_cellflux<<<cb, T, 0, s>>>(g, ph, q, w, fx, fy);
+        // lambda_L and Psi-bar: stage 2 -> dt/2 lam ; stage 1 -> dt lr2 + dt/2 lam, (1-2g) dt lr2 + dt/2 lam
+        const double *LA = stage == 2 ? lam : lr2, *LB = stage == 2 ? nullptr : lam;
+        const double aL = stage == 2 ? 0.5 * dt : dt, bL = 0.5 * dt;
+        const double aP = stage == 2 ? 0.5 * dt : (1.0 - 2.0 * gam) * dt, bP = 0.5 * dt;
+        for (int d = 0; d < ndir; ++d) {
+            long long nf = (long long)((d == 0 ? g.nx : g.ny) + 1) * (d == 0 ? g.ny : g.nx) * sf::NC;
+            k_face_adj<<<blocks_for(nf, T), T, 0, s>>>(g, d, q, d == 0 ? fx : fy, LA, aL, LB, bL, d == 0 ? fbx : fby, qbd);
+        }
+        k_cell_adj<<<cb, T, 0, s>>>(g, ph, q, w, fbx, fby, qbd, LA, aP, LB, bP, lq, sig);
+        if (stage == 2)
+            k_stage_adj<<<cb, T, 0, s>>>(g, ph, gam * dt, q, w, lq, nullptr, nullptr, lr2, sig);
+        else
+            k_stage_adj<<<cb, T, 0, s>>>(g, ph, gam * dt, q, w, lq, lr2, lam, out, sig);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_prims(const Grid &g, const Phys &ph, const double *q, const double *w, const double *lam,
+                                 double *pbar, cudaStream_t s) {
+    cudaMemsetAsync(pbar, 0, (size_t)g.plane * 11 * sizeof(double), s);
+    k_prims_adj<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, ph, q, w, lam, pbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double *x, long long n, double *out, cudaStream_t s) {
+    k_sum<<<1, 256, 0, s>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+} // namespace rmhd

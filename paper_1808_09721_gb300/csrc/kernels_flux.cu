@@ -14,7 +14,7 @@
 // i.e. the central part plus the two nonlinear corrections of the left- and
 // right-going reconstructions. Half-point quantities are computed once and
 // shared by the two faces that use them; the only division per face and
-// sign is one FP64 reciprocal (rcp.approx + one Newton step).
+// sign is one reciprocal (FP64: rcp.approx refined to round-off).
 //
 // Tiling: one CTA per TX x TY tile, one thread per interior cell. The tile and
 // a 2-cell halo of the state are staged in shared memory; boundary conditions
@@ -279,8 +279,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                     int idx = (fy0 + fy) * SW + fx0 + fx;
                     int il = idx - sstep, ir = idx + sstep;
                     FT Ap = hpg[2 * SN + idx], Am = hpg[3 * SN + idx];
-                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpg[2 * SN + il], Ap));
-                    FT wm = Am * s_rcp1(s_fma(FT(2), hpg[3 * SN + ir], Am));
+                    FT wp = Ap * s_rcp(s_fma(FT(2), hpg[2 * SN + il], Ap));
+                    FT wm = Am * s_rcp(s_fma(FT(2), hpg[3 * SN + ir], Am));
                     FT Xp = hpg[il] - hpg[idx];
                     FT Xm = hpg[SN + idx] - hpg[SN + ir];
                     fcg[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));

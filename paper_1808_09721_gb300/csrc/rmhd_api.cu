@@ -42,6 +42,7 @@ struct rmhd_ctx {
     int *h_status;     // pinned host [2]
     double *h_diag;    // pinned host [8]
     bool has_state;
+    bool fresh_prims;  // state set by rmhd_set_prims and not stepped since
     double t;
     cudaGraphExec_t graph;
     double graph_dt;
@@ -61,6 +62,14 @@ struct rmhd_ctx {
     double *Qsave, *Wsave;
     int tile_x, flux_blocks, stage_threads;
     double tab_dt;       // dt the tables were built for (<= 0: per-run CFL)
+    // recording for the discrete adjoint
+    bool recording;
+    int rec_nsteps, rec_K, rec_done;
+    double rec_dt;
+    char *rec_ws;
+    bool rec_own;
+    double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_fx, *rec_fy, *rec_fbx, *rec_fby,
+        *rec_qbd, *rec_sig, *rec_pbar, *rec_fin, *rec_sum;
     struct Timed { int kind; cudaEvent_t a, b; };
     std::vector<Timed> timed;
     std::string err;
@@ -249,8 +258,14 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->flux_blocks = 0;
     c->stage_threads = 128;
     c->tab_dt = -1.0;
+    c->recording = false;
+    c->rec_ws = nullptr;
+    c->rec_own = false;
+    c->rec_nsteps = c->rec_K = c->rec_done = 0;
+    c->rec_dt = 0.0;
     c->t = 0.0;
     c->has_state = false;
+    c->fresh_prims = false;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return RMHD_ERR_CUDA; }
     Layout L = layout(cfg);
     if (workspace) {
@@ -292,6 +307,7 @@ void rmhd_destroy(rmhd_ctx *c) {
     cudaFreeHost(c->h_status);
     cudaFreeHost(c->h_diag);
     if (c->h_tab) cudaFreeHost(c->h_tab);
+    if (c->rec_own && c->rec_ws) cudaFree(c->rec_ws);
     delete c;
 }
 
@@ -323,6 +339,9 @@ int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     if (st) return st;
     c->has_state = true;
     c->t = 0.0;
+    c->recording = false;
+    c->rec_done = 0;
+    c->fresh_prims = true;
     return RMHD_OK;
 }
 
@@ -443,6 +462,30 @@ int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
     if (!(dt > 0.0)) dt = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt must be positive (set cfl)");
     if (nsteps == 0) { if (t_out) *t_out = c->t; return RMHD_OK; }
+    if (c->recording) {
+        if (c->rec_done + nsteps > c->rec_nsteps)
+            return fail(c, RMHD_ERR_STATE, "imex_step: more steps than the armed recording holds (%d)", c->rec_nsteps);
+        if (c->rec_done > 0 && dt != c->rec_dt)
+            return fail(c, RMHD_ERR_INVALID, "imex_step: a recorded run needs one dt (%g, got %g)", c->rec_dt, dt);
+        c->rec_dt = dt;
+        const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+        const size_t pl = (size_t)c->g.plane * sizeof(double);
+        for (int n = 0; n < nsteps; ++n) {
+            if (c->rec_done % c->rec_K == 0) {
+                double *ck = c->rec_ck + (size_t)(c->rec_done / c->rec_K) * (nc + nw) * c->g.plane;
+                CK(c, cudaMemcpyAsync(ck, c->Q, nc * pl, cudaMemcpyDeviceToDevice, c->stream));
+                CK(c, cudaMemcpyAsync(ck + (size_t)nc * c->g.plane, c->W, nw * pl, cudaMemcpyDeviceToDevice, c->stream));
+            }
+            int st = enqueue_step(c, dt);
+            if (st) return st;
+            c->rec_done += 1;
+            c->t += dt;
+        }
+        c->fresh_prims = false;
+        if (t_out) *t_out = c->t;
+        return RMHD_OK;
+    }
+    c->fresh_prims = false;
     // Legacy default stream (no graph capture there) or profiling: launch directly.
     if (c->profiling || c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread) {
         for (int n = 0; n < nsteps; ++n) {
@@ -697,6 +740,164 @@ int rmhd_autotune(rmhd_ctx *c, int *choice) {
     choice[0] = c->tile_x;
     choice[1] = c->flux_blocks;
     choice[2] = c->stage_threads;
+    return RMHD_OK;
+}
+
+// ---------------------------------------------------------------- discrete adjoint
+struct RecLayout {
+    size_t ck, seg, lam, lamn, lq, lr2, fx, fy, fbx, fby, qbd, sig, pbar, fin, sum, total;
+};
+
+static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
+    const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    const size_t pl = (size_t)c->g.plane * sizeof(double);
+    const int nck = (nsteps + K - 1) / K;
+    RecLayout L;
+    size_t o = 0;
+    L.ck = o; o += align256((size_t)nck * (nc + nw) * pl);
+    L.seg = o; o += align256((size_t)K * 2 * (nc + nw) * pl);
+    L.lam = o; o += align256(nc * pl);
+    L.lamn = o; o += align256(nc * pl);
+    L.lq = o; o += align256(nc * pl);
+    L.lr2 = o; o += align256(nc * pl);
+    L.fx = o; o += align256(nc * pl);
+    L.fy = o; o += align256(nc * pl);
+    L.fbx = o; o += align256(nc * pl);
+    L.fby = o; o += align256(nc * pl);
+    L.qbd = o; o += align256(nc * pl);
+    L.sig = o; o += align256(pl);
+    L.pbar = o; o += align256(11 * pl);
+    L.fin = o; o += align256((size_t)(nc + nw) * pl);
+    L.sum = o; o += align256(sizeof(double));
+    L.total = o;
+    return L;
+}
+
+static int adjoint_supported(rmhd_ctx *c) {
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch)
+        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 single-grid contexts only");
+    if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3))
+        return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
+    return RMHD_OK;
+}
+
+int rmhd_recording_bytes(rmhd_ctx *c, int nsteps, int ckpt_every, size_t *bytes) {
+    if (!c || !bytes || nsteps < 1 || ckpt_every < 1) return fail(c, RMHD_ERR_INVALID, "recording_bytes: bad argument");
+    int st = adjoint_supported(c);
+    if (st) return st;
+    *bytes = rec_layout(c, nsteps, ckpt_every).total;
+    return RMHD_OK;
+}
+
+int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t bytes) {
+    if (!c || nsteps < 1 || ckpt_every < 1) return fail(c, RMHD_ERR_INVALID, "record: bad argument");
+    int st = adjoint_supported(c);
+    if (st) return st;
+    if (!c->has_state || !c->fresh_prims)
+        return fail(c, RMHD_ERR_STATE, "record: arm right after rmhd_set_prims (the gradient is w.r.t. those primitives)");
+    RecLayout L = rec_layout(c, nsteps, ckpt_every);
+    if (c->rec_own && c->rec_ws) { cudaFree(c->rec_ws); c->rec_ws = nullptr; c->rec_own = false; }
+    if (workspace) {
+        if (bytes < L.total || ((uintptr_t)workspace & 255)) return fail(c, RMHD_ERR_NOMEM, "record: workspace too small");
+        c->rec_ws = (char *)workspace;
+        c->rec_own = false;
+    } else {
+        if (cudaMalloc(&c->rec_ws, L.total) != cudaSuccess) return fail(c, RMHD_ERR_NOMEM, "record: allocation failed");
+        c->rec_own = true;
+    }
+    c->rec_ck = (double *)(c->rec_ws + L.ck);
+    c->rec_seg = (double *)(c->rec_ws + L.seg);
+    c->rec_lam = (double *)(c->rec_ws + L.lam);
+    c->rec_lamn = (double *)(c->rec_ws + L.lamn);
+    c->rec_lq = (double *)(c->rec_ws + L.lq);
+    c->rec_lr2 = (double *)(c->rec_ws + L.lr2);
+    c->rec_fx = (double *)(c->rec_ws + L.fx);
+    c->rec_fy = (double *)(c->rec_ws + L.fy);
+    c->rec_fbx = (double *)(c->rec_ws + L.fbx);
+    c->rec_fby = (double *)(c->rec_ws + L.fby);
+    c->rec_qbd = (double *)(c->rec_ws + L.qbd);
+    c->rec_sig = (double *)(c->rec_ws + L.sig);
+    c->rec_pbar = (double *)(c->rec_ws + L.pbar);
+    c->rec_fin = (double *)(c->rec_ws + L.fin);
+    c->rec_sum = (double *)(c->rec_ws + L.sum);
+    c->recording = true;
+    c->rec_nsteps = nsteps;
+    c->rec_K = ckpt_every;
+    c->rec_done = 0;
+    c->rec_dt = 0.0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return RMHD_OK;
+}
+
+// One forward step writing the stage states into caller buffers (same kernels
+// and arithmetic as enqueue_step, so the recomputation reproduces the run).
+static int enqueue_step_into(rmhd_ctx *c, double dt, double *q1, double *w1, double *q2, double *w2) {
+    const int m = c->cfg.model;
+    StageArgs s1{c->Q, c->W, q1, w1, c->status, kGamma * dt};
+    CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
+    FluxArgs f1{q1, w1, c->Q, c->R, c->ACC, c->status, dt, 1.0 - 2.0 * kGamma};
+    CK(c, launch_flux(m, c->cfg.precision, 1, c->g, c->ph, f1, c->stream));
+    StageArgs s2{c->R, w1, q2, w2, c->status, kGamma * dt};
+    CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
+    FluxArgs f2{q2, w2, c->ACC, c->Q, c->W, c->status, dt, 0.0};
+    CK(c, launch_flux(m, c->cfg.precision, 2, c->g, c->ph, f2, c->stream));
+    return RMHD_OK;
+}
+
+int rmhd_adjoint_step(rmhd_ctx *c, const double *dJ_dcons, int where_in, double *dJ_dprims0, int where_out,
+                      double *dJ_dsigma) {
+    if (!c || !dJ_dcons || (where_in != RMHD_HOST && where_in != RMHD_DEVICE) ||
+        (dJ_dprims0 && where_out != RMHD_HOST && where_out != RMHD_DEVICE))
+        return fail(c, RMHD_ERR_INVALID, "adjoint_step: bad argument");
+    int st = adjoint_supported(c);
+    if (st) return st;
+    if (!c->recording || c->rec_done < 1) return fail(c, RMHD_ERR_STATE, "adjoint_step: no recorded steps (rmhd_record)");
+    const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    const size_t pl = (size_t)c->g.plane * sizeof(double);
+    const long long P = c->g.plane;
+    const double dt = c->rec_dt;
+    // lambda^N = dJ/dq^N
+    st = stage_in(c, dJ_dcons, nc, where_in);
+    if (st) return st;
+    CK(c, launch_pack(c->g, nc, c->stage_buf, c->rec_lam, c->stream));
+    // keep the final state
+    CK(c, cudaMemcpyAsync(c->rec_fin, c->Q, nc * pl, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->rec_fin + (size_t)nc * P, c->W, nw * pl, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->rec_sig, 0, pl, c->stream));
+    const int K = c->rec_K, nseg = (c->rec_done + K - 1) / K;
+    double *lam = c->rec_lam, *lamn = c->rec_lamn;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int s0 = seg * K, len = std::min(K, c->rec_done - s0);
+        const double *ck = c->rec_ck + (size_t)seg * (nc + nw) * P;
+        CK(c, cudaMemcpyAsync(c->Q, ck, nc * pl, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->W, ck + (size_t)nc * P, nw * pl, cudaMemcpyDeviceToDevice, c->stream));
+        for (int s = 0; s < len; ++s) {
+            double *b = c->rec_seg + (size_t)s * 2 * (nc + nw) * P;
+            st = enqueue_step_into(c, dt, b, b + (size_t)nc * P, b + (size_t)(nc + nw) * P, b + (size_t)(2 * nc + nw) * P);
+            if (st) return st;
+        }
+        for (int s = len - 1; s >= 0; --s) {
+            double *b = c->rec_seg + (size_t)s * 2 * (nc + nw) * P;
+            CK(c, launch_adjoint_step(c->g, c->ph, dt, lam, lamn, b, b + (size_t)nc * P, b + (size_t)(nc + nw) * P,
+                                      b + (size_t)(2 * nc + nw) * P, c->rec_fx, c->rec_fy, c->rec_fbx, c->rec_fby,
+                                      c->rec_qbd, c->rec_lq, c->rec_lr2, c->rec_sig, c->stream));
+            std::swap(lam, lamn);
+        }
+    }
+    // initial primitives: adjoint of the prims -> cons map at checkpoint 0
+    CK(c, launch_adjoint_prims(c->g, c->ph, c->rec_ck, c->rec_ck + (size_t)nc * P, lam, c->rec_pbar, c->stream));
+    CK(c, launch_sum(c->rec_sig, c->g.ncell, c->rec_sum, c->stream));
+    if (dJ_dprims0) {
+        CK(c, launch_unpack(c->g, 11, c->rec_pbar, c->stage_buf, c->stream));
+        st = stage_out(c, dJ_dprims0, 11, where_out);
+        if (st) return st;
+    }
+    CK(c, cudaMemcpyAsync(c->h_diag, c->rec_sum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->Q, c->rec_fin, nc * pl, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->W, c->rec_fin + (size_t)nc * P, nw * pl, cudaMemcpyDeviceToDevice, c->stream));
+    st = read_status(c, "adjoint_step");
+    if (st) return st;
+    if (dJ_dsigma) *dJ_dsigma = c->h_diag[0];
     return RMHD_OK;
 }
 

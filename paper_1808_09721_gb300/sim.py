@@ -124,6 +124,28 @@ class Sim:
     def check(self):
         self._check(self.lib.rmhd_check(self.h), "check")
 
+    def record(self, nsteps: int, ckpt_every: int = 10):
+        """Arm recording of the next `nsteps` steps for the discrete adjoint
+        (call right after set_prims). The checkpoint workspace is a torch tensor."""
+        torch = _torch()
+        nbytes = C.c_size_t()
+        self._check(self.lib.rmhd_recording_bytes(self.h, nsteps, ckpt_every, C.byref(nbytes)), "recording_bytes")
+        self.rec_workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self._check(self.lib.rmhd_record(self.h, nsteps, ckpt_every, C.c_void_p(self.rec_workspace.data_ptr()),
+                                         nbytes.value), "record")
+
+    def adjoint(self, dJ_dcons, out=None):
+        """Reverse the recorded steps: dJ/dq(final) -> (dJ/d prims0, dJ/d sigma)."""
+        if isinstance(dJ_dcons, np.ndarray):
+            dJ_dcons = np.ascontiguousarray(dJ_dcons, dtype=np.float64)
+        if out is None:
+            out = np.empty((11, self.ny, self.nx))
+        pin, wi, _k1 = self._ptr(dJ_dcons, self.nc, False)
+        pout, wo, _k2 = self._ptr(out, 11, True)
+        gs = C.c_double()
+        self._check(self.lib.rmhd_adjoint_step(self.h, pin, wi, pout, wo, C.byref(gs)), "adjoint_step")
+        return out, gs.value
+
     def set_profiling(self, on: bool):
         self._check(self.lib.rmhd_set_profiling(self.h, int(bool(on))), "set_profiling")
 

@@ -1,0 +1,139 @@
+"""Discrete adjoint of the SSP2(222) step (single fluid, FP64) through the C
+ABI and the torch.autograd.Function: gradients of the final-state functional
+J = sum (B_x^2 + B_y^2 + 2 B_z^2) dV (= integral of B_z^2 + |B|^2) with respect
+to the initial primitives and sigma, checked against central finite
+differences of the GPU forward run and of the CPU oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1808_09721_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_09721_gb300 import _lib
+    from paper_1808_09721_gb300 import build as B
+    B.build()
+    _lib.load()
+    from paper_1808_09721_gb300.adjoint import ImexSteps
+    from paper_1808_09721_gb300.sim import Sim
+    return torch, Sim, ImexSteps
+
+
+def functional_np(q, wl):
+    dv = wl.dx * (wl.dy if wl.ny > 1 else 1.0)
+    return float((q[5] ** 2 + q[6] ** 2 + 2.0 * q[7] ** 2).sum() * dv)
+
+
+def gpu_J(Sim, wl, prims, nsteps):
+    s = Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl)
+    s.set_prims(np.ascontiguousarray(prims))
+    s.step(wl.dt, nsteps)
+    s.check()
+    return functional_np(s.cons(), wl)
+
+
+def oracle_J(wl, prims, nsteps):
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
+    o.set_prims(np.ascontiguousarray(prims))
+    o.step(wl.dt, nsteps)
+    return functional_np(o.cons(), wl)
+
+
+def gradients(env, wl, nsteps, ckpt):
+    torch, Sim, ImexSteps = env
+    p0 = torch.tensor(wl.prims, dtype=torch.float64, device="cuda", requires_grad=True)
+    sig = torch.tensor(wl.sigma, dtype=torch.float64, requires_grad=True)
+    q = ImexSteps.apply(p0, sig, wl, nsteps, ckpt)
+    dv = wl.dx * (wl.dy if wl.ny > 1 else 1.0)
+    J = ((q[5] ** 2 + q[6] ** 2 + 2.0 * q[7] ** 2).sum() * dv)
+    J.backward()
+    return float(J), p0.grad.cpu().numpy(), float(sig.grad)
+
+
+def direction(wl, seed):
+    """Smooth random perturbation of every primitive field, scaled to the field."""
+    rng = np.random.default_rng(seed)
+    d = np.zeros_like(wl.prims)
+    ny, nx = wl.ny, wl.nx
+    y, x = np.meshgrid(np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
+    for v in range(11):
+        a, b, c = rng.normal(size=3)
+        shape = np.sin(2 * np.pi * (x + a)) * np.cos(2 * np.pi * (y + b)) + 0.3 * c
+        scale = max(np.abs(wl.prims[v]).max(), 1e-3)
+        d[v] = scale * shape
+    return d
+
+
+CASES = [
+    ("field_loop", lambda: WL.field_loop(n=24, nsteps=12), 12, 5),
+    ("brio_wu_1d", lambda: WL.brio_wu(nx=40), 10, 4),
+    ("khi_stiff", lambda: WL.khi(n=16, seed=3, sigma=1e5), 6, 3),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", CASES)
+def test_adjoint_matches_finite_differences(env, name, make, nsteps, ckpt):
+    torch, Sim, _ = env
+    wl = make()
+    J, gp, gs = gradients(env, wl, nsteps, ckpt)
+    assert abs(J - gpu_J(Sim, wl, wl.prims, nsteps)) <= 1e-14 * abs(J)
+    # sigma: J is insensitive to sigma in the stiff limit (dJ/dsigma ~ 1/sigma^2),
+    # so the difference step is 1e-3 sigma (truncation ~1e-6 relative) and the
+    # bound includes the forward run's round-off floor (1e-13 |J|) divided by h
+    h = 1e-3 * wl.sigma
+    fd = (gpu_J(Sim, dataclasses.replace(wl, sigma=wl.sigma + h), wl.prims, nsteps) -
+          gpu_J(Sim, dataclasses.replace(wl, sigma=wl.sigma - h), wl.prims, nsteps)) / (2 * h)
+    assert abs(gs - fd) <= 1e-4 * abs(fd) + 1e-13 * abs(J) / h, (gs, fd)
+    # initial primitives, two random directions
+    for seed in (1, 2):
+        d = direction(wl, seed)
+        h = 1e-6
+        fd = (gpu_J(Sim, wl, wl.prims + h * d, nsteps) - gpu_J(Sim, wl, wl.prims - h * d, nsteps)) / (2 * h)
+        ad = float((gp * d).sum())
+        assert abs(ad - fd) <= 1e-5 * abs(fd), (name, seed, ad, fd)
+
+
+def test_adjoint_matches_oracle_finite_differences(env):
+    """Directional derivatives of the oracle's FP64 run (central differences)
+    agree with the GPU adjoint gradient."""
+    wl = WL.field_loop(n=16, nsteps=8)
+    nsteps = 8
+    J, gp, gs = gradients(env, wl, nsteps, 3)
+    assert abs(J - oracle_J(wl, wl.prims, nsteps)) <= 1e-9 * abs(J)
+    for seed in (3, 4):
+        d = direction(wl, seed)
+        h = 1e-5
+        fd = (oracle_J(wl, wl.prims + h * d, nsteps) - oracle_J(wl, wl.prims - h * d, nsteps)) / (2 * h)
+        ad = float((gp * d).sum())
+        assert abs(ad - fd) <= 1e-6 * abs(fd), (seed, ad, fd)
+    h = 1e-3 * wl.sigma
+    fd = (oracle_J(dataclasses.replace(wl, sigma=wl.sigma + h), wl.prims, nsteps) -
+          oracle_J(dataclasses.replace(wl, sigma=wl.sigma - h), wl.prims, nsteps)) / (2 * h)
+    assert abs(gs - fd) <= 1e-4 * abs(fd) + 1e-13 * abs(J) / h, (gs, fd)
+
+
+def test_adjoint_restores_state_and_repeats(env):
+    """The adjoint leaves the final state in place and can be called again."""
+    torch, Sim, _ = env
+    wl = WL.field_loop(n=12, nsteps=6)
+    s = Sim.from_workload(wl)
+    s.record(6, 4)
+    s.step(wl.dt, 6)
+    before = s.cons()
+    lam = np.zeros_like(before)
+    lam[5:8] = 2.0 * before[5:8] * np.array([1.0, 1.0, 2.0])[:, None, None]  # dJ/dB
+    g1, s1 = s.adjoint(lam)
+    np.testing.assert_array_equal(s.cons(), before)
+    g2, s2 = s.adjoint(lam)
+    # the face transposes accumulate with FP64 atomics: sums agree to round-off
+    # of the largest entry, not bit for bit
+    np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-12 * np.abs(g1).max())
+    assert abs(s2 - s1) <= 1e-10 * abs(s1)
