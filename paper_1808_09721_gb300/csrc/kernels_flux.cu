@@ -37,11 +37,12 @@ __device__ __forceinline__ int map_index(int i, int n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// The status word is one 64-bit key (cell << 8 | -code), initialised to all
+// ones; atomicMin keeps the smallest failing cell together with its own code.
 __device__ __forceinline__ void record_status(int *status, int st, long long cell) {
-    if (st != 0) {
-        atomicCAS(status, 0, st);
-        atomicMin(status + 1, (int)cell);
-    }
+    if (st != 0)
+        atomicMin(reinterpret_cast<unsigned long long *>(status),
+                  ((unsigned long long)cell << 8) | (unsigned long long)((-st) & 0xff));
 }
 
 // ---- model adaptors ------------------------------------------------------

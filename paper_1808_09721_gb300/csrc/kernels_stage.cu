@@ -11,11 +11,12 @@ namespace rmhd {
 static constexpr int kStageThreads = 128;
 static constexpr int kNRef = 2;  // FP64 refinement passes per stage solve
 
+// The status word is one 64-bit key (cell << 8 | -code), initialised to all
+// ones; atomicMin keeps the smallest failing cell together with its own code.
 __device__ __forceinline__ void record(int *status, int st, long long cell) {
-    if (st != 0) {
-        atomicCAS(status, 0, st);
-        atomicMin(status + 1, (int)cell);
-    }
+    if (st != 0)
+        atomicMin(reinterpret_cast<unsigned long long *>(status),
+                  ((unsigned long long)cell << 8) | (unsigned long long)((-st) & 0xff));
 }
 
 __device__ __forceinline__ int wrap(int i, int n, int bc) {

@@ -12,12 +12,12 @@
 //   1. Newton on G in FP32 until the FP32 residual stalls (~1e-7 relative).
 //      Jacobian columns come from forward-mode duals through the same code,
 //      the pressure root's derivative by the implicit-function theorem.
-//   2. A fixed number of FP64 refinement passes: evaluate G in FP64 (one FP64
-//      Newton step of the pressure root per pass, started from a first-order
-//      prediction) and correct E with the FP32 inverse Jacobian. Each pass
-//      gains ~6-7 digits. The evaluation point of the last pass (~1e-13 from
-//      the FP64 root) is returned with its own primitives, so E and v are
-//      consistent; the last correction only checks convergence.
+//   2. FP64 refinement passes (two for almost every cell): evaluate G in FP64
+//      (one FP64 Newton step of the pressure root per pass, started from a
+//      first-order prediction) and correct E with the FP32 inverse Jacobian.
+//      Each pass gains ~6-7 digits. The first evaluation point (from the
+//      second on) where |G| is at round-off of the magnitude of G's terms is
+//      returned with its own primitives, so E and v are consistent.
 #pragma once
 #include "device_math.cuh"
 
@@ -224,24 +224,41 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
 
     // ---- FP64 refinement passes. Pass k evaluates G in FP64 at E_k (one FP64
     // pressure step, started from a first-order prediction) and forms the
-    // correction dE_k with the FP32 inverse Jacobian. The last pass's
-    // evaluation point is the result: its primitives are exactly those of the
-    // returned E (J amplifies any E/v mismatch by sigma), and its correction,
-    // ~1e-13 relative after the first pass, only gates convergence.
+    // correction dE_k with the FP32 inverse Jacobian. The evaluation point at
+    // which |G| reaches round-off of the magnitude of G's terms (at least the
+    // NREF-th) is the result, with its own primitives (J amplifies any E/v
+    // mismatch by sigma). Cells that need it take extra passes (up to 8).
+    // Magnitude of the terms of G (its round-off scale). The products inside
+    // v x B and v.E are bounded one by one: in a near-static cell the two
+    // products of a cross-product component can cancel to ~1e-9 of their size.
+    float gs = 0.f;
+    {
+        const float av[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
+        const float aB[3] = {fabsf(Bf[0]), fabsf(Bf[1]), fabsf(Bf[2])};
+        const float vEn = av[0] * fabsf(E[0]) + av[1] * fabsf(E[1]) + av[2] * fabsf(E[2]);
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, l = (i + 2) % 3;
+            const float cr = av[j] * aB[l] + av[l] * aB[j];
+            gs = fmaxf(gs, fabsf(E[i]) + fabsf(rEf[i]) +
+                               adtf * (fabsf(rhoef) * av[i] + sigf * W * (fabsf(E[i]) + cr + vEn * av[i])));
+        }
+        gs = fmaxf(gs, 1e-30f);
+    }
     double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
     double pdd = (double)p;
     const double rdf = (double)(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
-    double last = 0.0;
-    for (int pass = 0; pass < NREF; ++pass) {
+    double gres = 0.0;
+    for (int pass = 0; pass < 8; ++pass) {
         em_split(Ed, Sv, B, tauB, r[D], St64, a64, S264);
         pdd -= pres_resid(pdd, a64, S264, r[D], gm1, gam) * rdf;
         stage_resid(Ed, pdd, St64, a64, B, rE, r[RHOE], k.adt, k.sigma, G64, v64, W64);
+        gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
+        if (pass >= NREF - 1 && gres <= 1e-12 * (double)gs) break;
         float Gf[3] = {(float)G64[0], (float)G64[1], (float)G64[2]};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
-        last = fmax(fmax(fabs((double)dE[0]), fabs((double)dE[1])), fabs((double)dE[2]));
-        if (pass == NREF - 1) break;
+        if (pass == 7) break;
         // first-order prediction of the pressure at the corrected E
         pdd -= (double)(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
         Ed[0] -= (double)dE[0];
@@ -256,8 +273,7 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
     q[EX] = Ed[0];
     q[EY] = Ed[1];
     q[EZ] = Ed[2];
-    double sc = fmax((double)scale, fmax(fmax(fabs(Ed[0]), fabs(Ed[1])), fabs(Ed[2])));
-    if (!(pdd > 0.0) || !(last <= 1e-10 * sc) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
+    if (!(pdd > 0.0) || !(gres <= 1e-9 * (double)gs) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
     return ST_OK;
 }
 

@@ -360,27 +360,47 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     }
     if (!have_jac) return sf::ST_NEWTON;
 
-    // ---- FP64 refinement passes (as for one fluid: the last evaluation point
-    // is the result, with its own primitives; its correction gates convergence)
+    // ---- FP64 refinement passes (as for one fluid: the evaluation point where
+    // |G| reaches round-off of the magnitude of G's terms is the result, with
+    // its own primitives; extra passes, up to 8, only where needed)
+    float gs = 1e-30f;  // magnitude of the terms of G (round-off scale), FP32
+    {
+        const float mu[2] = {cf.mu_e, cf.mu_p};
+        float M0 = 0.f, M1n = 0.f, Jn = 0.f, vr = 0.f;
+        for (int sp = 0; sp < 2; ++sp) {
+            float vn = fabsf(v[sp][0]) + fabsf(v[sp][1]) + fabsf(v[sp][2]);
+            M0 += mu[sp] * mu[sp] * cf.Ds[sp];
+            M1n += mu[sp] * mu[sp] * cf.Ds[sp] * vn;
+            Jn += fabsf(mu[sp]) * cf.Ds[sp] * vn;
+            vr += fabsf(mu[sp]) * cf.Ds[sp];
+        }
+        const float En = fabsf(x[4]) + fabsf(x[5]) + fabsf(x[6]);
+        const float Bn = fabsf(cf.B[0]) + fabsf(cf.B[1]) + fabsf(cf.B[2]);
+        const float src = M0 * En + M1n * Bn + cf.eta * (M0 * Jn + vr * M1n);
+        for (int i = 0; i < 7; ++i) gs = fmaxf(gs, fabsf(x[i]) + fabsf(cf.rx[i]));
+        gs = fmaxf(gs, cf.adt * cf.imur * src);
+        gs = fmaxf(gs, cf.adt * Jn);
+    }
     double xd[7], pdd[2] = {(double)p[0], (double)p[1]};
     const double rdf[2] = {(double)(1.f / dfdp[0]), (double)(1.f / dfdp[1])};
     for (int i = 0; i < 7; ++i) xd[i] = (double)x[i];
     double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
-    double last = 0.0;
-    for (int pass = 0; pass < NREF; ++pass) {
+    double gres = 0.0;
+    for (int pass = 0; pass < 8; ++pass) {
         split_x(c, xd, St64, a64, S264);
         for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
         stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
+        gres = 0.0;
+        for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
+        if (pass >= NREF - 1 && gres <= 1e-12 * (double)gs) break;
+        if (pass == 7) break;
         float Gf[7], dx[7];
         for (int i = 0; i < 7; ++i) Gf[i] = (float)G64[i];
-        last = 0.0;
         for (int i = 0; i < 7; ++i) {
             float s = 0.f;
             for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * Gf[j];
             dx[i] = s;
-            last = fmax(last, fabs((double)s));
         }
-        if (pass == NREF - 1) break;
         for (int s = 0; s < 2; ++s) {
             float dp = 0.f;
             for (int i = 0; i < 7; ++i) dp += dpdx[s][i] * dx[i];
@@ -402,9 +422,7 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
         q[EX + i] = xd[4 + i];
     }
     q[TAUB] = xd[3] * c.mur;
-    double sc = (double)scale;
-    for (int i = 0; i < 7; ++i) sc = fmax(sc, fabs(xd[i]));
-    if (!ok || !(last <= 1e-10 * sc)) return sf::ST_NEWTON;
+    if (!ok || !(gres <= 1e-9 * (double)gs)) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
 

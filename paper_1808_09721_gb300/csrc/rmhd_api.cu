@@ -39,7 +39,7 @@ struct rmhd_ctx {
     size_t ws_bytes;
     double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
     int *status;       // device [2]
-    int *h_status;     // pinned host [2]
+    int *h_status;     // pinned host copy of the 64-bit status key
     double *h_diag;    // pinned host [8]
     bool has_state;
     bool fresh_prims;  // state set by rmhd_set_prims and not stepped since
@@ -207,21 +207,25 @@ const char *rmhd_last_error(const rmhd_ctx *ctx) {
     return ctx->err.c_str();
 }
 
+// Device status word: one 64-bit key (first failing cell << 8 | -code), all
+// ones when no cell failed.
 static int reset_status(rmhd_ctx *c) {
-    int init[2] = {0, INT_MAX};
-    CK(c, cudaMemcpyAsync(c->status, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->status, 0xff, sizeof(unsigned long long), c->stream));
     return RMHD_OK;
 }
 
 // synchronise and decode the device status word
 static int read_status(rmhd_ctx *c, const char *what) {
-    CK(c, cudaMemcpyAsync(c->h_status, c->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    int code = c->h_status[0], cell = c->h_status[1];
-    if (code == 0) return RMHD_OK;
+    unsigned long long key;
+    memcpy(&key, c->h_status, sizeof key);
+    if (key == ~0ull) return RMHD_OK;
+    const int code = -(int)(key & 0xff);
+    const long long cell = (long long)(key >> 8);
     int st = reset_status(c);
     if (st) return st;
-    int i = cell % c->cfg.nx, j = cell / c->cfg.nx;
+    int i = (int)(cell % c->cfg.nx), j = (int)(cell / c->cfg.nx);
     const char *kind = code == RMHD_ERR_NEWTON ? "implicit-stage solve did not converge"
                        : code == RMHD_ERR_C2P  ? "primitive recovery failed"
                                                : "inadmissible primitive state";

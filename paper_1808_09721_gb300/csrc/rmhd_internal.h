@@ -38,7 +38,7 @@ struct FluxArgs {
     const double *base;  // q^n (mode 1) or the accumulator (mode 2), NC planes
     double *out1;
     double *out2;
-    int *status;         // [0] first error code, [1] smallest failing cell
+    int *status;         // 64-bit key: smallest failing cell << 8 | -code (all ones: none)
     double dt;
     double c_src;        // (1 - 2 gamma_ssp) for mode 1
 };

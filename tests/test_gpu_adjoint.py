@@ -55,7 +55,7 @@ def gradients(env, wl, nsteps, ckpt):
     dv = wl.dx * (wl.dy if wl.ny > 1 else 1.0)
     J = ((q[5] ** 2 + q[6] ** 2 + 2.0 * q[7] ** 2).sum() * dv)
     J.backward()
-    return float(J), p0.grad.cpu().numpy(), float(sig.grad)
+    return J.item(), p0.grad.cpu().numpy(), sig.grad.item()
 
 
 def direction(wl, seed):

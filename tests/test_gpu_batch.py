@@ -74,3 +74,19 @@ def test_autotune_keeps_state_and_results(Sim):
     b.check()
     # the tile width only changes which CTA computes a cell, not its arithmetic
     np.testing.assert_array_equal(a.cons(), b.cons())
+
+
+def test_full_512_tube_configuration(Sim):
+    """The benchmark's 512-tube ensemble (N up to 4096, sigma up to 1e6, density
+    and pressure ratios up to 100) runs without solver failures in the mixed
+    form, and the tube with the coldest dense right state near the initial jump
+    (run 215) matches the oracle."""
+    runs = WL.batch_tubes(count=512, seed=2)
+    b = Sim.batch(runs, precision=1)
+    b.step(0.0, 25)
+    b.check()
+    got = b.unpack(b.cons())
+    for r in (215, 0, 511):
+        want = _oracle(runs[r], 25)
+        l1 = np.abs(got[r] - want).reshape(14, -1).mean(axis=1) / parity_scale(0, want)
+        assert np.all(l1 <= 1e-4), (r, l1)
