@@ -39,11 +39,11 @@ METRIC = "cell-updates/s per IMEX step, FP64 vs mixed, % HBM roofline; adjoint/f
 UNIT = "cell-updates/s"
 WORKLOAD = "khi-2d-1024x1024 (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=4/3, sigma=1e3, SSP2(222), WENO3+LF)"
 
-# Algorithmic FP64 operations per interior cell for each kernel of the FP64
-# form on a 2-D grid (counted from the kernels' arithmetic; each FP64 pipe
-# instruction -- add, mul, fma, approximate reciprocal/rsqrt, conversion --
-# counts as one op). See DESIGN.md "Roofline".
-FP64_OPS_PER_CELL = {"stage": 210.0, "flux1": 960.0, "flux2": 1010.0}
+# FP64 arithmetic instructions (add, mul, fma; one op each) per interior cell
+# for each kernel of the FP64 form on a 2-D grid, counted by ncu's
+# smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
+# The FP64 pipe issues 2 of them per clock per SM, which sets the ALU peak.
+FP64_OPS_PER_CELL = {"stage": 171.0, "flux1": 1042.0, "flux2": 1082.0}
 # Algorithmic HBM bytes per cell for each kernel (read once + written once).
 BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
 

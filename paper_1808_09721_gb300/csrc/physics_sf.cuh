@@ -134,6 +134,24 @@ __device__ __forceinline__ bool inv3(const float m[9], float inv[9]) {
     return true;
 }
 
+// Magnitude of the terms of the stage residual G at (E, v, W) in FP32: the
+// round-off scale of G. The products inside v x B and v.E are bounded one by
+// one, because in a near-static cell the two products of a cross-product
+// component can cancel to ~1e-9 of their size.
+__device__ __forceinline__ float resid_scale(const float E[3], const float rE[3], const float v[3], const float B[3],
+                                             float W, float rhoe, float adt, float sig) {
+    const float av[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
+    const float aB[3] = {fabsf(B[0]), fabsf(B[1]), fabsf(B[2])};
+    const float vEn = av[0] * fabsf(E[0]) + av[1] * fabsf(E[1]) + av[2] * fabsf(E[2]);
+    float gs = 1e-30f;
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, l = (i + 2) % 3;
+        const float cr = av[j] * aB[l] + av[l] * aB[j];
+        gs = fmaxf(gs, fabsf(E[i]) + fabsf(rE[i]) + adt * (fabsf(rhoe) * av[i] + sig * W * (fabsf(E[i]) + cr + vEn * av[i])));
+    }
+    return gs;
+}
+
 // Status codes recorded per cell (match the library's error codes).
 enum { ST_OK = 0, ST_NEWTON = -3, ST_C2P = -4 };
 
@@ -198,6 +216,9 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * G[0] + Minv[3 * i + 1] * G[1] + Minv[3 * i + 2] * G[2];
         float dn = fmaxf(fmaxf(fabsf(dE[0]), fabsf(dE[1])), fabsf(dE[2]));
         if (dn <= 2e-7f * fmaxf(scale, fmaxf(fmaxf(fabsf(E[0]), fabsf(E[1])), fabsf(E[2])))) break;
+        // |G| at the FP32 noise floor (p and v carry ~2e-7 relative error):
+        // further FP32 steps cannot improve E; the FP64 passes take over
+        if (gn <= 1e-6f * resid_scale(E, rEf, v, Bf, W, rhoef, adtf, sigf)) break;
         // backtracking on |G|_inf
         float t = 1.f;
         bool accepted = false;
@@ -211,6 +232,7 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
                 if (gt < gn || t < 0.02f) {
                     E[0] = Et[0]; E[1] = Et[1]; E[2] = Et[2];
                     p = pt; dfdp = dft; G[0] = Gt[0]; G[1] = Gt[1]; G[2] = Gt[2];
+                    v[0] = vt[0]; v[1] = vt[1]; v[2] = vt[2]; W = Wt;
                     gn = gt;
                     accepted = true;
                     break;
@@ -228,22 +250,7 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
     // which |G| reaches round-off of the magnitude of G's terms (at least the
     // NREF-th) is the result, with its own primitives (J amplifies any E/v
     // mismatch by sigma). Cells that need it take extra passes (up to 8).
-    // Magnitude of the terms of G (its round-off scale). The products inside
-    // v x B and v.E are bounded one by one: in a near-static cell the two
-    // products of a cross-product component can cancel to ~1e-9 of their size.
-    float gs = 0.f;
-    {
-        const float av[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
-        const float aB[3] = {fabsf(Bf[0]), fabsf(Bf[1]), fabsf(Bf[2])};
-        const float vEn = av[0] * fabsf(E[0]) + av[1] * fabsf(E[1]) + av[2] * fabsf(E[2]);
-        for (int i = 0; i < 3; ++i) {
-            const int j = (i + 1) % 3, l = (i + 2) % 3;
-            const float cr = av[j] * aB[l] + av[l] * aB[j];
-            gs = fmaxf(gs, fabsf(E[i]) + fabsf(rEf[i]) +
-                               adtf * (fabsf(rhoef) * av[i] + sigf * W * (fabsf(E[i]) + cr + vEn * av[i])));
-        }
-        gs = fmaxf(gs, 1e-30f);
-    }
+    const float gs = resid_scale(E, rEf, v, Bf, W, rhoef, adtf, sigf);  // round-off scale of G
     double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
     double pdd = (double)p;
     const double rdf = (double)(1.f / dfdp);

@@ -255,6 +255,28 @@ __device__ __forceinline__ bool invert(float m[N * N], float inv[N * N]) {
     return true;
 }
 
+// Magnitude of the terms of the stage residual G at (x, v) in FP32: the
+// round-off scale of G (norms bound the products inside the sources).
+__device__ __forceinline__ float resid_scale(const Cell<float> &cf, const float x[7], const float v[2][3]) {
+    const float mu[2] = {cf.mu_e, cf.mu_p};
+    float M0 = 0.f, M1n = 0.f, Jn = 0.f, vr = 0.f;
+    for (int sp = 0; sp < 2; ++sp) {
+        float vn = fabsf(v[sp][0]) + fabsf(v[sp][1]) + fabsf(v[sp][2]);
+        M0 += mu[sp] * mu[sp] * cf.Ds[sp];
+        M1n += mu[sp] * mu[sp] * cf.Ds[sp] * vn;
+        Jn += fabsf(mu[sp]) * cf.Ds[sp] * vn;
+        vr += fabsf(mu[sp]) * cf.Ds[sp];
+    }
+    const float En = fabsf(x[4]) + fabsf(x[5]) + fabsf(x[6]);
+    const float Bn = fabsf(cf.B[0]) + fabsf(cf.B[1]) + fabsf(cf.B[2]);
+    const float src = M0 * En + M1n * Bn + cf.eta * (M0 * Jn + vr * M1n);
+    float gs = 1e-30f;
+    for (int i = 0; i < 7; ++i) gs = fmaxf(gs, fabsf(x[i]) + fabsf(cf.rx[i]));
+    gs = fmaxf(gs, cf.adt * cf.imur * src);
+    gs = fmaxf(gs, cf.adt * Jn);
+    return gs;
+}
+
 struct StageConst {
     double adt, cpsi;
 };
@@ -333,6 +355,8 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
             xn = fmaxf(xn, fabsf(x[i]));
         }
         if (dn <= 2e-7f * xn) break;
+        // |G| at the FP32 noise floor: the FP64 passes take over
+        if (gn <= 1e-6f * resid_scale(cf, x, v)) break;
         float t = 1.f;
         bool accepted = false;
         for (int ls = 0; ls < 8; ++ls) {
@@ -348,6 +372,7 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
                 for (int i = 0; i < 7; ++i) gt = fmaxf(gt, fabsf(Gt[i]));
                 if (gt < gn || t < 0.02f) {
                     for (int i = 0; i < 7; ++i) { x[i] = xt[i]; G[i] = Gt[i]; }
+                    for (int i = 0; i < 3; ++i) { v[0][i] = vt[0][i]; v[1][i] = vt[1][i]; }
                     p[0] = pt[0]; p[1] = pt[1]; dfdp[0] = dft[0]; dfdp[1] = dft[1];
                     gn = gt;
                     accepted = true;
@@ -363,24 +388,7 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     // ---- FP64 refinement passes (as for one fluid: the evaluation point where
     // |G| reaches round-off of the magnitude of G's terms is the result, with
     // its own primitives; extra passes, up to 8, only where needed)
-    float gs = 1e-30f;  // magnitude of the terms of G (round-off scale), FP32
-    {
-        const float mu[2] = {cf.mu_e, cf.mu_p};
-        float M0 = 0.f, M1n = 0.f, Jn = 0.f, vr = 0.f;
-        for (int sp = 0; sp < 2; ++sp) {
-            float vn = fabsf(v[sp][0]) + fabsf(v[sp][1]) + fabsf(v[sp][2]);
-            M0 += mu[sp] * mu[sp] * cf.Ds[sp];
-            M1n += mu[sp] * mu[sp] * cf.Ds[sp] * vn;
-            Jn += fabsf(mu[sp]) * cf.Ds[sp] * vn;
-            vr += fabsf(mu[sp]) * cf.Ds[sp];
-        }
-        const float En = fabsf(x[4]) + fabsf(x[5]) + fabsf(x[6]);
-        const float Bn = fabsf(cf.B[0]) + fabsf(cf.B[1]) + fabsf(cf.B[2]);
-        const float src = M0 * En + M1n * Bn + cf.eta * (M0 * Jn + vr * M1n);
-        for (int i = 0; i < 7; ++i) gs = fmaxf(gs, fabsf(x[i]) + fabsf(cf.rx[i]));
-        gs = fmaxf(gs, cf.adt * cf.imur * src);
-        gs = fmaxf(gs, cf.adt * Jn);
-    }
+    const float gs = resid_scale(cf, x, v);  // round-off scale of G
     double xd[7], pdd[2] = {(double)p[0], (double)p[1]};
     const double rdf[2] = {(double)(1.f / dfdp[0]), (double)(1.f / dfdp[1])};
     for (int i = 0; i < 7; ++i) xd[i] = (double)x[i];
