@@ -45,6 +45,14 @@ __device__ __forceinline__ void record_status(int *status, int st, long long cel
                   ((unsigned long long)cell << 8) | (unsigned long long)((-st) & 0xff));
 }
 
+// Barrier over the NTHR threads of component group grp (named barrier 1 + grp;
+// barrier 0 is __syncthreads). The half-point and face buffers are private to
+// a group, so the rounds of the reconstruction only synchronise the group.
+template <int NTHR>
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(NTHR) : "memory");
+}
+
 // ---- model adaptors ------------------------------------------------------
 // Per-cell quantities staged once per tile (aux), the flux of one cell from
 // shared memory, the nonzero source entries of an interior cell, and the
@@ -72,8 +80,8 @@ struct SFModel {
         aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
         aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
     }
-    template <class FT>
-    static __device__ __forceinline__ void cell_flux(const double *st, const double *aux, int SN, int idx, int dir,
+    template <class FT, class ST>
+    static __device__ __forceinline__ void cell_flux(const ST *st, const double *aux, int SN, int idx, int dir,
                                                      const Phys &ph, FT f[NC]) {
         (void)ph;
         const FT vd = (FT)st[(NC + sf::VX + dir) * SN + idx];
@@ -85,7 +93,7 @@ struct SFModel {
         for (int i = 0; i < 3; ++i)
             f[sf::SX + i] = Zv * (FT)st[(NC + sf::VX + i) * SN + idx] - (FT)st[(sf::EX + i) * SN + idx] * Ed -
                             (FT)st[(sf::BX + i) * SN + idx] * Bd;
-        f[sf::SX + dir] += (FT)aux[4 * SN + idx];
+        if (dir == 0) f[sf::SX] += (FT)aux[4 * SN + idx]; else f[sf::SY] += (FT)aux[4 * SN + idx];
         f[sf::TAU] = (FT)st[(sf::SX + dir) * SN + idx] - f[sf::D];
         const FT EX = (FT)st[sf::EX * SN + idx], EY = (FT)st[sf::EY * SN + idx], EZ = (FT)st[sf::EZ * SN + idx];
         const FT BX = (FT)st[sf::BX * SN + idx], BY = (FT)st[sf::BY * SN + idx], BZ = (FT)st[sf::BZ * SN + idx];
@@ -126,8 +134,8 @@ struct TFModel {
                : (c >= tf::EX && c <= tf::EZ ? 4 + c - tf::EX : (c == tf::PSI ? 7 : (c == tf::PHI ? 8 : -1)));
     }
     static __device__ __forceinline__ void prep(const double *, int, int, const Phys &, double *) {}
-    template <class FT>
-    static __device__ __forceinline__ void cell_flux(const double *st, const double *aux, int SN, int idx, int dir,
+    template <class FT, class ST>
+    static __device__ __forceinline__ void cell_flux(const ST *st, const double *aux, int SN, int idx, int dir,
                                                      const Phys &ph, FT f[NC]) {
         (void)aux;
         FT qf[NC], wf[NW];
@@ -163,9 +171,14 @@ template <class M, int TX, int TY, int G, class FT, int MODE>
 struct FluxSmem {
     static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     static constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH, NL = TX * TY;
+    // FP32 flux arithmetic reads an FP32 copy of the staged state (converted
+    // once per staged value); the FP64 copy serves the FP64 current, sources
+    // and recovery
+    static constexpr bool SHADOW = sizeof(FT) < sizeof(double);
     // byte offsets
     static constexpr size_t st = 0;
-    static constexpr size_t aux = st + sizeof(double) * NV * SN;
+    static constexpr size_t st32 = st + sizeof(double) * NV * SN;
+    static constexpr size_t aux = st32 + (SHADOW ? sizeof(float) * NV * SN : 0);
     static constexpr size_t src = aux + sizeof(double) * M::NAUX * SN;
     static constexpr size_t fl = src + sizeof(double) * M::NS * NL;
     static constexpr size_t hp = fl + sizeof(FT) * NC * SN;
@@ -189,6 +202,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     constexpr int NR = (NC + G - 1) / G; // component rounds
 
     double *st = reinterpret_cast<double *>(smem_raw + L_::st);   // [NV][SH][SW]
+    FT *st32 = reinterpret_cast<FT *>(smem_raw + L_::st32);       // [NV][SH][SW] (FP32 form only)
     double *aux = reinterpret_cast<double *>(smem_raw + L_::aux); // [NAUX][SH][SW]
     double *src = reinterpret_cast<double *>(smem_raw + L_::src); // [NS][NL] (interior cells)
     FT *fl = reinterpret_cast<FT *>(smem_raw + L_::fl);           // [NC][SH][SW]
@@ -206,7 +220,9 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
         int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
         int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
         const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-        st[e] = srcp[base + (long long)gj * g.nx + gi];
+        const double val = srcp[base + (long long)gj * g.nx + gi];
+        st[e] = val;
+        if (L_::SHADOW) st32[e] = (FT)val;
     }
     __syncthreads();
     // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
@@ -241,7 +257,10 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int cy = e / ncx, cx = e - cy * ncx;
             int idx = (cy0 + cy) * SW + cx0 + cx;
             FT f[NC];
-            M::template cell_flux<FT>(st, aux, SN, idx, dir, ph, f);
+            if constexpr (L_::SHADOW)
+                M::template cell_flux<FT>(st32, aux, SN, idx, dir, ph, f);
+            else
+                M::template cell_flux<FT>(st, aux, SN, idx, dir, ph, f);
 #pragma unroll
             for (int v = 0; v < NC; ++v) fl[v * SN + idx] = f[v];
         }
@@ -258,11 +277,12 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             if (active) {
                 const FT *fv = fl + c * SN;
                 const double *qv = st + c * SN;
+                const FT *qv32 = st32 + c * SN;
                 for (int e = lid; e < nhx * nhy; e += NL) {
                     int hy = e / nhx, hx = e - hy * nhx;
                     int idx = (hy0 + hy) * SW + hx0 + hx;
                     FT df = fv[idx + sstep] - fv[idx];
-                    FT dq = FT(qv[idx + sstep] - qv[idx]);
+                    FT dq = L_::SHADOW ? qv32[idx + sstep] - qv32[idx] : FT(qv[idx + sstep] - qv[idx]);
                     FT ep = df + dq, em = df - dq;
                     FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
                     hpg[idx] = ep;
@@ -271,7 +291,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                     hpg[3 * SN + idx] = am * am;
                 }
             }
-            __syncthreads();
+            group_sync<NL>(grp);
             // 3c. face values of component c
             if (active) {
                 const FT *fv = fl + c * SN;
@@ -280,14 +300,14 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                     int idx = (fy0 + fy) * SW + fx0 + fx;
                     int il = idx - sstep, ir = idx + sstep;
                     FT Ap = hpg[2 * SN + idx], Am = hpg[3 * SN + idx];
-                    FT wp = Ap * s_rcp(s_fma(FT(2), hpg[2 * SN + il], Ap));
-                    FT wm = Am * s_rcp(s_fma(FT(2), hpg[3 * SN + ir], Am));
+                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpg[2 * SN + il], Ap));
+                    FT wm = Am * s_rcp1(s_fma(FT(2), hpg[3 * SN + ir], Am));
                     FT Xp = hpg[il] - hpg[idx];
                     FT Xm = hpg[SN + idx] - hpg[SN + ir];
                     fcg[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
                 }
             }
-            __syncthreads();
+            group_sync<NL>(grp);
             // 3d. flux difference into the owned cell's accumulator
             if (active) L[r] = s_fma(fcg[oy * SW + ox - sstep] - fcg[oy * SW + ox], inv4h, L[r]);
         }

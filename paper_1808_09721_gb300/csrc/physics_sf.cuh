@@ -328,14 +328,15 @@ __device__ __forceinline__ void flux(const T q[NC], const T w[NW], const T J[3],
     const T E2B2 = q[EX] * q[EX] + q[EY] * q[EY] + q[EZ] * q[EZ] + q[BX] * q[BX] + q[BY] * q[BY] + q[BZ] * q[BZ];
     const T pem = w[P] + T(0.5) * E2B2;
     const T Z = (q[TAU] - T(0.5) * E2B2) + q[D] + w[P];
-    const T vd = w[VX + dir], Ed = q[EX + dir], Bd = q[BX + dir];
+    // selects instead of indices computed from dir keep the arrays in registers
+    const T vd = dir == 0 ? w[VX] : w[VY], Ed = dir == 0 ? q[EX] : q[EY], Bd = dir == 0 ? q[BX] : q[BY];
     const T Zv = Z * vd;
     f[D] = q[D] * vd;
     f[SX] = Zv * w[VX] - q[EX] * Ed - q[BX] * Bd;
     f[SY] = Zv * w[VY] - q[EY] * Ed - q[BY] * Bd;
     f[SZ] = Zv * w[VZ] - q[EZ] * Ed - q[BZ] * Bd;
-    f[SX + dir] += pem;
-    f[TAU] = q[SX + dir] - q[D] * vd;
+    if (dir == 0) f[SX] += pem; else f[SY] += pem;
+    f[TAU] = (dir == 0 ? q[SX] : q[SY]) - q[D] * vd;
     if (dir == 0) {
         f[BX] = q[PHI]; f[BY] = -q[EZ]; f[BZ] = q[EY];
         f[EX] = q[PSI]; f[EY] = q[BZ]; f[EZ] = -q[BY];
@@ -343,7 +344,7 @@ __device__ __forceinline__ void flux(const T q[NC], const T w[NW], const T J[3],
         f[BX] = q[EZ]; f[BY] = q[PHI]; f[BZ] = -q[EX];
         f[EX] = -q[BZ]; f[EY] = q[PSI]; f[EZ] = q[BX];
     }
-    f[RHOE] = J[dir];
+    f[RHOE] = dir == 0 ? J[0] : J[1];
     f[PSI] = Ed;
     f[PHI] = Bd;
 }
