@@ -113,18 +113,27 @@ class ClockSampler:
 
 
 def natural_scale(model, want, mu_ref=1.0):
-    """Per-variable scale used for errors (vector components share one; the
-    charge/cleaning fields are scaled by the field magnitude)."""
+    """Per-variable scale used for errors: vector components share one; the
+    charge/cleaning fields are scaled by the field magnitude; for two fluids
+    the mu-weighted totals (Dbar, Sbar, taubar) by mu_ref times D, S, tau."""
     import numpy as np
     m = np.abs(want).reshape(want.shape[0], -1).max(axis=1)
     s = m.copy()
-    for a, b in ((1, 4), (5, 8), (8, 11)):
-        s[a:b] = m[a:b].max()
-    s[11:14] = np.maximum(m[11:14], max(s[5], s[8]))
+    if model == 0:
+        for a, b in ((1, 4), (5, 8), (8, 11)):
+            s[a:b] = m[a:b].max()
+        s[11:14] = np.maximum(m[11:14], max(s[5], s[8]))
+    else:
+        for a, b in ((1, 4), (6, 9), (10, 13), (13, 16)):
+            s[a:b] = m[a:b].max()
+        s[5] = max(m[5], mu_ref * m[0])
+        s[6:9] = max(s[6], mu_ref * s[1])
+        s[9] = max(m[9], mu_ref * m[4])
+        s[16:18] = np.maximum(m[16:18], max(s[10], s[13]))
     return np.maximum(s, 1e-300)
 
 
-def cpu_baseline(seconds: float = 12.0):
+def cpu_baseline(seconds: float = 15.0):
     """FP64 CPU oracle on the host cores: KHI recipe at 128 x 128 (a bounded
     sample of the benchmark workload), as many steps as fit in ~`seconds`."""
     import oracle as O
@@ -137,7 +146,7 @@ def cpu_baseline(seconds: float = 12.0):
     t0 = time.perf_counter()
     s.step(wl.dt, 1)
     t1 = time.perf_counter() - t0
-    steps = max(1, min(200, int(seconds / max(t1, 1e-6))))
+    steps = max(1, min(5000, int(seconds / max(t1, 1e-6))))
     t0 = time.perf_counter()
     s.step(wl.dt, steps)
     el = time.perf_counter() - t0
@@ -172,7 +181,7 @@ def run_reference(args, rank, world):
     s.step(wl.dt, args.steps)
     el = time.perf_counter() - t0
     value = args.steps * wl.cells / el
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
@@ -193,6 +202,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-ensemble workload")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false", help="skip the adjoint-cost workload")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the two-fluid 512^2 and Brio-Wu 1-D workloads")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -233,9 +244,11 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_run(precision, profile):
-        sim = Sim.from_workload(wl, precision=precision, device=f"cuda:{local}")
-        sim.step(wl.dt, W)
+    def timed_run(precision, profile, w=None, k=None):
+        w = wl if w is None else w
+        k = K if k is None else k
+        sim = Sim.from_workload(w, precision=precision, device=f"cuda:{local}")
+        sim.step(w.dt, W)
         sim.check()
         sim.set_profiling(profile)
         st = sim.stream
@@ -243,7 +256,7 @@ def main():
         barrier()
         torch.cuda.synchronize()
         e0.record(st)
-        sim.step(wl.dt, K)
+        sim.step(w.dt, k)
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
@@ -264,6 +277,29 @@ def main():
     total_cells = world * wl.cells
     value = total_cells * K / (ms64 * 1e-3)
     value_mx = total_cells * K / (msmx * 1e-3)
+
+    # the other single-grid workloads: two-fluid current sheet 512^2 (FP64 and
+    # mixed) and the 1-D Brio-Wu tube (400 cells, launch-bound, 100 steps)
+    extra = None
+    if args.extra:
+        tfw = WL.tf_sheet(n=512, seed=1)
+        tf64, ms_tf64, _ = timed_run(FP64, False, tfw)
+        tfmx, ms_tfmx, _ = timed_run(MIXED, False, tfw)
+        qa, qb = tf64.cons(), tfmx.cons()
+        l1_tf = float(np.max(np.abs(qb - qa).reshape(qa.shape[0], -1).mean(axis=1) /
+                             natural_scale(1, qa, abs(tfw.mu_p))))
+        del tf64, tfmx
+        bw = WL.brio_wu()
+        bws, ms_bw, _ = timed_run(FP64, False, bw, 100)
+        del bws
+        extra = {"two_fluid_512": {"fp64": world * tfw.cells * K / (ms_tf64 * 1e-3),
+                                   "mixed": world * tfw.cells * K / (ms_tfmx * 1e-3),
+                                   "ms_per_step_fp64": ms_tf64 / K, "ms_per_step_mixed": ms_tfmx / K,
+                                   "rel_l1_mixed_vs_fp64": l1_tf, "unit": UNIT,
+                                   "workload": "two-fluid current sheet 512x512, mu=+-1e3, sigma=1e4, periodic"},
+                 "brio_wu_400": {"fp64": world * bw.cells * 100 / (ms_bw * 1e-3), "unit": UNIT,
+                                 "us_per_step": 1e3 * ms_bw / 100,
+                                 "workload": "1-D Brio-Wu tube, 400 cells, sigma=100, 100 graph-captured steps"}}
 
     # batched ensemble: 512 independent 1-D shock tubes, N ~ U{100..4096},
     # sigma log-uniform in [1, 1e6], own CFL dt, mixed form, one graph per step
@@ -399,6 +435,7 @@ def main():
                                       "achieved_gbs": step_bytes * value / world / 1e9,
                                       "frac": step_bytes * value / world / 1e9 / hbm_gbs},
                 "batch": batch,
+                "other_workloads": extra,
                 "adjoint": adjoint,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                         "d2h_bytes_per_step": io_bytes},

@@ -56,7 +56,7 @@ __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, do
 __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, const double *LA, double aL,
                            const double *LB, double bL, double *fbar, double *qbar) {
     const int n = dir == 0 ? g.nx : g.ny, m = dir == 0 ? g.ny : g.nx, bc = dir == 0 ? g.bcx : g.bcy;
-    const double h4 = 0.25 / (dir == 0 ? g.dx : g.dy);
+    const double h4 = dir == 0 ? g.rdx4 : g.rdy4;
     const long long nf = (long long)(n + 1) * m * sf::NC;
     const double eps4 = 4e-6;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {

@@ -249,7 +249,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
 #pragma unroll 1
     for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
         const int sstep = dir == 0 ? 1 : SW;
-        const FT inv4h = FT(0.25 / (dir == 0 ? g.dx : g.dy));
+        const FT inv4h = FT(dir == 0 ? g.rdx4 : g.rdy4);
         // 3a. physical flux of every cell the reconstruction needs
         const int ncx = dir == 0 ? SW : TX, ncy = dir == 0 ? TY : SH;
         const int cx0 = dir == 0 ? 0 : 2, cy0 = dir == 0 ? OY : 0;
@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(TX *G, 1) k_flux_batch(Grid g, Phys ph, FluxAr
         gt.nx = b.nx[run];
         gt.ny = 1;
         gt.dx = b.dx[run];
+        gt.rdx4 = b.rdx4[run];
         Phys pt = ph;
         pt.sigma = b.sigma[run];
         pt.eta = b.eta[run];

@@ -57,7 +57,7 @@ struct rmhd_ctx {
     int *d_nx, *d_run_of;
     int2 *d_work;
     long long *d_off;
-    double *d_dx, *d_dt, *d_sigma, *d_eta, *d_adt, *d_cpsi;
+    double *d_dx, *d_rdx4, *d_dt, *d_sigma, *d_eta, *d_adt, *d_cpsi;
     double *h_tab;       // pinned host staging for the per-run time-step tables
     double *Qsave, *Wsave;
     int tile_x, flux_blocks, stage_threads;
@@ -123,12 +123,14 @@ static Grid make_grid(const rmhd_config *cfg) {
     g.plane = (g.ncell + 63) / 64 * 64;
     g.dx = (cfg->xmax - cfg->xmin) / cfg->nx;
     g.dy = cfg->ny > 1 ? (cfg->ymax - cfg->ymin) / cfg->ny : 1.0;
+    g.rdx4 = 0.25 / g.dx;
+    g.rdy4 = 0.25 / g.dy;
     return g;
 }
 
 struct Layout {
     size_t Q, W, Q1, W1, R, ACC, stage, scratch, diag, status;
-    size_t nx, off, dx, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
+    size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
 
@@ -143,6 +145,8 @@ static Grid make_grid_n(const rmhd_config *cfg, long long ncell) {
     g.plane = (ncell + 63) / 64 * 64;
     g.dx = 1.0;
     g.dy = 1.0;
+    g.rdx4 = 0.25;
+    g.rdy4 = 0.25;
     return g;
 }
 
@@ -165,11 +169,12 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
-    L.nx = L.off = L.dx = L.dt = L.sigma = L.eta = L.adt = L.cpsi = L.work = L.run_of = L.Qsave = L.Wsave = 0;
+    L.nx = L.off = L.dx = L.rdx4 = L.dt = L.sigma = L.eta = L.adt = L.cpsi = L.work = L.run_of = L.Qsave = L.Wsave = 0;
     if (nruns > 0) {
         L.nx = o; o += align256((size_t)nruns * sizeof(int));
         L.off = o; o += align256((size_t)nruns * sizeof(long long));
         L.dx = o; o += align256((size_t)nruns * sizeof(double));
+        L.rdx4 = o; o += align256((size_t)nruns * sizeof(double));
         L.dt = o; o += align256((size_t)nruns * sizeof(double));
         L.sigma = o; o += align256((size_t)nruns * sizeof(double));
         L.eta = o; o += align256((size_t)nruns * sizeof(double));
@@ -623,6 +628,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->d_nx = (int *)(c->ws + L.nx);
     c->d_off = (long long *)(c->ws + L.off);
     c->d_dx = (double *)(c->ws + L.dx);
+    c->d_rdx4 = (double *)(c->ws + L.rdx4);
     c->d_dt = (double *)(c->ws + L.dt);
     c->d_sigma = (double *)(c->ws + L.sigma);
     c->d_eta = (double *)(c->ws + L.eta);
@@ -637,13 +643,14 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->run_dx.resize(nruns);
     c->run_sigma.resize(nruns);
     std::vector<int> run_of(g.ncell);
-    std::vector<double> eta(nruns);
+    std::vector<double> eta(nruns), rdx4(nruns);
     long long o = 0;
     for (int r = 0; r < nruns; ++r) {
         c->run_off[r] = o;
         c->run_dx[r] = (base->xmax - base->xmin) / nx[r];
         c->run_sigma[r] = sigma ? sigma[r] : base->sigma;
         eta[r] = 1.0 / c->run_sigma[r];
+        rdx4[r] = 0.25 / c->run_dx[r];
         for (int i = 0; i < nx[r]; ++i) run_of[o + i] = r;
         o += nx[r];
     }
@@ -651,6 +658,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     bool ok = cudaMemcpy(c->d_nx, nx, nruns * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->d_off, c->run_off.data(), nruns * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->d_dx, c->run_dx.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_rdx4, rdx4.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->d_sigma, c->run_sigma.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->d_eta, eta.data(), nruns * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->d_run_of, run_of.data(), g.ncell * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -661,6 +669,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     b.nx = c->d_nx;
     b.offset = c->d_off;
     b.dx = c->d_dx;
+    b.rdx4 = c->d_rdx4;
     b.dt = c->d_dt;
     b.sigma = c->d_sigma;
     b.eta = c->d_eta;

@@ -15,6 +15,7 @@ struct Grid {
     long long ncell;   // nx * ny
     long long plane;
     double dx, dy;
+    double rdx4, rdy4;  // 0.25 / dx, 0.25 / dy (host-computed)
 };
 
 // Physical constants of a run plus host-precomputed reciprocals (the device
@@ -60,6 +61,7 @@ struct BatchArgs {
     const int *nx;             // cells per run
     const long long *offset;   // first packed cell of each run
     const double *dx, *dt;     // cell width and time step per run
+    const double *rdx4;        // 0.25 / dx per run
     const double *sigma, *eta; // conductivity and 1/sigma per run
     const double *adt, *cpsi;  // a_ii dt and 1/(1 + a_ii dt kappa) per run
     const int *run_of;         // run of every packed cell
