@@ -245,12 +245,14 @@ def main():
         return float(t.item())
 
     def timed_run(precision, profile, w=None, k=None):
+        """W warm-up steps, then k timed steps as one CUDA graph per step
+        (the production path). With `profile`, k more steps follow with
+        per-launch CUDA events (no graph) for the per-kernel times."""
         w = wl if w is None else w
         k = K if k is None else k
         sim = Sim.from_workload(w, precision=precision, device=f"cuda:{local}")
         sim.step(w.dt, W)
         sim.check()
-        sim.set_profiling(profile)
         st = sim.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
@@ -261,9 +263,14 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1)
-        kt = sim.kernel_times() if profile else None
-        sim.set_profiling(False)
         sim.check()
+        kt = None
+        if profile:
+            sim.set_profiling(True)
+            sim.step(w.dt, k)
+            kt = sim.kernel_times()
+            sim.set_profiling(False)
+            sim.check()
         return sim, max_over_ranks(ms), kt
 
     with ClockSampler(local) as clk:
