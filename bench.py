@@ -290,8 +290,8 @@ def main():
     extra = None
     if args.extra:
         tfw = WL.tf_sheet(n=512, seed=1)
-        tf64, ms_tf64, _ = timed_run(FP64, False, tfw)
-        tfmx, ms_tfmx, _ = timed_run(MIXED, False, tfw)
+        tf64, ms_tf64, kt_tf64 = timed_run(FP64, True, tfw)
+        tfmx, ms_tfmx, kt_tfmx = timed_run(MIXED, True, tfw)
         qa, qb = tf64.cons(), tfmx.cons()
         l1_tf = float(np.max(np.abs(qb - qa).reshape(qa.shape[0], -1).mean(axis=1) /
                              natural_scale(1, qa, abs(tfw.mu_p))))
@@ -303,6 +303,8 @@ def main():
                                    "mixed": world * tfw.cells * K / (ms_tfmx * 1e-3),
                                    "ms_per_step_fp64": ms_tf64 / K, "ms_per_step_mixed": ms_tfmx / K,
                                    "rel_l1_mixed_vs_fp64": l1_tf, "unit": UNIT,
+                                   "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_tf64.items()},
+                                   "kernels_ms_per_launch_mixed": {k: v[0] / max(v[1], 1) for k, v in kt_tfmx.items()},
                                    "workload": "two-fluid current sheet 512x512, mu=+-1e3, sigma=1e4, periodic"},
                  "brio_wu_400": {"fp64": world * bw.cells * 100 / (ms_bw * 1e-3), "unit": UNIT,
                                  "us_per_step": 1e3 * ms_bw / 100,

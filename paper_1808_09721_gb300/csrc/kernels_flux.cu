@@ -329,14 +329,20 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
         const int slot = M::src_slot(c);
         const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
         const double Lv = (double)L[r];
+        // (slot is uniform over the group: components without a source skip its terms)
         if (MODE == 1) {
             if (inside) {
                 const double b = a.base[c * g.plane + cell];
-                a.out1[c * g.plane + cell] = fma(a.c_src * dt, s, fma(dt, Lv, b));
-                a.out2[c * g.plane + cell] = fma(hdt, Lv + s, b);
+                if (slot >= 0) {
+                    a.out1[c * g.plane + cell] = fma(a.c_src * dt, s, fma(dt, Lv, b));
+                    a.out2[c * g.plane + cell] = fma(hdt, Lv + s, b);
+                } else {
+                    a.out1[c * g.plane + cell] = fma(dt, Lv, b);
+                    a.out2[c * g.plane + cell] = fma(hdt, Lv, b);
+                }
             }
         } else {
-            const double qn = inside ? fma(hdt, Lv + s, a.base[c * g.plane + cell]) : 0.0;
+            const double qn = inside ? fma(hdt, slot >= 0 ? Lv + s : Lv, a.base[c * g.plane + cell]) : 0.0;
             if (inside) a.out1[c * g.plane + cell] = qn;
             qn_sm[c * NL + lid] = qn;
         }
@@ -406,7 +412,11 @@ static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &
 template <class M, class FT, int MODE>
 static cudaError_t launch_flux_m(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
     constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
-    if (g.ny == 1) return launch_flux_t<M, 128, 1, G, FT, MODE>(g, ph, a, s);
+    // 1-D: 32-cell tiles while one wave of them does not fill the 152 SMs
+    // (short tubes are latency-bound on a few SMs), 128-cell tiles beyond
+    if (g.ny == 1)
+        return g.nx <= 32 * 152 ? launch_flux_t<M, 32, 1, G, FT, MODE>(g, ph, a, s)
+                                : launch_flux_t<M, 128, 1, G, FT, MODE>(g, ph, a, s);
     return launch_flux_t<M, 32, 8, G, FT, MODE>(g, ph, a, s);
 }
 
