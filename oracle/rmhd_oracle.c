@@ -506,11 +506,24 @@ static int stage_residual(const stage_ctx *c, const double *x, double *G, double
 static double norm2sq(int n, const double *a) { double s = 0.0; for (int i = 0; i < n; i++) s += a[i] * a[i]; return s; }
 static double norminf(int n, const double *a) { double s = 0.0; for (int i = 0; i < n; i++) if (fabs(a[i]) > s) s = fabs(a[i]); return s; }
 
+/* Scale of round-off in the unknowns: max(|x|, |r_x|, |B|, |E|). x and r_x
+ * enter G together; the field magnitude bounds the Ohm's-law terms of the E
+ * rows (sigma W (E + v x B - (v.E) v), divided by the Jacobian ~ 1 + adt sigma W),
+ * whose products can cancel to far below themselves when the root E ~ 0. */
+static double stage_scale(const stage_ctx *c, int n, const double *x, const double *rs)
+{
+    const double *B = c->r + (c->model == MODEL_SF ? SF_B : TF_B);
+    const double *E = x + (c->model == MODEL_SF ? 0 : 4);
+    double sc = fmax(norminf(n, x), norminf(n, rs));
+    sc = fmax(sc, fmax(norminf(3, B), norminf(3, E)));
+    return fmax(sc, 1e-300);
+}
+
 /* Newton with forward-difference Jacobian and backtracking (Armijo 1e-4,
  * step halved down to 2^-10) from the start x; stops at a round-off fixed
- * point: the accepted step is at most 4 ulp of max(|x|, |r_x|), or the merit
- * 1/2|G|^2 can no longer be decreased while the Newton step is below 1e-10 of
- * that scale (G has reached its round-off floor). */
+ * point: the accepted step is at most 4 ulp of the round-off scale
+ * (stage_scale), or the merit 1/2|G|^2 can no longer be decreased while the
+ * Newton step is below 1e-10 of that scale (G has reached its round-off floor). */
 static int newton_from(const stage_ctx *c, double *x, double *q, double *w, int *iters)
 {
     int n = nunk(c->model);
@@ -550,8 +563,7 @@ static int newton_from(const stage_ctx *c, double *x, double *q, double *w, int 
             }
             t *= 0.5;
         }
-        /* x and r_x enter G together, so round-off in G is relative to both */
-        double scale = fmax(fmax(norminf(n, x), norminf(n, rs)), 1e-300);
+        double scale = stage_scale(c, n, x, rs);
         double step = t * norminf(n, dx);
         if (!accepted) {
             /* No decrease of the merit: G is at its round-off floor. That is the
