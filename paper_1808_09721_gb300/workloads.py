@@ -192,6 +192,27 @@ def field_loop(n: int = 256, seed: int = 3, gamma: float = 2.0, cfl: float = 0.4
                     PERIODIC, PERIODIC, cfl, nsteps, prims)
 
 
+def field_loop_bz(n: int = 64, b0: float = 1e-3, radius: float = 0.3, sigma: float = 1e5,
+                  gamma: float = 2.0, cfl: float = 0.4, rho: float = 3.0, p: float = 1.0,
+                  v=(0.1, 0.1, 0.0), shift: float = 0.0) -> Workload:
+    """Field loop of the convergence test (Sec. 4.3): on [-1/2, 1/2]^2, periodic,
+    rho = 3, v = (0.1, 0.1, 0), p = 1, B_z = b0 (R - r) for r <= R, else 0 (b0 = 1e-3;
+    R is not printed: 0.3), E = -v x B, sigma = 1e5, Gamma = 2. `shift` = t samples
+    the exactly advected profile B_z(x - v t) instead (uniform v: pure advection)."""
+    h = 1.0 / n
+    xc = -0.5 + (np.arange(n) + 0.5) * h
+    Y, X = np.meshgrid(xc, xc, indexing="ij")
+    X = (X - v[0] * shift + 0.5) % 1.0 - 0.5
+    Y = (Y - v[1] * shift + 0.5) % 1.0 - 0.5
+    r = np.sqrt(X ** 2 + Y ** 2)
+    z = np.zeros((n, n))
+    B = np.stack([z, z, np.where(r <= radius, b0 * (radius - r), 0.0)])
+    vv = np.stack([z + v[0], z + v[1], z + v[2]])
+    prims = _sf_prims(np.full((n, n), rho), vv, np.full((n, n), p), B, _ideal_e(vv, B))
+    return Workload("field_loop_bz", RESISTIVE, n, n, (-0.5, 0.5), (-0.5, 0.5), gamma, sigma,
+                    PERIODIC, PERIODIC, cfl, 0, prims)
+
+
 def current_sheet(nx: int = 100, sigma: float = 100.0, t0: float = 1.0, b0: float = 1.0,
                   xlim=(-1.5, 1.5), gamma: float = 2.0, cfl: float = 0.4,
                   p: float = 50.0) -> Workload:

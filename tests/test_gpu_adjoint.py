@@ -137,3 +137,56 @@ def test_adjoint_restores_state_and_repeats(env):
     # of the largest entry, not bit for bit
     np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-12 * np.abs(g1).max())
     assert abs(s2 - s1) <= 1e-10 * abs(s1)
+
+
+def oracle_lin_J(wl, prims, lam, nsteps):
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
+    o.set_prims(np.ascontiguousarray(prims))
+    o.step(wl.dt, nsteps)
+    return float((lam * o.cons()).sum())
+
+
+def oracle_gradient(wl, lam, nsteps, rel=1e-5):
+    """Every entry of dJ/d(prims) of the oracle's forward run, J = sum lam * q,
+    by Richardson-extrapolated central differences (steps rel and rel/2 of the
+    field's magnitude). Accurate to ~1e-7 of max|g|: the solvers' round-off
+    divided by the step, and the WENO3 weights vary on the sqrt(eps) ~ 1e-3
+    scale of the data's differences, which bounds the step from above."""
+    p = wl.prims
+    g = np.zeros_like(p)
+    for v in range(p.shape[0]):
+        h = rel * max(np.abs(p[v]).max(), 1e-2)
+        for idx in np.ndindex(p.shape[1:]):
+            def J(d):
+                q = p.copy()
+                q[(v,) + idx] += d
+                return oracle_lin_J(wl, q, lam, nsteps)
+            d1 = (J(h) - J(-h)) / (2 * h)
+            d2 = (J(h / 2) - J(-h / 2)) / h
+            g[(v,) + idx] = (4 * d2 - d1) / 3
+    return g
+
+
+TINY = [
+    ("brio_wu_10", lambda: WL.brio_wu(nx=10), 3, 2),
+    ("field_loop_6x6", lambda: WL.field_loop(n=6, nsteps=3), 3, 2),
+    ("khi_6x6_stiff", lambda: WL.khi(n=6, seed=3, sigma=1e5), 3, 2),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", TINY)
+def test_adjoint_gradient_entrywise_vs_oracle(env, name, make, nsteps, ckpt):
+    """Brute force on tiny grids: every entry of the GPU adjoint's gradient
+    against the oracle's full difference gradient (the oracle's forward map,
+    not the GPU's), for a random linear functional of the final state."""
+    torch, Sim, _ = env
+    wl = make()
+    lam = np.random.default_rng(5).normal(size=(14,) + wl.prims.shape[1:])
+    s = Sim.from_workload(wl)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, _ = s.adjoint(np.ascontiguousarray(lam))
+    go = oracle_gradient(wl, lam, nsteps)
+    err = np.abs(gp - go).max() / np.abs(go).max()
+    assert err <= 2e-6, (name, err)

@@ -76,17 +76,37 @@ def test_autotune_keeps_state_and_results(Sim):
     np.testing.assert_array_equal(a.cons(), b.cons())
 
 
-def test_full_512_tube_configuration(Sim):
+def _sampled(runs):
+    """Tubes checked against the oracle: the first and last, the one with the
+    coldest dense right state near the initial jump (215), the stiffest and
+    the longest."""
+    sig = int(np.argmax([w.sigma for w in runs]))
+    big = int(np.argmax([w.nx for w in runs]))
+    return sorted({0, 215, len(runs) - 1, sig, big})
+
+
+def test_full_512_tube_configuration_mixed(Sim):
     """The benchmark's 512-tube ensemble (N up to 4096, sigma up to 1e6, density
-    and pressure ratios up to 100) runs without solver failures in the mixed
-    form, and the tube with the coldest dense right state near the initial jump
-    (run 215) matches the oracle."""
+    and pressure ratios up to 100), its whole 400-step run in the mixed form:
+    no solver failure anywhere, and the sampled tubes match the oracle."""
     runs = WL.batch_tubes(count=512, seed=2)
     b = Sim.batch(runs, precision=1)
-    b.step(0.0, 25)
+    b.step(0.0, 400)
     b.check()
     got = b.unpack(b.cons())
-    for r in (215, 0, 511):
-        want = _oracle(runs[r], 25)
+    for r in _sampled(runs):
+        want = _oracle(runs[r], 400)
         l1 = np.abs(got[r] - want).reshape(14, -1).mean(axis=1) / parity_scale(0, want)
         assert np.all(l1 <= 1e-4), (r, l1)
+
+
+def test_full_512_tube_configuration_fp64(Sim):
+    """The same 400-step run in the FP64 form: sampled tubes within 1e-9."""
+    runs = WL.batch_tubes(count=512, seed=2)
+    b = Sim.batch(runs)
+    b.step(0.0, 400)
+    b.check()
+    got = b.unpack(b.cons())
+    for r in _sampled(runs):
+        err = parity_errors(0, got[r], _oracle(runs[r], 400))
+        assert np.all(err <= 1e-9), (r, runs[r].nx, runs[r].sigma, err)
