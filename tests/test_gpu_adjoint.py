@@ -190,3 +190,25 @@ def test_adjoint_gradient_entrywise_vs_oracle(env, name, make, nsteps, ckpt):
     go = oracle_gradient(wl, lam, nsteps)
     err = np.abs(gp - go).max() / np.abs(go).max()
     assert err <= 2e-6, (name, err)
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", TINY)
+def test_adjoint_matches_autodiff_oracle(env, name, make, nsteps, ckpt):
+    """The GPU adjoint against the exact gradient of the same discrete step
+    from the differentiable oracle (reverse-mode autograd of a PyTorch-CPU FP64
+    restatement, pinned to the C oracle): every entry of dJ/d(prims) and dJ/dsigma."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = make()
+    lam = np.random.default_rng(5).normal(size=(14,) + wl.prims.shape[1:])
+    s = Sim.from_workload(wl)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(lam))
+    _, go, gso, _ = A.gradient(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y,
+                               wl.dx, wl.dy, lam)
+    err = np.abs(gp - go).max() / np.abs(go).max()
+    print(name, "entrywise relative error", err, "dJ/dsigma", gs, gso)
+    assert err <= 1e-9, (name, err)
+    assert abs(gs - gso) <= 1e-9 * abs(gso) + 1e-12 * np.abs(go).max(), (name, gs, gso)

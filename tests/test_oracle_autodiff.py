@@ -1,0 +1,71 @@
+"""Pins of the differentiable oracle (oracle/autodiff_sf.py, PyTorch CPU, FP64)
+that serves as the reference of the discrete adjoint: its forward run agrees
+with the independent C oracle to round-off, and its autograd gradient agrees
+with Richardson-extrapolated central differences of the C oracle's forward
+map (accurate to ~1e-7: solver round-off over the step, and WENO3 weights
+that vary on the sqrt(eps) ~ 1e-3 scale of the data's differences)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import parity_errors
+from paper_1808_09721_gb300 import workloads as WL
+
+A = pytest.importorskip("oracle.autodiff_sf")
+
+CASES = [
+    ("brio_wu_10", lambda: WL.brio_wu(nx=10), 3),
+    ("field_loop_6x6", lambda: WL.field_loop(n=6, nsteps=3), 3),
+    ("khi_6x6_stiff", lambda: WL.khi(n=6, seed=3, sigma=1e5), 3),
+]
+
+
+def c_oracle(wl, prims, nsteps, sigma=None):
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma if sigma is None else sigma,
+              wl.bc_x, wl.bc_y)
+    o.set_prims(np.ascontiguousarray(prims))
+    o.step(wl.dt, nsteps)
+    return o.cons()
+
+
+def ad(wl, lam, nsteps):
+    return A.gradient(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, lam)
+
+
+@pytest.mark.parametrize("name,make,nsteps", CASES)
+def test_forward_matches_c_oracle(name, make, nsteps):
+    wl = make()
+    lam = np.zeros((14,) + wl.prims.shape[1:])
+    _, _, _, q = ad(wl, lam, nsteps)
+    err = parity_errors(0, q, c_oracle(wl, wl.prims, nsteps))
+    assert np.all(err <= 1e-12), (name, err)
+
+
+def test_gradient_matches_c_oracle_differences():
+    wl = WL.brio_wu(nx=10)
+    nsteps = 3
+    lam = np.random.default_rng(5).normal(size=(14,) + wl.prims.shape[1:])
+    _, g, gs, _ = ad(wl, lam, nsteps)
+
+    def J(prims, sigma=None):
+        return float((lam * c_oracle(wl, prims, nsteps, sigma)).sum())
+
+    fd = np.zeros_like(g)
+    for v in range(11):
+        h = 1e-5 * max(np.abs(wl.prims[v]).max(), 1e-2)
+        for idx in np.ndindex(wl.prims.shape[1:]):
+            def Jd(d):
+                p = wl.prims.copy()
+                p[(v,) + idx] += d
+                return J(p)
+            d1 = (Jd(h) - Jd(-h)) / (2 * h)
+            d2 = (Jd(h / 2) - Jd(-h / 2)) / h
+            fd[(v,) + idx] = (4 * d2 - d1) / 3
+    assert np.abs(g - fd).max() <= 1e-6 * np.abs(fd).max()
+    h = 1e-4 * wl.sigma
+    d1 = (J(wl.prims, wl.sigma + h) - J(wl.prims, wl.sigma - h)) / (2 * h)
+    d2 = (J(wl.prims, wl.sigma + h / 2) - J(wl.prims, wl.sigma - h / 2)) / h
+    fs = (4 * d2 - d1) / 3
+    assert abs(gs - fs) <= 1e-6 * abs(fs), (gs, fs)
