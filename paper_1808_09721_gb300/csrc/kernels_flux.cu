@@ -22,7 +22,8 @@
 // ghost cells exist in HBM. Per direction the physical flux of every needed
 // cell is computed once into shared memory, then each component is
 // reconstructed and differenced. The epilogue fuses the SSP2(222) stage
-// update (Table 1) and, after the second pass, the final primitive recovery.
+// update (Table 1); after the second pass it carries the stage-2 primitives
+// forward as the next warm start (the final recovery runs on demand).
 #include "rmhd_internal.h"
 #include "physics_sf.cuh"
 #include "physics_tf.cuh"
@@ -35,14 +36,6 @@ __device__ __forceinline__ int map_index(int i, int n, int bc) {
         return i < 0 ? i + n : i;
     }
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
-}
-
-// The status word is one 64-bit key (cell << 8 | -code), initialised to all
-// ones; atomicMin keeps the smallest failing cell together with its own code.
-__device__ __forceinline__ void record_status(int *status, int st, long long cell) {
-    if (st != 0)
-        atomicMin(reinterpret_cast<unsigned long long *>(status),
-                  ((unsigned long long)cell << 8) | (unsigned long long)((-st) & 0xff));
 }
 
 // Barrier over the NTHR threads of component group grp (named barrier 1 + grp;
@@ -118,10 +111,6 @@ struct SFModel {
         s[3] = fma(-ph.kappa, st[sf::PSI * SN + idx], st[sf::RHOE * SN + idx]);
         s[4] = -ph.kappa * st[sf::PHI * SN + idx];
     }
-    static __device__ __forceinline__ int recover(const double q[NC], const double wold[NW], const Phys &ph,
-                                                  double w[NW]) {
-        return sf::recover(q, wold[sf::P], ph.gamma, w);
-    }
 };
 
 struct TFModel {
@@ -156,10 +145,6 @@ struct TFModel {
         tf::source(q, w, ph, full);
         s[0] = full[tf::SBX]; s[1] = full[tf::SBY]; s[2] = full[tf::SBZ]; s[3] = full[tf::TAUB];
         s[4] = full[tf::EX]; s[5] = full[tf::EY]; s[6] = full[tf::EZ]; s[7] = full[tf::PSI]; s[8] = full[tf::PHI];
-    }
-    static __device__ __forceinline__ int recover(const double q[NC], const double wold[NW], const Phys &ph,
-                                                  double w[NW]) {
-        return tf::recover(q, wold, ph, w);
     }
 };
 
@@ -319,9 +304,6 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const bool inside = gi < g.nx && gj < g.ny;
     const long long cell = base + (long long)gj * g.nx + gi;
     const double dt = a.dt, hdt = 0.5 * a.dt;
-    // [NC][NL] staging of q^{n+1} for the recovery (mode 2): reuses the q planes
-    // of the staged state, which are dead here (only the primitive planes are read)
-    double *qn_sm = st;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int c = r * G + grp;
@@ -341,26 +323,15 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                     a.out2[c * g.plane + cell] = fma(hdt, Lv, b);
                 }
             }
-        } else {
-            const double qn = inside ? fma(hdt, slot >= 0 ? Lv + s : Lv, a.base[c * g.plane + cell]) : 0.0;
-            if (inside) a.out1[c * g.plane + cell] = qn;
-            qn_sm[c * NL + lid] = qn;
+        } else if (inside) {
+            a.out1[c * g.plane + cell] = fma(hdt, slot >= 0 ? Lv + s : Lv, a.base[c * g.plane + cell]);
         }
     }
-    if (MODE == 2) {
-        __syncthreads();
-        if (grp == 0 && inside) {
-            double qn[NC], wold[NW], wn[NW];
-#pragma unroll
-            for (int v = 0; v < NC; ++v) qn[v] = qn_sm[v * NL + lid];
-#pragma unroll
-            for (int v = 0; v < NW; ++v) wold[v] = st[(NC + v) * SN + oy * SW + ox];
-            int stc = M::recover(qn, wold, ph, wn);
-            record_status(a.status, stc, cell);
-#pragma unroll
-            for (int v = 0; v < NW; ++v) a.out2[v * g.plane + cell] = wn[v];
-        }
-    }
+    // Mode 2: the primitives of q^{n+1} are not recovered here -- the next
+    // stage-1 solve recovers those of its own state, and output calls recover
+    // on demand. The stage-2 primitives are carried instead as the warm start.
+    if (MODE == 2 && inside)
+        for (int v = grp; v < NW; v += G) a.out2[v * g.plane + cell] = st[(NC + v) * SN + oy * SW + ox];
 }
 
 template <class M, int TX, int TY, int G, class FT, int MODE>

@@ -43,6 +43,7 @@ struct rmhd_ctx {
     double *h_diag;    // pinned host [8]
     bool has_state;
     bool fresh_prims;  // state set by rmhd_set_prims and not stepped since
+    bool w_stale;      // W holds a warm start (stage-2 primitives), not the primitives of Q
     double t;
     cudaGraphExec_t graph;
     double graph_dt;
@@ -275,6 +276,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->t = 0.0;
     c->has_state = false;
     c->fresh_prims = false;
+    c->w_stale = false;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return RMHD_ERR_CUDA; }
     Layout L = layout(cfg);
     if (workspace) {
@@ -351,12 +353,26 @@ int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     c->recording = false;
     c->rec_done = 0;
     c->fresh_prims = true;
+    c->w_stale = false;
+    return RMHD_OK;
+}
+
+// A step leaves in W the stage-2 primitives (the next solve's warm start);
+// the primitives of Q are recovered here when an output call needs them.
+static int ensure_prims(rmhd_ctx *c, const char *what) {
+    if (!c->w_stale) return RMHD_OK;
+    CK(c, launch_recover(c->cfg.model, c->g, c->ph, c->Q, c->W, c->status, c->stream));
+    int st = read_status(c, what);
+    if (st) return st;
+    c->w_stale = false;
     return RMHD_OK;
 }
 
 int rmhd_get_prims(rmhd_ctx *c, double *prims, int where) {
     if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_prims: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_prims: no state (call rmhd_set_prims first)");
+    int st0 = ensure_prims(c, "get_prims");
+    if (st0) return st0;
     CK(c, launch_get_prims(c->cfg.model, c->g, c->ph, c->Q, c->W, c->stage_buf, c->stream));
     return stage_out(c, prims, model_np(c->cfg.model), where);
 }
@@ -379,6 +395,7 @@ int rmhd_set_cons(rmhd_ctx *c, const double *cons, int where) {
     st = read_status(c, "set_cons");
     if (st) return st;
     c->has_state = true;
+    c->w_stale = false;
     return RMHD_OK;
 }
 
@@ -491,10 +508,12 @@ int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
             c->t += dt;
         }
         c->fresh_prims = false;
+        c->w_stale = true;
         if (t_out) *t_out = c->t;
         return RMHD_OK;
     }
     c->fresh_prims = false;
+    c->w_stale = true;
     // Legacy default stream (no graph capture there) or profiling: launch directly.
     if (c->profiling || c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread) {
         for (int n = 0; n < nsteps; ++n) {
@@ -946,6 +965,8 @@ int rmhd_check(rmhd_ctx *c) {
 int rmhd_diagnostics(rmhd_ctx *c, double *out) {
     if (!c || !out) return fail(c, RMHD_ERR_INVALID, "diagnostics: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "diagnostics: no state");
+    int st = ensure_prims(c, "diagnostics");
+    if (st) return st;
     CK(c, launch_diagnostics(c->cfg.model, c->g, c->ph, c->Q, c->W, c->scratch, c->diag, c->stream));
     CK(c, cudaMemcpyAsync(c->h_diag, c->diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
