@@ -54,7 +54,7 @@ struct SFModel {
     static constexpr int NC = sf::NC, NW = sf::NW;
     static constexpr int NAUX = 5;  // J (3), Z = rho h W^2, p + (E^2 + B^2)/2
     static constexpr int NS = 5;    // source slots: E (3), psi, phi
-    static constexpr int G_FP64 = 4, G_FP32 = 4;
+    static constexpr int G_FP64 = 4, G_FP32 = 2;
     static __device__ __forceinline__ int src_slot(int c) {
         return c >= sf::EX && c <= sf::EZ ? c - sf::EX : (c == sf::PSI ? 3 : (c == sf::PHI ? 4 : -1));
     }
@@ -73,8 +73,32 @@ struct SFModel {
         aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
         aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
     }
-    template <class FT, class ST>
-    static __device__ __forceinline__ void cell_flux(const ST *st, const double *aux, int SN, int idx, int dir,
+    // FP32 form: one staged cell from its NV doubles x: the FP64 current and
+    // auxiliaries (stored in FT) and, for an interior cell (s != nullptr), the
+    // FP64 source entries
+    template <class FT>
+    static __device__ __forceinline__ void stage_cell(const double *x, const Phys &ph, FT *aux, int SN, int idx,
+                                                      double *s) {
+        const double *q = x, *w = x + NC;
+        double J[3];
+        sf::current(q, w, ph.sigma, J);
+        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
+                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
+        aux[0 * SN + idx] = (FT)J[0];
+        aux[1 * SN + idx] = (FT)J[1];
+        aux[2 * SN + idx] = (FT)J[2];
+        aux[3 * SN + idx] = (FT)(fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P]);
+        aux[4 * SN + idx] = (FT)fma(0.5, E2B2, w[sf::P]);
+        if (s) {
+            s[0] = -J[0];
+            s[1] = -J[1];
+            s[2] = -J[2];
+            s[3] = fma(-ph.kappa, q[sf::PSI], q[sf::RHOE]);
+            s[4] = -ph.kappa * q[sf::PHI];
+        }
+    }
+    template <class FT, class ST, class AT>
+    static __device__ __forceinline__ void cell_flux(const ST *st, const AT *aux, int SN, int idx, int dir,
                                                      const Phys &ph, FT f[NC]) {
         (void)ph;
         const FT vd = (FT)st[(NC + sf::VX + dir) * SN + idx];
@@ -118,13 +142,21 @@ struct TFModel {
     static constexpr int NAUX = 0;
     static constexpr int NS = 9;  // Sbar (3), taubar, E (3), psi, phi
     static constexpr int G_FP64 = 2, G_FP32 = 4;
+    template <class FT>
+    static __device__ __forceinline__ void stage_cell(const double *x, const Phys &ph, FT *, int, int, double *s) {
+        if (!s) return;
+        double full[NC];
+        tf::source(x, x + NC, ph, full);
+        s[0] = full[tf::SBX]; s[1] = full[tf::SBY]; s[2] = full[tf::SBZ]; s[3] = full[tf::TAUB];
+        s[4] = full[tf::EX]; s[5] = full[tf::EY]; s[6] = full[tf::EZ]; s[7] = full[tf::PSI]; s[8] = full[tf::PHI];
+    }
     static __device__ __forceinline__ int src_slot(int c) {
         return c >= tf::SBX && c <= tf::TAUB ? c - tf::SBX
                : (c >= tf::EX && c <= tf::EZ ? 4 + c - tf::EX : (c == tf::PSI ? 7 : (c == tf::PHI ? 8 : -1)));
     }
     static __device__ __forceinline__ void prep(const double *, int, int, const Phys &, double *) {}
-    template <class FT, class ST>
-    static __device__ __forceinline__ void cell_flux(const ST *st, const double *aux, int SN, int idx, int dir,
+    template <class FT, class ST, class AT>
+    static __device__ __forceinline__ void cell_flux(const ST *st, const AT *aux, int SN, int idx, int dir,
                                                      const Phys &ph, FT f[NC]) {
         (void)aux;
         FT qf[NC], wf[NW];
@@ -156,15 +188,15 @@ template <class M, int TX, int TY, int G, class FT, int MODE>
 struct FluxSmem {
     static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     static constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH, NL = TX * TY;
-    // FP32 flux arithmetic reads an FP32 copy of the staged state (converted
-    // once per staged value); the FP64 copy serves the FP64 current, sources
-    // and recovery
+    // FP32 form: only an FP32 copy of the staged state is kept (converted once
+    // per staged value); the FP64 current and sources are computed from the
+    // loaded doubles while staging, and the auxiliaries are kept in FP32
     static constexpr bool SHADOW = sizeof(FT) < sizeof(double);
     // byte offsets
     static constexpr size_t st = 0;
-    static constexpr size_t st32 = st + sizeof(double) * NV * SN;
+    static constexpr size_t st32 = st + (SHADOW ? 0 : sizeof(double) * NV * SN);
     static constexpr size_t aux = st32 + (SHADOW ? sizeof(float) * NV * SN : 0);
-    static constexpr size_t src = aux + sizeof(double) * M::NAUX * SN;
+    static constexpr size_t src = aux + (SHADOW ? sizeof(float) : sizeof(double)) * M::NAUX * SN;
     static constexpr size_t fl = src + sizeof(double) * M::NS * NL;
     static constexpr size_t hp = fl + sizeof(FT) * NC * SN;
     static constexpr size_t fc = hp + sizeof(FT) * 4 * G * SN;
@@ -198,28 +230,55 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const int grp = tid / NL, lid = tid - grp * NL;
 
     __syncthreads();  // the previous tile of a persistent CTA is done with shared memory
-    // 1. stage the tile + halo (boundary conditions by index map)
-    for (int e = tid; e < NV * SN; e += NT) {
-        int v = e / SN, r = e - v * SN;
-        int sy = r / SW, sx = r - sy * SW;
-        int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
-        int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
-        const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-        const double val = srcp[base + (long long)gj * g.nx + gi];
-        st[e] = val;
-        if (L_::SHADOW) st32[e] = (FT)val;
-    }
-    __syncthreads();
-    // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
-    if (M::NAUX > 0)
-        for (int e = tid; e < SN; e += NT) M::prep(st, SN, e, ph, aux);
-    __syncthreads();
-    for (int e = tid; e < NL; e += NT) {
-        int ty = e / TX, tx = e - ty * TX;
-        double s[M::NS];
-        M::source(st, aux, SN, (ty + OY) * SW + tx + 2, ph, s);
+    if constexpr (L_::SHADOW) {
+        // 1-2 (FP32 form). One thread per staged cell (boundary conditions by
+        // index map): its FP32 copy, its FP64 current and auxiliaries, and the
+        // FP64 sources of interior cells.
+        FT *aux32 = reinterpret_cast<FT *>(smem_raw + L_::aux);
+        for (int e = tid; e < SN; e += NT) {
+            const int sy = e / SW, sx = e - sy * SW;
+            const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
+            const int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
+            const long long gc = base + (long long)gj * g.nx + gi;
+            double x[NV];
 #pragma unroll
-        for (int k = 0; k < M::NS; ++k) src[k * NL + e] = s[k];
+            for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
+#pragma unroll
+            for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) st32[v * SN + e] = (FT)x[v];
+            const int tx = sx - 2, ty = sy - OY;
+            const bool interior = tx >= 0 && tx < TX && ty >= 0 && ty < TY;
+            double s[M::NS];
+            M::template stage_cell<FT>(x, ph, aux32, SN, e, interior ? s : nullptr);
+            if (interior) {
+#pragma unroll
+                for (int k = 0; k < M::NS; ++k) src[k * NL + ty * TX + tx] = s[k];
+            }
+        }
+        __syncthreads();
+    } else {
+        // 1. stage the tile + halo (boundary conditions by index map)
+        for (int e = tid; e < NV * SN; e += NT) {
+            int v = e / SN, r = e - v * SN;
+            int sy = r / SW, sx = r - sy * SW;
+            int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
+            int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
+            const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
+            st[e] = srcp[base + (long long)gj * g.nx + gi];
+        }
+        __syncthreads();
+        // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
+        if (M::NAUX > 0)
+            for (int e = tid; e < SN; e += NT) M::prep(st, SN, e, ph, aux);
+        __syncthreads();
+        for (int e = tid; e < NL; e += NT) {
+            int ty = e / TX, tx = e - ty * TX;
+            double s[M::NS];
+            M::source(st, aux, SN, (ty + OY) * SW + tx + 2, ph, s);
+#pragma unroll
+            for (int k = 0; k < M::NS; ++k) src[k * NL + e] = s[k];
+        }
     }
 
     const int tx = lid % TX, ty = lid / TX;
@@ -243,7 +302,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int idx = (cy0 + cy) * SW + cx0 + cx;
             FT f[NC];
             if constexpr (L_::SHADOW)
-                M::template cell_flux<FT>(st32, aux, SN, idx, dir, ph, f);
+                M::template cell_flux<FT>(st32, reinterpret_cast<const FT *>(aux), SN, idx, dir, ph, f);
             else
                 M::template cell_flux<FT>(st, aux, SN, idx, dir, ph, f);
 #pragma unroll
@@ -261,7 +320,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             // 3b. half points of component c (group grp)
             if (active) {
                 const FT *fv = fl + c * SN;
-                const double *qv = st + c * SN;
+                const double *qv = st + (L_::SHADOW ? 0 : c * SN);
                 const FT *qv32 = st32 + c * SN;
                 for (int e = lid; e < nhx * nhy; e += NL) {
                     int hy = e / nhx, hx = e - hy * nhx;
@@ -331,11 +390,12 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     // stage-1 solve recovers those of its own state, and output calls recover
     // on demand. The stage-2 primitives are carried instead as the warm start.
     if (MODE == 2 && inside)
-        for (int v = grp; v < NW; v += G) a.out2[v * g.plane + cell] = st[(NC + v) * SN + oy * SW + ox];
+        for (int v = grp; v < NW; v += G)
+            a.out2[v * g.plane + cell] = L_::SHADOW ? a.w[v * g.plane + cell] : st[(NC + v) * SN + oy * SW + ox];
 }
 
 template <class M, int TX, int TY, int G, class FT, int MODE>
-__global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs a) {
+__global__ void __launch_bounds__(TX *TY *G, TX *TY *G <= 512 ? 2 : 1) k_flux(Grid g, Phys ph, FluxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     flux_tile<M, TX, TY, G, FT, MODE>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY, 0, smem_raw);
 }
@@ -344,7 +404,7 @@ __global__ void __launch_bounds__(TX *TY *G, 1) k_flux(Grid g, Phys ph, FluxArgs
 // plane: persistent CTAs walk the work list of (run, first cell) tiles; each
 // run has its own size, cell width, time step and conductivity.
 template <class M, int TX, int G, class FT, int MODE>
-__global__ void __launch_bounds__(TX *G, 1) k_flux_batch(Grid g, Phys ph, FluxArgs a, BatchArgs b) {
+__global__ void __launch_bounds__(TX *G, TX *G <= 512 ? 2 : 1) k_flux_batch(Grid g, Phys ph, FluxArgs a, BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int w = blockIdx.x; w < b.nwork; w += gridDim.x) {
         const int2 item = b.work[w];  // (run, first cell)
