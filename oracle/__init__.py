@@ -43,7 +43,7 @@ class _Cfg(C.Structure):
     _fields_ = [("model", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
                 ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("gamma", C.c_double), ("sigma", C.c_double), ("mu_e", C.c_double), ("mu_p", C.c_double),
-                ("kappa", C.c_double), ("bc_x", C.c_int), ("bc_y", C.c_int)]
+                ("kappa", C.c_double), ("bc_x", C.c_int), ("bc_y", C.c_int), ("scheme", C.c_int)]
 
 
 _lib = None
@@ -214,13 +214,14 @@ def get_threads() -> int:
 
 # ---------------------------------------------------------------- grid simulation
 class Sim:
-    """A grid run of the oracle: SSP2(222) IMEX steps with WENO3/LF fluxes."""
+    """A grid run of the oracle: SSP2(222) (scheme 0, Table 1) or SSP3(332)
+    (scheme 1, Table 2) IMEX steps with WENO3/LF fluxes."""
 
     def __init__(self, model, nx, ny, xlim, ylim, gamma, sigma, bc_x, bc_y,
-                 mu_e=-1.0, mu_p=1.0, kappa=1.0):
+                 mu_e=-1.0, mu_p=1.0, kappa=1.0, scheme=0):
         self.model, self.nx, self.ny = model, nx, ny
         self.cfg = _Cfg(model, nx, ny, xlim[0], xlim[1], ylim[0], ylim[1], gamma, sigma,
-                        mu_e, mu_p, kappa, bc_x, bc_y)
+                        mu_e, mu_p, kappa, bc_x, bc_y, scheme)
         self.h = lib().orc_create(C.byref(self.cfg))
         if not self.h:
             raise OracleError(-1, "orc_create")

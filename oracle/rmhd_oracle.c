@@ -1,5 +1,5 @@
 /*
- * rmhd_oracle.c -- plain FP64 CPU oracle for one SSP2(222) IMEX step of
+ * rmhd_oracle.c -- plain FP64 CPU oracle for one SSP2(222) or SSP3(332) IMEX step of
  * resistive single-fluid and two-fluid special-relativistic MHD, written from
  * Wright & Hawke, "Resistive and multi-fluid RMHD on graphics processing
  * units" (arXiv:1808.09721).
@@ -20,7 +20,8 @@
  *     then a one-unknown root in the pressure p (Newton with bisection
  *     safeguard) is iterated to a round-off fixed point. Two-fluid states are
  *     first split into species with the linear decomposition of Sec. 2.1.3.
- *   - Sec. 2.2.1, Eq. (implicit stage) and Table 1: the SSP2(222) IMEX step.
+ *   - Sec. 2.2.1, Eq. (implicit stage) and Tables 1-2: the SSP2(222) and
+ *     SSP3(332) IMEX steps.
  *     Each implicit stage q = r + a*dt*Psi(q) is a per-cell root. Components
  *     with zero source are equal to r; psi and phi are linear; the remaining
  *     unknowns (E for one fluid; Sbar, taubar, E for two fluids) are found by
@@ -62,6 +63,7 @@ typedef struct {
     double xmin, xmax, ymin, ymax;
     double gamma, sigma, mu_e, mu_p, kappa;
     int bc_x, bc_y;
+    int scheme;      /* 0: SSP2(222) (Table 1), 1: SSP3(332) (Table 2) */
 } orc_cfg;
 
 /* Levi-Civita symbol on {0,1,2}. */
@@ -627,7 +629,7 @@ int orc_tf_implicit(const double *r, double adt, double gamma, double sigma, dou
 }
 
 /* ------------------------------------------------------------------ */
-/* Grid, boundary conditions, flux divergence, SSP2(222) step          */
+/* Grid, boundary conditions, flux divergence, IMEX steps              */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
@@ -640,6 +642,7 @@ typedef struct {
     int fail_cell;   /* first failing interior cell (j*nx + i), -1 if none */
     double *q, *w;   /* state with ghosts: [var][NY][NX] */
     double *q1, *w1, *q2, *w2, *L1, *L2, *P1, *P2, *r;
+    double *q3, *w3, *L3, *P3;  /* third stage of SSP3(332) */
 } orc_sim;
 
 static size_t cells(const orc_sim *s) { return (size_t)s->NX * s->NY; }
@@ -677,6 +680,7 @@ orc_sim *orc_create(const orc_cfg *cfg)
 {
     if (cfg->nx < 1 || cfg->ny < 1) return NULL;
     if (cfg->model != MODEL_SF && cfg->model != MODEL_TF) return NULL;
+    if (cfg->scheme != 0 && cfg->scheme != 1) return NULL;
     orc_sim *s = calloc(1, sizeof(orc_sim));
     s->cfg = *cfg;
     s->nc = cfg->model == MODEL_SF ? SF_NC : TF_NC;
@@ -696,6 +700,8 @@ orc_sim *orc_create(const orc_cfg *cfg)
     s->L1 = calloc(nq, sizeof(double)); s->L2 = calloc(nq, sizeof(double));
     s->P1 = calloc(nq, sizeof(double)); s->P2 = calloc(nq, sizeof(double));
     s->r = calloc(nq, sizeof(double));
+    s->q3 = calloc(nq, sizeof(double)); s->w3 = calloc(nw, sizeof(double));
+    s->L3 = calloc(nq, sizeof(double)); s->P3 = calloc(nq, sizeof(double));
     return s;
 }
 
@@ -704,6 +710,7 @@ void orc_destroy(orc_sim *s)
     if (!s) return;
     free(s->q); free(s->w); free(s->q1); free(s->w1); free(s->q2); free(s->w2);
     free(s->L1); free(s->L2); free(s->P1); free(s->P2); free(s->r);
+    free(s->q3); free(s->w3); free(s->L3); free(s->P3);
     free(s);
 }
 
@@ -890,6 +897,24 @@ static int implicit_field(orc_sim *s, const double *r, double adt, double *qo, d
     return status;
 }
 
+/* Ghosts of the new state, then its primitives by recovery (Sec. 2.1.3). */
+static int recover_state(orc_sim *s)
+{
+    int nc = s->nc, nx = s->cfg.nx, ny = s->cfg.ny, status = ORC_OK;
+    fill_ghosts(s, s->q, nc);
+    for (int j = s->gy; j < s->gy + ny; j++)
+        for (int i = s->gx; i < s->gx + nx; i++) {
+            double qc[TF_NC], wc[TF_NW];
+            get_cell(s, s->q, nc, j, i, qc);
+            int c = s->cfg.model == MODEL_SF ? orc_sf_c2p(qc, s->cfg.gamma, wc)
+                                             : orc_tf_c2p(qc, s->cfg.gamma, s->cfg.mu_e, s->cfg.mu_p, wc);
+            if (c && status == ORC_OK) { status = ORC_ERR_C2P; s->fail_cell = (j - s->gy) * nx + (i - s->gx); }
+            put_cell(s, s->w, s->nw, j, i, wc);
+        }
+    fill_ghosts(s, s->w, s->nw);
+    return status;
+}
+
 /* One SSP2(222) IMEX step (Table 1 with gamma = 1 - 1/sqrt(2)):
  *   q1 = q^n + g dt Psi(q1)
  *   q2 = q^n + dt L(q1) + (1 - 2g) dt Psi(q1) + g dt Psi(q2)
@@ -918,26 +943,55 @@ int orc_ssp2_step(orc_sim *s, double dt)
                 size_t k = at(s, v, j, i);
                 s->q[k] = s->q[k] + 0.5 * dt * (s->L1[k] + s->L2[k]) + 0.5 * dt * (s->P1[k] + s->P2[k]);
             }
-    fill_ghosts(s, s->q, nc);
-    int status = ORC_OK;
-    for (int j = s->gy; j < s->gy + ny; j++)
-        for (int i = s->gx; i < s->gx + nx; i++) {
-            double qc[TF_NC], wc[TF_NW];
-            get_cell(s, s->q, nc, j, i, qc);
-            int c = s->cfg.model == MODEL_SF ? orc_sf_c2p(qc, s->cfg.gamma, wc)
-                                             : orc_tf_c2p(qc, s->cfg.gamma, s->cfg.mu_e, s->cfg.mu_p, wc);
-            if (c && status == ORC_OK) { status = ORC_ERR_C2P; s->fail_cell = (j - s->gy) * nx + (i - s->gx); }
-            put_cell(s, s->w, s->nw, j, i, wc);
-        }
-    fill_ghosts(s, s->w, s->nw);
     s->t += dt;
-    return status;
+    return recover_state(s);
+}
+
+/* One SSP3(332) IMEX step (Table 2 with gamma = 1 - 1/sqrt(2)): explicit
+ * tableau rows (0,0,0), (1,0,0), (1/4,1/4,0); implicit rows (g,0,0),
+ * (1-2g,g,0), (1/2-g,0,g); weights (1/6,1/6,2/3) for both.
+ *   q1 = q^n + g dt Psi(q1)
+ *   q2 = q^n + dt L(q1) + dt [(1 - 2g) Psi(q1) + g Psi(q2)]
+ *   q3 = q^n + dt [L(q1) + L(q2)]/4 + dt [(1/2 - g) Psi(q1) + g Psi(q3)]
+ *   q^{n+1} = q^n + dt [L1/6 + L2/6 + 2 L3/3] + dt [Psi1/6 + Psi2/6 + 2 Psi3/3] */
+int orc_ssp3_step(orc_sim *s, double dt)
+{
+    const double g = 1.0 - 1.0 / sqrt(2.0);
+    int nc = s->nc, nx = s->cfg.nx, ny = s->cfg.ny;
+    size_t n = cells(s) * nc;
+    int st = implicit_field(s, s->q, g * dt, s->q1, s->w1);
+    if (st) return st;
+    fill_ghosts(s, s->q1, nc); fill_ghosts(s, s->w1, s->nw);
+    source_field(s, s->q1, s->w1, s->P1);
+    orc_flux_divergence(s, s->q1, s->w1, s->L1);
+    for (size_t k = 0; k < n; k++) s->r[k] = s->q[k] + dt * s->L1[k] + (1.0 - 2.0 * g) * dt * s->P1[k];
+    st = implicit_field(s, s->r, g * dt, s->q2, s->w2);
+    if (st) return st;
+    fill_ghosts(s, s->q2, nc); fill_ghosts(s, s->w2, s->nw);
+    source_field(s, s->q2, s->w2, s->P2);
+    orc_flux_divergence(s, s->q2, s->w2, s->L2);
+    for (size_t k = 0; k < n; k++)
+        s->r[k] = s->q[k] + 0.25 * dt * (s->L1[k] + s->L2[k]) + (0.5 - g) * dt * s->P1[k];
+    st = implicit_field(s, s->r, g * dt, s->q3, s->w3);
+    if (st) return st;
+    fill_ghosts(s, s->q3, nc); fill_ghosts(s, s->w3, s->nw);
+    source_field(s, s->q3, s->w3, s->P3);
+    orc_flux_divergence(s, s->q3, s->w3, s->L3);
+    for (int v = 0; v < nc; v++)
+        for (int j = s->gy; j < s->gy + ny; j++)
+            for (int i = s->gx; i < s->gx + nx; i++) {
+                size_t k = at(s, v, j, i);
+                s->q[k] = s->q[k] + dt * (s->L1[k] / 6.0 + s->L2[k] / 6.0 + 2.0 * s->L3[k] / 3.0) +
+                          dt * (s->P1[k] / 6.0 + s->P2[k] / 6.0 + 2.0 * s->P3[k] / 3.0);
+            }
+    s->t += dt;
+    return recover_state(s);
 }
 
 int orc_step(orc_sim *s, double dt, int nsteps)
 {
     for (int k = 0; k < nsteps; k++) {
-        int st = orc_ssp2_step(s, dt);
+        int st = s->cfg.scheme == 1 ? orc_ssp3_step(s, dt) : orc_ssp2_step(s, dt);
         if (st) return st;
     }
     return ORC_OK;
