@@ -58,6 +58,11 @@ extern "C" {
 #define RMHD_HOST 0
 #define RMHD_DEVICE 1
 
+/* IMEX integrators of Sec. 2.2.1: SSP2(222) (Table 1; 2 implicit stages and
+ * 2 flux passes per step) and SSP3(332) (Table 2; 3 + 3), gamma = 1 - 1/sqrt(2). */
+#define RMHD_SSP2 0
+#define RMHD_SSP3 1
+
 typedef struct rmhd_config {
     int model;        /* RMHD_RESISTIVE or RMHD_TWO_FLUID */
     int nx, ny;       /* interior cells; ny = 1 is a 1-D run along x */
@@ -69,7 +74,8 @@ typedef struct rmhd_config {
     double cfl;       /* dt = cfl * min(dx, dy) when rmhd_imex_step gets dt <= 0 */
     int bc_x, bc_y;   /* RMHD_OUTFLOW or RMHD_PERIODIC */
     int precision;    /* RMHD_FP64 or RMHD_MIXED */
-    int reserved[5];  /* set to 0 */
+    int scheme;       /* RMHD_SSP2 (0, Table 1) or RMHD_SSP3 (1, Table 2); batches: RMHD_SSP2 */
+    int reserved[4];  /* set to 0 */
 } rmhd_config;
 
 typedef struct rmhd_ctx rmhd_ctx;

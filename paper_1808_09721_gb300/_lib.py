@@ -18,6 +18,7 @@ ERRORS = {-1: "RMHD_ERR_INVALID", -2: "RMHD_ERR_CUDA", -3: "RMHD_ERR_NEWTON", -4
 RESISTIVE, TWO_FLUID = 0, 1
 OUTFLOW, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
+SSP2, SSP3 = 0, 1  # IMEX integrators of Tables 1 and 2
 HOST, DEVICE = 0, 1
 
 # every symbol include/rmhd.h declares
@@ -33,7 +34,8 @@ class Config(C.Structure):
                 ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("gamma", C.c_double), ("sigma", C.c_double), ("mu_e", C.c_double), ("mu_p", C.c_double),
                 ("kappa", C.c_double), ("cfl", C.c_double),
-                ("bc_x", C.c_int), ("bc_y", C.c_int), ("precision", C.c_int), ("reserved", C.c_int * 5)]
+                ("bc_x", C.c_int), ("bc_y", C.c_int), ("precision", C.c_int), ("scheme", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class RmhdError(RuntimeError):

@@ -184,7 +184,7 @@ struct TFModel {
 // G component groups of TX*TY threads each: thread (g, l) owns interior cell l
 // and components c = g, g + G, g + 2G, ...; one round of the reconstruction
 // handles G components at once (one per group).
-template <class M, int TX, int TY, int G, class FT, int MODE>
+template <class M, int TX, int TY, int G, class FT, int NOUT>
 struct FluxSmem {
     static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     static constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH, NL = TX * TY;
@@ -207,10 +207,10 @@ struct FluxSmem {
 // cell (i, j) lives at base + j * nx + i in every variable plane. All threads
 // of the CTA call it; it starts with a barrier so that a persistent CTA can
 // process tiles back to back.
-template <class M, int TX, int TY, int G, class FT, int MODE>
+template <class M, int TX, int TY, int G, class FT, int NOUT>
 __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const FluxArgs &a, int i0, int j0,
                                           long long base, unsigned char *smem_raw) {
-    using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
+    using L_ = FluxSmem<M, TX, TY, G, FT, NOUT>;
     constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     constexpr bool TWO_D = TY > 1;
     constexpr int SW = L_::SW, SH = L_::SH, SN = L_::SN, NL = L_::NL;
@@ -362,48 +362,42 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const int gi = i0 + tx, gj = j0 + ty;
     const bool inside = gi < g.nx && gj < g.ny;
     const long long cell = base + (long long)gj * g.nx + gi;
-    const double dt = a.dt, hdt = 0.5 * a.dt;
+    const double dt = a.dt;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int c = r * G + grp;
-        if (c >= NC) continue;
+        if (c >= NC || !inside) continue;
+        // (slot is uniform over the group: components without a source skip its terms)
         const int slot = M::src_slot(c);
         const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
         const double Lv = (double)L[r];
-        // (slot is uniform over the group: components without a source skip its terms)
-        if (MODE == 1) {
-            if (inside) {
-                const double b = a.base[c * g.plane + cell];
-                if (slot >= 0) {
-                    a.out1[c * g.plane + cell] = fma(a.c_src * dt, s, fma(dt, Lv, b));
-                    a.out2[c * g.plane + cell] = fma(hdt, Lv + s, b);
-                } else {
-                    a.out1[c * g.plane + cell] = fma(dt, Lv, b);
-                    a.out2[c * g.plane + cell] = fma(hdt, Lv, b);
-                }
-            }
-        } else if (inside) {
-            a.out1[c * g.plane + cell] = fma(hdt, slot >= 0 ? Lv + s : Lv, a.base[c * g.plane + cell]);
+        const long long o = (long long)c * g.plane + cell;
+        double b = a.base[0][o];
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) {
+            if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];  // outputs often share q^n
+            const double v0 = fma(dt * a.aL[k], Lv, b);
+            a.out[k][o] = slot >= 0 ? fma(dt * a.aS[k], s, v0) : v0;
         }
     }
-    // Mode 2: the primitives of q^{n+1} are not recovered here -- the next
-    // stage-1 solve recovers those of its own state, and output calls recover
-    // on demand. The stage-2 primitives are carried instead as the warm start.
-    if (MODE == 2 && inside)
+    // Last pass of a step: the primitives of q^{n+1} are not recovered here --
+    // the next stage-1 solve recovers those of its own state, and output calls
+    // recover on demand. The stage primitives are carried as the warm start.
+    if (a.wcarry && inside)
         for (int v = grp; v < NW; v += G)
-            a.out2[v * g.plane + cell] = L_::SHADOW ? a.w[v * g.plane + cell] : st[(NC + v) * SN + oy * SW + ox];
+            a.wcarry[v * g.plane + cell] = L_::SHADOW ? a.w[v * g.plane + cell] : st[(NC + v) * SN + oy * SW + ox];
 }
 
-template <class M, int TX, int TY, int G, class FT, int MODE>
+template <class M, int TX, int TY, int G, class FT, int NOUT>
 __global__ void __launch_bounds__(TX *TY *G, TX *TY *G <= 512 ? 2 : 1) k_flux(Grid g, Phys ph, FluxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    flux_tile<M, TX, TY, G, FT, MODE>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY, 0, smem_raw);
+    flux_tile<M, TX, TY, G, FT, NOUT>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY, 0, smem_raw);
 }
 
 // Batched ensemble of 1-D runs packed one after another in every variable
 // plane: persistent CTAs walk the work list of (run, first cell) tiles; each
 // run has its own size, cell width, time step and conductivity.
-template <class M, int TX, int G, class FT, int MODE>
+template <class M, int TX, int G, class FT, int NOUT>
 __global__ void __launch_bounds__(TX *G, TX *G <= 512 ? 2 : 1) k_flux_batch(Grid g, Phys ph, FluxArgs a, BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int w = blockIdx.x; w < b.nwork; w += gridDim.x) {
@@ -419,89 +413,96 @@ __global__ void __launch_bounds__(TX *G, TX *G <= 512 ? 2 : 1) k_flux_batch(Grid
         pt.eta = b.eta[run];
         FluxArgs at = a;
         at.dt = b.dt[run];
-        flux_tile<M, TX, 1, G, FT, MODE>(gt, pt, at, item.y, 0, b.offset[run], smem_raw);
+        flux_tile<M, TX, 1, G, FT, NOUT>(gt, pt, at, item.y, 0, b.offset[run], smem_raw);
     }
 }
 
-template <class M, int TX, int TY, int G, class FT, int MODE>
+template <class M, int TX, int TY, int G, class FT, int NOUT>
 static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
-    using L_ = FluxSmem<M, TX, TY, G, FT, MODE>;
+    using L_ = FluxSmem<M, TX, TY, G, FT, NOUT>;
     static_assert(L_::total <= 227 * 1024, "shared memory budget");
     const size_t smem = L_::total;
     static bool configured = false;  // attribute is per device function; set once
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, G, FT, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, G, FT, NOUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((g.nx + TX - 1) / TX, TY > 1 ? (g.ny + TY - 1) / TY : g.ny);
-    k_flux<M, TX, TY, G, FT, MODE><<<grid, TX * TY * G, smem, s>>>(g, ph, a);
+    k_flux<M, TX, TY, G, FT, NOUT><<<grid, TX * TY * G, smem, s>>>(g, ph, a);
     return cudaGetLastError();
 }
 
-template <class M, class FT, int MODE>
+template <class M, class FT, int NOUT>
 static cudaError_t launch_flux_m(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
     constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
     // 1-D: 32-cell tiles while one wave of them does not fill the 152 SMs
     // (short tubes are latency-bound on a few SMs), 128-cell tiles beyond
     if (g.ny == 1)
-        return g.nx <= 32 * 152 ? launch_flux_t<M, 32, 1, G, FT, MODE>(g, ph, a, s)
-                                : launch_flux_t<M, 128, 1, G, FT, MODE>(g, ph, a, s);
-    return launch_flux_t<M, 32, 8, G, FT, MODE>(g, ph, a, s);
+        return g.nx <= 32 * 152 ? launch_flux_t<M, 32, 1, G, FT, NOUT>(g, ph, a, s)
+                                : launch_flux_t<M, 128, 1, G, FT, NOUT>(g, ph, a, s);
+    return launch_flux_t<M, 32, 8, G, FT, NOUT>(g, ph, a, s);
 }
 
-cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+template <class M, class FT>
+static cudaError_t launch_flux_n(int nout, const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
+    if (nout == 1) return launch_flux_m<M, FT, 1>(g, ph, a, s);
+    if (nout == 2) return launch_flux_m<M, FT, 2>(g, ph, a, s);
+    if (nout == 3) return launch_flux_m<M, FT, 3>(g, ph, a, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                         cudaStream_t s) {
-    if (model == 0) {
-        if (precision == 0)
-            return mode == 1 ? launch_flux_m<SFModel, double, 1>(g, ph, a, s) : launch_flux_m<SFModel, double, 2>(g, ph, a, s);
-        return mode == 1 ? launch_flux_m<SFModel, float, 1>(g, ph, a, s) : launch_flux_m<SFModel, float, 2>(g, ph, a, s);
-    }
-    if (precision == 0)
-        return mode == 1 ? launch_flux_m<TFModel, double, 1>(g, ph, a, s) : launch_flux_m<TFModel, double, 2>(g, ph, a, s);
-    return mode == 1 ? launch_flux_m<TFModel, float, 1>(g, ph, a, s) : launch_flux_m<TFModel, float, 2>(g, ph, a, s);
+    if (model == 0)
+        return precision == 0 ? launch_flux_n<SFModel, double>(nout, g, ph, a, s)
+                              : launch_flux_n<SFModel, float>(nout, g, ph, a, s);
+    return precision == 0 ? launch_flux_n<TFModel, double>(nout, g, ph, a, s)
+                          : launch_flux_n<TFModel, float>(nout, g, ph, a, s);
 }
 
 // ---- batched ensemble ------------------------------------------------------
-template <class M, int TX, class FT, int MODE>
+template <class M, int TX, class FT, int NOUT>
 static cudaError_t launch_fb_t(const Grid &g, const Phys &ph, const FluxArgs &a, const BatchArgs &b, int blocks,
                                cudaStream_t s) {
     constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
-    using L_ = FluxSmem<M, TX, 1, G, FT, MODE>;
+    using L_ = FluxSmem<M, TX, 1, G, FT, NOUT>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux_batch<M, TX, G, FT, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_flux_batch<M, TX, G, FT, NOUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L_::total);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_flux_batch<M, TX, G, FT, MODE><<<blocks, TX * G, L_::total, s>>>(g, ph, a, b);
+    k_flux_batch<M, TX, G, FT, NOUT><<<blocks, TX * G, L_::total, s>>>(g, ph, a, b);
     return cudaGetLastError();
 }
 
-template <class M, class FT, int MODE>
+template <class M, class FT, int NOUT>
 static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a, const BatchArgs &b, int tile_x,
                                int blocks, cudaStream_t s) {
-    if (tile_x == 64) return launch_fb_t<M, 64, FT, MODE>(g, ph, a, b, blocks, s);
-    if (tile_x == 256) return launch_fb_t<M, 256, FT, MODE>(g, ph, a, b, blocks, s);
-    return launch_fb_t<M, 128, FT, MODE>(g, ph, a, b, blocks, s);
+    if (tile_x == 64) return launch_fb_t<M, 64, FT, NOUT>(g, ph, a, b, blocks, s);
+    if (tile_x == 256) return launch_fb_t<M, 256, FT, NOUT>(g, ph, a, b, blocks, s);
+    return launch_fb_t<M, 128, FT, NOUT>(g, ph, a, b, blocks, s);
 }
 
-cudaError_t launch_flux_batch(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+// Batches run SSP2(222): passes with two outputs (r2, acc) and one (q^{n+1}).
+cudaError_t launch_flux_batch(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                               const BatchArgs &b, int tile_x, int blocks, cudaStream_t s) {
+    if (nout != 1 && nout != 2) return cudaErrorInvalidValue;
     if (model == 0) {
         if (precision == 0)
-            return mode == 1 ? launch_fb_m<SFModel, double, 1>(g, ph, a, b, tile_x, blocks, s)
-                             : launch_fb_m<SFModel, double, 2>(g, ph, a, b, tile_x, blocks, s);
-        return mode == 1 ? launch_fb_m<SFModel, float, 1>(g, ph, a, b, tile_x, blocks, s)
-                         : launch_fb_m<SFModel, float, 2>(g, ph, a, b, tile_x, blocks, s);
+            return nout == 2 ? launch_fb_m<SFModel, double, 2>(g, ph, a, b, tile_x, blocks, s)
+                             : launch_fb_m<SFModel, double, 1>(g, ph, a, b, tile_x, blocks, s);
+        return nout == 2 ? launch_fb_m<SFModel, float, 2>(g, ph, a, b, tile_x, blocks, s)
+                         : launch_fb_m<SFModel, float, 1>(g, ph, a, b, tile_x, blocks, s);
     }
     if (precision == 0)
-        return mode == 1 ? launch_fb_m<TFModel, double, 1>(g, ph, a, b, tile_x, blocks, s)
-                         : launch_fb_m<TFModel, double, 2>(g, ph, a, b, tile_x, blocks, s);
-    return mode == 1 ? launch_fb_m<TFModel, float, 1>(g, ph, a, b, tile_x, blocks, s)
-                     : launch_fb_m<TFModel, float, 2>(g, ph, a, b, tile_x, blocks, s);
+        return nout == 2 ? launch_fb_m<TFModel, double, 2>(g, ph, a, b, tile_x, blocks, s)
+                         : launch_fb_m<TFModel, double, 1>(g, ph, a, b, tile_x, blocks, s);
+    return nout == 2 ? launch_fb_m<TFModel, float, 2>(g, ph, a, b, tile_x, blocks, s)
+                     : launch_fb_m<TFModel, float, 1>(g, ph, a, b, tile_x, blocks, s);
 }
 
 template <class M, int TX, class FT>

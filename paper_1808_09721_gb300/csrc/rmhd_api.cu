@@ -38,6 +38,7 @@ struct rmhd_ctx {
     char *ws;
     size_t ws_bytes;
     double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
+    double *R3;  // SSP3(332): q^n + dt/4 L1 + (1/2 - gamma) dt Psi1 (null for SSP2)
     int *status;       // device [2]
     int *h_status;     // pinned host copy of the 64-bit status key
     double *h_diag;    // pinned host [8]
@@ -111,6 +112,7 @@ static int validate(const rmhd_config *cfg) {
     if ((cfg->bc_x != RMHD_OUTFLOW && cfg->bc_x != RMHD_PERIODIC) || (cfg->bc_y != RMHD_OUTFLOW && cfg->bc_y != RMHD_PERIODIC))
         return RMHD_ERR_INVALID;
     if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED) return RMHD_ERR_INVALID;
+    if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
     return RMHD_OK;
 }
 
@@ -130,7 +132,7 @@ static Grid make_grid(const rmhd_config *cfg) {
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, stage, scratch, diag, status;
+    size_t Q, W, Q1, W1, R, ACC, R3, stage, scratch, diag, status;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -165,6 +167,8 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.Q1 = o; o += align256(nc * pl);
     L.W1 = o; o += align256(nw * pl);
     L.R = o; o += align256(nc * pl);
+    L.R3 = 0;
+    if (cfg->scheme == RMHD_SSP3) { L.R3 = o; o += align256(nc * pl); }
     L.ACC = o; o += align256(nc * pl);
     L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
@@ -294,6 +298,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->W1 = (double *)(c->ws + L.W1);
     c->R = (double *)(c->ws + L.R);
     c->ACC = (double *)(c->ws + L.ACC);
+    c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -424,19 +429,50 @@ static int toc(rmhd_ctx *c) {
         if (st_) return st_;            \
     } while (0)
 
+// Flux-pass arguments: the stage state (q, w), then outputs added one by one
+// as out = base + dt (aL L + aS Psi).
+static FluxArgs flux_args(const double *q, const double *w, double dt) {
+    FluxArgs a{};
+    a.q = q;
+    a.w = w;
+    a.dt = dt;
+    return a;
+}
+static int add_out(FluxArgs &a, int k, const double *base, double *out, double aL, double aS) {
+    a.base[k] = base;
+    a.out[k] = out;
+    a.aL[k] = aL;
+    a.aS[k] = aS;
+    return k + 1;
+}
+
+// SSP2(222) flux passes (Table 1): pass 1 forms r2 = q^n + dt L1 + (1 - 2g) dt Psi1
+// and acc = q^n + dt/2 (L1 + Psi1); pass 2 forms q^{n+1} = acc + dt/2 (L2 + Psi2).
+static int ssp2_pass1(rmhd_ctx *c, const double *q1, const double *w1, double dt, FluxArgs &a) {
+    a = flux_args(q1, w1, dt);
+    int n = add_out(a, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma);
+    return add_out(a, n, c->Q, c->ACC, 0.5, 0.5);
+}
+static int ssp2_pass2(rmhd_ctx *c, const double *q2, const double *w2, double dt, FluxArgs &a) {
+    a = flux_args(q2, w2, dt);
+    a.wcarry = c->W;
+    return add_out(a, 0, c->ACC, c->Q, 0.5, 0.5);
+}
+
 // One SSP2(222) step of a batch: per-run dt, a_ii dt and 1/(1 + a_ii dt kappa)
 // come from the device tables (uploaded by upload_dt_tables).
 static int enqueue_step_batch(rmhd_ctx *c) {
     const int m = c->cfg.model;
+    FluxArgs f;
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, 0.0};
     LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s1, c->bargs, c->stage_threads, c->stream));
-    FluxArgs f1{c->Q1, c->W1, c->Q, c->R, c->ACC, c->status, 0.0, 1.0 - 2.0 * kGamma};
-    LAUNCH(c, RMHD_K_FLUX1, launch_flux_batch(m, c->cfg.precision, 1, c->g, c->ph, f1, c->bargs, c->tile_x,
+    int n = ssp2_pass1(c, c->Q1, c->W1, 0.0, f);
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux_batch(m, c->cfg.precision, n, c->g, c->ph, f, c->bargs, c->tile_x,
                                               c->flux_blocks, c->stream));
     StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, 0.0};
     LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s2, c->bargs, c->stage_threads, c->stream));
-    FluxArgs f2{c->Q1, c->W1, c->ACC, c->Q, c->W, c->status, 0.0, 0.0};
-    LAUNCH(c, RMHD_K_FLUX2, launch_flux_batch(m, c->cfg.precision, 2, c->g, c->ph, f2, c->bargs, c->tile_x,
+    n = ssp2_pass2(c, c->Q1, c->W1, 0.0, f);
+    LAUNCH(c, RMHD_K_FLUX2, launch_flux_batch(m, c->cfg.precision, n, c->g, c->ph, f, c->bargs, c->tile_x,
                                               c->flux_blocks, c->stream));
     return RMHD_OK;
 }
@@ -461,18 +497,51 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
     return RMHD_OK;
 }
 
-// Enqueue one SSP2(222) step with time step dt.
-static int enqueue_step(rmhd_ctx *c, double dt) {
-    if (c->batch) return enqueue_step_batch(c);
-    const int m = c->cfg.model;
+// SSP3(332) step (Table 2): three implicit stages (each in place in Q1/W1)
+// and three flux passes:
+//   pass 1: r2 = q^n + dt L1 + (1 - 2g) dt Psi1,  r3' = q^n + dt/4 L1 + (1/2 - g) dt Psi1,
+//           acc = q^n + dt/6 (L1 + Psi1)
+//   pass 2: r3 = r3' + dt/4 L2,  acc += dt/6 (L2 + Psi2)
+//   pass 3: q^{n+1} = acc + 2 dt/3 (L3 + Psi3)
+static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
+    const int m = c->cfg.model, pr = c->cfg.precision;
+    FluxArgs f;
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
-    FluxArgs f1{c->Q1, c->W1, c->Q, c->R, c->ACC, c->status, dt, 1.0 - 2.0 * kGamma};
-    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, c->cfg.precision, 1, c->g, c->ph, f1, c->stream));
+    f = flux_args(c->Q1, c->W1, dt);
+    int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma);
+    n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma);
+    n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
     StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
-    FluxArgs f2{c->Q1, c->W1, c->ACC, c->Q, c->W, c->status, dt, 0.0};
-    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, c->cfg.precision, 2, c->g, c->ph, f2, c->stream));
+    f = flux_args(c->Q1, c->W1, dt);
+    n = add_out(f, 0, c->R3, c->R, 0.25, 0.0);
+    n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
+    StageArgs s3{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s3, c->stream));
+    f = flux_args(c->Q1, c->W1, dt);
+    f.wcarry = c->W;
+    n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0);
+    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
+    return RMHD_OK;
+}
+
+// Enqueue one IMEX step with time step dt.
+static int enqueue_step(rmhd_ctx *c, double dt) {
+    if (c->batch) return enqueue_step_batch(c);
+    if (c->cfg.scheme == RMHD_SSP3) return enqueue_step_ssp3(c, dt);
+    const int m = c->cfg.model;
+    FluxArgs f;
+    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
+    int n = ssp2_pass1(c, c->Q1, c->W1, dt, f);
+    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
+    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
+    n = ssp2_pass2(c, c->Q1, c->W1, dt, f);
+    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
     return RMHD_OK;
 }
 
@@ -563,6 +632,7 @@ static int validate_batch(const rmhd_config *base, int nruns, const int *nx, con
         if (sigma && !(sigma[r] > 0.0 && std::isfinite(sigma[r]))) return RMHD_ERR_INVALID;
     }
     if (tot > (1LL << 31) - 1) return RMHD_ERR_INVALID;
+    if (base->scheme != RMHD_SSP2) return RMHD_ERR_INVALID;
     one.nx = (int)std::min<long long>(tot, 1 << 30);
     return validate(&one);
 }
@@ -640,6 +710,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->W1 = (double *)(c->ws + L.W1);
     c->R = (double *)(c->ws + L.R);
     c->ACC = (double *)(c->ws + L.ACC);
+    c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -806,8 +877,8 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch)
-        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 single-grid contexts only");
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->cfg.scheme != RMHD_SSP2)
+        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 SSP2(222) single-grid contexts only");
     if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
     return RMHD_OK;
@@ -865,14 +936,15 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
 // and arithmetic as enqueue_step, so the recomputation reproduces the run).
 static int enqueue_step_into(rmhd_ctx *c, double dt, double *q1, double *w1, double *q2, double *w2) {
     const int m = c->cfg.model;
+    FluxArgs f;
     StageArgs s1{c->Q, c->W, q1, w1, c->status, kGamma * dt};
     CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
-    FluxArgs f1{q1, w1, c->Q, c->R, c->ACC, c->status, dt, 1.0 - 2.0 * kGamma};
-    CK(c, launch_flux(m, c->cfg.precision, 1, c->g, c->ph, f1, c->stream));
+    int n = ssp2_pass1(c, q1, w1, dt, f);
+    CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
     StageArgs s2{c->R, w1, q2, w2, c->status, kGamma * dt};
     CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
-    FluxArgs f2{q2, w2, c->ACC, c->Q, c->W, c->status, dt, 0.0};
-    CK(c, launch_flux(m, c->cfg.precision, 2, c->g, c->ph, f2, c->stream));
+    n = ssp2_pass2(c, q2, w2, dt, f);
+    CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
     return RMHD_OK;
 }
 

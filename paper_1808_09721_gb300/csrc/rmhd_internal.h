@@ -28,20 +28,18 @@ struct Phys {
     double imur;     // 1 / mur
 };
 
-// Coefficients of one flux pass.
-//  mode 1 (after stage 1):  out1 = base + dt L + c_src dt Psi      (stage-2 explicit part)
-//                           out2 = base + dt/2 (L + Psi)           (carried accumulator)
-//  mode 2 (after stage 2):  out1 = base + dt/2 (L + Psi)           (q^{n+1})
-//                           out2 = primitives of out1               (recovery)
+// One flux pass of an IMEX step (Eq. implicit stage / correction stage):
+// L and Psi of the stage state are combined into nout (1-3) outputs, e.g. for
+// SSP2(222) pass 1: r2 = q^n + dt L + (1 - 2 gamma) dt Psi and
+// acc = q^n + dt/2 (L + Psi); pass 2: q^{n+1} = acc + dt/2 (L + Psi).
 struct FluxArgs {
-    const double *q;     // stage state, NC planes
-    const double *w;     // stage primitives, NW planes
-    const double *base;  // q^n (mode 1) or the accumulator (mode 2), NC planes
-    double *out1;
-    double *out2;
-    int *status;         // 64-bit key: smallest failing cell << 8 | -code (all ones: none)
+    const double *q;        // stage state, NC planes
+    const double *w;        // stage primitives, NW planes
+    const double *base[3];  // base of each output (may be the output itself: in-place update)
+    double *out[3];         // out[k] = base[k] + dt (aL[k] L + aS[k] Psi), k < nout
+    double aL[3], aS[3];
+    double *wcarry;         // if not null: the stage primitives are copied here (next warm start)
     double dt;
-    double c_src;        // (1 - 2 gamma_ssp) for mode 1
 };
 
 struct StageArgs {
@@ -69,7 +67,7 @@ struct BatchArgs {
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s);
-cudaError_t launch_flux(int model, int precision, int mode, const Grid &g, const Phys &ph, const FluxArgs &a,
+cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                         cudaStream_t s);
 // primitives (user layout, device) -> conserved + internal primitives
 cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const double *prims, double *q, double *w,

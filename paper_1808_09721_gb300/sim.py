@@ -23,12 +23,12 @@ class Sim:
 
     def __init__(self, model: int, nx: int, ny: int, xlim, ylim, gamma: float, sigma: float,
                  bc_x: int, bc_y: int, cfl: float = 0.4, mu_e: float = -1.0, mu_p: float = 1.0,
-                 kappa: float = 1.0, precision: int = L.FP64, device=None):
+                 kappa: float = 1.0, precision: int = L.FP64, device=None, scheme: int = L.SSP2):
         torch = _torch()
         self.lib = L.load()
         self.device = torch.device("cuda" if device is None else device)
         self.cfg = L.Config(model, nx, ny, xlim[0], xlim[1], ylim[0], ylim[1], gamma, sigma, mu_e, mu_p,
-                            kappa, cfl, bc_x, bc_y, precision)
+                            kappa, cfl, bc_x, bc_y, precision, scheme)
         self.model, self.nx, self.ny = model, nx, ny
         nbytes = C.c_size_t()
         self._check(self.lib.rmhd_workspace_bytes(C.byref(self.cfg), C.byref(nbytes)), None)
@@ -49,9 +49,9 @@ class Sim:
         return BatchSim(workloads, precision, device)
 
     @classmethod
-    def from_workload(cls, wl, precision: int = L.FP64, device=None):
+    def from_workload(cls, wl, precision: int = L.FP64, device=None, scheme: int = L.SSP2):
         s = cls(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl,
-                wl.mu_e, wl.mu_p, wl.kappa, precision, device)
+                wl.mu_e, wl.mu_p, wl.kappa, precision, device, scheme)
         s.set_prims(wl.prims)
         return s
 

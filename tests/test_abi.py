@@ -77,3 +77,17 @@ def test_batch_workspace_bytes(lib):
     bad = (C.c_int * 2)(10, 0)
     assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 2, bad, C.byref(n)) == -1
     assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 0, nx, C.byref(n)) == -1
+
+
+def test_scheme_selection(lib):
+    """SSP3(332) (scheme 1, Table 2) needs one more 14-plane buffer than
+    SSP2(222); other schemes are invalid; batches take SSP2(222) only."""
+    n2, n3 = C.c_size_t(), C.c_size_t()
+    assert lib.rmhd_workspace_bytes(C.byref(_cfg(scheme=0)), C.byref(n2)) == 0
+    assert lib.rmhd_workspace_bytes(C.byref(_cfg(scheme=1)), C.byref(n3)) == 0
+    plane = (64 * 32 + 63) // 64 * 64 * 8
+    assert n3.value - n2.value == (14 * plane + 255) // 256 * 256
+    assert lib.rmhd_workspace_bytes(C.byref(_cfg(scheme=2)), C.byref(n3)) == -1
+    nx = (C.c_int * 2)(100, 200)
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1, scheme=1)), 2, nx, C.byref(n3)) == -1
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1, scheme=0)), 2, nx, C.byref(n3)) == 0
