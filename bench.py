@@ -247,13 +247,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_run(precision, profile, w=None, k=None):
+    def timed_run(precision, profile, w=None, k=None, scheme=0):
         """W warm-up steps, then k timed steps as one CUDA graph per step
         (the production path). With `profile`, k more steps follow with
         per-launch CUDA events (no graph) for the per-kernel times."""
         w = wl if w is None else w
         k = K if k is None else k
-        sim = Sim.from_workload(w, precision=precision, device=f"cuda:{local}")
+        sim = Sim.from_workload(w, precision=precision, device=f"cuda:{local}", scheme=scheme)
         sim.step(w.dt, W)
         sim.check()
         st = sim.stream
@@ -302,6 +302,9 @@ def main():
         bw = WL.brio_wu()
         bws, ms_bw, _ = timed_run(FP64, False, bw, 100)
         del bws
+        s3, ms_s3, kt_s3 = timed_run(FP64, True, None, None, 1)
+        s3m, ms_s3m, _ = timed_run(MIXED, False, None, None, 1)
+        del s3, s3m
         extra = {"two_fluid_512": {"fp64": world * tfw.cells * K / (ms_tf64 * 1e-3),
                                    "mixed": world * tfw.cells * K / (ms_tfmx * 1e-3),
                                    "ms_per_step_fp64": ms_tf64 / K, "ms_per_step_mixed": ms_tfmx / K,
@@ -309,6 +312,12 @@ def main():
                                    "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_tf64.items()},
                                    "kernels_ms_per_launch_mixed": {k: v[0] / max(v[1], 1) for k, v in kt_tfmx.items()},
                                    "workload": "two-fluid current sheet 512x512, mu=+-1e3, sigma=1e4, periodic"},
+                 "khi_1024_ssp3": {"fp64": world * wl.cells * K / (ms_s3 * 1e-3),
+                                   "mixed": world * wl.cells * K / (ms_s3m * 1e-3),
+                                   "ms_per_step_fp64": ms_s3 / K, "ms_per_step_mixed": ms_s3m / K,
+                                   "unit": UNIT,
+                                   "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_s3.items()},
+                                   "workload": "KHI 1024x1024 with SSP3(332) (Table 2): 3 implicit stages, 3 flux passes"},
                  "brio_wu_400": {"fp64": world * bw.cells * 100 / (ms_bw * 1e-3), "unit": UNIT,
                                  "us_per_step": 1e3 * ms_bw / 100,
                                  "workload": "1-D Brio-Wu tube, 400 cells, sigma=100, 100 graph-captured steps"}}
