@@ -122,13 +122,18 @@ def natural_scale(model, want, mu_ref=1.0):
     import numpy as np
     m = np.abs(want).reshape(want.shape[0], -1).max(axis=1)
     s = m.copy()
+    bs, es = (5, 8) if model == 0 else (10, 13)
+    B, E = want[bs:bs + 3], want[es:es + 3]
+    exb = float(np.max(np.sqrt((B * B).sum(axis=0) * (E * E).sum(axis=0))))  # S includes E x B
     if model == 0:
         for a, b in ((1, 4), (5, 8), (8, 11)):
             s[a:b] = m[a:b].max()
+        s[1:4] = max(s[1], exb)
         s[11:14] = np.maximum(m[11:14], max(s[5], s[8]))
     else:
         for a, b in ((1, 4), (6, 9), (10, 13), (13, 16)):
             s[a:b] = m[a:b].max()
+        s[1:4] = max(s[1], exb)
         s[5] = max(m[5], mu_ref * m[0])
         s[6:9] = max(s[6], mu_ref * s[1])
         s[9] = max(m[9], mu_ref * m[4])
@@ -302,6 +307,9 @@ def main():
         bw = WL.brio_wu()
         bws, ms_bw, _ = timed_run(FP64, False, bw, 100)
         del bws
+        tbw = WL.tf_brio_wu(nx=1600)
+        tbws, ms_tbw, _ = timed_run(FP64, False, tbw, 100)
+        del tbws
         s3, ms_s3, kt_s3 = timed_run(FP64, True, None, None, 1)
         s3m, ms_s3m, _ = timed_run(MIXED, False, None, None, 1)
         del s3, s3m
@@ -318,6 +326,9 @@ def main():
                                    "unit": UNIT,
                                    "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_s3.items()},
                                    "workload": "KHI 1024x1024 with SSP3(332) (Table 2): 3 implicit stages, 3 flux passes"},
+                 "tf_brio_wu_1600": {"fp64": world * tbw.cells * 100 / (ms_tbw * 1e-3), "unit": UNIT,
+                                     "us_per_step": 1e3 * ms_tbw / 100,
+                                     "workload": "1-D two-fluid Brio-Wu, pair plasma mu=+-1e3, 1600 cells, 100 steps"},
                  "brio_wu_400": {"fp64": world * bw.cells * 100 / (ms_bw * 1e-3), "unit": UNIT,
                                  "us_per_step": 1e3 * ms_bw / 100,
                                  "workload": "1-D Brio-Wu tube, 400 cells, sigma=100, 100 graph-captured steps"}}

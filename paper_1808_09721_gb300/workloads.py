@@ -144,6 +144,49 @@ def tf_sheet(n: int = 512, seed: int = 1, sigma: float = 1e4, mu: float = 1e3,
                     PERIODIC, PERIODIC, cfl, nsteps, np.ascontiguousarray(prims), mu_e=-mu, mu_p=mu)
 
 
+def _tf_species_prims(rho, p, v, B, E, mu_e, mu_p):
+    """Neutral two-species plasma from totals: equal number densities (charges
+    +-q, so masses m_s ~ 1/|mu_s| and rho_p / rho_e = |mu_e / mu_p|), equal
+    temperatures (p_s = p / 2), both species moving with v."""
+    frac_e = abs(mu_p) / (abs(mu_e) + abs(mu_p))
+    return np.concatenate([(frac_e * rho)[None], v, (0.5 * p)[None],
+                           ((1.0 - frac_e) * rho)[None], v, (0.5 * p)[None], B, E]).astype(np.float64)
+
+
+def tf_brio_wu(nx: int = 1600, mu_p: float = 1e3, mass_ratio: float = 1.0, sigma: float = 1e4,
+               gamma: float = 2.0, cfl: float = 0.4) -> Workload:
+    """Two-fluid Brio-Wu tube (Sec. 4.1): x in [0, 1], outflow, (rho, p, B_x, B_y) =
+    (1, 1, 0.5, 1) left and (0.125, 0.1, 0.5, -1) right of x = 1/2, v = 0, E = 0,
+    run to T = 0.4. mu_p = 1e3; mu_e = -mass_ratio * mu_p (1: pair plasma; 100:
+    electron-proton). sigma (eta = 1/sigma) and Gamma are not printed: 1e4 and 2."""
+    x = _centres(0.0, 1.0, nx)[None, :]
+    left = x < 0.5
+    z = np.zeros_like(x)
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    B = np.stack([z + 0.5, np.where(left, 1.0, -1.0), z])
+    v = np.stack([z, z, z])
+    mu_e = -mass_ratio * mu_p
+    prims = _tf_species_prims(rho, p, v, B, np.stack([z, z, z]), mu_e, mu_p)
+    dt = cfl / nx
+    return Workload("tf_brio_wu", TWO_FLUID, nx, 1, (0.0, 1.0), (0.0, 1.0), gamma, sigma,
+                    OUTFLOW, OUTFLOW, cfl, int(round(0.4 / dt)), np.ascontiguousarray(prims),
+                    mu_e=mu_e, mu_p=mu_p)
+
+
+def tf_current_sheet(nx: int = 50, mu: float = 1e3, sigma: float = 100.0, t0: float = 1.0, b0: float = 1.0,
+                     xlim=(-1.5, 1.5), gamma: float = 2.0, cfl: float = 0.4, p: float = 50.0) -> Workload:
+    """Two-fluid self-similar current sheet (Sec. 4.2), pair plasma mu = +-1e3:
+    rho = 1, p = 50 (halves per species), v = 0, E = 0, B_y = b0 erf(x sqrt(sigma / t0) / 2)."""
+    x = _centres(xlim[0], xlim[1], nx)[None, :]
+    z = np.zeros_like(x)
+    by = b0 * np.vectorize(math.erf)(0.5 * x * math.sqrt(sigma / t0))
+    prims = _tf_species_prims(np.ones_like(x), np.full_like(x, p), np.stack([z, z, z]), np.stack([z, by, z]),
+                              np.stack([z, z, z]), -mu, mu)
+    return Workload("tf_current_sheet", TWO_FLUID, nx, 1, xlim, (0.0, 1.0), gamma, sigma,
+                    OUTFLOW, OUTFLOW, cfl, 0, np.ascontiguousarray(prims), mu_e=-mu, mu_p=mu)
+
+
 def batch_tubes(count: int = 512, seed: int = 2, nmin: int = 100, nmax: int = 4096,
                 gamma: float = 4.0 / 3.0, cfl: float = 0.4, nsteps: int = 400) -> list:
     """Independent 1-D shock tubes on [0, 1], outflow: N ~ U{nmin..nmax},

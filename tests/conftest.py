@@ -33,6 +33,8 @@ def parity_scale(model, want, mu_ref=1.0):
     Each conserved variable is compared relative to the natural size of the
     terms that make it up, not to its own maximum when that is a cancellation:
       - vector components share one scale (max over the three components);
+      - S = rho h W^2 v + E x B (Eq. resistive prims): the scale of S includes
+        max |E| |B|, since the two parts cancel in near-static magnetised states;
       - two fluids: Dbar, Sbar, taubar are sums of mu_s-weighted species terms
         (Eq. twoFluid cons), so their scale is mu_ref times that of D, S, tau;
       - varrho, psi, phi (charge and divergence-cleaning fields, Sec. 2.1.1)
@@ -41,16 +43,22 @@ def parity_scale(model, want, mu_ref=1.0):
     import numpy as np
     m = np.abs(want).reshape(want.shape[0], -1).max(axis=1)
     s = m.copy()
+    bs, es = (5, 8) if model == 0 else (10, 13)
+    B, E = want[bs:bs + 3], want[es:es + 3]
+    # S = rho h W^2 v + E x B (Eq. resistive prims): its natural size includes |E| |B|
+    exb = float(np.max(np.sqrt((B * B).sum(axis=0) * (E * E).sum(axis=0))))
     if model == 0:
         groups = [(1, 4), (5, 8), (8, 11)]
         for a, b in groups:
             s[a:b] = m[a:b].max()
+        s[1:4] = max(s[1], exb)
         em = max(s[5], s[8])
         for v in (11, 12, 13):
             s[v] = max(m[v], em)
     else:
         for a, b in [(1, 4), (6, 9), (10, 13), (13, 16)]:
             s[a:b] = m[a:b].max()
+        s[1:4] = max(s[1], exb)
         s[5] = max(m[5], mu_ref * m[0])
         s[6:9] = max(s[6], mu_ref * s[1])
         s[9] = max(m[9], mu_ref * m[4])

@@ -205,3 +205,25 @@ def test_error_growth_curve(Sim, name, make, mu_ref, marks):
         curve[m] = float(rel_linf(g.cons(), o.cons(), mu_ref).max())
     print(name, "max relative error vs steps:", curve)
     assert all(e <= TOL for e in curve.values()), curve
+
+
+@pytest.mark.parametrize("nx,mass_ratio", [(400, 1.0), (200, 100.0)])
+def test_two_fluid_brio_wu_full_run(Sim, nx, mass_ratio):
+    """Two-fluid Brio-Wu (Sec. 4.1) to T = 0.4: pair plasma (mu = +-1e3) and
+    electron-proton plasma (mu_e = -100 mu_p)."""
+    wl = WL.tf_brio_wu(nx=nx, mass_ratio=mass_ratio)
+    g, o = run_pair(Sim, wl, wl.nsteps)
+    err = rel_linf(g.cons(), o.cons(), max(abs(wl.mu_e), abs(wl.mu_p)))
+    assert np.all(err <= TOL), err
+
+
+def test_two_fluid_current_sheet_full_run(Sim):
+    """Two-fluid current sheet (Sec. 4.2), N = 100, 9 time units (750 steps)."""
+    import dataclasses
+    import math
+    wl = WL.tf_current_sheet(nx=100)
+    nst = int(math.ceil(9.0 / wl.dt))
+    wl = dataclasses.replace(wl, cfl=wl.cfl * (9.0 / nst) / wl.dt)
+    g, o = run_pair(Sim, wl, nst)
+    err = rel_linf(g.cons(), o.cons(), 1e3)
+    assert np.all(err <= TOL), err

@@ -48,3 +48,25 @@ def test_field_loop_converges_between_first_and_second_order():
     e = [_loop_error(n) for n in (16, 32, 64)]
     rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
     assert all(1.2 <= r <= 2.0 for r in rates), (e, rates)
+
+
+def _tf_sheet_error(n):
+    wl = WL.tf_current_sheet(nx=n)
+    sim = O.Sim(O.MODEL_TF, wl.nx, 1, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y,
+                mu_e=wl.mu_e, mu_p=wl.mu_p)
+    sim.set_prims(wl.prims)
+    T = 9.0
+    nst = int(math.ceil(T / wl.dt))
+    sim.step(T / nst, nst)
+    x = wl.xlim[0] + (np.arange(n) + 0.5) * (wl.xlim[1] - wl.xlim[0]) / n
+    exact = np.array([math.erf(0.5 * xx * math.sqrt(wl.sigma / 10.0)) for xx in x])
+    return np.mean(np.abs(sim.prims()[11, 0] - exact))  # B_y of the two-fluid primitives
+
+
+def test_two_fluid_current_sheet_diffuses_like_erf():
+    """Sec. 4.2 with the two-fluid model (pair plasma, mu = +-1e3, eta = 1/sigma,
+    sigma = 100): the field follows the same resistive diffusion profile, and the
+    L1 error against it falls with N."""
+    e50, e100, e200 = _tf_sheet_error(50), _tf_sheet_error(100), _tf_sheet_error(200)
+    assert e100 < 2e-3, (e50, e100, e200)
+    assert e50 > 3.0 * e100 and e200 < 0.5 * e100, (e50, e100, e200)
