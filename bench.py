@@ -141,6 +141,18 @@ def natural_scale(model, want, mu_ref=1.0):
     return np.maximum(s, 1e-300)
 
 
+def reduce_max(x: float, world: int, device: str) -> float:
+    """Max of a per-rank value (elapsed time) over all ranks of the process
+    group (NCCL on the GPUs; any backend whose device is given)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(seconds: float = 15.0):
     """FP64 CPU oracle on the host cores: KHI recipe at 128 x 128 (a bounded
     sample of the benchmark workload), as many steps as fit in ~`seconds`."""
@@ -246,11 +258,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, f"cuda:{local}")
 
     def timed_run(precision, profile, w=None, k=None, scheme=0):
         """W warm-up steps, then k timed steps as one CUDA graph per step
