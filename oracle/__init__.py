@@ -43,7 +43,8 @@ class _Cfg(C.Structure):
     _fields_ = [("model", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
                 ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("gamma", C.c_double), ("sigma", C.c_double), ("mu_e", C.c_double), ("mu_p", C.c_double),
-                ("kappa", C.c_double), ("bc_x", C.c_int), ("bc_y", C.c_int), ("scheme", C.c_int)]
+                ("kappa", C.c_double), ("bc_x", C.c_int), ("bc_y", C.c_int), ("scheme", C.c_int),
+                ("nz", C.c_int), ("zmin", C.c_double), ("zmax", C.c_double), ("bc_z", C.c_int)]
 
 
 _lib = None
@@ -218,10 +219,11 @@ class Sim:
     (scheme 1, Table 2) IMEX steps with WENO3/LF fluxes."""
 
     def __init__(self, model, nx, ny, xlim, ylim, gamma, sigma, bc_x, bc_y,
-                 mu_e=-1.0, mu_p=1.0, kappa=1.0, scheme=0):
-        self.model, self.nx, self.ny = model, nx, ny
+                 mu_e=-1.0, mu_p=1.0, kappa=1.0, scheme=0, nz=1, zlim=(0.0, 1.0), bc_z=1):
+        """nz > 1 makes a 3-D grid (needs ny > 1); arrays are then [var][nz][ny][nx]."""
+        self.model, self.nx, self.ny, self.nz = model, nx, ny, max(1, nz)
         self.cfg = _Cfg(model, nx, ny, xlim[0], xlim[1], ylim[0], ylim[1], gamma, sigma,
-                        mu_e, mu_p, kappa, bc_x, bc_y, scheme)
+                        mu_e, mu_p, kappa, bc_x, bc_y, scheme, self.nz, zlim[0], zlim[1], bc_z)
         self.h = lib().orc_create(C.byref(self.cfg))
         if not self.h:
             raise OracleError(-1, "orc_create")
@@ -235,41 +237,45 @@ class Sim:
     def nc(self):
         return NC[self.model]
 
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx) if self.nz > 1 else (self.ny, self.nx)
+
     def _check(self, st, what):
         if st:
             raise OracleError(st, f"{what} (first failing cell {lib().orc_fail_cell(self.h)})")
 
     def set_prims(self, prims):
         a = _vec(prims)
-        assert a.size == NP[self.model] * self.nx * self.ny
+        assert a.size == NP[self.model] * self.nx * self.ny * self.nz
         self._check(lib().orc_set_prims(self.h, _p(a)), "set_prims")
 
     def set_cons(self, cons):
         a = _vec(cons)
-        assert a.size == self.nc * self.nx * self.ny
+        assert a.size == self.nc * self.nx * self.ny * self.nz
         self._check(lib().orc_set_cons(self.h, _p(a)), "set_cons")
 
     def step(self, dt, nsteps=1):
         self._check(lib().orc_step(self.h, dt, nsteps), "step")
 
     def cons(self):
-        out = np.zeros((self.nc, self.ny, self.nx))
+        out = np.zeros((self.nc,) + self.shape)
         lib().orc_get_cons(self.h, _p(out))
         return out
 
     def prims(self):
-        out = np.zeros((NP[self.model], self.ny, self.nx))
+        out = np.zeros((NP[self.model],) + self.shape)
         lib().orc_get_prims(self.h, _p(out))
         return out
 
     def flux_divergence(self):
-        out = np.zeros((self.nc, self.ny, self.nx))
+        out = np.zeros((self.nc,) + self.shape)
         lib().orc_current_L(self.h, _p(out))
         return out
 
     def stage_solve(self, adt):
-        q = np.zeros((self.nc, self.ny, self.nx))
-        w = np.zeros((NW[self.model], self.ny, self.nx))
+        q = np.zeros((self.nc,) + self.shape)
+        w = np.zeros((NW[self.model],) + self.shape)
         self._check(lib().orc_stage_solve(self.h, adt, _p(q), _p(w)), "stage_solve")
         return q, w
 

@@ -64,6 +64,9 @@ typedef struct {
     double gamma, sigma, mu_e, mu_p, kappa;
     int bc_x, bc_y;
     int scheme;      /* 0: SSP2(222) (Table 1), 1: SSP3(332) (Table 2) */
+    int nz;          /* cells along z (0 or 1: no z direction) */
+    double zmin, zmax;
+    int bc_z;
 } orc_cfg;
 
 /* Levi-Civita symbol on {0,1,2}. */
@@ -635,9 +638,11 @@ int orc_tf_implicit(const double *r, double adt, double gamma, double sigma, dou
 typedef struct {
     orc_cfg cfg;
     int nc, nw, np;
-    int gx, gy;      /* ghost layers: 2 in x; 2 in y when ny > 1, else 0 */
-    int NX, NY;      /* padded extents */
-    double dx, dy;
+    int nz;          /* cells along z (1: 1-D or 2-D grid) */
+    int gx, gy, gz;  /* ghost layers: 2 in x; 2 in y (z) when ny (nz) > 1, else 0 */
+    int NX, NY, NZ;  /* padded extents */
+    int NR;          /* padded rows NY * NZ: arrays are [var][NZ][NY][NX] = [var][NR][NX] */
+    double dx, dy, dz;
     double t;
     int fail_cell;   /* first failing interior cell (j*nx + i), -1 if none */
     double *q, *w;   /* state with ghosts: [var][NY][NX] */
@@ -645,34 +650,55 @@ typedef struct {
     double *q3, *w3, *L3, *P3;  /* third stage of SSP3(332) */
 } orc_sim;
 
-static size_t cells(const orc_sim *s) { return (size_t)s->NX * s->NY; }
-static size_t at(const orc_sim *s, int v, int j, int i) { return ((size_t)v * s->NY + j) * s->NX + i; }
+static size_t cells(const orc_sim *s) { return (size_t)s->NX * s->NR; }
+/* element (v, padded row R, padded column i); row R = k * NY + j */
+static size_t at(const orc_sim *s, int v, int R, int i) { return ((size_t)v * s->NR + R) * s->NX + i; }
+/* interior rows r = kk * ny + jj (the user layout [nz][ny][nx]) and their padded row */
+static int nrows(const orc_sim *s) { return s->cfg.ny * s->nz; }
+static int row_of(const orc_sim *s, int r) { return (r / s->cfg.ny + s->gz) * s->NY + r % s->cfg.ny + s->gy; }
 
 /* Fill ghost cells of an array with nv variables. Outflow copies the nearest
- * interior cell; periodic wraps. x ghosts first, then y ghosts over the full
- * padded row so corners are consistent. */
+ * interior cell; periodic wraps. x ghosts of the interior rows first, then y
+ * ghost rows over the padded x extent, then z ghost planes over the padded
+ * (y, x) extent, so edges and corners are consistent. */
+static int ghost_src(int g, int n, int ng, int bc)
+{
+    /* padded index g (outside [ng, ng + n)) -> the padded interior index it copies */
+    int lo = ng, hi = ng + n - 1;
+    if (bc == BC_PERIODIC) return g < lo ? g + n : g - n;
+    return g < lo ? lo : hi;
+}
+
 static void fill_ghosts(const orc_sim *s, double *a, int nv)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny, gx = s->gx, gy = s->gy;
+    int nx = s->cfg.nx, ny = s->cfg.ny, nz = s->nz, gx = s->gx, gy = s->gy, gz = s->gz;
     for (int v = 0; v < nv; v++) {
-        for (int j = gy; j < gy + ny; j++)
+        for (int r = 0; r < nrows(s); r++) {
+            int R = row_of(s, r);
             for (int g = 0; g < gx; g++) {
                 int il = g, ir = gx + nx + g;
-                int sl, sr;
-                if (s->cfg.bc_x == BC_PERIODIC) { sl = il + nx; sr = ir - nx; }
-                else { sl = gx; sr = gx + nx - 1; }
-                a[at(s, v, j, il)] = a[at(s, v, j, sl)];
-                a[at(s, v, j, ir)] = a[at(s, v, j, sr)];
+                a[at(s, v, R, il)] = a[at(s, v, R, ghost_src(il, nx, gx, s->cfg.bc_x))];
+                a[at(s, v, R, ir)] = a[at(s, v, R, ghost_src(ir, nx, gx, s->cfg.bc_x))];
             }
-        for (int g = 0; g < gy; g++)
-            for (int i = 0; i < s->NX; i++) {
+        }
+        for (int k = gz; k < gz + nz; k++)
+            for (int g = 0; g < gy; g++) {
                 int jl = g, jr = gy + ny + g;
-                int sl, sr;
-                if (s->cfg.bc_y == BC_PERIODIC) { sl = jl + ny; sr = jr - ny; }
-                else { sl = gy; sr = gy + ny - 1; }
-                a[at(s, v, jl, i)] = a[at(s, v, sl, i)];
-                a[at(s, v, jr, i)] = a[at(s, v, sr, i)];
+                int sl = ghost_src(jl, ny, gy, s->cfg.bc_y), sr = ghost_src(jr, ny, gy, s->cfg.bc_y);
+                for (int i = 0; i < s->NX; i++) {
+                    a[at(s, v, k * s->NY + jl, i)] = a[at(s, v, k * s->NY + sl, i)];
+                    a[at(s, v, k * s->NY + jr, i)] = a[at(s, v, k * s->NY + sr, i)];
+                }
             }
+        for (int g = 0; g < gz; g++) {
+            int kl = g, kr = gz + nz + g;
+            int sl = ghost_src(kl, nz, gz, s->cfg.bc_z), sr = ghost_src(kr, nz, gz, s->cfg.bc_z);
+            for (int j = 0; j < s->NY; j++)
+                for (int i = 0; i < s->NX; i++) {
+                    a[at(s, v, kl * s->NY + j, i)] = a[at(s, v, sl * s->NY + j, i)];
+                    a[at(s, v, kr * s->NY + j, i)] = a[at(s, v, sr * s->NY + j, i)];
+                }
+        }
     }
 }
 
@@ -681,17 +707,23 @@ orc_sim *orc_create(const orc_cfg *cfg)
     if (cfg->nx < 1 || cfg->ny < 1) return NULL;
     if (cfg->model != MODEL_SF && cfg->model != MODEL_TF) return NULL;
     if (cfg->scheme != 0 && cfg->scheme != 1) return NULL;
+    if (cfg->nz > 1 && cfg->ny < 2) return NULL;
     orc_sim *s = calloc(1, sizeof(orc_sim));
     s->cfg = *cfg;
     s->nc = cfg->model == MODEL_SF ? SF_NC : TF_NC;
     s->nw = cfg->model == MODEL_SF ? SF_NW : TF_NW;
     s->np = cfg->model == MODEL_SF ? SF_NP : TF_NP;
+    s->nz = cfg->nz > 1 ? cfg->nz : 1;
     s->gx = 2;
     s->gy = cfg->ny > 1 ? 2 : 0;
+    s->gz = s->nz > 1 ? 2 : 0;
     s->NX = cfg->nx + 2 * s->gx;
     s->NY = cfg->ny + 2 * s->gy;
+    s->NZ = s->nz + 2 * s->gz;
+    s->NR = s->NY * s->NZ;
     s->dx = (cfg->xmax - cfg->xmin) / cfg->nx;
     s->dy = (cfg->ymax - cfg->ymin) / cfg->ny;
+    s->dz = s->nz > 1 ? (cfg->zmax - cfg->zmin) / s->nz : 1.0;
     s->fail_cell = -1;
     size_t nq = cells(s) * s->nc, nw = cells(s) * s->nw;
     s->q = calloc(nq, sizeof(double)); s->w = calloc(nw, sizeof(double));
@@ -715,10 +747,10 @@ void orc_destroy(orc_sim *s)
 }
 
 /* Gather/scatter one cell's variables from/to an SoA array. */
-static void get_cell(const orc_sim *s, const double *a, int nv, int j, int i, double *c)
-{ for (int v = 0; v < nv; v++) c[v] = a[at(s, v, j, i)]; }
-static void put_cell(const orc_sim *s, double *a, int nv, int j, int i, const double *c)
-{ for (int v = 0; v < nv; v++) a[at(s, v, j, i)] = c[v]; }
+static void get_cell(const orc_sim *s, const double *a, int nv, int R, int i, double *c)
+{ for (int v = 0; v < nv; v++) c[v] = a[at(s, v, R, i)]; }
+static void put_cell(const orc_sim *s, double *a, int nv, int R, int i, const double *c)
+{ for (int v = 0; v < nv; v++) a[at(s, v, R, i)] = c[v]; }
 
 /* Set the initial state from user primitives [np][ny][nx] (interior cells).
  * psi = phi = 0 (Sec. 2.1.1). For one fluid the charge density is
@@ -726,34 +758,37 @@ static void put_cell(const orc_sim *s, double *a, int nv, int j, int i, const do
  * differences, neighbours taken through the boundary conditions. */
 int orc_set_prims(orc_sim *s, const double *prims)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny, np = s->np;
+    int nx = s->cfg.nx, ny = s->cfg.ny, np = s->np, nr = nrows(s);
     /* stage the user primitives in a ghosted array to take div E */
     double *P = calloc(cells(s) * np, sizeof(double));
     for (int v = 0; v < np; v++)
-        for (int j = 0; j < ny; j++)
+        for (int r = 0; r < nr; r++)
             for (int i = 0; i < nx; i++)
-                P[at(s, v, j + s->gy, i + s->gx)] = prims[((size_t)v * ny + j) * nx + i];
+                P[at(s, v, row_of(s, r), i + s->gx)] = prims[((size_t)v * nr + r) * nx + i];
     fill_ghosts(s, P, np);
     int status = ORC_OK;
-    for (int j = s->gy; j < s->gy + ny && status == ORC_OK; j++)
+    for (int r = 0; r < nr && status == ORC_OK; r++) {
+        int R = row_of(s, r);
         for (int i = s->gx; i < s->gx + nx; i++) {
             double pc[TF_NP], qc[TF_NC], wc[TF_NW];
-            get_cell(s, P, np, j, i, pc);
+            get_cell(s, P, np, R, i, pc);
             int st;
             if (s->cfg.model == MODEL_SF) {
-                int ex = 8, ey = 9;
-                double divE = (P[at(s, ex, j, i + 1)] - P[at(s, ex, j, i - 1)]) / (2.0 * s->dx);
-                if (ny > 1) divE += (P[at(s, ey, j + 1, i)] - P[at(s, ey, j - 1, i)]) / (2.0 * s->dy);
+                int ex = 8, ey = 9, ez = 10;
+                double divE = (P[at(s, ex, R, i + 1)] - P[at(s, ex, R, i - 1)]) / (2.0 * s->dx);
+                if (ny > 1) divE += (P[at(s, ey, R + 1, i)] - P[at(s, ey, R - 1, i)]) / (2.0 * s->dy);
+                if (s->nz > 1) divE += (P[at(s, ez, R + s->NY, i)] - P[at(s, ez, R - s->NY, i)]) / (2.0 * s->dz);
                 st = orc_sf_p2c(pc, divE, 0.0, 0.0, s->cfg.gamma, qc);
                 memcpy(wc, pc, SF_NW * sizeof(double));
             } else {
                 st = orc_tf_p2c(pc, 0.0, 0.0, s->cfg.gamma, s->cfg.mu_e, s->cfg.mu_p, qc);
                 memcpy(wc, pc, TF_NW * sizeof(double));
             }
-            if (st) { status = st; s->fail_cell = (j - s->gy) * nx + (i - s->gx); break; }
-            put_cell(s, s->q, s->nc, j, i, qc);
-            put_cell(s, s->w, s->nw, j, i, wc);
+            if (st) { status = st; s->fail_cell = r * nx + (i - s->gx); break; }
+            put_cell(s, s->q, s->nc, R, i, qc);
+            put_cell(s, s->w, s->nw, R, i, wc);
         }
+    }
     free(P);
     fill_ghosts(s, s->q, s->nc);
     fill_ghosts(s, s->w, s->nw);
@@ -764,21 +799,22 @@ int orc_set_prims(orc_sim *s, const double *prims)
 /* Overwrite the conserved state (interior [nc][ny][nx]) and recover primitives. */
 int orc_set_cons(orc_sim *s, const double *cons)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny;
+    int nx = s->cfg.nx, nr = nrows(s);
     for (int v = 0; v < s->nc; v++)
-        for (int j = 0; j < ny; j++)
+        for (int r = 0; r < nr; r++)
             for (int i = 0; i < nx; i++)
-                s->q[at(s, v, j + s->gy, i + s->gx)] = cons[((size_t)v * ny + j) * nx + i];
+                s->q[at(s, v, row_of(s, r), i + s->gx)] = cons[((size_t)v * nr + r) * nx + i];
     fill_ghosts(s, s->q, s->nc);
     int status = ORC_OK;
-    for (int j = s->gy; j < s->gy + ny; j++)
+    for (int r = 0; r < nr; r++)
         for (int i = s->gx; i < s->gx + nx; i++) {
             double qc[TF_NC], wc[TF_NW];
-            get_cell(s, s->q, s->nc, j, i, qc);
+            int R = row_of(s, r);
+            get_cell(s, s->q, s->nc, R, i, qc);
             int st = s->cfg.model == MODEL_SF ? orc_sf_c2p(qc, s->cfg.gamma, wc)
                                               : orc_tf_c2p(qc, s->cfg.gamma, s->cfg.mu_e, s->cfg.mu_p, wc);
-            if (st && status == ORC_OK) { status = st; s->fail_cell = (j - s->gy) * nx + (i - s->gx); }
-            put_cell(s, s->w, s->nw, j, i, wc);
+            if (st && status == ORC_OK) { status = st; s->fail_cell = r * nx + (i - s->gx); }
+            put_cell(s, s->w, s->nw, R, i, wc);
         }
     fill_ghosts(s, s->w, s->nw);
     return status;
@@ -786,11 +822,11 @@ int orc_set_cons(orc_sim *s, const double *cons)
 
 static void copy_interior_out(const orc_sim *s, const double *a, int nv, double *out)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny;
+    int nx = s->cfg.nx, nr = nrows(s);
     for (int v = 0; v < nv; v++)
-        for (int j = 0; j < ny; j++)
+        for (int r = 0; r < nr; r++)
             for (int i = 0; i < nx; i++)
-                out[((size_t)v * ny + j) * nx + i] = a[at(s, v, j + s->gy, i + s->gx)];
+                out[((size_t)v * nr + r) * nx + i] = a[at(s, v, row_of(s, r), i + s->gx)];
 }
 
 int orc_get_cons(const orc_sim *s, double *out) { copy_interior_out(s, s->q, s->nc, out); return ORC_OK; }
@@ -799,14 +835,14 @@ int orc_get_cons(const orc_sim *s, double *out) { copy_interior_out(s, s->q, s->
  * ((rho, v, p)_e, (rho, v, p)_p, B, E). */
 int orc_get_prims(const orc_sim *s, double *out)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny;
-    size_t n = (size_t)nx * ny;
+    int nx = s->cfg.nx, nr = nrows(s);
+    size_t n = (size_t)nx * nr;
     copy_interior_out(s, s->w, s->nw, out);
     int b = s->cfg.model == MODEL_SF ? SF_B : TF_B;
     for (int c = 0; c < 6; c++)
-        for (int j = 0; j < ny; j++)
+        for (int r = 0; r < nr; r++)
             for (int i = 0; i < nx; i++)
-                out[(s->nw + c) * n + (size_t)j * nx + i] = s->q[at(s, b + c, j + s->gy, i + s->gx)];
+                out[(s->nw + c) * n + (size_t)r * nx + i] = s->q[at(s, b + c, row_of(s, r), i + s->gx)];
     return ORC_OK;
 }
 
@@ -825,22 +861,24 @@ static void cell_flux(const orc_sim *s, const double *qc, const double *wc, int 
  * q and w must have their ghost cells filled. Writes interior cells of L. */
 void orc_flux_divergence(orc_sim *s, const double *q, const double *w, double *L)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny, nc = s->nc, nw = s->nw;
-    int ndir = ny > 1 ? 2 : 1;
+    int nx = s->cfg.nx, ny = s->cfg.ny, nc = s->nc, nw = s->nw, nr = nrows(s);
     memset(L, 0, cells(s) * nc * sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = s->gy; j < s->gy + ny; j++) {
+    for (int r = 0; r < nr; r++) {
+        int R = row_of(s, r);
         for (int i = s->gx; i < s->gx + nx; i++) {
             double Lc[TF_NC] = { 0 };
-            for (int k = 0; k < ndir; k++) {
-                int di = k == 0 ? 1 : 0, dj = k == 0 ? 0 : 1;
-                double dxk = k == 0 ? s->dx : s->dy;
+            for (int k = 0; k < 3; k++) {
+                if ((k == 1 && ny < 2) || (k == 2 && s->nz < 2)) continue;
+                /* neighbour steps along direction k: columns (x) or rows (y: 1, z: NY) */
+                int di = k == 0 ? 1 : 0, dR = k == 0 ? 0 : (k == 1 ? 1 : s->NY);
+                double dxk = k == 0 ? s->dx : (k == 1 ? s->dy : s->dz);
                 /* fluxes at the four cells i-2..i+1 and i-1..i+2 */
                 double fp[5][TF_NC], fm[5][TF_NC];
                 for (int o = -2; o <= 2; o++) {
                     double qc[TF_NC], wc[TF_NW], f[TF_NC];
-                    get_cell(s, q, nc, j + o * dj, i + o * di, qc);
-                    get_cell(s, w, nw, j + o * dj, i + o * di, wc);
+                    get_cell(s, q, nc, R + o * dR, i + o * di, qc);
+                    get_cell(s, w, nw, R + o * dR, i + o * di, wc);
                     cell_flux(s, qc, wc, k, f);
                     for (int v = 0; v < nc; v++) {
                         fp[o + 2][v] = 0.5 * (f[v] + qc[v]);
@@ -855,43 +893,45 @@ void orc_flux_divergence(orc_sim *s, const double *q, const double *w, double *L
                     Lc[v] -= (Fr - Fl) / dxk;
                 }
             }
-            for (int v = 0; v < nc; v++) L[at(s, v, j, i)] = Lc[v];
+            for (int v = 0; v < nc; v++) L[at(s, v, R, i)] = Lc[v];
         }
     }
 }
 
 static void source_field(orc_sim *s, const double *q, const double *w, double *P)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny;
+    int nx = s->cfg.nx, nr = nrows(s);
 #pragma omp parallel for schedule(static)
-    for (int j = s->gy; j < s->gy + ny; j++)
+    for (int r = 0; r < nr; r++)
         for (int i = s->gx; i < s->gx + nx; i++) {
             double qc[TF_NC], wc[TF_NW], sc[TF_NC];
-            get_cell(s, q, s->nc, j, i, qc);
-            get_cell(s, w, s->nw, j, i, wc);
+            int R = row_of(s, r);
+            get_cell(s, q, s->nc, R, i, qc);
+            get_cell(s, w, s->nw, R, i, wc);
             if (s->cfg.model == MODEL_SF) orc_sf_source(qc, wc, s->cfg.sigma, s->cfg.kappa, sc);
             else orc_tf_source(qc, wc, s->cfg.sigma, s->cfg.kappa, s->cfg.mu_e, s->cfg.mu_p, sc);
-            put_cell(s, P, s->nc, j, i, sc);
+            put_cell(s, P, s->nc, R, i, sc);
         }
 }
 
 /* Solve the implicit stage q_out = r + adt Psi(q_out) on every interior cell. */
 static int implicit_field(orc_sim *s, const double *r, double adt, double *qo, double *wo)
 {
-    int nx = s->cfg.nx, ny = s->cfg.ny, status = ORC_OK, fail = -1;
+    int nx = s->cfg.nx, nr = nrows(s), status = ORC_OK, fail = -1;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = s->gy; j < s->gy + ny; j++)
+    for (int rr = 0; rr < nr; rr++)
         for (int i = s->gx; i < s->gx + nx; i++) {
             double rc[TF_NC], qc[TF_NC], wc[TF_NW];
-            get_cell(s, r, s->nc, j, i, rc);
+            int R = row_of(s, rr), cell = rr * nx + (i - s->gx);
+            get_cell(s, r, s->nc, R, i, rc);
             stage_ctx c = { s->cfg.model, rc, adt, s->cfg.gamma, s->cfg.sigma, s->cfg.kappa, s->cfg.mu_e, s->cfg.mu_p };
             int st = stage_solve(&c, qc, wc);
             if (st) {
 #pragma omp critical
-                { if (status == ORC_OK || (j - s->gy) * nx + (i - s->gx) < fail) { status = st; fail = (j - s->gy) * nx + (i - s->gx); } }
+                { if (status == ORC_OK || cell < fail) { status = st; fail = cell; } }
             }
-            put_cell(s, qo, s->nc, j, i, qc);
-            put_cell(s, wo, s->nw, j, i, wc);
+            put_cell(s, qo, s->nc, R, i, qc);
+            put_cell(s, wo, s->nw, R, i, wc);
         }
     if (status) s->fail_cell = fail;
     return status;
@@ -900,16 +940,17 @@ static int implicit_field(orc_sim *s, const double *r, double adt, double *qo, d
 /* Ghosts of the new state, then its primitives by recovery (Sec. 2.1.3). */
 static int recover_state(orc_sim *s)
 {
-    int nc = s->nc, nx = s->cfg.nx, ny = s->cfg.ny, status = ORC_OK;
+    int nc = s->nc, nx = s->cfg.nx, nr = nrows(s), status = ORC_OK;
     fill_ghosts(s, s->q, nc);
-    for (int j = s->gy; j < s->gy + ny; j++)
+    for (int r = 0; r < nr; r++)
         for (int i = s->gx; i < s->gx + nx; i++) {
             double qc[TF_NC], wc[TF_NW];
-            get_cell(s, s->q, nc, j, i, qc);
+            int R = row_of(s, r);
+            get_cell(s, s->q, nc, R, i, qc);
             int c = s->cfg.model == MODEL_SF ? orc_sf_c2p(qc, s->cfg.gamma, wc)
                                              : orc_tf_c2p(qc, s->cfg.gamma, s->cfg.mu_e, s->cfg.mu_p, wc);
-            if (c && status == ORC_OK) { status = ORC_ERR_C2P; s->fail_cell = (j - s->gy) * nx + (i - s->gx); }
-            put_cell(s, s->w, s->nw, j, i, wc);
+            if (c && status == ORC_OK) { status = ORC_ERR_C2P; s->fail_cell = r * nx + (i - s->gx); }
+            put_cell(s, s->w, s->nw, R, i, wc);
         }
     fill_ghosts(s, s->w, s->nw);
     return status;
@@ -924,7 +965,7 @@ static int recover_state(orc_sim *s)
 int orc_ssp2_step(orc_sim *s, double dt)
 {
     const double g = 1.0 - 1.0 / sqrt(2.0);
-    int nc = s->nc, nx = s->cfg.nx, ny = s->cfg.ny;
+    int nc = s->nc, nx = s->cfg.nx;
     size_t n = cells(s) * nc;
     int st = implicit_field(s, s->q, g * dt, s->q1, s->w1);
     if (st) return st;
@@ -938,9 +979,9 @@ int orc_ssp2_step(orc_sim *s, double dt)
     source_field(s, s->q2, s->w2, s->P2);
     orc_flux_divergence(s, s->q2, s->w2, s->L2);
     for (int v = 0; v < nc; v++)
-        for (int j = s->gy; j < s->gy + ny; j++)
+        for (int rr = 0; rr < nrows(s); rr++)
             for (int i = s->gx; i < s->gx + nx; i++) {
-                size_t k = at(s, v, j, i);
+                size_t k = at(s, v, row_of(s, rr), i);
                 s->q[k] = s->q[k] + 0.5 * dt * (s->L1[k] + s->L2[k]) + 0.5 * dt * (s->P1[k] + s->P2[k]);
             }
     s->t += dt;
@@ -957,7 +998,7 @@ int orc_ssp2_step(orc_sim *s, double dt)
 int orc_ssp3_step(orc_sim *s, double dt)
 {
     const double g = 1.0 - 1.0 / sqrt(2.0);
-    int nc = s->nc, nx = s->cfg.nx, ny = s->cfg.ny;
+    int nc = s->nc, nx = s->cfg.nx;
     size_t n = cells(s) * nc;
     int st = implicit_field(s, s->q, g * dt, s->q1, s->w1);
     if (st) return st;
@@ -978,9 +1019,9 @@ int orc_ssp3_step(orc_sim *s, double dt)
     source_field(s, s->q3, s->w3, s->P3);
     orc_flux_divergence(s, s->q3, s->w3, s->L3);
     for (int v = 0; v < nc; v++)
-        for (int j = s->gy; j < s->gy + ny; j++)
+        for (int rr = 0; rr < nrows(s); rr++)
             for (int i = s->gx; i < s->gx + nx; i++) {
-                size_t k = at(s, v, j, i);
+                size_t k = at(s, v, row_of(s, rr), i);
                 s->q[k] = s->q[k] + dt * (s->L1[k] / 6.0 + s->L2[k] / 6.0 + 2.0 * s->L3[k] / 3.0) +
                           dt * (s->P1[k] / 6.0 + s->P2[k] / 6.0 + 2.0 * s->P3[k] / 3.0);
             }
