@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("gamma", C.c_double), ("sigma", C.c_double), ("mu_e", C.c_double), ("mu_p", C.c_double),
                 ("kappa", C.c_double), ("cfl", C.c_double),
                 ("bc_x", C.c_int), ("bc_y", C.c_int), ("precision", C.c_int), ("scheme", C.c_int),
-                ("reserved", C.c_int * 4)]
+                ("nz", C.c_int), ("bc_z", C.c_int), ("zlen", C.c_double)]
 
 
 class RmhdError(RuntimeError):

@@ -110,17 +110,22 @@ struct SFModel {
         for (int i = 0; i < 3; ++i)
             f[sf::SX + i] = Zv * (FT)st[(NC + sf::VX + i) * SN + idx] - (FT)st[(sf::EX + i) * SN + idx] * Ed -
                             (FT)st[(sf::BX + i) * SN + idx] * Bd;
-        if (dir == 0) f[sf::SX] += (FT)aux[4 * SN + idx]; else f[sf::SY] += (FT)aux[4 * SN + idx];
+        const FT pem = (FT)aux[4 * SN + idx];
+        if (dir == 0) f[sf::SX] += pem; else if (dir == 1) f[sf::SY] += pem; else f[sf::SZ] += pem;
         f[sf::TAU] = (FT)st[(sf::SX + dir) * SN + idx] - f[sf::D];
         const FT EX = (FT)st[sf::EX * SN + idx], EY = (FT)st[sf::EY * SN + idx], EZ = (FT)st[sf::EZ * SN + idx];
         const FT BX = (FT)st[sf::BX * SN + idx], BY = (FT)st[sf::BY * SN + idx], BZ = (FT)st[sf::BZ * SN + idx];
         const FT psi = (FT)st[sf::PSI * SN + idx], phi = (FT)st[sf::PHI * SN + idx];
+        // B^i: -eps^{ijd} E_j + delta_id phi;  E^i: eps^{ijd} B_j + delta_id psi
         if (dir == 0) {
             f[sf::BX] = phi; f[sf::BY] = -EZ; f[sf::BZ] = EY;
             f[sf::EX] = psi; f[sf::EY] = BZ; f[sf::EZ] = -BY;
-        } else {
+        } else if (dir == 1) {
             f[sf::BX] = EZ; f[sf::BY] = phi; f[sf::BZ] = -EX;
             f[sf::EX] = -BZ; f[sf::EY] = psi; f[sf::EZ] = BX;
+        } else {
+            f[sf::BX] = -EY; f[sf::BY] = EX; f[sf::BZ] = phi;
+            f[sf::EX] = BY; f[sf::EY] = -BX; f[sf::EZ] = psi;
         }
         f[sf::RHOE] = (FT)aux[dir * SN + idx];
         f[sf::PSI] = Ed;
@@ -207,7 +212,7 @@ struct FluxSmem {
 // cell (i, j) lives at base + j * nx + i in every variable plane. All threads
 // of the CTA call it; it starts with a barrier so that a persistent CTA can
 // process tiles back to back.
-template <class M, int TX, int TY, int G, class FT, int NOUT>
+template <class M, int TX, int TY, int G, class FT, int NOUT, int DIRS = (TY > 1 ? 3 : 1)>
 __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const FluxArgs &a, int i0, int j0,
                                           long long base, unsigned char *smem_raw) {
     using L_ = FluxSmem<M, TX, TY, G, FT, NOUT>;
@@ -239,7 +244,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             const int sy = e / SW, sx = e - sy * SW;
             const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
             const int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
-            const long long gc = base + (long long)gj * g.nx + gi;
+            const long long gc = base + (long long)gj * g.row + gi;
             double x[NV];
 #pragma unroll
             for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
@@ -250,8 +255,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             const int tx = sx - 2, ty = sy - OY;
             const bool interior = tx >= 0 && tx < TX && ty >= 0 && ty < TY;
             double s[M::NS];
-            M::template stage_cell<FT>(x, ph, aux32, SN, e, interior ? s : nullptr);
-            if (interior) {
+            M::template stage_cell<FT>(x, ph, aux32, SN, e, interior && NOUT > 0 ? s : nullptr);
+            if (interior && NOUT > 0) {
 #pragma unroll
                 for (int k = 0; k < M::NS; ++k) src[k * NL + ty * TX + tx] = s[k];
             }
@@ -265,14 +270,14 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
             int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
             const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-            st[e] = srcp[base + (long long)gj * g.nx + gi];
+            st[e] = srcp[base + (long long)gj * g.row + gi];
         }
         __syncthreads();
         // 2. per-cell auxiliaries of every staged cell, then sources of interior cells
         if (M::NAUX > 0)
             for (int e = tid; e < SN; e += NT) M::prep(st, SN, e, ph, aux);
         __syncthreads();
-        for (int e = tid; e < NL; e += NT) {
+        for (int e = tid; e < (NOUT > 0 ? NL : 0); e += NT) {
             int ty = e / TX, tx = e - ty * TX;
             double s[M::NS];
             M::source(st, aux, SN, (ty + OY) * SW + tx + 2, ph, s);
@@ -292,6 +297,10 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     FT *fcg = fc + grp * SN;
 #pragma unroll 1
     for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
+        if (!((DIRS >> dir) & 1)) continue;
+        // physical direction of the flux: the tile's second dimension is z in
+        // the z pass of a 3-D grid (DIRS = 2)
+        const int pdir = DIRS == 2 ? 2 : dir;
         const int sstep = dir == 0 ? 1 : SW;
         const FT inv4h = FT(dir == 0 ? g.rdx4 : g.rdy4);
         // 3a. physical flux of every cell the reconstruction needs
@@ -302,9 +311,9 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int idx = (cy0 + cy) * SW + cx0 + cx;
             FT f[NC];
             if constexpr (L_::SHADOW)
-                M::template cell_flux<FT>(st32, reinterpret_cast<const FT *>(aux), SN, idx, dir, ph, f);
+                M::template cell_flux<FT>(st32, reinterpret_cast<const FT *>(aux), SN, idx, pdir, ph, f);
             else
-                M::template cell_flux<FT>(st, aux, SN, idx, dir, ph, f);
+                M::template cell_flux<FT>(st, aux, SN, idx, pdir, ph, f);
 #pragma unroll
             for (int v = 0; v < NC; ++v) fl[v * SN + idx] = f[v];
         }
@@ -361,37 +370,47 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     // 4. epilogue: each thread updates its own components of its cell
     const int gi = i0 + tx, gj = j0 + ty;
     const bool inside = gi < g.nx && gj < g.ny;
-    const long long cell = base + (long long)gj * g.nx + gi;
+    const long long cell = base + (long long)gj * g.row + gi;
     const double dt = a.dt;
+    if constexpr (NOUT == 0) {
+        // x-y pass of a 3-D grid: L_x + L_y only
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int c = r * G + grp;
-        if (c >= NC || !inside) continue;
-        // (slot is uniform over the group: components without a source skip its terms)
-        const int slot = M::src_slot(c);
-        const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
-        const double Lv = (double)L[r];
-        const long long o = (long long)c * g.plane + cell;
-        double b = a.base[0][o];
-#pragma unroll
-        for (int k = 0; k < NOUT; ++k) {
-            if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];  // outputs often share q^n
-            const double v0 = fma(dt * a.aL[k], Lv, b);
-            a.out[k][o] = slot >= 0 ? fma(dt * a.aS[k], s, v0) : v0;
+        for (int r = 0; r < NR; ++r) {
+            const int c = r * G + grp;
+            if (c < NC && inside) a.lout[(long long)c * g.plane + cell] = (double)L[r];
         }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int c = r * G + grp;
+            if (c >= NC || !inside) continue;
+            // (slot is uniform over the group: components without a source skip its terms)
+            const int slot = M::src_slot(c);
+            const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
+            const long long o = (long long)c * g.plane + cell;
+            const double Lv = a.lin ? (double)L[r] + a.lin[o] : (double)L[r];
+            double b = a.base[0][o];
+#pragma unroll
+            for (int k = 0; k < NOUT; ++k) {
+                if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];  // outputs often share q^n
+                const double v0 = fma(dt * a.aL[k], Lv, b);
+                a.out[k][o] = slot >= 0 ? fma(dt * a.aS[k], s, v0) : v0;
+            }
+        }
+        // Last pass of a step: the primitives of q^{n+1} are not recovered here --
+        // the next stage-1 solve recovers those of its own state, and output calls
+        // recover on demand. The stage primitives are carried as the warm start.
+        if (a.wcarry && inside)
+            for (int v = grp; v < NW; v += G)
+                a.wcarry[v * g.plane + cell] = L_::SHADOW ? a.w[v * g.plane + cell] : st[(NC + v) * SN + oy * SW + ox];
     }
-    // Last pass of a step: the primitives of q^{n+1} are not recovered here --
-    // the next stage-1 solve recovers those of its own state, and output calls
-    // recover on demand. The stage primitives are carried as the warm start.
-    if (a.wcarry && inside)
-        for (int v = grp; v < NW; v += G)
-            a.wcarry[v * g.plane + cell] = L_::SHADOW ? a.w[v * g.plane + cell] : st[(NC + v) * SN + oy * SW + ox];
 }
 
-template <class M, int TX, int TY, int G, class FT, int NOUT>
+template <class M, int TX, int TY, int G, class FT, int NOUT, int DIRS>
 __global__ void __launch_bounds__(TX *TY *G, TX *TY *G <= 512 ? 2 : 1) k_flux(Grid g, Phys ph, FluxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    flux_tile<M, TX, TY, G, FT, NOUT>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY, 0, smem_raw);
+    flux_tile<M, TX, TY, G, FT, NOUT, DIRS>(g, ph, a, blockIdx.x * TX, blockIdx.y * TY,
+                                             (long long)blockIdx.z * g.zoff, smem_raw);
 }
 
 // Batched ensemble of 1-D runs packed one after another in every variable
@@ -417,20 +436,20 @@ __global__ void __launch_bounds__(TX *G, TX *G <= 512 ? 2 : 1) k_flux_batch(Grid
     }
 }
 
-template <class M, int TX, int TY, int G, class FT, int NOUT>
-static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
+template <class M, int TX, int TY, int G, class FT, int NOUT, int DIRS = (TY > 1 ? 3 : 1)>
+static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz = 1) {
     using L_ = FluxSmem<M, TX, TY, G, FT, NOUT>;
     static_assert(L_::total <= 227 * 1024, "shared memory budget");
     const size_t smem = L_::total;
     static bool configured = false;  // attribute is per device function; set once
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, G, FT, NOUT>,
+        cudaError_t e = cudaFuncSetAttribute(k_flux<M, TX, TY, G, FT, NOUT, DIRS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((g.nx + TX - 1) / TX, TY > 1 ? (g.ny + TY - 1) / TY : g.ny);
-    k_flux<M, TX, TY, G, FT, NOUT><<<grid, TX * TY * G, smem, s>>>(g, ph, a);
+    dim3 grid((g.nx + TX - 1) / TX, TY > 1 ? (g.ny + TY - 1) / TY : g.ny, gz);
+    k_flux<M, TX, TY, G, FT, NOUT, DIRS><<<grid, TX * TY * G, smem, s>>>(g, ph, a);
     return cudaGetLastError();
 }
 
@@ -485,6 +504,45 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
     if (tile_x == 64) return launch_fb_t<M, 64, FT, NOUT>(g, ph, a, b, blocks, s);
     if (tile_x == 256) return launch_fb_t<M, 256, FT, NOUT>(g, ph, a, b, blocks, s);
     return launch_fb_t<M, 128, FT, NOUT>(g, ph, a, b, blocks, s);
+}
+
+// 3-D grids, one fluid. Pass 1: every x-y plane (blockIdx.z = k) with the
+// 2-D tile, both in-plane directions, L_x + L_y written to lbuf. Pass 2: the
+// x-z slabs (blockIdx.z = j; the tile's second dimension is z, rows nx*ny
+// apart), the z direction only, lbuf added, then the combinations.
+template <class FT>
+static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, const FluxArgs &a, double *lbuf,
+                                    cudaStream_t s) {
+    constexpr int G = sizeof(FT) == 8 ? SFModel::G_FP64 : SFModel::G_FP32;
+    Grid gxy = g;
+    gxy.row = g.nx;
+    gxy.zoff = (long long)g.nx * g.ny;
+    FluxArgs axy = a;
+    axy.lout = lbuf;
+    axy.lin = nullptr;
+    axy.wcarry = nullptr;
+    cudaError_t e = launch_flux_t<SFModel, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
+    if (e != cudaSuccess) return e;
+    Grid gz = g;
+    gz.ny = g.nz;
+    gz.bcy = g.bcz;
+    gz.dy = g.dz;
+    gz.rdy4 = g.rdz4;
+    gz.row = (long long)g.nx * g.ny;
+    gz.zoff = g.nx;
+    FluxArgs az = a;
+    az.lout = nullptr;
+    az.lin = lbuf;
+    if (nout == 1) return launch_flux_t<SFModel, 32, 8, G, FT, 1, 2>(gz, ph, az, s, g.ny);
+    if (nout == 2) return launch_flux_t<SFModel, 32, 8, G, FT, 2, 2>(gz, ph, az, s, g.ny);
+    if (nout == 3) return launch_flux_t<SFModel, 32, 8, G, FT, 3, 2>(gz, ph, az, s, g.ny);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_flux_3d(int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
+                           double *lbuf, cudaStream_t s) {
+    return precision == 0 ? launch_flux_3d_t<double>(nout, g, ph, a, lbuf, s)
+                          : launch_flux_3d_t<float>(nout, g, ph, a, lbuf, s);
 }
 
 // Batches run SSP2(222): passes with two outputs (r2, acc) and one (q^{n+1}).

@@ -131,13 +131,16 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
 }
 
 // ---------------------------------------------------------------- prims -> cons
-// user primitives are dense [np][ny][nx]; the state uses padded planes.
+// user primitives are dense [np][nz][ny][nx]; the state uses padded planes.
 __global__ void k_set_prims_sf(Grid g, Phys ph, const double *U, double *q, double *w, int *status) {
     using namespace sf;
-    const long long n = g.ncell;
+    const long long n = g.ncell, nxy = (long long)g.nx * g.ny;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
-        int j = (int)(cell / g.nx), i = (int)(cell - (long long)j * g.nx);
+        const int kz = (int)(cell / nxy);
+        const long long c2 = cell - kz * nxy;  // index within the x-y plane
+        int j = (int)(c2 / g.nx), i = (int)(c2 - (long long)j * g.nx);
+        const long long pz = kz * nxy;         // first cell of the plane
         double rho = U[0 * n + cell], v[3] = {U[1 * n + cell], U[2 * n + cell], U[3 * n + cell]}, p = U[4 * n + cell];
         double B[3] = {U[5 * n + cell], U[6 * n + cell], U[7 * n + cell]};
         double E[3] = {U[8 * n + cell], U[9 * n + cell], U[10 * n + cell]};
@@ -146,10 +149,14 @@ __global__ void k_set_prims_sf(Grid g, Phys ph, const double *U, double *q, doub
         if (!ok) { record(status, -1, cell); continue; }
         // Gauss's law varrho = div E, central differences with the boundary map
         int il = wrap(i - 1, g.nx, g.bcx), ir = wrap(i + 1, g.nx, g.bcx);
-        double divE = (U[8 * n + (long long)j * g.nx + ir] - U[8 * n + (long long)j * g.nx + il]) / (2.0 * g.dx);
+        double divE = (U[8 * n + pz + (long long)j * g.nx + ir] - U[8 * n + pz + (long long)j * g.nx + il]) / (2.0 * g.dx);
         if (g.ny > 1) {
             int jl = wrap(j - 1, g.ny, g.bcy), jr = wrap(j + 1, g.ny, g.bcy);
-            divE += (U[9 * n + (long long)jr * g.nx + i] - U[9 * n + (long long)jl * g.nx + i]) / (2.0 * g.dy);
+            divE += (U[9 * n + pz + (long long)jr * g.nx + i] - U[9 * n + pz + (long long)jl * g.nx + i]) / (2.0 * g.dy);
+        }
+        if (g.nz > 1) {
+            int kl = wrap(kz - 1, g.nz, g.bcz), kr = wrap(kz + 1, g.nz, g.bcz);
+            divE += (U[10 * n + kr * nxy + c2] - U[10 * n + kl * nxy + c2]) / (2.0 * g.dz);
         }
         double W = 1.0 / sqrt(1.0 - v2);
         double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
@@ -420,7 +427,7 @@ __global__ void k_diag_final(Grid g, double cfl, const double *scratch, int nblo
     double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nblocks; ++b)
         for (int k = 0; k < 8; ++k) r[k] = (k == 5) ? fmax(r[k], scratch[b * 8 + k]) : r[k] + scratch[b * 8 + k];
-    double vol = g.dx * (g.ny > 1 ? g.dy : 1.0);
+    double vol = g.dx * (g.ny > 1 ? g.dy : 1.0) * (g.nz > 1 ? g.dz : 1.0);
     for (int k = 0; k < 5; ++k) out[k] = r[k] * vol;
     out[5] = r[5];
     out[6] = r[6];

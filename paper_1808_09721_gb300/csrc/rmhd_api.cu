@@ -38,7 +38,8 @@ struct rmhd_ctx {
     char *ws;
     size_t ws_bytes;
     double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
-    double *R3;  // SSP3(332): q^n + dt/4 L1 + (1/2 - gamma) dt Psi1 (null for SSP2)
+    double *R3;    // SSP3(332): q^n + dt/4 L1 + (1/2 - gamma) dt Psi1 (null for SSP2)
+    double *LBUF;  // 3-D grids: L_x + L_y of the current flux pass (null otherwise)
     int *status;       // device [2]
     int *h_status;     // pinned host copy of the 64-bit status key
     double *h_diag;    // pinned host [8]
@@ -113,6 +114,12 @@ static int validate(const rmhd_config *cfg) {
         return RMHD_ERR_INVALID;
     if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED) return RMHD_ERR_INVALID;
     if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
+    if (cfg->nz < 0) return RMHD_ERR_INVALID;
+    if (cfg->nz > 1) {
+        if (cfg->ny < 2 || cfg->model != RMHD_RESISTIVE || !(cfg->zlen > 0.0)) return RMHD_ERR_INVALID;
+        if (cfg->bc_z != RMHD_OUTFLOW && cfg->bc_z != RMHD_PERIODIC) return RMHD_ERR_INVALID;
+        if ((long long)cfg->nx * cfg->ny * cfg->nz > (1LL << 31) - 1) return RMHD_ERR_INVALID;
+    }
     return RMHD_OK;
 }
 
@@ -122,17 +129,23 @@ static Grid make_grid(const rmhd_config *cfg) {
     g.ny = cfg->ny;
     g.bcx = cfg->bc_x;
     g.bcy = cfg->bc_y;
-    g.ncell = (long long)cfg->nx * cfg->ny;
+    g.nz = cfg->nz > 1 ? cfg->nz : 1;
+    g.bcz = cfg->bc_z;
+    g.ncell = (long long)cfg->nx * cfg->ny * g.nz;
     g.plane = (g.ncell + 63) / 64 * 64;
     g.dx = (cfg->xmax - cfg->xmin) / cfg->nx;
     g.dy = cfg->ny > 1 ? (cfg->ymax - cfg->ymin) / cfg->ny : 1.0;
+    g.dz = g.nz > 1 ? cfg->zlen / g.nz : 1.0;
     g.rdx4 = 0.25 / g.dx;
     g.rdy4 = 0.25 / g.dy;
+    g.rdz4 = 0.25 / g.dz;
+    g.row = cfg->nx;
+    g.zoff = (long long)cfg->nx * cfg->ny;
     return g;
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, R3, stage, scratch, diag, status;
+    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, stage, scratch, diag, status;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -150,6 +163,12 @@ static Grid make_grid_n(const rmhd_config *cfg, long long ncell) {
     g.dy = 1.0;
     g.rdx4 = 0.25;
     g.rdy4 = 0.25;
+    g.nz = 1;
+    g.bcz = 0;
+    g.dz = 1.0;
+    g.rdz4 = 0.25;
+    g.row = ncell;
+    g.zoff = 0;
     return g;
 }
 
@@ -169,6 +188,8 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.R = o; o += align256(nc * pl);
     L.R3 = 0;
     if (cfg->scheme == RMHD_SSP3) { L.R3 = o; o += align256(nc * pl); }
+    L.LBUF = 0;
+    if (cfg->nz > 1) { L.LBUF = o; o += align256(nc * pl); }
     L.ACC = o; o += align256(nc * pl);
     L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
@@ -299,6 +320,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->R = (double *)(c->ws + L.R);
     c->ACC = (double *)(c->ws + L.ACC);
     c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
+    c->LBUF = L.LBUF ? (double *)(c->ws + L.LBUF) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -497,6 +519,20 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
     return RMHD_OK;
 }
 
+// One flux pass of a single grid (3-D grids take the two-pass path).
+static cudaError_t flux_pass(rmhd_ctx *c, int nout, const FluxArgs &f) {
+    if (c->g.nz > 1) return launch_flux_3d(c->cfg.precision, nout, c->g, c->ph, f, c->LBUF, c->stream);
+    return launch_flux(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->stream);
+}
+
+// Smallest cell width (the CFL time step uses it).
+static double min_width(const rmhd_ctx *c) {
+    double h = c->g.dx;
+    if (c->cfg.ny > 1) h = std::min(h, c->g.dy);
+    if (c->g.nz > 1) h = std::min(h, c->g.dz);
+    return h;
+}
+
 // SSP3(332) step (Table 2): three implicit stages (each in place in Q1/W1)
 // and three flux passes:
 //   pass 1: r2 = q^n + dt L1 + (1 - 2g) dt Psi1,  r3' = q^n + dt/4 L1 + (1/2 - g) dt Psi1,
@@ -504,7 +540,7 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
 //   pass 2: r3 = r3' + dt/4 L2,  acc += dt/6 (L2 + Psi2)
 //   pass 3: q^{n+1} = acc + 2 dt/3 (L3 + Psi3)
 static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
-    const int m = c->cfg.model, pr = c->cfg.precision;
+    const int m = c->cfg.model;
     FluxArgs f;
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
@@ -512,19 +548,19 @@ static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
     int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma);
     n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma);
     n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
-    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
+    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
     StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
     f = flux_args(c->Q1, c->W1, dt);
     n = add_out(f, 0, c->R3, c->R, 0.25, 0.0);
     n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
-    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
+    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
     StageArgs s3{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s3, c->stream));
     f = flux_args(c->Q1, c->W1, dt);
     f.wcarry = c->W;
     n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0);
-    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, pr, n, c->g, c->ph, f, c->stream));
+    LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
     return RMHD_OK;
 }
 
@@ -537,11 +573,11 @@ static int enqueue_step(rmhd_ctx *c, double dt) {
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
     int n = ssp2_pass1(c, c->Q1, c->W1, dt, f);
-    LAUNCH(c, RMHD_K_FLUX1, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
+    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
     StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
     n = ssp2_pass2(c, c->Q1, c->W1, dt, f);
-    LAUNCH(c, RMHD_K_FLUX2, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
+    LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
     return RMHD_OK;
 }
 
@@ -554,7 +590,7 @@ int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
         if (st) return st;
         dt = dt > 0.0 ? dt : c->cfg.cfl * c->run_dx[0];  // time of run 0 is reported
     }
-    if (!(dt > 0.0)) dt = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
+    if (!(dt > 0.0)) dt = c->cfg.cfl * min_width(c);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt must be positive (set cfl)");
     if (nsteps == 0) { if (t_out) *t_out = c->t; return RMHD_OK; }
     if (c->recording) {
@@ -632,7 +668,7 @@ static int validate_batch(const rmhd_config *base, int nruns, const int *nx, con
         if (sigma && !(sigma[r] > 0.0 && std::isfinite(sigma[r]))) return RMHD_ERR_INVALID;
     }
     if (tot > (1LL << 31) - 1) return RMHD_ERR_INVALID;
-    if (base->scheme != RMHD_SSP2) return RMHD_ERR_INVALID;
+    if (base->scheme != RMHD_SSP2 || base->nz > 1) return RMHD_ERR_INVALID;
     one.nx = (int)std::min<long long>(tot, 1 << 30);
     return validate(&one);
 }
@@ -711,6 +747,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->R = (double *)(c->ws + L.R);
     c->ACC = (double *)(c->ws + L.ACC);
     c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
+    c->LBUF = L.LBUF ? (double *)(c->ws + L.LBUF) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -877,8 +914,9 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->cfg.scheme != RMHD_SSP2)
-        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 SSP2(222) single-grid contexts only");
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->cfg.scheme != RMHD_SSP2 ||
+        c->g.nz > 1)
+        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 SSP2(222) 1-D/2-D single-grid contexts only");
     if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
     return RMHD_OK;
@@ -1043,7 +1081,7 @@ int rmhd_diagnostics(rmhd_ctx *c, double *out) {
     CK(c, cudaMemcpyAsync(c->h_diag, c->diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 7; ++k) out[k] = c->h_diag[k];
-    out[7] = c->cfg.cfl * (c->cfg.ny > 1 ? std::min(c->g.dx, c->g.dy) : c->g.dx);
+    out[7] = c->cfg.cfl * min_width(c);
     return RMHD_OK;
 }
 

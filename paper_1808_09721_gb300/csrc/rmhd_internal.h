@@ -16,6 +16,12 @@ struct Grid {
     long long plane;
     double dx, dy;
     double rdx4, rdy4;  // 0.25 / dx, 0.25 / dy (host-computed)
+    int nz, bcz;        // 3-D grids: cells and boundary condition along z (nz = 1: none)
+    double dz, rdz4;
+    // Index map of a flux tile: cell (i, j) of the tile's 2-D grid sits at
+    // zoff * blockIdx.z + j * row + i (x-y planes: row = nx, zoff = nx ny;
+    // x-z slabs of a 3-D grid: row = nx ny, zoff = nx).
+    long long row, zoff;
 };
 
 // Physical constants of a run plus host-precomputed reciprocals (the device
@@ -39,6 +45,8 @@ struct FluxArgs {
     double *out[3];         // out[k] = base[k] + dt (aL[k] L + aS[k] Psi), k < nout
     double aL[3], aS[3];
     double *wcarry;         // if not null: the stage primitives are copied here (next warm start)
+    double *lout;           // nout = 0 (x-y pass of a 3-D grid): L_x + L_y is written here, nothing else
+    const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
     double dt;
 };
 
@@ -69,6 +77,10 @@ struct BatchArgs {
 cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s);
 cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                         cudaStream_t s);
+// 3-D grids (one fluid): x-y pass into lbuf (L_x + L_y), then the z pass on x-z
+// slabs adds L_z and forms the nout combinations of `a`.
+cudaError_t launch_flux_3d(int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
+                           double *lbuf, cudaStream_t s);
 // primitives (user layout, device) -> conserved + internal primitives
 cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const double *prims, double *q, double *w,
                              int *status, cudaStream_t s);

@@ -23,12 +23,15 @@ class Sim:
 
     def __init__(self, model: int, nx: int, ny: int, xlim, ylim, gamma: float, sigma: float,
                  bc_x: int, bc_y: int, cfl: float = 0.4, mu_e: float = -1.0, mu_p: float = 1.0,
-                 kappa: float = 1.0, precision: int = L.FP64, device=None, scheme: int = L.SSP2):
+                 kappa: float = 1.0, precision: int = L.FP64, device=None, scheme: int = L.SSP2,
+                 nz: int = 1, zlim=(0.0, 1.0), bc_z: int = L.PERIODIC):
+        """nz > 1 makes a 3-D grid (resistive model; arrays [var][nz][ny][nx])."""
         torch = _torch()
         self.lib = L.load()
         self.device = torch.device("cuda" if device is None else device)
+        self.nz = max(1, nz)
         self.cfg = L.Config(model, nx, ny, xlim[0], xlim[1], ylim[0], ylim[1], gamma, sigma, mu_e, mu_p,
-                            kappa, cfl, bc_x, bc_y, precision, scheme)
+                            kappa, cfl, bc_x, bc_y, precision, scheme, self.nz, bc_z, zlim[1] - zlim[0])
         self.model, self.nx, self.ny = model, nx, ny
         nbytes = C.c_size_t()
         self._check(self.lib.rmhd_workspace_bytes(C.byref(self.cfg), C.byref(nbytes)), None)
@@ -42,6 +45,11 @@ class Sim:
         self._check(self.lib.rmhd_create(C.byref(self.h), C.byref(self.cfg), C.c_void_p(self.stream.cuda_stream),
                                          C.c_void_p(self.workspace.data_ptr()), nbytes.value), None)
 
+    @property
+    def shape(self):
+        nz = getattr(self, "nz", 1)
+        return (nz, self.ny, self.nx) if nz > 1 else (self.ny, self.nx)
+
     @classmethod
     def batch(cls, workloads, precision: int = L.FP64, device=None):
         """One context for many independent 1-D runs (same model, x-range,
@@ -51,7 +59,7 @@ class Sim:
     @classmethod
     def from_workload(cls, wl, precision: int = L.FP64, device=None, scheme: int = L.SSP2):
         s = cls(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl,
-                wl.mu_e, wl.mu_p, wl.kappa, precision, device, scheme)
+                wl.mu_e, wl.mu_p, wl.kappa, precision, device, scheme, wl.nz, wl.zlim, wl.bc_z)
         s.set_prims(wl.prims)
         return s
 
@@ -78,7 +86,7 @@ class Sim:
     def _ptr(self, a, nvar, writable):
         """(pointer, where, keepalive) for a numpy array or a CUDA tensor."""
         torch = _torch()
-        n = nvar * self.nx * self.ny
+        n = nvar * self.nx * self.ny * getattr(self, "nz", 1)
         if isinstance(a, torch.Tensor):
             assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
             # order the library's stream after the producer of `a` on torch's stream
@@ -104,14 +112,14 @@ class Sim:
 
     def prims(self, out=None):
         if out is None:
-            out = np.empty((self.np, self.ny, self.nx))
+            out = np.empty((self.np,) + self.shape)
         p, where, _keep = self._ptr(out, self.np, True)
         self._check(self.lib.rmhd_get_prims(self.h, p, where), "get_prims")
         return out
 
     def cons(self, out=None):
         if out is None:
-            out = np.empty((self.nc, self.ny, self.nx))
+            out = np.empty((self.nc,) + self.shape)
         p, where, _keep = self._ptr(out, self.nc, True)
         self._check(self.lib.rmhd_get_cons(self.h, p, where), "get_cons")
         return out
@@ -139,7 +147,7 @@ class Sim:
         if isinstance(dJ_dcons, np.ndarray):
             dJ_dcons = np.ascontiguousarray(dJ_dcons, dtype=np.float64)
         if out is None:
-            out = np.empty((11, self.ny, self.nx))
+            out = np.empty((11,) + self.shape)
         pin, wi, _k1 = self._ptr(dJ_dcons, self.nc, False)
         pout, wo, _k2 = self._ptr(out, 11, True)
         gs = C.c_double()

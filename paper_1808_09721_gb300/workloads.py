@@ -40,10 +40,13 @@ class Workload:
     bc_y: int
     cfl: float
     nsteps: int
-    prims: np.ndarray = field(repr=False)  # [n_prim][ny][nx] float64
+    prims: np.ndarray = field(repr=False)  # [n_prim][ny][nx] ([n_prim][nz][ny][nx] in 3-D) float64
     mu_e: float = -1.0
     mu_p: float = 1.0
     kappa: float = 1.0
+    nz: int = 1
+    zlim: tuple = (0.0, 1.0)
+    bc_z: int = 1
 
     @property
     def dx(self):
@@ -54,13 +57,19 @@ class Workload:
         return (self.ylim[1] - self.ylim[0]) / self.ny
 
     @property
+    def dz(self):
+        return (self.zlim[1] - self.zlim[0]) / self.nz
+
+    @property
     def dt(self):
         h = self.dx if self.ny == 1 else min(self.dx, self.dy)
+        if self.nz > 1:
+            h = min(h, self.dz)
         return self.cfl * h
 
     @property
     def cells(self):
-        return self.nx * self.ny
+        return self.nx * self.ny * self.nz
 
     def with_prims(self, prims, **kw):
         return replace(self, prims=prims, **kw)
@@ -119,6 +128,29 @@ def khi(n: int = 1024, seed: int = 0, sigma: float = 1e3, gamma: float = 4.0 / 3
     E = _ideal_e(v, B)
     return Workload("khi", RESISTIVE, n, ny, (-0.5, 0.5), (-0.5, 0.5), gamma, sigma,
                     PERIODIC, PERIODIC, cfl, nsteps, _sf_prims(rho, v, p, B, E))
+
+
+def khi3d(n: int = 128, seed: int = 0, sigma: float = 1e3, gamma: float = 4.0 / 3.0,
+          a: float = 0.05, cfl: float = 0.4, nsteps: int = 50, shape=None) -> Workload:
+    """3-D Kelvin-Helmholtz shear layer on [-1/2, 1/2]^3, periodic: the KHI
+    recipe of `khi` extended along z (rho and v_x depend on y), seeded noise
+    1e-3 U(-1, 1) on v_y and v_z, p = 1, B = (0.1, 0, 0), E = -v x B.
+    `shape` = (nz, ny, nx) for a non-cubic grid."""
+    nz, ny, nx = (n, n, n) if shape is None else shape
+    x = _centres(-0.5, 0.5, nx)
+    y = _centres(-0.5, 0.5, ny)
+    zc = _centres(-0.5, 0.5, nz)
+    Z, Y, X = np.meshgrid(zc, y, x, indexing="ij")
+    band = 0.5 * (np.tanh((Y + 0.25) / a) - np.tanh((Y - 0.25) / a))
+    rng = np.random.default_rng(seed)
+    rho = 1.0 - 0.9 * band
+    v = np.stack([0.25 * (2.0 * band - 1.0), 1e-3 * rng.uniform(-1.0, 1.0, size=X.shape),
+                  1e-3 * rng.uniform(-1.0, 1.0, size=X.shape)])
+    zero = np.zeros_like(X)
+    B = np.stack([zero + 0.1, zero, zero])
+    prims = _sf_prims(rho, v, np.ones_like(X), B, _ideal_e(v, B))
+    return Workload("khi3d", RESISTIVE, nx, ny, (-0.5, 0.5), (-0.5, 0.5), gamma, sigma,
+                    PERIODIC, PERIODIC, cfl, nsteps, prims, nz=nz, zlim=(-0.5, 0.5), bc_z=PERIODIC)
 
 
 def tf_sheet(n: int = 512, seed: int = 1, sigma: float = 1e4, mu: float = 1e3,
