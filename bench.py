@@ -318,6 +318,10 @@ def main():
         tbw = WL.tf_brio_wu(nx=1600)
         tbws, ms_tbw, _ = timed_run(FP64, False, tbw, 100)
         del tbws
+        k3 = WL.khi3d(n=128, seed=0)
+        s3d, ms_3d, kt_3d = timed_run(FP64, True, k3)
+        s3dm, ms_3dm, _ = timed_run(MIXED, False, k3)
+        del s3d, s3dm
         s3, ms_s3, kt_s3 = timed_run(FP64, True, None, None, 1)
         s3m, ms_s3m, _ = timed_run(MIXED, False, None, None, 1)
         del s3, s3m
@@ -334,6 +338,11 @@ def main():
                                    "unit": UNIT,
                                    "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_s3.items()},
                                    "workload": "KHI 1024x1024 with SSP3(332) (Table 2): 3 implicit stages, 3 flux passes"},
+                 "khi3d_128": {"fp64": world * k3.cells * K / (ms_3d * 1e-3),
+                               "mixed": world * k3.cells * K / (ms_3dm * 1e-3),
+                               "ms_per_step_fp64": ms_3d / K, "ms_per_step_mixed": ms_3dm / K, "unit": UNIT,
+                               "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_3d.items()},
+                               "workload": "3-D KHI 128^3 periodic, SSP2(222); flux pass = x-y pass + z pass"},
                  "tf_brio_wu_1600": {"fp64": world * tbw.cells * 100 / (ms_tbw * 1e-3), "unit": UNIT,
                                      "us_per_step": 1e3 * ms_tbw / 100,
                                      "workload": "1-D two-fluid Brio-Wu, pair plasma mu=+-1e3, 1600 cells, 100 steps"},
