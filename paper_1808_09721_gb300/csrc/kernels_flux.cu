@@ -371,7 +371,6 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const int gi = i0 + tx, gj = j0 + ty;
     const bool inside = gi < g.nx && gj < g.ny;
     const long long cell = base + (long long)gj * g.row + gi;
-    const double dt = a.dt;
     if constexpr (NOUT == 0) {
         // x-y pass of a 3-D grid: L_x + L_y only
 #pragma unroll
@@ -393,8 +392,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
 #pragma unroll
             for (int k = 0; k < NOUT; ++k) {
                 if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];  // outputs often share q^n
-                const double v0 = fma(dt * a.aL[k], Lv, b);
-                a.out[k][o] = slot >= 0 ? fma(dt * a.aS[k], s, v0) : v0;
+                const double v0 = fma(a.cL[k], Lv, b);
+                a.out[k][o] = slot >= 0 ? fma(a.cS[k], s, v0) : v0;
             }
         }
         // Last pass of a step: the primitives of q^{n+1} are not recovered here --
@@ -431,7 +430,12 @@ __global__ void __launch_bounds__(TX *G, TX *G <= 512 ? 2 : 1) k_flux_batch(Grid
         pt.sigma = b.sigma[run];
         pt.eta = b.eta[run];
         FluxArgs at = a;
-        at.dt = b.dt[run];
+        const double dtr = b.dt[run];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            at.cL[k] = a.cL[k] * dtr;
+            at.cS[k] = a.cS[k] * dtr;
+        }
         flux_tile<M, TX, 1, G, FT, NOUT>(gt, pt, at, item.y, 0, b.offset[run], smem_raw);
     }
 }

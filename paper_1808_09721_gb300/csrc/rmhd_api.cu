@@ -453,32 +453,35 @@ static int toc(rmhd_ctx *c) {
 
 // Flux-pass arguments: the stage state (q, w), then outputs added one by one
 // as out = base + dt (aL L + aS Psi).
-static FluxArgs flux_args(const double *q, const double *w, double dt) {
+// Coefficients carry the time step: dt > 0 for single grids; batches pass
+// dt = 0 and get per-unit-dt coefficients, which the kernel scales by each
+// run's own dt.
+static FluxArgs flux_args(const double *q, const double *w) {
     FluxArgs a{};
     a.q = q;
     a.w = w;
-    a.dt = dt;
     return a;
 }
-static int add_out(FluxArgs &a, int k, const double *base, double *out, double aL, double aS) {
+static int add_out(FluxArgs &a, int k, const double *base, double *out, double aL, double aS, double dt) {
+    const double sc = dt > 0.0 ? dt : 1.0;
     a.base[k] = base;
     a.out[k] = out;
-    a.aL[k] = aL;
-    a.aS[k] = aS;
+    a.cL[k] = aL * sc;
+    a.cS[k] = aS * sc;
     return k + 1;
 }
 
 // SSP2(222) flux passes (Table 1): pass 1 forms r2 = q^n + dt L1 + (1 - 2g) dt Psi1
 // and acc = q^n + dt/2 (L1 + Psi1); pass 2 forms q^{n+1} = acc + dt/2 (L2 + Psi2).
 static int ssp2_pass1(rmhd_ctx *c, const double *q1, const double *w1, double dt, FluxArgs &a) {
-    a = flux_args(q1, w1, dt);
-    int n = add_out(a, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma);
-    return add_out(a, n, c->Q, c->ACC, 0.5, 0.5);
+    a = flux_args(q1, w1);
+    int n = add_out(a, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
+    return add_out(a, n, c->Q, c->ACC, 0.5, 0.5, dt);
 }
 static int ssp2_pass2(rmhd_ctx *c, const double *q2, const double *w2, double dt, FluxArgs &a) {
-    a = flux_args(q2, w2, dt);
+    a = flux_args(q2, w2);
     a.wcarry = c->W;
-    return add_out(a, 0, c->ACC, c->Q, 0.5, 0.5);
+    return add_out(a, 0, c->ACC, c->Q, 0.5, 0.5, dt);
 }
 
 // One SSP2(222) step of a batch: per-run dt, a_ii dt and 1/(1 + a_ii dt kappa)
@@ -544,22 +547,22 @@ static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
     FluxArgs f;
     StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
-    f = flux_args(c->Q1, c->W1, dt);
-    int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma);
-    n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma);
-    n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
+    f = flux_args(c->Q1, c->W1);
+    int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
+    n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma, dt);
+    n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
     LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
     StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
-    f = flux_args(c->Q1, c->W1, dt);
-    n = add_out(f, 0, c->R3, c->R, 0.25, 0.0);
-    n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0);
+    f = flux_args(c->Q1, c->W1);
+    n = add_out(f, 0, c->R3, c->R, 0.25, 0.0, dt);
+    n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
     LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
     StageArgs s3{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s3, c->stream));
-    f = flux_args(c->Q1, c->W1, dt);
+    f = flux_args(c->Q1, c->W1);
     f.wcarry = c->W;
-    n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0);
+    n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0, dt);
     LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
     return RMHD_OK;
 }

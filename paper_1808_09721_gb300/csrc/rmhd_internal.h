@@ -42,12 +42,11 @@ struct FluxArgs {
     const double *q;        // stage state, NC planes
     const double *w;        // stage primitives, NW planes
     const double *base[3];  // base of each output (may be the output itself: in-place update)
-    double *out[3];         // out[k] = base[k] + dt (aL[k] L + aS[k] Psi), k < nout
-    double aL[3], aS[3];
+    double *out[3];         // out[k] = base[k] + cL[k] L + cS[k] Psi, k < nout
+    double cL[3], cS[3];    // dt times the tableau coefficients (batches: per unit dt, scaled per run)
     double *wcarry;         // if not null: the stage primitives are copied here (next warm start)
     double *lout;           // nout = 0 (x-y pass of a 3-D grid): L_x + L_y is written here, nothing else
     const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
-    double dt;
 };
 
 struct StageArgs {
