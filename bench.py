@@ -141,6 +141,14 @@ def natural_scale(model, want, mu_ref=1.0):
     return np.maximum(s, 1e-300)
 
 
+def rel_l1(model, got, want, mu_ref=1.0):
+    """Largest over variables of mean |got - want| / natural scale."""
+    import numpy as np
+    nv = want.shape[0]
+    w3 = want.reshape(nv, -1, 1)
+    return float(np.max(np.abs(got - want).reshape(nv, -1).mean(axis=1) / natural_scale(model, w3, mu_ref)))
+
+
 def reduce_max(x: float, world: int, device: str) -> float:
     """Max of a per-rank value (elapsed time) over all ranks of the process
     group (NCCL on the GPUs; any backend whose device is given)."""
@@ -320,10 +328,12 @@ def main():
         del tbws
         k3 = WL.khi3d(n=128, seed=0)
         s3d, ms_3d, kt_3d = timed_run(FP64, True, k3)
-        s3dm, ms_3dm, _ = timed_run(MIXED, False, k3)
+        s3dm, ms_3dm, _ = timed_run(MIXED, True, k3)
+        l1_3d = rel_l1(0, s3dm.cons(), s3d.cons())
         del s3d, s3dm
         s3, ms_s3, kt_s3 = timed_run(FP64, True, None, None, 1)
-        s3m, ms_s3m, _ = timed_run(MIXED, False, None, None, 1)
+        s3m, ms_s3m, _ = timed_run(MIXED, True, None, None, 1)
+        l1_s3 = rel_l1(0, s3m.cons(), s3.cons())
         del s3, s3m
         extra = {"two_fluid_512": {"fp64": world * tfw.cells * K / (ms_tf64 * 1e-3),
                                    "mixed": world * tfw.cells * K / (ms_tfmx * 1e-3),
@@ -335,12 +345,14 @@ def main():
                  "khi_1024_ssp3": {"fp64": world * wl.cells * K / (ms_s3 * 1e-3),
                                    "mixed": world * wl.cells * K / (ms_s3m * 1e-3),
                                    "ms_per_step_fp64": ms_s3 / K, "ms_per_step_mixed": ms_s3m / K,
+                                   "rel_l1_mixed_vs_fp64": l1_s3,
                                    "unit": UNIT,
                                    "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_s3.items()},
                                    "workload": "KHI 1024x1024 with SSP3(332) (Table 2): 3 implicit stages, 3 flux passes"},
                  "khi3d_128": {"fp64": world * k3.cells * K / (ms_3d * 1e-3),
                                "mixed": world * k3.cells * K / (ms_3dm * 1e-3),
                                "ms_per_step_fp64": ms_3d / K, "ms_per_step_mixed": ms_3dm / K, "unit": UNIT,
+                               "rel_l1_mixed_vs_fp64": l1_3d,
                                "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_3d.items()},
                                "workload": "3-D KHI 128^3 periodic, SSP2(222); flux pass = x-y pass + z pass"},
                  "tf_brio_wu_1600": {"fp64": world * tbw.cells * 100 / (ms_tbw * 1e-3), "unit": UNIT,
@@ -380,9 +392,17 @@ def main():
         torch.cuda.synchronize()
         bsim.check()
         full_ms = e0.elapsed_time(e1)
+        # error of the mixed form: every tube's 400-step state against the FP64 run
+        b64 = Sim.batch(runs, precision=FP64, device=f"cuda:{local}")
+        b64.step(0.0, 400)
+        b64.check()
+        gm, g64 = bsim.unpack(bsim.cons()), b64.unpack(b64.cons())
+        l1_batch = max(rel_l1(0, a, b) for a, b in zip(gm, g64))
+        del b64
         batch = {"value": world * bcells * K / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms / K,
                  "runs": len(runs), "cells": bcells, "dtype": "f32 flux / f64 source",
                  "full_run_400_steps_s": full_ms * 1e-3, "autotune": choice,
+                 "rel_l1_mixed_vs_fp64_max_over_tubes": l1_batch,
                  "workload": "512 1-D resistive shock tubes, N~U{100..4096}, sigma log-uniform [1,1e6], "
                              "Gamma=4/3, own CFL dt, one CUDA graph per step"}
         del bsim

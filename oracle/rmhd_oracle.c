@@ -665,7 +665,11 @@ static int ghost_src(int g, int n, int ng, int bc)
 {
     /* padded index g (outside [ng, ng + n)) -> the padded interior index it copies */
     int lo = ng, hi = ng + n - 1;
-    if (bc == BC_PERIODIC) return g < lo ? g + n : g - n;
+    if (bc == BC_PERIODIC) {
+        /* wrap modulo n: also for grids with fewer interior cells than ghost layers */
+        int t = (g - ng) % n;
+        return ng + (t < 0 ? t + n : t);
+    }
     return g < lo ? lo : hi;
 }
 

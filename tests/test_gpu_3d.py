@@ -97,3 +97,15 @@ def test_khi3d_ssp3_and_mixed(Sim):
     want = o.cons()
     l1 = np.abs(g.cons() - want).reshape(14, -1).mean(axis=1) / parity_scale(0, want.reshape(14, -1, 1))
     assert np.all(l1 <= 1e-4), l1
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 5), (3, 2, 1), (5, 9, 2)])
+def test_tiny_3d_grids(Sim, shape):
+    """Degenerate 3-D grids: extents smaller than the stencil, a single cell
+    across x, outflow along z."""
+    wl = WL.khi3d(shape=shape, seed=4)
+    import dataclasses
+    wl = dataclasses.replace(wl, bc_z=0)
+    g, o = run_pair(Sim, wl, 2)
+    err = parity_errors(0, g.cons().reshape(14, -1, 1), o.cons().reshape(14, -1, 1))
+    assert np.all(err <= TOL), err

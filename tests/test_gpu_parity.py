@@ -158,11 +158,13 @@ def test_diagnostics_conservation(Sim):
     assert abs(d1["dt_cfl"] - wl.dt) < 1e-15
 
 
-def test_full_size_khi_sampled_cells(Sim):
-    """Full 1024^2 KHI in the bench's launch configuration: one step on the GPU;
-    sampled cells checked against the oracle on 16 x 16 periodic windows (a cell
-    after one step depends only on cells within 4 of it)."""
-    wl = WL.khi(n=1024, seed=0)
+@pytest.mark.parametrize("n", [1024, 8192])
+def test_full_size_khi_sampled_cells(Sim, n):
+    """KHI in the bench's launch configuration -- the 1024^2 benchmark grid and
+    an 8192^2 grid (67 M cells, ~45 GB of state and workspace in HBM): one step
+    on the GPU; sampled cells checked against the oracle on 16 x 16 periodic
+    windows (a cell after one step depends only on cells within 4 of it)."""
+    wl = WL.khi(n=n, seed=0)
     g = Sim.from_workload(wl)
     g.step(wl.dt, 1)
     g.check()
@@ -170,9 +172,9 @@ def test_full_size_khi_sampled_cells(Sim):
     rng = np.random.default_rng(9)
     h = 8
     for _ in range(6):
-        j0, i0 = (int(x) for x in rng.integers(0, 1024, size=2))
-        jj = (np.arange(j0 - h, j0 + h) % 1024)
-        ii = (np.arange(i0 - h, i0 + h) % 1024)
+        j0, i0 = (int(x) for x in rng.integers(0, n, size=2))
+        jj = (np.arange(j0 - h, j0 + h) % n)
+        ii = (np.arange(i0 - h, i0 + h) % n)
         win = np.ascontiguousarray(wl.prims[:, jj][:, :, ii])
         sub = wl.with_prims(win, nx=2 * h, ny=2 * h, bc_x=WL.OUTFLOW, bc_y=WL.OUTFLOW,
                             xlim=(0.0, 2 * h * wl.dx), ylim=(0.0, 2 * h * wl.dy))

@@ -202,3 +202,21 @@ def test_constant_state_has_zero_divergence():
     sim = O.Sim(O.MODEL_SF, 8, 8, (0, 1), (0, 1), 4.0 / 3.0, 1e3, O.BC_PERIODIC, O.BC_PERIODIC)
     sim.set_cons(_uniform_cons(8, 8, prim, 0.2, 0.1, 0.05))
     assert np.max(np.abs(sim.flux_divergence())) == 0.0
+
+
+def test_periodic_wrap_narrower_than_stencil():
+    """Periodic boundary condition: ghosts wrap modulo the extent, also when a
+    direction has fewer cells than ghost layers. A 1-cell-wide periodic x
+    direction is uniform along x, so the run equals the same data with 3
+    identical copies along x."""
+    wl = WL.khi(n=8, seed=2)
+    p1 = np.ascontiguousarray(wl.prims[:, :, :1])
+    p3 = np.ascontiguousarray(np.repeat(p1, 3, axis=2))
+    out = []
+    for p, nx in ((p1, 1), (p3, 3)):
+        s = O.Sim(O.MODEL_SF, nx, 8, (0, nx / 8), (-0.5, 0.5), wl.gamma, wl.sigma, O.BC_PERIODIC, O.BC_PERIODIC)
+        s.set_prims(p)
+        s.step(wl.dt, 2)
+        out.append(s.cons())
+    assert np.all(np.isfinite(out[0]))
+    np.testing.assert_array_equal(out[0][:, :, 0], out[1][:, :, 1])
