@@ -45,6 +45,11 @@ template <int NTHR>
 __device__ __forceinline__ void group_sync(int grp) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(NTHR) : "memory");
 }
+// Barrier over NTHR threads with an explicit named-barrier id.
+template <int NTHR>
+__device__ __forceinline__ void named_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHR) : "memory");
+}
 
 // ---- model adaptors ------------------------------------------------------
 // Per-cell quantities staged once per tile (aux), the flux of one cell from
@@ -222,6 +227,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     constexpr int NT = NL * G;
     constexpr int OY = TWO_D ? 2 : 0;   // SMEM row of the first interior row
     constexpr int NR = (NC + G - 1) / G; // component rounds
+    constexpr int LAST = NC - (NR - 1) * G;  // groups with a component in the last round
+    constexpr bool PAIR = 2 * LAST == G;     // the last round pairs groups up
 
     double *st = reinterpret_cast<double *>(smem_raw + L_::st);   // [NV][SH][SW]
     FT *st32 = reinterpret_cast<FT *>(smem_raw + L_::st32);       // [NV][SH][SW] (FP32 form only)
@@ -293,8 +300,6 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     for (int r = 0; r < NR; ++r) L[r] = FT(0);
 
     const FT eps4 = FT(4e-6);
-    FT *hpg = hp + grp * 4 * SN;
-    FT *fcg = fc + grp * SN;
 #pragma unroll 1
     for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
         if (!((DIRS >> dir) & 1)) continue;
@@ -324,45 +329,58 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
         const int fx0 = dir == 0 ? 1 : 2, fy0 = dir == 0 ? OY : 1;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int c = r * G + grp;
+            // When exactly half of the groups have a component in the last
+            // round, groups p and p + LAST pair up on component r G + p (p <
+            // LAST): both work on its half points and faces (in group p's
+            // buffers, 2 NL threads, pair barrier 1 + G + p); group p, which
+            // owns the component, accumulates it.
+            const bool pair_round = PAIR && r == NR - 1;
+            const int cg = pair_round ? grp % LAST : grp;  // group whose component and buffers are used
+            const int c = r * G + cg;
             const bool active = c < NC;
-            // 3b. half points of component c (group grp)
+            const int wid = pair_round ? (grp / LAST) * NL + lid : lid;
+            const int wstride = pair_round ? 2 * NL : NL;
+            FT *hpw = hp + cg * 4 * SN;
+            FT *fcw = fc + cg * SN;
+            // the partner writes group cg's buffers: both must be done with the previous round
+            if (pair_round) named_sync<2 * NL>(1 + G + cg);
+            // 3b. half points of component c
             if (active) {
                 const FT *fv = fl + c * SN;
                 const double *qv = st + (L_::SHADOW ? 0 : c * SN);
                 const FT *qv32 = st32 + c * SN;
-                for (int e = lid; e < nhx * nhy; e += NL) {
+                for (int e = wid; e < nhx * nhy; e += wstride) {
                     int hy = e / nhx, hx = e - hy * nhx;
                     int idx = (hy0 + hy) * SW + hx0 + hx;
                     FT df = fv[idx + sstep] - fv[idx];
                     FT dq = L_::SHADOW ? qv32[idx + sstep] - qv32[idx] : FT(qv[idx + sstep] - qv[idx]);
                     FT ep = df + dq, em = df - dq;
                     FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
-                    hpg[idx] = ep;
-                    hpg[SN + idx] = em;
-                    hpg[2 * SN + idx] = ap * ap;
-                    hpg[3 * SN + idx] = am * am;
+                    hpw[idx] = ep;
+                    hpw[SN + idx] = em;
+                    hpw[2 * SN + idx] = ap * ap;
+                    hpw[3 * SN + idx] = am * am;
                 }
             }
-            group_sync<NL>(grp);
+            if (pair_round) named_sync<2 * NL>(1 + G + cg); else group_sync<NL>(grp);
             // 3c. face values of component c
             if (active) {
                 const FT *fv = fl + c * SN;
-                for (int e = lid; e < nfx * nfy; e += NL) {
+                for (int e = wid; e < nfx * nfy; e += wstride) {
                     int fy = e / nfx, fx = e - fy * nfx;
                     int idx = (fy0 + fy) * SW + fx0 + fx;
                     int il = idx - sstep, ir = idx + sstep;
-                    FT Ap = hpg[2 * SN + idx], Am = hpg[3 * SN + idx];
-                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpg[2 * SN + il], Ap));
-                    FT wm = Am * s_rcp1(s_fma(FT(2), hpg[3 * SN + ir], Am));
-                    FT Xp = hpg[il] - hpg[idx];
-                    FT Xm = hpg[SN + idx] - hpg[SN + ir];
-                    fcg[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+                    FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
+                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpw[2 * SN + il], Ap));
+                    FT wm = Am * s_rcp1(s_fma(FT(2), hpw[3 * SN + ir], Am));
+                    FT Xp = hpw[il] - hpw[idx];
+                    FT Xm = hpw[SN + idx] - hpw[SN + ir];
+                    fcw[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
                 }
             }
-            group_sync<NL>(grp);
+            if (pair_round) named_sync<2 * NL>(1 + G + cg); else group_sync<NL>(grp);
             // 3d. flux difference into the owned cell's accumulator
-            if (active) L[r] = s_fma(fcg[oy * SW + ox - sstep] - fcg[oy * SW + ox], inv4h, L[r]);
+            if (active && cg == grp) L[r] = s_fma(fcw[oy * SW + ox - sstep] - fcw[oy * SW + ox], inv4h, L[r]);
         }
         __syncthreads();
     }
