@@ -75,8 +75,8 @@ typedef struct rmhd_config {
     int bc_x, bc_y;   /* RMHD_OUTFLOW or RMHD_PERIODIC */
     int precision;    /* RMHD_FP64 or RMHD_MIXED */
     int scheme;       /* RMHD_SSP2 (0, Table 1) or RMHD_SSP3 (1, Table 2); batches: RMHD_SSP2 */
-    int nz;           /* cells along z; 0 or 1: a 1-D or 2-D grid. nz > 1 (3-D) needs ny > 1, the
-                         resistive model, a single grid; arrays are then [n_var][nz][ny][nx] */
+    int nz;           /* cells along z; 0 or 1: a 1-D or 2-D grid. nz > 1 (3-D) needs ny > 1 and a
+                         single grid (not a batch); arrays are then [n_var][nz][ny][nx] */
     int bc_z;         /* RMHD_OUTFLOW or RMHD_PERIODIC along z (3-D only) */
     double zlen;      /* extent of the grid along z (3-D only), dz = zlen / nz */
 } rmhd_config;

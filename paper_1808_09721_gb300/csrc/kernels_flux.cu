@@ -528,14 +528,14 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
     return launch_fb_t<M, 128, FT, NOUT>(g, ph, a, b, blocks, s);
 }
 
-// 3-D grids, one fluid. Pass 1: every x-y plane (blockIdx.z = k) with the
+// 3-D grids. Pass 1: every x-y plane (blockIdx.z = k) with the
 // 2-D tile, both in-plane directions, L_x + L_y written to lbuf. Pass 2: the
 // x-z slabs (blockIdx.z = j; the tile's second dimension is z, rows nx*ny
 // apart), the z direction only, lbuf added, then the combinations.
-template <class FT>
+template <class M, class FT>
 static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, const FluxArgs &a, double *lbuf,
                                     cudaStream_t s) {
-    constexpr int G = sizeof(FT) == 8 ? SFModel::G_FP64 : SFModel::G_FP32;
+    constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
     Grid gxy = g;
     gxy.row = g.nx;
     gxy.zoff = (long long)g.nx * g.ny;
@@ -543,7 +543,7 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     axy.lout = lbuf;
     axy.lin = nullptr;
     axy.wcarry = nullptr;
-    cudaError_t e = launch_flux_t<SFModel, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
+    cudaError_t e = launch_flux_t<M, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
     if (e != cudaSuccess) return e;
     Grid gz = g;
     gz.ny = g.nz;
@@ -555,16 +555,19 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     FluxArgs az = a;
     az.lout = nullptr;
     az.lin = lbuf;
-    if (nout == 1) return launch_flux_t<SFModel, 32, 8, G, FT, 1, 2>(gz, ph, az, s, g.ny);
-    if (nout == 2) return launch_flux_t<SFModel, 32, 8, G, FT, 2, 2>(gz, ph, az, s, g.ny);
-    if (nout == 3) return launch_flux_t<SFModel, 32, 8, G, FT, 3, 2>(gz, ph, az, s, g.ny);
+    if (nout == 1) return launch_flux_t<M, 32, 8, G, FT, 1, 2>(gz, ph, az, s, g.ny);
+    if (nout == 2) return launch_flux_t<M, 32, 8, G, FT, 2, 2>(gz, ph, az, s, g.ny);
+    if (nout == 3) return launch_flux_t<M, 32, 8, G, FT, 3, 2>(gz, ph, az, s, g.ny);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_flux_3d(int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
+cudaError_t launch_flux_3d(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                            double *lbuf, cudaStream_t s) {
-    return precision == 0 ? launch_flux_3d_t<double>(nout, g, ph, a, lbuf, s)
-                          : launch_flux_3d_t<float>(nout, g, ph, a, lbuf, s);
+    if (model == 0)
+        return precision == 0 ? launch_flux_3d_t<SFModel, double>(nout, g, ph, a, lbuf, s)
+                              : launch_flux_3d_t<SFModel, float>(nout, g, ph, a, lbuf, s);
+    return precision == 0 ? launch_flux_3d_t<TFModel, double>(nout, g, ph, a, lbuf, s)
+                          : launch_flux_3d_t<TFModel, float>(nout, g, ph, a, lbuf, s);
 }
 
 // Batches run SSP2(222): passes with two outputs (r2, acc) and one (q^{n+1}).

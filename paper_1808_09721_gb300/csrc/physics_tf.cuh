@@ -49,7 +49,8 @@ __device__ __forceinline__ void flux(const T q[NC], const T w[NW], T mu_e, T mu_
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const T *ws = w + 5 * s;
-        const T vd = dir == 0 ? ws[VX] : ws[VY];  // selects keep the arrays in registers
+        // selects (not indices computed from dir) keep the arrays in registers
+        const T vd = dir == 0 ? ws[VX] : (dir == 1 ? ws[VY] : ws[VZ]);
         const T Dv = Ds[s] * vd;
         const T Zv = ws[ZZ] * vd;
         f[D] += Dv;
@@ -57,25 +58,30 @@ __device__ __forceinline__ void flux(const T q[NC], const T w[NW], T mu_e, T mu_
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             T Sij = Zv * ws[VX + i];
-            if ((i == 0 && dir == 0) || (i == 1 && dir == 1)) Sij += ws[P];
+            if (i == dir) Sij += ws[P];
             f[SX + i] += Sij;
             f[SBX + i] += mu[s] * Sij;
         }
         f[TAUB] += mu[s] * (Zv - Dv);
     }
     const T E2B2 = q[EX] * q[EX] + q[EY] * q[EY] + q[EZ] * q[EZ] + q[BX] * q[BX] + q[BY] * q[BY] + q[BZ] * q[BZ];
-    const T Ed = dir == 0 ? q[EX] : q[EY], Bd = dir == 0 ? q[BX] : q[BY];
+    const T Ed = dir == 0 ? q[EX] : (dir == 1 ? q[EY] : q[EZ]);
+    const T Bd = dir == 0 ? q[BX] : (dir == 1 ? q[BY] : q[BZ]);
     f[SX] -= q[EX] * Ed + q[BX] * Bd;
     f[SY] -= q[EY] * Ed + q[BY] * Bd;
     f[SZ] -= q[EZ] * Ed + q[BZ] * Bd;
-    if (dir == 0) f[SX] += T(0.5) * E2B2; else f[SY] += T(0.5) * E2B2;
-    f[TAU] = (dir == 0 ? q[SX] : q[SY]) - f[D];
+    if (dir == 0) f[SX] += T(0.5) * E2B2; else if (dir == 1) f[SY] += T(0.5) * E2B2; else f[SZ] += T(0.5) * E2B2;
+    f[TAU] = (dir == 0 ? q[SX] : (dir == 1 ? q[SY] : q[SZ])) - f[D];
+    // B^i: -eps^{ijd} E_j + delta_id phi;  E^i: eps^{ijd} B_j + delta_id psi
     if (dir == 0) {
         f[BX] = q[PHI]; f[BY] = -q[EZ]; f[BZ] = q[EY];
         f[EX] = q[PSI]; f[EY] = q[BZ]; f[EZ] = -q[BY];
-    } else {
+    } else if (dir == 1) {
         f[BX] = q[EZ]; f[BY] = q[PHI]; f[BZ] = -q[EX];
         f[EX] = -q[BZ]; f[EY] = q[PSI]; f[EZ] = q[BX];
+    } else {
+        f[BX] = -q[EY]; f[BY] = q[EX]; f[BZ] = q[PHI];
+        f[EX] = q[BY]; f[EY] = -q[BX]; f[EZ] = q[PSI];
     }
     f[PSI] = Ed;
     f[PHI] = Bd;

@@ -116,7 +116,7 @@ static int validate(const rmhd_config *cfg) {
     if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
     if (cfg->nz < 0) return RMHD_ERR_INVALID;
     if (cfg->nz > 1) {
-        if (cfg->ny < 2 || cfg->model != RMHD_RESISTIVE || !(cfg->zlen > 0.0)) return RMHD_ERR_INVALID;
+        if (cfg->ny < 2 || !(cfg->zlen > 0.0)) return RMHD_ERR_INVALID;
         if (cfg->bc_z != RMHD_OUTFLOW && cfg->bc_z != RMHD_PERIODIC) return RMHD_ERR_INVALID;
         if ((long long)cfg->nx * cfg->ny * cfg->nz > (1LL << 31) - 1) return RMHD_ERR_INVALID;
     }
@@ -524,7 +524,7 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
 
 // One flux pass of a single grid (3-D grids take the two-pass path).
 static cudaError_t flux_pass(rmhd_ctx *c, int nout, const FluxArgs &f) {
-    if (c->g.nz > 1) return launch_flux_3d(c->cfg.precision, nout, c->g, c->ph, f, c->LBUF, c->stream);
+    if (c->g.nz > 1) return launch_flux_3d(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->LBUF, c->stream);
     return launch_flux(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->stream);
 }
 

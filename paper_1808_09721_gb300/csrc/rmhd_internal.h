@@ -76,9 +76,9 @@ struct BatchArgs {
 cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s);
 cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                         cudaStream_t s);
-// 3-D grids (one fluid): x-y pass into lbuf (L_x + L_y), then the z pass on x-z
-// slabs adds L_z and forms the nout combinations of `a`.
-cudaError_t launch_flux_3d(int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
+// 3-D grids: x-y pass into lbuf (L_x + L_y), then the z pass on x-z slabs
+// adds L_z and forms the nout combinations of `a`.
+cudaError_t launch_flux_3d(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                            double *lbuf, cudaStream_t s);
 // primitives (user layout, device) -> conserved + internal primitives
 cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const double *prims, double *q, double *w,

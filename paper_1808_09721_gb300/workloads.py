@@ -219,6 +219,27 @@ def tf_current_sheet(nx: int = 50, mu: float = 1e3, sigma: float = 100.0, t0: fl
                     OUTFLOW, OUTFLOW, cfl, 0, np.ascontiguousarray(prims), mu_e=-mu, mu_p=mu)
 
 
+def tf_sheet3d(shape=(64, 64, 64), seed: int = 1, sigma: float = 1e4, mu: float = 1e3,
+               gamma: float = 4.0 / 3.0, width: float = 0.05, cfl: float = 0.4, nsteps: int = 20) -> Workload:
+    """The two-fluid pair-plasma current sheet of `tf_sheet` on [-1/2, 1/2]^3,
+    periodic, (nz, ny, nx) = shape: B_y = tanh(x / width), per species
+    rho_s = p_s = 1/2, seeded 1e-4 U(-1, 1) noise on v_y and v_z of each species."""
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(_centres(-0.5, 0.5, nz), _centres(-0.5, 0.5, ny), _centres(-0.5, 0.5, nx),
+                          indexing="ij")
+    rng = np.random.default_rng(seed)
+    z = np.zeros_like(X)
+    half = np.full_like(X, 0.5)
+    ve = np.stack([z, 1e-4 * rng.uniform(-1.0, 1.0, size=X.shape), 1e-4 * rng.uniform(-1.0, 1.0, size=X.shape)])
+    vp = np.stack([z, 1e-4 * rng.uniform(-1.0, 1.0, size=X.shape), 1e-4 * rng.uniform(-1.0, 1.0, size=X.shape)])
+    B = np.stack([z, np.tanh(X / width), z])
+    E = _ideal_e(0.5 * (ve + vp), B)
+    prims = np.concatenate([half[None], ve, half[None], half[None], vp, half[None], B, E]).astype(np.float64)
+    return Workload("tf_sheet3d", TWO_FLUID, nx, ny, (-0.5, 0.5), (-0.5, 0.5), gamma, sigma,
+                    PERIODIC, PERIODIC, cfl, nsteps, np.ascontiguousarray(prims), mu_e=-mu, mu_p=mu,
+                    nz=nz, zlim=(-0.5, 0.5), bc_z=PERIODIC)
+
+
 def batch_tubes(count: int = 512, seed: int = 2, nmin: int = 100, nmax: int = 4096,
                 gamma: float = 4.0 / 3.0, cfl: float = 0.4, nsteps: int = 400) -> list:
     """Independent 1-D shock tubes on [0, 1], outflow: N ~ U{nmin..nmax},

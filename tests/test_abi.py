@@ -94,13 +94,15 @@ def test_scheme_selection(lib):
 
 
 def test_3d_configuration(lib):
-    """nz > 1: one more 14-plane buffer (L_x + L_y of a flux pass); needs ny > 1,
-    the resistive model and zlen > 0; not for batches."""
+    """nz > 1: one more N_c-plane buffer (L_x + L_y of a flux pass); needs ny > 1
+    and zlen > 0; not for batches."""
     n2, n3 = C.c_size_t(), C.c_size_t()
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(nz=1)), C.byref(n2)) == 0
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(nz=4, zlen=1.0)), C.byref(n3)) == 0
     assert n3.value > 4 * n2.value
-    for bad in (dict(nz=4, zlen=0.0), dict(nz=4, zlen=1.0, ny=1), dict(nz=4, zlen=1.0, model=1),
+    n4 = C.c_size_t()
+    assert lib.rmhd_workspace_bytes(C.byref(_cfg(nz=4, zlen=1.0, model=1)), C.byref(n4)) == 0
+    for bad in (dict(nz=4, zlen=0.0), dict(nz=4, zlen=1.0, ny=1),
                 dict(nz=4, zlen=1.0, bc_z=5), dict(nz=-2)):
         assert lib.rmhd_workspace_bytes(C.byref(_cfg(**bad)), C.byref(n3)) == -1, bad
     nx = (C.c_int * 2)(100, 200)

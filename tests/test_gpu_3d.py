@@ -109,3 +109,24 @@ def test_tiny_3d_grids(Sim, shape):
     g, o = run_pair(Sim, wl, 2)
     err = parity_errors(0, g.cons().reshape(14, -1, 1), o.cons().reshape(14, -1, 1))
     assert np.all(err <= TOL), err
+
+
+def test_two_fluid_3d(Sim):
+    """Two-fluid model on a 3-D grid (18 variables, z pass with the two-fluid
+    flux along z): FP64 parity and the mixed form's L1 error."""
+    wl = WL.tf_sheet3d(shape=(8, 12, 10), seed=3)
+    g = Sim.from_workload(wl)
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y,
+              mu_e=wl.mu_e, mu_p=wl.mu_p, kappa=wl.kappa, nz=wl.nz, zlim=wl.zlim, bc_z=wl.bc_z)
+    o.set_prims(wl.prims)
+    g.step(wl.dt, 3)
+    g.check()
+    o.step(wl.dt, 3)
+    want = o.cons()
+    err = parity_errors(1, g.cons().reshape(18, -1, 1), want.reshape(18, -1, 1), 1e3)
+    assert np.all(err <= TOL), err
+    gm = Sim.from_workload(wl, precision=1)
+    gm.step(wl.dt, 3)
+    gm.check()
+    l1 = np.abs(gm.cons() - want).reshape(18, -1).mean(axis=1) / parity_scale(1, want.reshape(18, -1, 1), 1e3)
+    assert np.all(l1 <= 1e-4), l1
