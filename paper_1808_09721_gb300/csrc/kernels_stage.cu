@@ -46,8 +46,14 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_sf(Grid g, Phys ph, Sta
     }
 }
 
-__global__ void __launch_bounds__(kStageThreads) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
+// Two fluids: the 7 x 7 Jacobian and its inverse of each thread live in a
+// strided slice of shared memory (not in local memory: the pivoted
+// Gauss-Jordan indexes them with run-time rows).
+static constexpr int kStageThreadsTF = 64;
+__global__ void __launch_bounds__(kStageThreadsTF) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace tf;
+    __shared__ float sJ[49 * kStageThreadsTF], sM[49 * kStageThreadsTF];
+    const Mat Jm{sJ + threadIdx.x, kStageThreadsTF}, Minv{sM + threadIdx.x, kStageThreadsTF};
     tf::StageConst k{a.adt, cpsi};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_tf(Grid g, Phys ph, Sta
         for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
 #pragma unroll
         for (int v = 0; v < NW; ++v) ww[v] = a.wwarm[v * g.plane + cell];
-        int st = stage_solve<kNRef>(r, ww, k, ph, q, w);
+        int st = stage_solve<kNRef>(r, ww, k, ph, q, w, Jm, Minv);
         record(a.status, st, cell);
 #pragma unroll
         for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
@@ -74,7 +80,7 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
     double cpsi = 1.0 / (1.0 + a.adt * ph.kappa);
     int blocks = grid_for(g.ncell, kStageThreads);
     if (model == 0) k_stage_sf<<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
-    else k_stage_tf<<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+    else k_stage_tf<<<grid_for(g.ncell, kStageThreadsTF), kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
     return cudaGetLastError();
 }
 
@@ -113,7 +119,8 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
         for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
 #pragma unroll
         for (int v = 0; v < NW; ++v) ww[v] = a.wwarm[v * g.plane + cell];
-        int st = stage_solve<kNRef>(r, ww, k, pr, q, w);
+        float jl[49], ml[49];
+        int st = stage_solve<kNRef>(r, ww, k, pr, q, w, tf::Mat{jl, 1}, tf::Mat{ml, 1});
         record(a.status, st, cell);
 #pragma unroll
         for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];

@@ -234,9 +234,17 @@ __device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], cons
     G[3] = (x[3] - c.rx[3]) - k1 * tb;
 }
 
+// Per-thread N x N scratch matrix: a strided slice of shared memory (element
+// k at p[k * stride]) or a local array (stride 1).
+struct Mat {
+    float *p;
+    int stride;
+    __device__ __forceinline__ float &operator[](int k) const { return p[k * stride]; }
+};
+
 // In-place inverse of an n x n FP32 matrix (Gauss-Jordan, partial pivoting).
 template <int N>
-__device__ __forceinline__ bool invert(float m[N * N], float inv[N * N]) {
+__device__ __forceinline__ bool invert(Mat m, Mat inv) {
 #pragma unroll
     for (int i = 0; i < N * N; ++i) inv[i] = (i % (N + 1) == 0) ? 1.f : 0.f;
     for (int c = 0; c < N; ++c) {
@@ -287,9 +295,12 @@ struct StageConst {
     double adt, cpsi;
 };
 
+// Solve one implicit stage for one cell (two fluids). Jm and Minv are the
+// caller's 7 x 7 FP32 scratch for the Jacobian and its inverse.
+
 template <int NREF>
 __device__ int stage_solve(const double r[NC], const double wwarm[NW], const StageConst &k, const Phys &ph,
-                           double q[NC], double w[NW]) {
+                           double q[NC], double w[NW], Mat Jm, Mat Minv) {
     const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
     const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
     for (int i = 0; i < NC; ++i) q[i] = r[i];
@@ -332,10 +343,9 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     float gn = 0.f;
     for (int i = 0; i < 7; ++i) gn = fmaxf(gn, fabsf(G[i]));
 
-    float Minv[49], dpdx[2][7];
+    float dpdx[2][7];
     bool have_jac = false;
     for (int it = 0; it < 30; ++it) {
-        float Jm[49];
         for (int kc = 0; kc < 7; ++kc) {
             Dual<float> xd[7];
             for (int i = 0; i < 7; ++i) xd[i] = Dual<float>(x[i], i == kc ? 1.f : 0.f);
