@@ -38,6 +38,14 @@ __device__ __forceinline__ double s_rcp1(double x) {
     double e = fma(-x, y, 1.0);
     return fma(y, e, y);
 }
+// a/x with a single Newton step: with t = a y0 and e = 1 - x y0, a/x = t/(1 - e)
+// ~ t (1 + e); relative error ~e^2 ~ 2^-38 in 3 FP64 ops after the approximation.
+__device__ __forceinline__ double s_div1(double a, double x) {
+    double y = approx_rcp(x);
+    double t = a * y;
+    double e = fma(-x, y, 1.0);
+    return fma(t, e, t);
+}
 // 1/sqrt(x) = y0 (1 - e)^(-1/2) with e = 1 - x y0^2:  y0 (1 + e/2 + 3 e^2/8) + O(e^3).
 __device__ __forceinline__ double s_rsqrt(double x) {
     double y = approx_rsqrt(x);
@@ -51,6 +59,7 @@ __device__ __forceinline__ float s_rcp(float x) {
     return y;
 }
 __device__ __forceinline__ float s_rcp1(float x) { return s_rcp(x); }
+__device__ __forceinline__ float s_div1(float a, float x) { return a * s_rcp(x); }
 __device__ __forceinline__ float s_rsqrt(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

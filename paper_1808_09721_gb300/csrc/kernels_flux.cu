@@ -13,8 +13,19 @@
 //   w+ = A+_{i+1/2} / (A+_{i+1/2} + 2 A+_{i-1/2}),  w- = A-_{i+1/2} / (A-_{i+1/2} + 2 A-_{i+3/2}),
 // i.e. the central part plus the two nonlinear corrections of the left- and
 // right-going reconstructions. Half-point quantities are computed once and
-// shared by the two faces that use them; the only division per face and
-// sign is one reciprocal (FP64: rcp.approx refined to round-off).
+// shared by the two faces that use them; each weight costs one approximate
+// reciprocal and one Newton step (FP64).
+//
+// Maxwell pairs. The fluxes of B, E, psi and phi are signed copies of one
+// another: along a direction every such component a has f_a = s q_b for a
+// partner b with f_b = s q_a, s = +-1 (along x: f_Bx = phi, f_phi = Bx;
+// f_By = -Ez, f_Ez = -By; ...). Then e+_b = s e+_a and e-_b = -s e-_a, so the
+// pair shares A+- and both weights, and with P = w+ (e+_{i-1/2} - e+_{i+1/2})
+// and M = w- (e-_{i+1/2} - e-_{i+3/2}) of component a,
+//   4 F_a = 2 s (q_b,i + q_b,i+1) + P + M,   4 F_b = s [2 (q_a,i + q_a,i+1) + P - M].
+// One half-point and weight computation serves both components. The eight
+// components form two blocks of two pairs per direction; a block keeps the
+// same four components in x and y, so one component group owns it.
 //
 // Tiling: one CTA per TX x TY tile, one thread per interior cell. The tile and
 // a 2-cell halo of the state are staged in shared memory; boundary conditions
@@ -45,11 +56,6 @@ template <int NTHR>
 __device__ __forceinline__ void group_sync(int grp) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(NTHR) : "memory");
 }
-// Barrier over NTHR threads with an explicit named-barrier id.
-template <int NTHR>
-__device__ __forceinline__ void named_sync(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHR) : "memory");
-}
 
 // ---- model adaptors ------------------------------------------------------
 // Per-cell quantities staged once per tile (aux), the flux of one cell from
@@ -60,6 +66,12 @@ struct SFModel {
     static constexpr int NAUX = 5;  // J (3), Z = rho h W^2, p + (E^2 + B^2)/2
     static constexpr int NS = 5;    // source slots: E (3), psi, phi
     static constexpr int G_FP64 = 4, G_FP32 = 2;
+    // components with their own flux (D, S, tau, varrho); the Maxwell
+    // components (B, E, psi, phi) are reconstructed in pairs
+    static constexpr int NGEN = 6;
+    static constexpr int KB4 = 0;  // generic components of a Maxwell-block group when G = 4
+    static __host__ __device__ constexpr int gen_comp(int i) { return i < 5 ? i : sf::RHOE; }
+    static constexpr int BX = sf::BX, EX = sf::EX, PSI = sf::PSI, PHI = sf::PHI;
     static __device__ __forceinline__ int src_slot(int c) {
         return c >= sf::EX && c <= sf::EZ ? c - sf::EX : (c == sf::PSI ? 3 : (c == sf::PHI ? 4 : -1));
     }
@@ -152,6 +164,11 @@ struct TFModel {
     static constexpr int NAUX = 0;
     static constexpr int NS = 9;  // Sbar (3), taubar, E (3), psi, phi
     static constexpr int G_FP64 = 2, G_FP32 = 4;
+    // components with their own flux (D, S, tau, Dbar, Sbar, taubar)
+    static constexpr int NGEN = 10;
+    static constexpr int KB4 = 1;  // generic components of a Maxwell-block group when G = 4
+    static __host__ __device__ constexpr int gen_comp(int i) { return i; }
+    static constexpr int BX = tf::BX, EX = tf::EX, PSI = tf::PSI, PHI = tf::PHI;
     template <class FT>
     static __device__ __forceinline__ void stage_cell(const double *x, const Phys &ph, FT *, int, int, double *s) {
         if (!s) return;
@@ -192,8 +209,25 @@ struct TFModel {
 
 // ---- the fused flux kernel -----------------------------------------------
 // G component groups of TX*TY threads each: thread (g, l) owns interior cell l
-// and components c = g, g + G, g + 2G, ...; one round of the reconstruction
-// handles G components at once (one per group).
+// and the components of group g. Groups 0 and 1 own one Maxwell block each
+// (plus KB generic components), groups 2 and 3 (G = 4) KO generic components
+// each; a group reconstructs its components one after another, synchronising
+// only itself.
+
+// Component in slot `slot` of Maxwell block b. In the x and y directions
+// block 0 = (Bx, By, Ez, phi) and block 1 = (Ex, Ey, Bz, psi): along x the
+// pairs are slots (0, 3) and (1, 2), along y (1, 3) and (0, 2). In the z pass
+// of a 3-D grid (the tile's second direction is z) block 0 = (Bx, Bz, Ey, phi)
+// and block 1 = (By, Ez, Ex, psi), paired like y.
+template <class M, bool ZP>
+__device__ __forceinline__ int em_comp(int b, int slot) {
+    if (!ZP) {
+        if (b == 0) return slot == 0 ? M::BX : slot == 1 ? M::BX + 1 : slot == 2 ? M::EX + 2 : M::PHI;
+        return slot == 0 ? M::EX : slot == 1 ? M::EX + 1 : slot == 2 ? M::BX + 2 : M::PSI;
+    }
+    if (b == 0) return slot == 0 ? M::BX : slot == 1 ? M::BX + 2 : slot == 2 ? M::EX + 1 : M::PHI;
+    return slot == 0 ? M::BX + 1 : slot == 1 ? M::EX + 2 : slot == 2 ? M::EX : M::PSI;
+}
 template <class M, int TX, int TY, int G, class FT, int NOUT>
 struct FluxSmem {
     static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
@@ -208,9 +242,9 @@ struct FluxSmem {
     static constexpr size_t aux = st32 + (SHADOW ? sizeof(float) * NV * SN : 0);
     static constexpr size_t src = aux + (SHADOW ? sizeof(float) : sizeof(double)) * M::NAUX * SN;
     static constexpr size_t fl = src + sizeof(double) * M::NS * NL;
-    static constexpr size_t hp = fl + sizeof(FT) * NC * SN;
+    static constexpr size_t hp = fl + sizeof(FT) * M::NGEN * SN;
     static constexpr size_t fc = hp + sizeof(FT) * 4 * G * SN;
-    static constexpr size_t total = fc + sizeof(FT) * G * SN;
+    static constexpr size_t total = fc + sizeof(FT) * 2 * G * SN;
 };
 
 // One tile: interior cells [i0, i0 + TX) x [j0, j0 + TY) of the grid g whose
@@ -226,17 +260,21 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     constexpr int SW = L_::SW, SH = L_::SH, SN = L_::SN, NL = L_::NL;
     constexpr int NT = NL * G;
     constexpr int OY = TWO_D ? 2 : 0;   // SMEM row of the first interior row
-    constexpr int NR = (NC + G - 1) / G; // component rounds
-    constexpr int LAST = NC - (NR - 1) * G;  // groups with a component in the last round
-    constexpr bool PAIR = 2 * LAST == G;     // the last round pairs groups up
+    constexpr bool ZP = DIRS == 2;      // z pass of a 3-D grid
+    static_assert(G == 2 || G == 4, "component groups");
+    constexpr int NGEN = M::NGEN;
+    constexpr int KB = G == 2 ? NGEN / 2 : M::KB4;            // generic components of groups 0, 1
+    constexpr int KO = G == 2 ? 0 : (NGEN - 2 * KB) / (G - 2); // generic components of groups 2, 3
+    static_assert(2 * KB + (G - 2) * KO == NGEN, "every generic component has one owner");
+    constexpr int NSLOT = 4 + KB > KO ? 4 + KB : KO;            // accumulators per thread
 
     double *st = reinterpret_cast<double *>(smem_raw + L_::st);   // [NV][SH][SW]
     FT *st32 = reinterpret_cast<FT *>(smem_raw + L_::st32);       // [NV][SH][SW] (FP32 form only)
     double *aux = reinterpret_cast<double *>(smem_raw + L_::aux); // [NAUX][SH][SW]
     double *src = reinterpret_cast<double *>(smem_raw + L_::src); // [NS][NL] (interior cells)
-    FT *fl = reinterpret_cast<FT *>(smem_raw + L_::fl);           // [NC][SH][SW]
+    FT *fl = reinterpret_cast<FT *>(smem_raw + L_::fl);           // [NGEN][SH][SW] generic components
     FT *hp = reinterpret_cast<FT *>(smem_raw + L_::hp);           // [G][4][SH][SW]: e+, e-, A+, A-
-    FT *fc = reinterpret_cast<FT *>(smem_raw + L_::fc);           // [G][SH][SW]: 4 F at the face after the cell
+    FT *fc = reinterpret_cast<FT *>(smem_raw + L_::fc);           // [G][2][SH][SW]: 4 F at the face after the cell
 
     const int tid = threadIdx.x;
     const int grp = tid / NL, lid = tid - grp * NL;
@@ -295,20 +333,28 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
 
     const int tx = lid % TX, ty = lid / TX;
     const int ox = tx + 2, oy = ty + OY;  // owned cell in SMEM coordinates
-    FT L[NR];
+    const int own = oy * SW + ox;
+    FT L[NSLOT];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) L[r] = FT(0);
+    for (int k = 0; k < NSLOT; ++k) L[k] = FT(0);
 
     const FT eps4 = FT(4e-6);
+    FT *hpw = hp + grp * 4 * SN;  // this group's half-point and face buffers
+    FT *fcw = fc + grp * 2 * SN;
+    // component c of the staged state in the flux arithmetic type
+    auto qsm = [&](int c) -> const FT * {
+        if constexpr (L_::SHADOW) return st32 + c * SN;
+        else return reinterpret_cast<const FT *>(st + c * SN);
+    };
 #pragma unroll 1
     for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
         if (!((DIRS >> dir) & 1)) continue;
         // physical direction of the flux: the tile's second dimension is z in
-        // the z pass of a 3-D grid (DIRS = 2)
-        const int pdir = DIRS == 2 ? 2 : dir;
+        // the z pass of a 3-D grid
+        const int pdir = ZP ? 2 : dir;
         const int sstep = dir == 0 ? 1 : SW;
         const FT inv4h = FT(dir == 0 ? g.rdx4 : g.rdy4);
-        // 3a. physical flux of every cell the reconstruction needs
+        // 3a. physical flux of the generic components of every cell the reconstruction needs
         const int ncx = dir == 0 ? SW : TX, ncy = dir == 0 ? TY : SH;
         const int cx0 = dir == 0 ? 0 : 2, cy0 = dir == 0 ? OY : 0;
         for (int e = tid; e < ncx * ncy; e += NT) {
@@ -320,67 +366,107 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             else
                 M::template cell_flux<FT>(st, aux, SN, idx, pdir, ph, f);
 #pragma unroll
-            for (int v = 0; v < NC; ++v) fl[v * SN + idx] = f[v];
+            for (int k = 0; k < NGEN; ++k) fl[k * SN + idx] = f[M::gen_comp(k)];
         }
         __syncthreads();
         const int nhx = dir == 0 ? SW - 1 : TX, nhy = dir == 0 ? TY : SH - 1;
         const int hx0 = dir == 0 ? 0 : 2, hy0 = dir == 0 ? OY : 0;
         const int nfx = dir == 0 ? TX + 1 : TX, nfy = dir == 0 ? TY : TY + 1;
         const int fx0 = dir == 0 ? 1 : 2, fy0 = dir == 0 ? OY : 1;
+
+        // 3b-3d for one generic component c (flux in fl[k]): half points,
+        // faces, and the face difference of the owned cell (4 F_{i-1/2} - 4 F_{i+1/2})
+        auto generic = [&](int c, int k) -> FT {
+            const FT *fv = fl + k * SN;
+            const FT *qv = qsm(c);
+            for (int e = lid; e < nhx * nhy; e += NL) {
+                const int hy = e / nhx, hx = e - hy * nhx;
+                const int idx = (hy0 + hy) * SW + hx0 + hx;
+                const FT df = fv[idx + sstep] - fv[idx];
+                const FT dq = qv[idx + sstep] - qv[idx];
+                const FT ep = df + dq, em = df - dq;
+                const FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
+                hpw[idx] = ep;
+                hpw[SN + idx] = em;
+                hpw[2 * SN + idx] = ap * ap;
+                hpw[3 * SN + idx] = am * am;
+            }
+            group_sync<NL>(grp);
+            for (int e = lid; e < nfx * nfy; e += NL) {
+                const int fy = e / nfx, fx = e - fy * nfx;
+                const int idx = (fy0 + fy) * SW + fx0 + fx;
+                const int il = idx - sstep, ir = idx + sstep;
+                const FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
+                const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
+                const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
+                const FT Xp = hpw[il] - hpw[idx];
+                const FT Xm = hpw[SN + idx] - hpw[SN + ir];
+                fcw[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+            }
+            group_sync<NL>(grp);
+            return fcw[own - sstep] - fcw[own];
+        };
+        // the same for a Maxwell pair (a, b, s): f_a = s q_b, f_b = s q_a. The
+        // second face array holds s 4 F_b; da, db are the owned cell's face
+        // differences of 4 F_a and s 4 F_b
+        auto pair = [&](int ca, int cb, FT sg, FT &da, FT &db) {
+            const FT *qa = qsm(ca), *qb = qsm(cb);
+            for (int e = lid; e < nhx * nhy; e += NL) {
+                const int hy = e / nhx, hx = e - hy * nhx;
+                const int idx = (hy0 + hy) * SW + hx0 + hx;
+                const FT d_a = qa[idx + sstep] - qa[idx];
+                const FT d_b = qb[idx + sstep] - qb[idx];
+                const FT ep = s_fma(sg, d_b, d_a), em = s_fma(sg, d_b, -d_a);  // e+-_a
+                const FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
+                hpw[idx] = ep;
+                hpw[SN + idx] = em;
+                hpw[2 * SN + idx] = ap * ap;
+                hpw[3 * SN + idx] = am * am;
+            }
+            group_sync<NL>(grp);
+            for (int e = lid; e < nfx * nfy; e += NL) {
+                const int fy = e / nfx, fx = e - fy * nfx;
+                const int idx = (fy0 + fy) * SW + fx0 + fx;
+                const int il = idx - sstep, ir = idx + sstep;
+                const FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
+                const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
+                const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
+                const FT Xp = hpw[il] - hpw[idx];
+                const FT M_ = wm * (hpw[SN + idx] - hpw[SN + ir]);
+                fcw[idx] = s_fma(FT(2) * sg, qb[idx] + qb[ir], s_fma(wp, Xp, M_));
+                fcw[SN + idx] = s_fma(FT(2), qa[idx] + qa[ir], s_fma(wp, Xp, -M_));
+            }
+            group_sync<NL>(grp);
+            da = fcw[own - sstep] - fcw[own];
+            db = fcw[SN + own - sstep] - fcw[SN + own];
+        };
+
+        if (grp < 2) {
+            // Maxwell block grp: pair k = (slot sa, slot 3 - k), sa = dir for k = 0
+            // and 1 - dir for k = 1; the second pair has s = -1 for block 0 along
+            // x, block 1 along y, and block 0 in the z pass
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            // When exactly half of the groups have a component in the last
-            // round, groups p and p + LAST pair up on component r G + p (p <
-            // LAST): both work on its half points and faces (in group p's
-            // buffers, 2 NL threads, pair barrier 1 + G + p); group p, which
-            // owns the component, accumulates it.
-            const bool pair_round = PAIR && r == NR - 1;
-            const int cg = pair_round ? grp % LAST : grp;  // group whose component and buffers are used
-            const int c = r * G + cg;
-            const bool active = c < NC;
-            const int wid = pair_round ? (grp / LAST) * NL + lid : lid;
-            const int wstride = pair_round ? 2 * NL : NL;
-            FT *hpw = hp + cg * 4 * SN;
-            FT *fcw = fc + cg * SN;
-            // the partner writes group cg's buffers: both must be done with the previous round
-            if (pair_round) named_sync<2 * NL>(1 + G + cg);
-            // 3b. half points of component c
-            if (active) {
-                const FT *fv = fl + c * SN;
-                const double *qv = st + (L_::SHADOW ? 0 : c * SN);
-                const FT *qv32 = st32 + c * SN;
-                for (int e = wid; e < nhx * nhy; e += wstride) {
-                    int hy = e / nhx, hx = e - hy * nhx;
-                    int idx = (hy0 + hy) * SW + hx0 + hx;
-                    FT df = fv[idx + sstep] - fv[idx];
-                    FT dq = L_::SHADOW ? qv32[idx + sstep] - qv32[idx] : FT(qv[idx + sstep] - qv[idx]);
-                    FT ep = df + dq, em = df - dq;
-                    FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
-                    hpw[idx] = ep;
-                    hpw[SN + idx] = em;
-                    hpw[2 * SN + idx] = ap * ap;
-                    hpw[3 * SN + idx] = am * am;
-                }
+            for (int k = 0; k < 2; ++k) {
+                const int sa = k == 0 ? dir : 1 - dir;
+                const bool neg = k == 1 && (ZP ? grp != dir : grp == dir);
+                const FT sg = neg ? FT(-1) : FT(1);
+                FT da, db;
+                pair(em_comp<M, ZP>(grp, sa), em_comp<M, ZP>(grp, 3 - k), sg, da, db);
+                L[3 - k] = s_fma(db, sg * inv4h, L[3 - k]);
+                if (sa == 0) L[0] = s_fma(da, inv4h, L[0]);
+                else L[1] = s_fma(da, inv4h, L[1]);
             }
-            if (pair_round) named_sync<2 * NL>(1 + G + cg); else group_sync<NL>(grp);
-            // 3c. face values of component c
-            if (active) {
-                const FT *fv = fl + c * SN;
-                for (int e = wid; e < nfx * nfy; e += wstride) {
-                    int fy = e / nfx, fx = e - fy * nfx;
-                    int idx = (fy0 + fy) * SW + fx0 + fx;
-                    int il = idx - sstep, ir = idx + sstep;
-                    FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
-                    FT wp = Ap * s_rcp1(s_fma(FT(2), hpw[2 * SN + il], Ap));
-                    FT wm = Am * s_rcp1(s_fma(FT(2), hpw[3 * SN + ir], Am));
-                    FT Xp = hpw[il] - hpw[idx];
-                    FT Xm = hpw[SN + idx] - hpw[SN + ir];
-                    fcw[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
-                }
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int k = grp * KB + j;
+                L[4 + j] = s_fma(generic(M::gen_comp(k), k), inv4h, L[4 + j]);
             }
-            if (pair_round) named_sync<2 * NL>(1 + G + cg); else group_sync<NL>(grp);
-            // 3d. flux difference into the owned cell's accumulator
-            if (active && cg == grp) L[r] = s_fma(fcw[oy * SW + ox - sstep] - fcw[oy * SW + ox], inv4h, L[r]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KO; ++j) {
+                const int k = 2 * KB + (grp - 2) * KO + j;
+                L[j] = s_fma(generic(M::gen_comp(k), k), inv4h, L[j]);
+            }
         }
         __syncthreads();
     }
@@ -389,18 +475,23 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const int gi = i0 + tx, gj = j0 + ty;
     const bool inside = gi < g.nx && gj < g.ny;
     const long long cell = base + (long long)gj * g.row + gi;
+    // component accumulated in slot k of this thread (-1: none)
+    auto slot_comp = [&](int k) -> int {
+        if (grp < 2) return k < 4 ? em_comp<M, ZP>(grp, k) : (k < 4 + KB ? M::gen_comp(grp * KB + k - 4) : -1);
+        return k < KO ? M::gen_comp(2 * KB + (grp - 2) * KO + k) : -1;
+    };
     if constexpr (NOUT == 0) {
         // x-y pass of a 3-D grid: L_x + L_y only
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int c = r * G + grp;
-            if (c < NC && inside) a.lout[(long long)c * g.plane + cell] = (double)L[r];
+        for (int r = 0; r < NSLOT; ++r) {
+            const int c = slot_comp(r);
+            if (c >= 0 && inside) a.lout[(long long)c * g.plane + cell] = (double)L[r];
         }
     } else {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int c = r * G + grp;
-            if (c >= NC || !inside) continue;
+        for (int r = 0; r < NSLOT; ++r) {
+            const int c = slot_comp(r);
+            if (c < 0 || !inside) continue;
             // (slot is uniform over the group: components without a source skip its terms)
             const int slot = M::src_slot(c);
             const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
