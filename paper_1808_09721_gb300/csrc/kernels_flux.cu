@@ -35,6 +35,8 @@
 // reconstructed and differenced. The epilogue fuses the SSP2(222) stage
 // update (Table 1); after the second pass it carries the stage-2 primitives
 // forward as the next warm start (the final recovery runs on demand).
+#include <type_traits>
+
 #include "rmhd_internal.h"
 #include "physics_sf.cuh"
 #include "physics_tf.cuh"
@@ -346,17 +348,18 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
         if constexpr (L_::SHADOW) return st32 + c * SN;
         else return reinterpret_cast<const FT *>(st + c * SN);
     };
-#pragma unroll 1
-    for (int dir = 0; dir < (TWO_D ? 2 : 1); ++dir) {
-        if (!((DIRS >> dir) & 1)) continue;
+    // one direction of the tile (compile-time, so that the element loops
+    // index with constant strides and divisors)
+    auto sweep = [&](auto dir_c) {
+        constexpr int dir = decltype(dir_c)::value;
         // physical direction of the flux: the tile's second dimension is z in
         // the z pass of a 3-D grid
-        const int pdir = ZP ? 2 : dir;
-        const int sstep = dir == 0 ? 1 : SW;
+        constexpr int pdir = ZP ? 2 : dir;
+        constexpr int sstep = dir == 0 ? 1 : SW;
         const FT inv4h = FT(dir == 0 ? g.rdx4 : g.rdy4);
         // 3a. physical flux of the generic components of every cell the reconstruction needs
-        const int ncx = dir == 0 ? SW : TX, ncy = dir == 0 ? TY : SH;
-        const int cx0 = dir == 0 ? 0 : 2, cy0 = dir == 0 ? OY : 0;
+        constexpr int ncx = dir == 0 ? SW : TX, ncy = dir == 0 ? TY : SH;
+        constexpr int cx0 = dir == 0 ? 0 : 2, cy0 = dir == 0 ? OY : 0;
         for (int e = tid; e < ncx * ncy; e += NT) {
             int cy = e / ncx, cx = e - cy * ncx;
             int idx = (cy0 + cy) * SW + cx0 + cx;
@@ -369,10 +372,10 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             for (int k = 0; k < NGEN; ++k) fl[k * SN + idx] = f[M::gen_comp(k)];
         }
         __syncthreads();
-        const int nhx = dir == 0 ? SW - 1 : TX, nhy = dir == 0 ? TY : SH - 1;
-        const int hx0 = dir == 0 ? 0 : 2, hy0 = dir == 0 ? OY : 0;
-        const int nfx = dir == 0 ? TX + 1 : TX, nfy = dir == 0 ? TY : TY + 1;
-        const int fx0 = dir == 0 ? 1 : 2, fy0 = dir == 0 ? OY : 1;
+        constexpr int nhx = dir == 0 ? SW - 1 : TX, nhy = dir == 0 ? TY : SH - 1;
+        constexpr int hx0 = dir == 0 ? 0 : 2, hy0 = dir == 0 ? OY : 0;
+        constexpr int nfx = dir == 0 ? TX + 1 : TX, nfy = dir == 0 ? TY : TY + 1;
+        constexpr int fx0 = dir == 0 ? 1 : 2, fy0 = dir == 0 ? OY : 1;
 
         // 3b-3d for one generic component c (flux in fl[k]): half points,
         // faces, and the face difference of the owned cell (4 F_{i-1/2} - 4 F_{i+1/2})
@@ -447,7 +450,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             // x, block 1 along y, and block 0 in the z pass
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int sa = k == 0 ? dir : 1 - dir;
+                const int sa = k == 0 ? dir : 1 - dir;  // constant after unrolling
                 const bool neg = k == 1 && (ZP ? grp != dir : grp == dir);
                 const FT sg = neg ? FT(-1) : FT(1);
                 FT da, db;
@@ -469,7 +472,9 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             }
         }
         __syncthreads();
-    }
+    };
+    if constexpr ((DIRS & 1) != 0) sweep(std::integral_constant<int, 0>{});
+    if constexpr (TWO_D && (DIRS & 2) != 0) sweep(std::integral_constant<int, 1>{});
 
     // 4. epilogue: each thread updates its own components of its cell
     const int gi = i0 + tx, gj = j0 + ty;
