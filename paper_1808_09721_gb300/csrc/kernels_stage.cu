@@ -33,16 +33,9 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_sf(Grid g, Phys ph, Sta
     sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
-        double r[NC], q[NC], w[NW];
-#pragma unroll
-        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
-        double pw = a.wwarm[P * g.plane + cell];
-        int st = stage_solve<kNRef>(r, pw, k, q, w);
+        const double pw = a.wwarm[P * g.plane + cell];
+        const int st = stage_solve<kNRef>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
         record(a.status, st, cell);
-#pragma unroll
-        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
     }
 }
 
@@ -93,15 +86,8 @@ __global__ void k_stage_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
          cell += (long long)gridDim.x * blockDim.x) {
         const int run = b.run_of[cell];
         sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma};
-        double r[NC], q[NC], w[NW];
-#pragma unroll
-        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
-        int st = stage_solve<kNRef>(r, a.wwarm[P * g.plane + cell], k, q, w);
+        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
         record(a.status, st, cell);
-#pragma unroll
-        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
     }
 }
 

@@ -161,25 +161,46 @@ struct StageConst {
     double sigma, gamma;
 };
 
-// Solve one implicit stage for one cell. r: explicit part (14, FP64);
-// p_warm: pressure guess. Outputs q (14) and w = (v, p, W). NREF FP64 passes.
+// Solve one implicit stage for one cell. rp: the cell's explicit part (14
+// FP64 variables, ps apart); p_warm: pressure guess. Writes the cell's q (14,
+// through qp) and w = (v, p, W) (through wp), ps apart. NREF FP64 passes.
+// The FP64 inputs of the refinement passes are read again after the FP32
+// Newton phase instead of being held in registers through it (they are in
+// L1), which keeps the kernel at a higher occupancy.
 template <int NREF>
-__device__ int stage_solve(const double r[NC], double p_warm, const StageConst &k, double q[NC], double w[NW]) {
+__device__ int stage_solve(const double *rp, long long ps, double p_warm, const StageConst &k, double *qp,
+                           double *wp) {
     const double gm1 = k.gamma - 1.0, gam = k.gamma;
-    for (int i = 0; i < NC; ++i) q[i] = r[i];
-    q[PSI] = (r[PSI] + k.adt * r[RHOE]) * k.cpsi;
-    q[PHI] = r[PHI] * k.cpsi;
-
-    const double B[3] = {r[BX], r[BY], r[BZ]};
-    const double Sv[3] = {r[SX], r[SY], r[SZ]};
-    const double rE[3] = {r[EX], r[EY], r[EZ]};
-    const double tauB = r[TAU] - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    double tauB;
+    float Bf[3], Sf[3], rEf[3], tauBf, Df, rhoef;
+    {
+        const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
+        const double Sv[3] = {rp[SX * ps], rp[SY * ps], rp[SZ * ps]};
+        const double tau = rp[TAU * ps], Dd = rp[D * ps], rhoe = rp[RHOE * ps];
+        tauB = tau - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        for (int i = 0; i < 3; ++i) {
+            const double rEi = rp[(EX + i) * ps];
+            Bf[i] = (float)B[i];
+            Sf[i] = (float)Sv[i];
+            rEf[i] = (float)rEi;
+            qp[(EX + i) * ps] = rEi;  // replaced by the root; left as r_E if the solve fails
+        }
+        tauBf = (float)tauB;
+        Df = (float)Dd;
+        rhoef = (float)rhoe;
+        // source-free components equal r; psi and phi in closed form
+        qp[D * ps] = Dd;
+        qp[TAU * ps] = tau;
+        qp[RHOE * ps] = rhoe;
+        for (int i = 0; i < 3; ++i) {
+            qp[(SX + i) * ps] = Sv[i];
+            qp[(BX + i) * ps] = B[i];
+        }
+        qp[PSI * ps] = (rp[PSI * ps] + k.adt * rhoe) * k.cpsi;
+        qp[PHI * ps] = rp[PHI * ps] * k.cpsi;
+    }
 
     // ---- FP32 Newton
-    const float Bf[3] = {(float)B[0], (float)B[1], (float)B[2]};
-    const float Sf[3] = {(float)Sv[0], (float)Sv[1], (float)Sv[2]};
-    const float rEf[3] = {(float)rE[0], (float)rE[1], (float)rE[2]};
-    const float tauBf = (float)tauB, Df = (float)r[D], rhoef = (float)r[RHOE];
     const float adtf = (float)k.adt, sigf = (float)k.sigma, gm1f = (float)gm1, gamf = (float)gam;
     const float scale = fmaxf(fmaxf(fabsf(rEf[0]), fabsf(rEf[1])), fmaxf(fabsf(rEf[2]), 1e-30f));
 
@@ -251,15 +272,21 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
     // NREF-th) is the result, with its own primitives (J amplifies any E/v
     // mismatch by sigma). Cells that need it take extra passes (up to 8).
     const float gs = resid_scale(E, rEf, v, Bf, W, rhoef, adtf, sigf);  // round-off scale of G
+    // FP64 inputs, read again (the stores above keep the compiler from reusing
+    // the first loads' registers)
+    const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
+    const double Sv[3] = {rp[SX * ps], rp[SY * ps], rp[SZ * ps]};
+    const double rE[3] = {rp[EX * ps], rp[EY * ps], rp[EZ * ps]};
+    const double Dd = rp[D * ps], rhoe = rp[RHOE * ps];
     double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
     double pdd = (double)p;
     const double rdf = (double)(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
     double gres = 0.0;
     for (int pass = 0; pass < 8; ++pass) {
-        em_split(Ed, Sv, B, tauB, r[D], St64, a64, S264);
-        pdd -= pres_resid(pdd, a64, S264, r[D], gm1, gam) * rdf;
-        stage_resid(Ed, pdd, St64, a64, B, rE, r[RHOE], k.adt, k.sigma, G64, v64, W64);
+        em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
+        pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
+        stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
         gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
         if (pass >= NREF - 1 && gres <= 1e-12 * (double)gs) break;
         float Gf[3] = {(float)G64[0], (float)G64[1], (float)G64[2]};
@@ -272,15 +299,15 @@ __device__ int stage_solve(const double r[NC], double p_warm, const StageConst &
         Ed[1] -= (double)dE[1];
         Ed[2] -= (double)dE[2];
     }
-    w[VX] = v64[0];
-    w[VY] = v64[1];
-    w[VZ] = v64[2];
-    w[P] = pdd;
-    w[LOR] = W64;
-    q[EX] = Ed[0];
-    q[EY] = Ed[1];
-    q[EZ] = Ed[2];
-    if (!(pdd > 0.0) || !(gres <= 1e-9 * (double)gs) || !isfinite(Ed[0] + Ed[1] + Ed[2] + w[LOR])) return ST_NEWTON;
+    wp[VX * ps] = v64[0];
+    wp[VY * ps] = v64[1];
+    wp[VZ * ps] = v64[2];
+    wp[P * ps] = pdd;
+    wp[LOR * ps] = W64;
+    qp[EX * ps] = Ed[0];
+    qp[EY * ps] = Ed[1];
+    qp[EZ * ps] = Ed[2];
+    if (!(pdd > 0.0) || !(gres <= 1e-9 * (double)gs) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
     return ST_OK;
 }
 
