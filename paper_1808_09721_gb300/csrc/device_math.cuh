@@ -53,6 +53,47 @@ __device__ __forceinline__ double s_rsqrt(double x) {
     return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
+// Conversions between FP64 and FP32 on the integer pipes. The conversion
+// instructions run on the FP64 pipe, the one this library is bound by; these
+// use shifts and logic ops instead (both pipes idle in the FP64-bound kernels).
+//
+// f32_of: round to nearest (ties away from zero) on the first dropped bit,
+// FP32 subnormals included; magnitudes above the FP32 range (and infinities,
+// NaNs) give a signed infinity.
+__device__ __forceinline__ float f32_of(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // FP32 biased exponent
+    const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7fffffu, g = (lo >> 28) & 1u;
+    unsigned mag = (((unsigned)e << 23) | m) + g;
+    if (e <= 0) {  // FP32 subnormal range: shift the 24-bit significand down, then round
+        const unsigned t = 0x1000000u | (m << 1) | g;
+        mag = e < -23 ? 0u : ((t >> (1 - e)) + 1u) >> 1;
+    }
+    if (e >= 255) mag = 0x7f800000u;
+    return __uint_as_float(sign | mag);
+}
+// f64_of: exact for every FP32 value (subnormals normalised; infinities and
+// NaNs kept).
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 255u) hi |= 0x7ff00000u;
+    if (e == 0u) {  // zero or subnormal: m * 2^-149
+        const int s = __clz(m) - 8;  // shift that puts the leading bit at 23
+        const unsigned mn = (m << s) & 0x7fffffu;
+        hi = m ? (sign | ((unsigned)(897 - s) << 20) | (mn >> 3)) : sign;
+        lo = m ? (mn << 29) : 0u;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+// conversions to and from a flux arithmetic type T (identity for double)
+template <class T> __device__ __forceinline__ T to_t(double x) { return x; }
+template <> __device__ __forceinline__ float to_t<float>(double x) { return f32_of(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
+
 __device__ __forceinline__ float s_rcp(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

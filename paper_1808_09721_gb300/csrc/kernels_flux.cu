@@ -103,11 +103,11 @@ struct SFModel {
         sf::current(q, w, ph.sigma, J);
         const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
                             q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
-        aux[0 * SN + idx] = (FT)J[0];
-        aux[1 * SN + idx] = (FT)J[1];
-        aux[2 * SN + idx] = (FT)J[2];
-        aux[3 * SN + idx] = (FT)(fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P]);
-        aux[4 * SN + idx] = (FT)fma(0.5, E2B2, w[sf::P]);
+        aux[0 * SN + idx] = to_t<FT>(J[0]);
+        aux[1 * SN + idx] = to_t<FT>(J[1]);
+        aux[2 * SN + idx] = to_t<FT>(J[2]);
+        aux[3 * SN + idx] = to_t<FT>(fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P]);
+        aux[4 * SN + idx] = to_t<FT>(fma(0.5, E2B2, w[sf::P]));
         if (s) {
             s[0] = -J[0];
             s[1] = -J[1];
@@ -298,7 +298,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
 #pragma unroll
             for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) st32[v * SN + e] = (FT)x[v];
+            for (int v = 0; v < NV; ++v) st32[v * SN + e] = to_t<FT>(x[v]);
             const int tx = sx - 2, ty = sy - OY;
             const bool interior = tx >= 0 && tx < TX && ty >= 0 && ty < TY;
             double s[M::NS];
@@ -490,7 +490,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
 #pragma unroll
         for (int r = 0; r < NSLOT; ++r) {
             const int c = slot_comp(r);
-            if (c >= 0 && inside) a.lout[(long long)c * g.plane + cell] = (double)L[r];
+            if (c >= 0 && inside) a.lout[(long long)c * g.plane + cell] = to_f64(L[r]);
         }
     } else {
 #pragma unroll
@@ -501,7 +501,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             const int slot = M::src_slot(c);
             const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
             const long long o = (long long)c * g.plane + cell;
-            const double Lv = a.lin ? (double)L[r] + a.lin[o] : (double)L[r];
+            const double Lv = a.lin ? to_f64(L[r]) + a.lin[o] : to_f64(L[r]);
             double b = a.base[0][o];
 #pragma unroll
             for (int k = 0; k < NOUT; ++k) {

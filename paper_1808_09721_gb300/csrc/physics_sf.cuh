@@ -180,14 +180,14 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
         tauB = tau - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
         for (int i = 0; i < 3; ++i) {
             const double rEi = rp[(EX + i) * ps];
-            Bf[i] = (float)B[i];
-            Sf[i] = (float)Sv[i];
-            rEf[i] = (float)rEi;
+            Bf[i] = f32_of(B[i]);
+            Sf[i] = f32_of(Sv[i]);
+            rEf[i] = f32_of(rEi);
             qp[(EX + i) * ps] = rEi;  // replaced by the root; left as r_E if the solve fails
         }
-        tauBf = (float)tauB;
-        Df = (float)Dd;
-        rhoef = (float)rhoe;
+        tauBf = f32_of(tauB);
+        Df = f32_of(Dd);
+        rhoef = f32_of(rhoe);
         // source-free components equal r; psi and phi in closed form
         qp[D * ps] = Dd;
         qp[TAU * ps] = tau;
@@ -201,11 +201,11 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     }
 
     // ---- FP32 Newton
-    const float adtf = (float)k.adt, sigf = (float)k.sigma, gm1f = (float)gm1, gamf = (float)gam;
+    const float adtf = f32_of(k.adt), sigf = f32_of(k.sigma), gm1f = f32_of(gm1), gamf = f32_of(gam);
     const float scale = fmaxf(fmaxf(fabsf(rEf[0]), fabsf(rEf[1])), fmaxf(fabsf(rEf[2]), 1e-30f));
 
     float E[3] = {rEf[0], rEf[1], rEf[2]};
-    float p = (float)p_warm, dfdp = -1.f;
+    float p = f32_of(p_warm), dfdp = -1.f;
     float G[3], v[3], W, St[3], a, S2;
     em_split(E, Sf, Bf, tauBf, Df, St, a, S2);
     if (!pres_solve_f32(p, a, S2, Df, gm1f, gamf, dfdp)) return ST_C2P;
@@ -278,9 +278,9 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     const double Sv[3] = {rp[SX * ps], rp[SY * ps], rp[SZ * ps]};
     const double rE[3] = {rp[EX * ps], rp[EY * ps], rp[EZ * ps]};
     const double Dd = rp[D * ps], rhoe = rp[RHOE * ps];
-    double Ed[3] = {(double)E[0], (double)E[1], (double)E[2]};
-    double pdd = (double)p;
-    const double rdf = (double)(1.f / dfdp);
+    double Ed[3] = {f64_of(E[0]), f64_of(E[1]), f64_of(E[2])};
+    double pdd = f64_of(p);
+    const double rdf = f64_of(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
     double gres = 0.0;
     for (int pass = 0; pass < 8; ++pass) {
@@ -288,16 +288,16 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
         pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
         gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
-        if (pass >= NREF - 1 && gres <= 1e-12 * (double)gs) break;
-        float Gf[3] = {(float)G64[0], (float)G64[1], (float)G64[2]};
+        if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
+        float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
         if (pass == 7) break;
         // first-order prediction of the pressure at the corrected E
-        pdd -= (double)(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
-        Ed[0] -= (double)dE[0];
-        Ed[1] -= (double)dE[1];
-        Ed[2] -= (double)dE[2];
+        pdd -= f64_of(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
+        Ed[0] -= f64_of(dE[0]);
+        Ed[1] -= f64_of(dE[1]);
+        Ed[2] -= f64_of(dE[2]);
     }
     wp[VX * ps] = v64[0];
     wp[VY * ps] = v64[1];
@@ -307,7 +307,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
-    if (!(pdd > 0.0) || !(gres <= 1e-9 * (double)gs) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
+    if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
     return ST_OK;
 }
 
@@ -319,9 +319,9 @@ __device__ __forceinline__ int recover(const double q[NC], double p_warm, double
     const double tauB = q[TAU] - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
     double St[3], a, S2;
     em_split(E, Sv, B, tauB, q[D], St, a, S2);
-    float p = (float)p_warm, df = -1.f;
-    if (!pres_solve_f32(p, (float)a, (float)S2, (float)q[D], (float)gm1, (float)gamma, df)) return ST_C2P;
-    double pd = (double)p, rdf = (double)(1.f / df);
+    float p = f32_of(p_warm), df = -1.f;
+    if (!pres_solve_f32(p, f32_of(a), f32_of(S2), f32_of(q[D]), f32_of(gm1), f32_of(gamma), df)) return ST_C2P;
+    double pd = f64_of(p), rdf = f64_of(1.f / df);
     pd -= pres_resid(pd, a, S2, q[D], gm1, gamma) * rdf;
     pd -= pres_resid(pd, a, S2, q[D], gm1, gamma) * rdf;
     double rZ = s_rcp(a + pd);
