@@ -136,9 +136,9 @@ __device__ __forceinline__ int recover(const double q[NC], const double wold[NW]
     for (int s = 0; s < 2; ++s) {
         double a = ts[s] + Ds[s];
         double S2 = Ss[s][0] * Ss[s][0] + Ss[s][1] * Ss[s][1] + Ss[s][2] * Ss[s][2];
-        float p = (float)wold[5 * s + P], df = -1.f;
-        if (!sf::pres_solve_f32(p, (float)a, (float)S2, (float)Ds[s], (float)gm1, (float)gam, df)) return sf::ST_C2P;
-        double pd = (double)p, rdf = (double)(1.f / df);
+        float p = f32_of(wold[5 * s + P]), df = -1.f;
+        if (!sf::pres_solve_f32(p, f32_of(a), f32_of(S2), f32_of(Ds[s]), f32_of(gm1), f32_of(gam), df)) return sf::ST_C2P;
+        double pd = f64_of(p), rdf = f64_of(1.f / df);
         pd -= sf::pres_resid(pd, a, S2, Ds[s], gm1, gam) * rdf;
         pd -= sf::pres_resid(pd, a, S2, Ds[s], gm1, gam) * rdf;
         double Z = a + pd, rZ = s_rcp(Z);
@@ -322,18 +322,18 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     c.rx[3] = r[TAUB] * c.imur;
 
     Cell<float> cf;
-    cf.D = (float)c.D; cf.Ds[0] = (float)c.Ds[0]; cf.Ds[1] = (float)c.Ds[1];
-    for (int i = 0; i < 3; ++i) { cf.Sv[i] = (float)c.Sv[i]; cf.B[i] = (float)c.B[i]; }
-    cf.tauB = (float)c.tauB;
-    for (int i = 0; i < 7; ++i) cf.rx[i] = (float)c.rx[i];
-    cf.mu_e = (float)c.mu_e; cf.mu_p = (float)c.mu_p; cf.inv = (float)c.inv; cf.mur = (float)c.mur;
-    cf.imur = (float)c.imur; cf.eta = (float)c.eta; cf.adt = (float)c.adt; cf.gm1 = (float)gm1; cf.gam = (float)gam;
+    cf.D = f32_of(c.D); cf.Ds[0] = f32_of(c.Ds[0]); cf.Ds[1] = f32_of(c.Ds[1]);
+    for (int i = 0; i < 3; ++i) { cf.Sv[i] = f32_of(c.Sv[i]); cf.B[i] = f32_of(c.B[i]); }
+    cf.tauB = f32_of(c.tauB);
+    for (int i = 0; i < 7; ++i) cf.rx[i] = f32_of(c.rx[i]);
+    cf.mu_e = f32_of(c.mu_e); cf.mu_p = f32_of(c.mu_p); cf.inv = f32_of(c.inv); cf.mur = f32_of(c.mur);
+    cf.imur = f32_of(c.imur); cf.eta = f32_of(c.eta); cf.adt = f32_of(c.adt); cf.gm1 = f32_of(gm1); cf.gam = f32_of(gam);
 
     float scale = 1e-30f;
     for (int i = 0; i < 7; ++i) scale = fmaxf(scale, fabsf(cf.rx[i]));
 
     // ---- FP32 Newton
-    float x[7], p[2] = {(float)wwarm[P], (float)wwarm[5 + P]}, dfdp[2] = {-1.f, -1.f};
+    float x[7], p[2] = {f32_of(wwarm[P]), f32_of(wwarm[5 + P])}, dfdp[2] = {-1.f, -1.f};
     for (int i = 0; i < 7; ++i) x[i] = cf.rx[i];
     float St2[2][3], a[2], S2[2], G[7], v[2][3], Z[2];
     split_x(cf, x, St2, a, S2);
@@ -405,9 +405,9 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     // |G| reaches round-off of the magnitude of G's terms is the result, with
     // its own primitives; extra passes, up to 8, only where needed)
     const float gs = resid_scale(cf, x, v);  // round-off scale of G
-    double xd[7], pdd[2] = {(double)p[0], (double)p[1]};
-    const double rdf[2] = {(double)(1.f / dfdp[0]), (double)(1.f / dfdp[1])};
-    for (int i = 0; i < 7; ++i) xd[i] = (double)x[i];
+    double xd[7], pdd[2] = {f64_of(p[0]), f64_of(p[1])};
+    const double rdf[2] = {f64_of(1.f / dfdp[0]), f64_of(1.f / dfdp[1])};
+    for (int i = 0; i < 7; ++i) xd[i] = f64_of(x[i]);
     double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
     double gres = 0.0;
     for (int pass = 0; pass < 8; ++pass) {
@@ -416,10 +416,10 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
         stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
         gres = 0.0;
         for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
-        if (pass >= NREF - 1 && gres <= 1e-12 * (double)gs) break;
+        if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
         if (pass == 7) break;
         float Gf[7], dx[7];
-        for (int i = 0; i < 7; ++i) Gf[i] = (float)G64[i];
+        for (int i = 0; i < 7; ++i) Gf[i] = f32_of(G64[i]);
         for (int i = 0; i < 7; ++i) {
             float s = 0.f;
             for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * Gf[j];
@@ -428,9 +428,9 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
         for (int s = 0; s < 2; ++s) {
             float dp = 0.f;
             for (int i = 0; i < 7; ++i) dp += dpdx[s][i] * dx[i];
-            pdd[s] -= (double)dp;
+            pdd[s] -= f64_of(dp);
         }
-        for (int i = 0; i < 7; ++i) xd[i] -= (double)dx[i];
+        for (int i = 0; i < 7; ++i) xd[i] -= f64_of(dx[i]);
     }
     bool ok = true;
     for (int s = 0; s < 2; ++s) {
@@ -446,7 +446,7 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
         q[EX + i] = xd[4 + i];
     }
     q[TAUB] = xd[3] * c.mur;
-    if (!ok || !(gres <= 1e-9 * (double)gs)) return sf::ST_NEWTON;
+    if (!ok || !(gres <= 1e-9 * f64_of(gs))) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
 
