@@ -28,7 +28,9 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
 }
 
 // ---------------------------------------------------------------- stage
-__global__ void __launch_bounds__(kStageThreads) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
+// 5 blocks per SM (at most 96 registers): the solve is latency-bound, and
+// 20 warps per SM hide more of its FP64 and MUFU latency than 16 (no spills)
+__global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace sf;
     sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
@@ -43,24 +45,17 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_sf(Grid g, Phys ph, Sta
 // strided slice of shared memory (not in local memory: the pivoted
 // Gauss-Jordan indexes them with run-time rows).
 static constexpr int kStageThreadsTF = 64;
-__global__ void __launch_bounds__(kStageThreadsTF) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
+// 8 blocks per SM (at most 128 registers, a 32-byte spill): 16 warps per SM
+// instead of 8 hide the latency of the 7-unknown solve (measured 18% faster)
+__global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace tf;
     __shared__ float sJ[49 * kStageThreadsTF], sM[49 * kStageThreadsTF];
     const Mat Jm{sJ + threadIdx.x, kStageThreadsTF}, Minv{sM + threadIdx.x, kStageThreadsTF};
     tf::StageConst k{a.adt, cpsi};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
-        double r[NC], q[NC], w[NW], ww[NW];
-#pragma unroll
-        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) ww[v] = a.wwarm[v * g.plane + cell];
-        int st = stage_solve<kNRef>(r, ww, k, ph, q, w, Jm, Minv);
+        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm, Minv);
         record(a.status, st, cell);
-#pragma unroll
-        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
     }
 }
 
@@ -80,7 +75,8 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
 // ---------------------------------------------------------------- batched stage
 // One thread per packed cell; the run's a_ii dt, 1/(1 + a_ii dt kappa) and
 // conductivity come from the per-run tables.
-__global__ void k_stage_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
+// the block size is the autotuner's choice: cap registers as k_stage_sf's bounds do
+__global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
     using namespace sf;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
@@ -100,18 +96,10 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
         pr.sigma = b.sigma[run];
         pr.eta = b.eta[run];
         tf::StageConst k{b.adt[run], b.cpsi[run]};
-        double r[NC], q[NC], w[NW], ww[NW];
-#pragma unroll
-        for (int v = 0; v < NC; ++v) r[v] = a.r[v * g.plane + cell];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) ww[v] = a.wwarm[v * g.plane + cell];
         float jl[49], ml[49];
-        int st = stage_solve<kNRef>(r, ww, k, pr, q, w, tf::Mat{jl, 1}, tf::Mat{ml, 1});
+        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, pr, a.q + cell, a.w + cell,
+                                          tf::Mat{jl, 1}, tf::Mat{ml, 1});
         record(a.status, st, cell);
-#pragma unroll
-        for (int v = 0; v < NC; ++v) a.q[v * g.plane + cell] = q[v];
-#pragma unroll
-        for (int v = 0; v < NW; ++v) a.w[v * g.plane + cell] = w[v];
     }
 }
 

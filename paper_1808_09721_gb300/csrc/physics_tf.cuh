@@ -295,45 +295,61 @@ struct StageConst {
     double adt, cpsi;
 };
 
-// Solve one implicit stage for one cell (two fluids). Jm and Minv are the
-// caller's 7 x 7 FP32 scratch for the Jacobian and its inverse.
-
-template <int NREF>
-__device__ int stage_solve(const double r[NC], const double wwarm[NW], const StageConst &k, const Phys &ph,
-                           double q[NC], double w[NW], Mat Jm, Mat Minv) {
-    const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
-    const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
-    for (int i = 0; i < NC; ++i) q[i] = r[i];
-    q[PSI] = (r[PSI] + k.adt * r[DB]) * k.cpsi;  // varrho = Dbar has no source
-    q[PHI] = r[PHI] * k.cpsi;
-
-    Cell<double> c;
-    c.D = r[D];
-    c.Ds[0] = sp.ce_bar * r[DB] + sp.ce_tot * r[D];
-    c.Ds[1] = sp.cp_bar * r[DB] + sp.cp_tot * r[D];
-    for (int i = 0; i < 3; ++i) { c.Sv[i] = r[SX + i]; c.B[i] = r[BX + i]; }
-    c.tauB = r[TAU] - 0.5 * (c.B[0] * c.B[0] + c.B[1] * c.B[1] + c.B[2] * c.B[2]);
+// The FP64 data of a cell's stage solve from its explicit part r (variables
+// ps apart).
+__device__ __forceinline__ void load_cell(Cell<double> &c, const double *rp, long long ps, const Split &sp,
+                                          const StageConst &k, const Phys &ph) {
+    c.D = rp[D * ps];
+    const double Db = rp[DB * ps];
+    c.Ds[0] = sp.ce_bar * Db + sp.ce_tot * c.D;
+    c.Ds[1] = sp.cp_bar * Db + sp.cp_tot * c.D;
+    for (int i = 0; i < 3; ++i) { c.Sv[i] = rp[(SX + i) * ps]; c.B[i] = rp[(BX + i) * ps]; }
+    c.tauB = rp[TAU * ps] - 0.5 * (c.B[0] * c.B[0] + c.B[1] * c.B[1] + c.B[2] * c.B[2]);
     c.mu_e = ph.mu_e; c.mu_p = ph.mu_p; c.inv = ph.inv_dmu;
     c.mur = ph.mur;
     c.imur = ph.imur;
     c.eta = ph.eta;
-    c.adt = k.adt; c.gm1 = gm1; c.gam = gam;
-    for (int i = 0; i < 3; ++i) { c.rx[i] = r[SBX + i] * c.imur; c.rx[4 + i] = r[EX + i]; }
-    c.rx[3] = r[TAUB] * c.imur;
+    c.adt = k.adt; c.gm1 = ph.gamma - 1.0; c.gam = ph.gamma;
+    for (int i = 0; i < 3; ++i) { c.rx[i] = rp[(SBX + i) * ps] * c.imur; c.rx[4 + i] = rp[(EX + i) * ps]; }
+    c.rx[3] = rp[TAUB * ps] * c.imur;
+}
+
+// Solve one implicit stage for one cell (two fluids). rp: the cell's explicit
+// part (18 FP64 variables, ps apart); wwarm: its warm-start primitives (10,
+// ps apart). Writes q (18, through qp) and w (10, through wp). Jm and Minv
+// are the caller's 7 x 7 FP32 scratch for the Jacobian and its inverse. The
+// FP64 cell data are built again after the FP32 Newton phase rather than held
+// in registers through it.
+template <int NREF>
+__device__ int stage_solve(const double *rp, long long ps, const double *wwarm, const StageConst &k,
+                           const Phys &ph, double *qp, double *wp, Mat Jm, Mat Minv) {
+    const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
+    const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
 
     Cell<float> cf;
-    cf.D = f32_of(c.D); cf.Ds[0] = f32_of(c.Ds[0]); cf.Ds[1] = f32_of(c.Ds[1]);
-    for (int i = 0; i < 3; ++i) { cf.Sv[i] = f32_of(c.Sv[i]); cf.B[i] = f32_of(c.B[i]); }
-    cf.tauB = f32_of(c.tauB);
-    for (int i = 0; i < 7; ++i) cf.rx[i] = f32_of(c.rx[i]);
-    cf.mu_e = f32_of(c.mu_e); cf.mu_p = f32_of(c.mu_p); cf.inv = f32_of(c.inv); cf.mur = f32_of(c.mur);
-    cf.imur = f32_of(c.imur); cf.eta = f32_of(c.eta); cf.adt = f32_of(c.adt); cf.gm1 = f32_of(gm1); cf.gam = f32_of(gam);
+    {
+        Cell<double> c;
+        load_cell(c, rp, ps, sp, k, ph);
+        cf.D = f32_of(c.D); cf.Ds[0] = f32_of(c.Ds[0]); cf.Ds[1] = f32_of(c.Ds[1]);
+        for (int i = 0; i < 3; ++i) { cf.Sv[i] = f32_of(c.Sv[i]); cf.B[i] = f32_of(c.B[i]); }
+        cf.tauB = f32_of(c.tauB);
+        for (int i = 0; i < 7; ++i) cf.rx[i] = f32_of(c.rx[i]);
+        cf.mu_e = f32_of(c.mu_e); cf.mu_p = f32_of(c.mu_p); cf.inv = f32_of(c.inv); cf.mur = f32_of(c.mur);
+        cf.imur = f32_of(c.imur); cf.eta = f32_of(c.eta); cf.adt = f32_of(c.adt); cf.gm1 = f32_of(gm1);
+        cf.gam = f32_of(gam);
+        // source-free components equal r; psi and phi in closed form (varrho = Dbar has no source)
+        for (int v : {D, SX, SY, SZ, TAU, DB, BX, BY, BZ}) qp[v * ps] = rp[v * ps];
+        for (int i = 0; i < 3; ++i) qp[(EX + i) * ps] = rp[(EX + i) * ps];  // replaced by the root
+        for (int i = 0; i < 4; ++i) qp[(SBX + i) * ps] = rp[(SBX + i) * ps];  // replaced by the root
+        qp[PSI * ps] = (rp[PSI * ps] + k.adt * rp[DB * ps]) * k.cpsi;
+        qp[PHI * ps] = rp[PHI * ps] * k.cpsi;
+    }
 
     float scale = 1e-30f;
     for (int i = 0; i < 7; ++i) scale = fmaxf(scale, fabsf(cf.rx[i]));
 
     // ---- FP32 Newton
-    float x[7], p[2] = {f32_of(wwarm[P]), f32_of(wwarm[5 + P])}, dfdp[2] = {-1.f, -1.f};
+    float x[7], p[2] = {f32_of(wwarm[P * ps]), f32_of(wwarm[(5 + P) * ps])}, dfdp[2] = {-1.f, -1.f};
     for (int i = 0; i < 7; ++i) x[i] = cf.rx[i];
     float St2[2][3], a[2], S2[2], G[7], v[2][3], Z[2];
     split_x(cf, x, St2, a, S2);
@@ -405,6 +421,8 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     // |G| reaches round-off of the magnitude of G's terms is the result, with
     // its own primitives; extra passes, up to 8, only where needed)
     const float gs = resid_scale(cf, x, v);  // round-off scale of G
+    Cell<double> c;  // read again (the stores above keep the first loads from being reused)
+    load_cell(c, rp, ps, sp, k, ph);
     double xd[7], pdd[2] = {f64_of(p[0]), f64_of(p[1])};
     const double rdf[2] = {f64_of(1.f / dfdp[0]), f64_of(1.f / dfdp[1])};
     for (int i = 0; i < 7; ++i) xd[i] = f64_of(x[i]);
@@ -434,18 +452,18 @@ __device__ int stage_solve(const double r[NC], const double wwarm[NW], const Sta
     }
     bool ok = true;
     for (int s = 0; s < 2; ++s) {
-        w[5 * s + VX] = v64[s][0];
-        w[5 * s + VY] = v64[s][1];
-        w[5 * s + VZ] = v64[s][2];
-        w[5 * s + P] = pdd[s];
-        w[5 * s + ZZ] = Z64[s];
+        wp[(5 * s + VX) * ps] = v64[s][0];
+        wp[(5 * s + VY) * ps] = v64[s][1];
+        wp[(5 * s + VZ) * ps] = v64[s][2];
+        wp[(5 * s + P) * ps] = pdd[s];
+        wp[(5 * s + ZZ) * ps] = Z64[s];
         ok = ok && pdd[s] > 0.0 && isfinite(Z64[s]);
     }
     for (int i = 0; i < 3; ++i) {
-        q[SBX + i] = xd[i] * c.mur;
-        q[EX + i] = xd[4 + i];
+        qp[(SBX + i) * ps] = xd[i] * c.mur;
+        qp[(EX + i) * ps] = xd[4 + i];
     }
-    q[TAUB] = xd[3] * c.mur;
+    qp[TAUB * ps] = xd[3] * c.mur;
     if (!ok || !(gres <= 1e-9 * f64_of(gs))) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
