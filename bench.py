@@ -43,10 +43,10 @@ WORKLOAD = "khi-2d-1024x1024 (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=
 # for each kernel of the FP64 form on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
 # The FP64 pipe issues 2 of them per clock per SM, which sets the ALU peak.
-FP64_OPS_PER_CELL = {"stage": 172.0, "flux1": 745.0, "flux2": 717.0}
+FP64_OPS_PER_CELL = {"stage": 174.0, "flux1": 738.4, "flux2": 710.4}
 # DRAM bytes (read + write) per cell and launch of the same kernels, from the
 # ncu launch list of the KHI 1024^2 bench (dram__bytes_read.sum + write.sum).
-DRAM_BYTES_PER_CELL = {"stage": 220.8, "flux1": 447.7, "flux2": 387.1}
+DRAM_BYTES_PER_CELL = {"stage": 223.1, "flux1": 448.0, "flux2": 386.9}
 # Algorithmic HBM bytes per cell for each kernel (read once + written once).
 BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
 
