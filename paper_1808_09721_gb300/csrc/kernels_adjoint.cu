@@ -52,7 +52,9 @@ __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, do
 
 // Reverse of the face values along `dir`. One thread per (face, component):
 // faces k = -1 .. n-1 along dir (the face after cell k) for every line.
-// lambda_L of a cell = aL * LA + bL * LB (LB may be null).
+// Consecutive threads take neighbouring faces along x (dir 0) or neighbouring
+// lines (dir 1), so a warp's loads and atomics fall on consecutive cells of
+// one variable plane. lambda_L of a cell = aL * LA + bL * LB (LB may be null).
 __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, const double *LA, double aL,
                            const double *LB, double bL, double *fbar, double *qbar) {
     const int n = dir == 0 ? g.nx : g.ny, m = dir == 0 ? g.ny : g.nx, bc = dir == 0 ? g.bcx : g.bcy;
@@ -60,10 +62,18 @@ __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, co
     const long long nf = (long long)(n + 1) * m * sf::NC;
     const double eps4 = 4e-6;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(t % sf::NC);
-        const long long r = t / sf::NC;
-        const int k = (int)(r % (n + 1)) - 1;  // face after cell k
-        const int line = (int)(r / (n + 1));
+        int c, k, line;  // component, face after cell k, line
+        if (dir == 0) {
+            k = (int)(t % (n + 1)) - 1;
+            const long long r = t / (n + 1);
+            line = (int)(r % m);
+            c = (int)(r / m);
+        } else {
+            line = (int)(t % m);
+            const long long r = t / m;
+            k = (int)(r % (n + 1)) - 1;
+            c = (int)(r / (n + 1));
+        }
         auto cell = [&](int i) -> long long {
             int im = amap(i, n, bc);
             return dir == 0 ? (long long)line * g.nx + im : (long long)im * g.nx + line;
