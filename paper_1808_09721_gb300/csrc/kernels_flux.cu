@@ -68,6 +68,7 @@ struct SFModel {
     static constexpr int NAUX = 5;  // J (3), Z = rho h W^2, p + (E^2 + B^2)/2
     static constexpr int NS = 5;    // source slots: E (3), psi, phi
     static constexpr int G_FP64 = 4, G_FP32 = 2;
+    static constexpr bool SRCG = false;  // sources in shared memory
     // components with their own flux (D, S, tau, varrho); the Maxwell
     // components (B, E, psi, phi) are reconstructed in pairs
     static constexpr int NGEN = 6;
@@ -165,7 +166,10 @@ struct TFModel {
     static constexpr int NC = tf::NC, NW = tf::NW;
     static constexpr int NAUX = 0;
     static constexpr int NS = 9;  // Sbar (3), taubar, E (3), psi, phi
-    static constexpr int G_FP64 = 2, G_FP32 = 4;
+    static constexpr int G_FP64 = 4, G_FP32 = 4;
+    // FP64 2-D tiles: the 9 source entries per cell go through global scratch,
+    // which leaves room in shared memory for 4 component groups (1024 threads)
+    static constexpr bool SRCG = true;
     // components with their own flux (D, S, tau, Dbar, Sbar, taubar)
     static constexpr int NGEN = 10;
     static constexpr int KB4 = 1;  // generic components of a Maxwell-block group when G = 4
@@ -238,12 +242,14 @@ struct FluxSmem {
     // per staged value); the FP64 current and sources are computed from the
     // loaded doubles while staging, and the auxiliaries are kept in FP32
     static constexpr bool SHADOW = sizeof(FT) < sizeof(double);
+    // interior cells' sources through global scratch (FluxArgs::srcg) instead of shared memory
+    static constexpr bool SRCG = M::SRCG && !SHADOW && TY > 1;
     // byte offsets
     static constexpr size_t st = 0;
     static constexpr size_t st32 = st + (SHADOW ? 0 : sizeof(double) * NV * SN);
     static constexpr size_t aux = st32 + (SHADOW ? sizeof(float) * NV * SN : 0);
     static constexpr size_t src = aux + (SHADOW ? sizeof(float) : sizeof(double)) * M::NAUX * SN;
-    static constexpr size_t fl = src + sizeof(double) * M::NS * NL;
+    static constexpr size_t fl = src + (SRCG ? 0 : sizeof(double) * M::NS * NL);
     static constexpr size_t hp = fl + sizeof(FT) * M::NGEN * SN;
     static constexpr size_t fc = hp + sizeof(FT) * 4 * G * SN;
     static constexpr size_t total = fc + sizeof(FT) * 2 * G * SN;
@@ -328,8 +334,17 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int ty = e / TX, tx = e - ty * TX;
             double s[M::NS];
             M::source(st, aux, SN, (ty + OY) * SW + tx + 2, ph, s);
+            if constexpr (L_::SRCG) {
+                const int si = i0 + tx, sj = j0 + ty;
+                if (si < g.nx && sj < g.ny) {
+                    const long long sc = base + (long long)sj * g.row + si;
 #pragma unroll
-            for (int k = 0; k < M::NS; ++k) src[k * NL + e] = s[k];
+                    for (int k = 0; k < M::NS; ++k) a.srcg[(long long)k * g.plane + sc] = s[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < M::NS; ++k) src[k * NL + e] = s[k];
+            }
         }
     }
 
@@ -499,7 +514,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             if (c < 0 || !inside) continue;
             // (slot is uniform over the group: components without a source skip its terms)
             const int slot = M::src_slot(c);
-            const double s = slot >= 0 ? src[slot * NL + lid] : 0.0;
+            double s = 0.0;
+            if (slot >= 0) s = L_::SRCG ? a.srcg[(long long)slot * g.plane + cell] : src[slot * NL + lid];
             const long long o = (long long)c * g.plane + cell;
             const double Lv = a.lin ? to_f64(L[r]) + a.lin[o] : to_f64(L[r]);
             double b = a.base[0][o];

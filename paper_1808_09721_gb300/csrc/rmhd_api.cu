@@ -40,6 +40,7 @@ struct rmhd_ctx {
     double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
     double *R3;    // SSP3(332): q^n + dt/4 L1 + (1/2 - gamma) dt Psi1 (null for SSP2)
     double *LBUF;  // 3-D grids: L_x + L_y of the current flux pass (null otherwise)
+    double *SRCG;  // two fluids: source scratch of the FP64 flux kernel (null otherwise)
     int *status;       // device [2]
     int *h_status;     // pinned host copy of the 64-bit status key
     double *h_diag;    // pinned host [8]
@@ -145,7 +146,7 @@ static Grid make_grid(const rmhd_config *cfg) {
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, stage, scratch, diag, status;
+    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -190,6 +191,8 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     if (cfg->scheme == RMHD_SSP3) { L.R3 = o; o += align256(nc * pl); }
     L.LBUF = 0;
     if (cfg->nz > 1) { L.LBUF = o; o += align256(nc * pl); }
+    L.SRCG = 0;  // two fluids: source scratch of the FP64 flux kernel (9 planes)
+    if (cfg->model == RMHD_TWO_FLUID && nruns == 0) { L.SRCG = o; o += align256(9 * pl); }
     L.ACC = o; o += align256(nc * pl);
     L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
@@ -321,6 +324,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->ACC = (double *)(c->ws + L.ACC);
     c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
     c->LBUF = L.LBUF ? (double *)(c->ws + L.LBUF) : nullptr;
+    c->SRCG = L.SRCG ? (double *)(c->ws + L.SRCG) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -523,7 +527,9 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
 }
 
 // One flux pass of a single grid (3-D grids take the two-pass path).
-static cudaError_t flux_pass(rmhd_ctx *c, int nout, const FluxArgs &f) {
+static cudaError_t flux_pass(rmhd_ctx *c, int nout, const FluxArgs &f0) {
+    FluxArgs f = f0;
+    f.srcg = c->SRCG;
     if (c->g.nz > 1) return launch_flux_3d(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->LBUF, c->stream);
     return launch_flux(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->stream);
 }
@@ -751,6 +757,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->ACC = (double *)(c->ws + L.ACC);
     c->R3 = L.R3 ? (double *)(c->ws + L.R3) : nullptr;
     c->LBUF = L.LBUF ? (double *)(c->ws + L.LBUF) : nullptr;
+    c->SRCG = L.SRCG ? (double *)(c->ws + L.SRCG) : nullptr;
     c->stage_buf = (double *)(c->ws + L.stage);
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
@@ -981,10 +988,12 @@ static int enqueue_step_into(rmhd_ctx *c, double dt, double *q1, double *w1, dou
     StageArgs s1{c->Q, c->W, q1, w1, c->status, kGamma * dt};
     CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
     int n = ssp2_pass1(c, q1, w1, dt, f);
+    f.srcg = c->SRCG;
     CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
     StageArgs s2{c->R, w1, q2, w2, c->status, kGamma * dt};
     CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
     n = ssp2_pass2(c, q2, w2, dt, f);
+    f.srcg = c->SRCG;
     CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
     return RMHD_OK;
 }

@@ -47,6 +47,8 @@ struct FluxArgs {
     double *wcarry;         // if not null: the stage primitives are copied here (next warm start)
     double *lout;           // nout = 0 (x-y pass of a 3-D grid): L_x + L_y is written here, nothing else
     const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
+    double *srcg;           // two fluids, FP64, 2-D tiles: the interior cells' source entries (NS planes)
+                            // go through this scratch instead of shared memory
 };
 
 struct StageArgs {
