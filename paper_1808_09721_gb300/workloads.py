@@ -185,6 +185,52 @@ def _tf_species_prims(rho, p, v, B, E, mu_e, mu_p):
                            ((1.0 - frac_e) * rho)[None], v, (0.5 * p)[None], B, E]).astype(np.float64)
 
 
+def _smooth(rng, coords, amp, nmodes=3):
+    """Sum of nmodes random periodic Fourier modes (integer wave numbers 1..2
+    per axis on the unit-length axes `coords`), scaled to max |f| = amp."""
+    f = np.zeros(coords[0].shape)
+    for _ in range(nmodes):
+        k = rng.integers(0, 3, size=len(coords))
+        k[rng.integers(0, len(coords))] = rng.integers(1, 3)  # at least one nonzero wave number
+        phase = rng.uniform(0.0, 2.0 * np.pi)
+        f = f + rng.uniform(0.5, 1.0) * np.sin(2.0 * np.pi * sum(ki * c for ki, c in zip(k, coords)) + phase)
+    return amp * f / max(np.max(np.abs(f)), 1e-300)
+
+
+def random_smooth(shape, seed: int = 0, model: int = RESISTIVE, sigma: float = 10.0,
+                  gamma: float = 4.0 / 3.0, cfl: float = 0.4, bc: int = PERIODIC,
+                  mu: float = 1e3) -> Workload:
+    """Smooth random periodic fields on the unit box with every component
+    nonzero: rho, p in [0.5, 1.5], |v_i| <= 0.3, |B_i| <= 1 and
+    E = -v x B + dE with a smooth |dE_i| <= 0.1 (a resistive current). `shape`
+    = (nx,), (ny, nx) or (nz, ny, nx). Two fluids: the totals split into a
+    neutral pair plasma (mu_p = -mu_e = mu), the positive species' velocity
+    offset by a smooth |dv_i| <= 0.05 (a current carried by the species)."""
+    shape = tuple(shape)
+    nd = len(shape)
+    nz, ny, nx = (1,) * (3 - nd) + shape
+    axes = [(np.arange(n) + 0.5) / n for n in (nz, ny, nx)]
+    Z, Y, X = np.meshgrid(*axes, indexing="ij")
+    coords = [X, Y, Z][:nd]
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + _smooth(rng, coords, 0.5)
+    p = 1.0 + _smooth(rng, coords, 0.5)
+    v = np.stack([_smooth(rng, coords, 0.3) for _ in range(3)])
+    B = np.stack([_smooth(rng, coords, 1.0) for _ in range(3)])
+    E = _ideal_e(v, B) + np.stack([_smooth(rng, coords, 0.1) for _ in range(3)])
+    sq = (lambda a: a.reshape(a.shape[:-3] + (ny, nx))) if nz == 1 else (lambda a: a)
+    kw = dict(nz=nz, zlim=(0.0, 1.0), bc_z=bc) if nz > 1 else {}
+    if model == RESISTIVE:
+        prims = _sf_prims(sq(rho), sq(v), sq(p), sq(B), sq(E))
+        return Workload("random_smooth", RESISTIVE, nx, ny, (0.0, 1.0), (0.0, 1.0), gamma, sigma, bc, bc,
+                        cfl, 10, prims, **kw)
+    sp = _tf_species_prims(sq(rho), sq(p), sq(v), sq(B), sq(E), -mu, mu)
+    dv = np.stack([_smooth(rng, coords, 0.05) for _ in range(3)])
+    sp[6:9] += sq(dv)  # positive species' velocity (rows: rho_e, v_e, p_e, rho_p, v_p, p_p, B, E)
+    return Workload("random_smooth_tf", TWO_FLUID, nx, ny, (0.0, 1.0), (0.0, 1.0), gamma, sigma, bc, bc,
+                    cfl, 10, np.ascontiguousarray(sp), mu_e=-mu, mu_p=mu, **kw)
+
+
 def tf_brio_wu(nx: int = 1600, mu_p: float = 1e3, mass_ratio: float = 1.0, sigma: float = 1e4,
                gamma: float = 2.0, cfl: float = 0.4) -> Workload:
     """Two-fluid Brio-Wu tube (Sec. 4.1): x in [0, 1], outflow, (rho, p, B_x, B_y) =

@@ -1,0 +1,79 @@
+"""Random smooth fields with every component nonzero (all three of v, B and E,
+plus a resistive current), on the GPU through the C ABI against the oracle.
+
+In the flux kernels the Maxwell components (B, E, psi, phi) are reconstructed
+in pairs whose partner and sign depend on the direction (x, y, and z in the
+3-D z pass); with every field component of order one, a wrong partner or sign
+in any pair, direction or block would show at order one. Bars as elsewhere:
+relative L-infinity <= 1e-9 of the natural scale (FP64), mean relative error
+<= 1e-4 (mixed)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import parity_errors, parity_scale
+from paper_1808_09721_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_09721_gb300 import _lib
+    from paper_1808_09721_gb300 import build as B
+    B.build()
+    _lib.load()
+    from paper_1808_09721_gb300.sim import Sim as S
+    return S
+
+
+def run_pair(Sim, wl, nsteps, precision=0, scheme=0):
+    g = Sim.from_workload(wl, precision=precision, scheme=scheme)
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y,
+              mu_e=wl.mu_e, mu_p=wl.mu_p, kappa=wl.kappa, scheme=scheme, nz=wl.nz, zlim=wl.zlim, bc_z=wl.bc_z)
+    o.set_prims(wl.prims)
+    g.step(wl.dt, nsteps)
+    g.check()
+    o.step(wl.dt, nsteps)
+    nc = 14 if wl.model == 0 else 18
+    return g.cons().reshape(nc, -1, 1), o.cons().reshape(nc, -1, 1)
+
+
+CASES = [
+    ("1d_periodic", (70,), 0, WL.PERIODIC),
+    ("2d_periodic", (33, 45), 0, WL.PERIODIC),
+    ("2d_outflow", (33, 45), 0, WL.OUTFLOW),
+    ("3d_periodic", (10, 12, 18), 0, WL.PERIODIC),
+    ("3d_outflow", (9, 10, 35), 0, WL.OUTFLOW),
+    ("tf_2d_periodic", (24, 40), 1, WL.PERIODIC),
+    ("tf_3d_periodic", (6, 10, 12), 1, WL.PERIODIC),
+]
+
+
+@pytest.mark.parametrize("name,shape,model,bc", CASES, ids=[c[0] for c in CASES])
+def test_random_fields_fp64(Sim, name, shape, model, bc):
+    wl = WL.random_smooth(shape, seed=11, model=model, bc=bc)
+    got, want = run_pair(Sim, wl, 3)
+    err = parity_errors(model, got, want, 1e3 if model == 1 else 1.0)
+    assert np.all(err <= TOL), (name, err)
+
+
+@pytest.mark.parametrize("name,shape,model,bc", [CASES[1], CASES[3], CASES[5]], ids=["2d", "3d", "tf_2d"])
+def test_random_fields_ssp3_fp64(Sim, name, shape, model, bc):
+    wl = WL.random_smooth(shape, seed=12, model=model, bc=bc)
+    got, want = run_pair(Sim, wl, 2, scheme=1)
+    err = parity_errors(model, got, want, 1e3 if model == 1 else 1.0)
+    assert np.all(err <= TOL), (name, err)
+
+
+@pytest.mark.parametrize("name,shape,model,bc", [CASES[0], CASES[1], CASES[3], CASES[5]],
+                         ids=["1d", "2d", "3d", "tf_2d"])
+def test_random_fields_mixed(Sim, name, shape, model, bc):
+    wl = WL.random_smooth(shape, seed=13, model=model, bc=bc)
+    got, want = run_pair(Sim, wl, 3, precision=1)
+    mu_ref = 1e3 if model == 1 else 1.0
+    l1 = np.abs(got - want).reshape(got.shape[0], -1).mean(axis=1) / parity_scale(model, want, mu_ref)
+    assert np.all(l1 <= 1e-4), (name, l1)
