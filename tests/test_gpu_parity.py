@@ -186,6 +186,66 @@ def test_full_size_khi_sampled_cells(Sim, n):
         assert np.all(np.abs(got[:, j0, i0] - want) <= TOL * scale), (j0, i0)
 
 
+def _oracle_sub(sub, scheme=0):
+    o = O.Sim(sub.model, sub.nx, sub.ny, sub.xlim, sub.ylim, sub.gamma, sub.sigma, sub.bc_x, sub.bc_y,
+              kappa=sub.kappa, scheme=scheme, nz=sub.nz, zlim=sub.zlim, bc_z=sub.bc_z)
+    o.set_prims(sub.prims)
+    return o
+
+
+def test_full_size_khi_ssp3_sampled_cells(Sim):
+    """SSP3(332) on the 1024^2 benchmark grid, as the bench times it: one step,
+    sampled cells against the oracle on 16 x 16 windows (three flux passes: a
+    cell depends on cells within 6; outflow ghosts at the window edge reach 6
+    cells in, so the centre is exact)."""
+    wl = WL.khi(n=1024, seed=0)
+    n = wl.nx
+    g = Sim.from_workload(wl, scheme=1)
+    g.step(wl.dt, 1)
+    g.check()
+    got = g.cons()
+    from conftest import parity_scale
+    scale = parity_scale(0, got)
+    rng = np.random.default_rng(19)
+    h = 8
+    for _ in range(6):
+        j0, i0 = (int(x) for x in rng.integers(0, n, size=2))
+        jj, ii = np.arange(j0 - h, j0 + h) % n, np.arange(i0 - h, i0 + h) % n
+        win = np.ascontiguousarray(wl.prims[:, jj][:, :, ii])
+        sub = wl.with_prims(win, nx=2 * h, ny=2 * h, bc_x=WL.OUTFLOW, bc_y=WL.OUTFLOW,
+                            xlim=(0.0, 2 * h * wl.dx), ylim=(0.0, 2 * h * wl.dy))
+        o = _oracle_sub(sub, scheme=1)
+        o.step(wl.dt, 1)
+        want = o.cons()[:, h, h]
+        assert np.all(np.abs(got[:, j0, i0] - want) <= TOL * scale), (j0, i0)
+
+
+def test_full_size_khi3d_sampled_cells(Sim):
+    """The 3-D KHI 128^3 grid the bench times (x-y pass per plane, then the z
+    pass): one step, sampled cells against the oracle on 12^3 windows (a cell
+    depends on cells within 4 along each axis)."""
+    wl = WL.khi3d(n=128, seed=0)
+    g = Sim.from_workload(wl)
+    g.step(wl.dt, 1)
+    g.check()
+    got = g.cons()  # [14][nz][ny][nx]
+    from conftest import parity_scale
+    scale = parity_scale(0, got.reshape(14, -1, 1))
+    rng = np.random.default_rng(29)
+    h = 6
+    for _ in range(4):
+        k0, j0, i0 = (int(x) for x in rng.integers(0, 128, size=3))
+        kk, jj, ii = (np.arange(c - h, c + h) % 128 for c in (k0, j0, i0))
+        win = np.ascontiguousarray(wl.prims[:, kk][:, :, jj][:, :, :, ii])
+        sub = wl.with_prims(win, nx=2 * h, ny=2 * h, nz=2 * h, bc_x=WL.OUTFLOW, bc_y=WL.OUTFLOW,
+                            bc_z=WL.OUTFLOW, xlim=(0.0, 2 * h * wl.dx), ylim=(0.0, 2 * h * wl.dy),
+                            zlim=(0.0, 2 * h * wl.dz))
+        o = _oracle_sub(sub)
+        o.step(wl.dt, 1)
+        want = o.cons()[:, h, h, h]
+        assert np.all(np.abs(got[:, k0, j0, i0] - want) <= TOL * scale), (k0, j0, i0)
+
+
 @pytest.mark.parametrize("name,make,mu_ref,marks", [
     ("khi_64", lambda: WL.khi(n=64, seed=1), 1.0, (10, 50, 100, 200)),
     ("tf_sheet_48", lambda: WL.tf_sheet(n=48, seed=2), 1e3, (10, 50, 100)),
