@@ -32,12 +32,6 @@ __device__ __forceinline__ double s_rcp(double x) {
     double e = fma(-x, y, 1.0);
     return fma(y, fma(e, e, e), y);
 }
-// 1/x with a single Newton step y0 (1 + e): relative error ~e^2 ~ 2^-40.
-__device__ __forceinline__ double s_rcp1(double x) {
-    double y = approx_rcp(x);
-    double e = fma(-x, y, 1.0);
-    return fma(y, e, y);
-}
 // a/x with a single Newton step: with t = a y0 and e = 1 - x y0, a/x = t/(1 - e)
 // ~ t (1 + e); relative error ~e^2 ~ 2^-38 in 3 FP64 ops after the approximation.
 __device__ __forceinline__ double s_div1(double a, double x) {
@@ -99,7 +93,6 @@ __device__ __forceinline__ float s_rcp(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float s_rcp1(float x) { return s_rcp(x); }
 __device__ __forceinline__ float s_div1(float a, float x) { return a * s_rcp(x); }
 __device__ __forceinline__ float s_rsqrt(float x) {
     float y;
@@ -128,7 +121,6 @@ template <class T> __device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) 
 template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return Dual<T>(a.v - b, a.d); }
 template <class T> __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return Dual<T>(a - b.v, -b.d); }
 template <class T> __device__ __forceinline__ Dual<T> s_rcp(Dual<T> a) { T r = s_rcp(a.v); return Dual<T>(r, -a.d * r * r); }
-template <class T> __device__ __forceinline__ Dual<T> s_rcp1(Dual<T> a) { return s_rcp(a); }
 template <class T> __device__ __forceinline__ Dual<T> s_rsqrt(Dual<T> a) {
     T y = s_rsqrt(a.v);
     return Dual<T>(y, T(-0.5) * a.d * y * y * y);
