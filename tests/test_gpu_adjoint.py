@@ -101,6 +101,31 @@ def test_adjoint_matches_finite_differences(env, name, make, nsteps, ckpt):
         assert abs(ad - fd) <= 1e-5 * abs(fd), (name, seed, ad, fd)
 
 
+def test_adjoint_twenty_random_directions(env):
+    """Central differences (h = 1e-6) of the GPU forward run along 20 random
+    smooth directions of the initial primitives, each combined with a random
+    relative change of sigma, against the adjoint's directional derivative
+    (relative error <= 1e-5)."""
+    torch, Sim, _ = env
+    wl = WL.field_loop(n=24, nsteps=12)
+    nsteps = 12
+    J, gp, gs = gradients(env, wl, nsteps, 5)
+    rng = np.random.default_rng(21)
+    worst = 0.0
+    for seed in range(100, 120):
+        d = direction(wl, seed)
+        ds = float(rng.uniform(-1.0, 1.0)) * 1e-2 * wl.sigma  # sigma direction (scaled like the fields)
+        h = 1e-6
+        jp = gpu_J(Sim, dataclasses.replace(wl, sigma=wl.sigma + h * ds), wl.prims + h * d, nsteps)
+        jm = gpu_J(Sim, dataclasses.replace(wl, sigma=wl.sigma - h * ds), wl.prims - h * d, nsteps)
+        fd = (jp - jm) / (2 * h)
+        ad = float((gp * d).sum()) + gs * ds
+        rel = abs(ad - fd) / abs(fd)
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (seed, ad, fd)
+    print(f"20 directions: worst relative difference {worst:.2e}")
+
+
 def test_adjoint_matches_oracle_finite_differences(env):
     """Directional derivatives of the oracle's FP64 run (central differences)
     agree with the GPU adjoint gradient."""
