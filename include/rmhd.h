@@ -133,8 +133,9 @@ int rmhd_check(rmhd_ctx *ctx);
 
 /* Diagnostics of the current state (Sec. 2.1 invariants), written to out[8]:
  * sum D, sum tau, sum S_x, sum B_x, sum varrho (Dbar for two fluids)
- * (cell sums times dx dy), max |v|, number of non-finite conserved values,
- * and the CFL time step cfl * min(dx, dy). Synchronous. */
+ * (cell sums times the cell volume), max |v|, number of non-finite conserved
+ * values, and the CFL time step cfl * min(dx, dy, dz) over the grid's
+ * directions. Synchronous. */
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
 /* Discrete adjoint of the SSP2(222) step (single fluid, FP64, single grid with
