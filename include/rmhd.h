@@ -131,6 +131,26 @@ int rmhd_imex_step(rmhd_ctx *ctx, double dt, int nsteps, double *t_out);
  * in rmhd_last_error. */
 int rmhd_check(rmhd_ctx *ctx);
 
+/* Solver statistics (tracing; off by default). While enabled, every stage
+ * solve adds one count to two device histograms: by the number of FP32
+ * Newton iterations it took (hist[k], k = 1..30; hist[31]: 31 or more) and
+ * by the number of FP64 refinement passes (hist[32 + k - 1], k = 1..8).
+ * Counting uses device atomics and slows the stage kernels: it is for
+ * diagnostics, not for timed runs. rmhd_set_solver_stats(ctx, 1) clears the
+ * histograms and starts counting, 0 stops it; rmhd_solver_stats copies the
+ * 40 counts into the caller's host array `hist` and clears them.
+ * Synchronous. Errors: RMHD_ERR_INVALID, RMHD_ERR_CUDA. */
+int rmhd_set_solver_stats(rmhd_ctx *ctx, int enable);
+int rmhd_solver_stats(rmhd_ctx *ctx, unsigned long long *hist);
+
+/* Fault injection for tests of the error path, with no GPU fault involved:
+ * caps the FP64 refinement passes of every stage solve at `passes` (1..8;
+ * 0 restores the default, 8). A solve needs at least two passes to confirm
+ * convergence, so with a cap of 1 the next step records RMHD_ERR_NEWTON with
+ * the first failing cell (reported by rmhd_check), and the context stays
+ * usable. Errors: RMHD_ERR_INVALID (passes outside 0..8). */
+int rmhd_set_refinement_cap(rmhd_ctx *ctx, int passes);
+
 /* Diagnostics of the current state (Sec. 2.1 invariants), written to out[8]:
  * sum D, sum tau, sum S_x, sum B_x, sum varrho (Dbar for two fluids)
  * (cell sums times the cell volume), max |v|, number of non-finite conserved

@@ -32,7 +32,7 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
 // 20 warps per SM hide more of its FP64 and MUFU latency than 16 (no spills)
 __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace sf;
-    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma};
+    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const double pw = a.wwarm[P * g.plane + cell];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph
     using namespace tf;
     __shared__ float sJ[49 * kStageThreadsTF], sM[49 * kStageThreadsTF];
     const Mat Jm{sJ + threadIdx.x, kStageThreadsTF}, Minv{sM + threadIdx.x, kStageThreadsTF};
-    tf::StageConst k{a.adt, cpsi};
+    tf::StageConst k{a.adt, cpsi, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm, Minv);
@@ -81,7 +81,7 @@ __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, B
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const int run = b.run_of[cell];
-        sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma};
+        sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
         const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
         record(a.status, st, cell);
     }
@@ -95,7 +95,7 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
         Phys pr = ph;
         pr.sigma = b.sigma[run];
         pr.eta = b.eta[run];
-        tf::StageConst k{b.adt[run], b.cpsi[run]};
+        tf::StageConst k{b.adt[run], b.cpsi[run], a.maxpass > 0 ? a.maxpass : 8, a.hist};
         float jl[49], ml[49];
         const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, pr, a.q + cell, a.w + cell,
                                           tf::Mat{jl, 1}, tf::Mat{ml, 1});

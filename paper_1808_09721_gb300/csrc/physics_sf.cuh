@@ -159,7 +159,16 @@ struct StageConst {
     double adt;   // a_ii dt
     double cpsi;  // 1 / (1 + adt kappa)
     double sigma, gamma;
+    int maxpass;                // FP64 refinement passes at most (1..8)
+    unsigned long long *hist;   // if not null: histograms of FP32 iterations [32] and FP64 passes [8]
 };
+
+// Adds one solve to the histograms: by FP32 Newton iterations and by FP64 passes.
+__device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, int npass) {
+    if (!hist) return;
+    atomicAdd(&hist[nit < 31 ? nit : 31], 1ULL);
+    atomicAdd(&hist[32 + npass - 1], 1ULL);
+}
 
 // Solve one implicit stage for one cell. rp: the cell's explicit part (14
 // FP64 variables, ps apart); p_warm: pressure guess. Writes the cell's q (14,
@@ -214,7 +223,9 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
 
     float Minv[9], dpdE[3];
     bool have_jac = false;
+    int nit = 0;
     for (int it = 0; it < 24; ++it) {
+        nit = it + 1;
         // Jacobian columns dG/dE_k with duals; dp/dE_k by the implicit-function theorem
         float Jm[9];
         for (int kc = 0; kc < 3; ++kc) {
@@ -283,7 +294,8 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     const double rdf = f64_of(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
     double gres = 0.0;
-    for (int pass = 0; pass < 8; ++pass) {
+    int pass = 0;
+    for (; pass < k.maxpass; ++pass) {
         em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
         pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
@@ -292,7 +304,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
-        if (pass == 7) break;
+        if (pass == k.maxpass - 1) break;
         // first-order prediction of the pressure at the corrected E
         pdd -= f64_of(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
         Ed[0] -= f64_of(dE[0]);
@@ -307,6 +319,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
+    count_solve(k.hist, nit, pass + 1);
     if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
     return ST_OK;
 }

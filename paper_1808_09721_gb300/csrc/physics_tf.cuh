@@ -293,6 +293,8 @@ __device__ __forceinline__ float resid_scale(const Cell<float> &cf, const float 
 
 struct StageConst {
     double adt, cpsi;
+    int maxpass;               // FP64 refinement passes at most (1..8)
+    unsigned long long *hist;  // if not null: histograms of FP32 iterations [32] and FP64 passes [8]
 };
 
 // The FP64 data of a cell's stage solve from its explicit part r (variables
@@ -361,7 +363,9 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
 
     float dpdx[2][7];
     bool have_jac = false;
+    int nit = 0;
     for (int it = 0; it < 30; ++it) {
+        nit = it + 1;
         for (int kc = 0; kc < 7; ++kc) {
             Dual<float> xd[7];
             for (int i = 0; i < 7; ++i) xd[i] = Dual<float>(x[i], i == kc ? 1.f : 0.f);
@@ -428,14 +432,15 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
     for (int i = 0; i < 7; ++i) xd[i] = f64_of(x[i]);
     double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
     double gres = 0.0;
-    for (int pass = 0; pass < 8; ++pass) {
+    int pass = 0;
+    for (; pass < k.maxpass; ++pass) {
         split_x(c, xd, St64, a64, S264);
         for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
         stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
         gres = 0.0;
         for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
         if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
-        if (pass == 7) break;
+        if (pass == k.maxpass - 1) break;
         float Gf[7], dx[7];
         for (int i = 0; i < 7; ++i) Gf[i] = f32_of(G64[i]);
         for (int i = 0; i < 7; ++i) {
@@ -464,6 +469,7 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
         qp[(EX + i) * ps] = xd[4 + i];
     }
     qp[TAUB * ps] = xd[3] * c.mur;
+    sf::count_solve(k.hist, nit, pass + 1);
     if (!ok || !(gres <= 1e-9 * f64_of(gs))) return sf::ST_NEWTON;
     return sf::ST_OK;
 }

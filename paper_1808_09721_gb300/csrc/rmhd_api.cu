@@ -42,6 +42,9 @@ struct rmhd_ctx {
     double *LBUF;  // 3-D grids: L_x + L_y of the current flux pass (null otherwise)
     double *SRCG;  // two fluids: source scratch of the FP64 flux kernel (null otherwise)
     int *status;       // device [2]
+    unsigned long long *hist;  // device [40]: solver statistics (FP32 iterations, FP64 passes)
+    bool stats_on;             // count stage solves into hist
+    int maxpass;               // cap on the FP64 refinement passes (0: the kernels' default)
     int *h_status;     // pinned host copy of the 64-bit status key
     double *h_diag;    // pinned host [8]
     bool has_state;
@@ -146,7 +149,7 @@ static Grid make_grid(const rmhd_config *cfg) {
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status;
+    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status, hist;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -198,6 +201,7 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
+    L.hist = o; o += align256(40 * sizeof(unsigned long long));
     L.nx = L.off = L.dx = L.rdx4 = L.dt = L.sigma = L.eta = L.adt = L.cpsi = L.work = L.run_of = L.Qsave = L.Wsave = 0;
     if (nruns > 0) {
         L.nx = o; o += align256((size_t)nruns * sizeof(int));
@@ -329,6 +333,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
     c->status = (int *)(c->ws + L.status);
+    c->hist = (unsigned long long *)(c->ws + L.hist);
     if (cudaMallocHost(&c->h_status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->h_diag, 8 * sizeof(double)) != cudaSuccess) {
         if (c->own_ws) cudaFree(c->ws);
@@ -460,6 +465,13 @@ static int toc(rmhd_ctx *c) {
 // Coefficients carry the time step: dt > 0 for single grids; batches pass
 // dt = 0 and get per-unit-dt coefficients, which the kernel scales by each
 // run's own dt.
+// Stage-solve arguments with the context's statistics and refinement settings.
+static StageArgs stage_args(const rmhd_ctx *c, const double *r, const double *wwarm, double *q, double *w,
+                            double adt) {
+    StageArgs a{r, wwarm, q, w, c->status, adt, c->stats_on ? c->hist : nullptr, c->maxpass};
+    return a;
+}
+
 static FluxArgs flux_args(const double *q, const double *w) {
     FluxArgs a{};
     a.q = q;
@@ -493,12 +505,12 @@ static int ssp2_pass2(rmhd_ctx *c, const double *q2, const double *w2, double dt
 static int enqueue_step_batch(rmhd_ctx *c) {
     const int m = c->cfg.model;
     FluxArgs f;
-    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, 0.0};
+    StageArgs s1 = stage_args(c, c->Q, c->W, c->Q1, c->W1, 0.0);
     LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s1, c->bargs, c->stage_threads, c->stream));
     int n = ssp2_pass1(c, c->Q1, c->W1, 0.0, f);
     LAUNCH(c, RMHD_K_FLUX1, launch_flux_batch(m, c->cfg.precision, n, c->g, c->ph, f, c->bargs, c->tile_x,
                                               c->flux_blocks, c->stream));
-    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, 0.0};
+    StageArgs s2 = stage_args(c, c->R, c->W1, c->Q1, c->W1, 0.0);
     LAUNCH(c, RMHD_K_STAGE, launch_stage_batch(m, c->g, c->ph, s2, c->bargs, c->stage_threads, c->stream));
     n = ssp2_pass2(c, c->Q1, c->W1, 0.0, f);
     LAUNCH(c, RMHD_K_FLUX2, launch_flux_batch(m, c->cfg.precision, n, c->g, c->ph, f, c->bargs, c->tile_x,
@@ -551,20 +563,20 @@ static double min_width(const rmhd_ctx *c) {
 static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
     const int m = c->cfg.model;
     FluxArgs f;
-    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
+    StageArgs s1 = stage_args(c, c->Q, c->W, c->Q1, c->W1, kGamma * dt);
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
     f = flux_args(c->Q1, c->W1);
     int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
     n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma, dt);
     n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
     LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    StageArgs s2 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
     f = flux_args(c->Q1, c->W1);
     n = add_out(f, 0, c->R3, c->R, 0.25, 0.0, dt);
     n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
     LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s3{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    StageArgs s3 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s3, c->stream));
     f = flux_args(c->Q1, c->W1);
     f.wcarry = c->W;
@@ -579,11 +591,11 @@ static int enqueue_step(rmhd_ctx *c, double dt) {
     if (c->cfg.scheme == RMHD_SSP3) return enqueue_step_ssp3(c, dt);
     const int m = c->cfg.model;
     FluxArgs f;
-    StageArgs s1{c->Q, c->W, c->Q1, c->W1, c->status, kGamma * dt};
+    StageArgs s1 = stage_args(c, c->Q, c->W, c->Q1, c->W1, kGamma * dt);
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
     int n = ssp2_pass1(c, c->Q1, c->W1, dt, f);
     LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s2{c->R, c->W1, c->Q1, c->W1, c->status, kGamma * dt};
+    StageArgs s2 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
     LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
     n = ssp2_pass2(c, c->Q1, c->W1, dt, f);
     LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
@@ -762,6 +774,7 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->scratch = (double *)(c->ws + L.scratch);
     c->diag = (double *)(c->ws + L.diag);
     c->status = (int *)(c->ws + L.status);
+    c->hist = (unsigned long long *)(c->ws + L.hist);
     c->d_nx = (int *)(c->ws + L.nx);
     c->d_off = (long long *)(c->ws + L.off);
     c->d_dx = (double *)(c->ws + L.dx);
@@ -985,12 +998,12 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
 static int enqueue_step_into(rmhd_ctx *c, double dt, double *q1, double *w1, double *q2, double *w2) {
     const int m = c->cfg.model;
     FluxArgs f;
-    StageArgs s1{c->Q, c->W, q1, w1, c->status, kGamma * dt};
+    StageArgs s1 = stage_args(c, c->Q, c->W, q1, w1, kGamma * dt);
     CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
     int n = ssp2_pass1(c, q1, w1, dt, f);
     f.srcg = c->SRCG;
     CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
-    StageArgs s2{c->R, w1, q2, w2, c->status, kGamma * dt};
+    StageArgs s2 = stage_args(c, c->R, w1, q2, w2, kGamma * dt);
     CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
     n = ssp2_pass2(c, q2, w2, dt, f);
     f.srcg = c->SRCG;
@@ -1077,6 +1090,31 @@ int rmhd_kernel_times(rmhd_ctx *c, double *ms, int *counts) {
     }
     c->timed.clear();
     return st;
+}
+
+int rmhd_set_solver_stats(rmhd_ctx *c, int enable) {
+    if (!c) return RMHD_ERR_INVALID;
+    if (enable) CK(c, cudaMemsetAsync(c->hist, 0, 40 * sizeof(unsigned long long), c->stream));
+    c->stats_on = enable != 0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // captured with the old arguments
+    CK(c, cudaStreamSynchronize(c->stream));
+    return RMHD_OK;
+}
+
+int rmhd_solver_stats(rmhd_ctx *c, unsigned long long *hist) {
+    if (!c || !hist) return fail(c, RMHD_ERR_INVALID, "solver_stats: bad argument");
+    CK(c, cudaMemcpyAsync(hist, c->hist, 40 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemsetAsync(c->hist, 0, 40 * sizeof(unsigned long long), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return RMHD_OK;
+}
+
+int rmhd_set_refinement_cap(rmhd_ctx *c, int passes) {
+    if (!c) return RMHD_ERR_INVALID;
+    if (passes < 0 || passes > 8) return fail(c, RMHD_ERR_INVALID, "set_refinement_cap: passes must be 0..8");
+    c->maxpass = passes;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // captured with the old arguments
+    return RMHD_OK;
 }
 
 int rmhd_check(rmhd_ctx *c) {

@@ -58,6 +58,8 @@ struct StageArgs {
     double *w;           // its primitives, NW planes
     int *status;
     double adt;          // a_ii dt
+    unsigned long long *hist;  // if not null: per-solve histograms, FP32 Newton iterations [32] and FP64 passes [8]
+    int maxpass;               // cap on the FP64 refinement passes (0: the default, 8)
 };
 
 // Batched ensemble of independent 1-D runs packed one after another in every

@@ -163,6 +163,21 @@ class Sim:
         self._check(self.lib.rmhd_kernel_times(self.h, ms, n), "kernel_times")
         return {k: (ms[i], n[i]) for i, k in enumerate(("stage", "flux1", "flux2"))}
 
+    def set_solver_stats(self, on: bool):
+        """Start (clearing the counts) or stop counting stage solves into histograms."""
+        self._check(self.lib.rmhd_set_solver_stats(self.h, int(bool(on))), "set_solver_stats")
+
+    def solver_stats(self) -> dict:
+        """Histograms since the last read: {"fp32_iterations": {k: solves}, "fp64_passes": {k: solves}}."""
+        h = (C.c_ulonglong * 40)()
+        self._check(self.lib.rmhd_solver_stats(self.h, h), "solver_stats")
+        return {"fp32_iterations": {k: int(h[k]) for k in range(1, 32) if h[k]},
+                "fp64_passes": {k: int(h[32 + k - 1]) for k in range(1, 9) if h[32 + k - 1]}}
+
+    def set_refinement_cap(self, passes: int):
+        """Cap the FP64 refinement passes of the stage solves (0: default); 1 forces RMHD_ERR_NEWTON."""
+        self._check(self.lib.rmhd_set_refinement_cap(self.h, int(passes)), "set_refinement_cap")
+
     def diagnostics(self) -> dict:
         out = (C.c_double * 8)()
         self._check(self.lib.rmhd_diagnostics(self.h, out), "diagnostics")

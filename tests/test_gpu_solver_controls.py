@@ -1,0 +1,95 @@
+"""Solver statistics and host-side fault injection through the C ABI.
+
+Statistics: device histograms of the FP32 Newton iterations and FP64
+refinement passes of every stage solve (off by default). Fault injection: a
+cap on the FP64 refinement passes; with one pass no solve can confirm
+convergence, so the step records RMHD_ERR_NEWTON with the first failing cell,
+and the context must stay usable. Nothing here faults or traps the GPU."""
+import re
+
+import numpy as np
+import pytest
+
+from paper_1808_09721_gb300 import RmhdError
+from paper_1808_09721_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_09721_gb300 import _lib
+    from paper_1808_09721_gb300 import build as B
+    B.build()
+    _lib.load()
+    from paper_1808_09721_gb300.sim import Sim as S
+    return S
+
+
+@pytest.mark.parametrize("name,make,scheme,stages", [
+    ("khi_ssp2", lambda: WL.khi(n=64, seed=0), 0, 2),
+    ("khi_ssp3", lambda: WL.khi(n=48, seed=1), 1, 3),
+    ("tf_sheet", lambda: WL.tf_sheet(n=24, seed=2), 0, 2),
+])
+def test_solver_stats_count_every_solve(Sim, name, make, scheme, stages):
+    wl = make()
+    steps = 3
+    g = Sim.from_workload(wl, scheme=scheme)
+    ref = Sim.from_workload(wl, scheme=scheme)
+    g.set_solver_stats(True)
+    g.step(wl.dt, steps)
+    g.check()
+    st = g.solver_stats()
+    n = stages * steps * wl.cells
+    assert sum(st["fp32_iterations"].values()) == n, st
+    assert sum(st["fp64_passes"].values()) == n, st
+    assert min(st["fp64_passes"]) >= 2, st  # convergence is confirmed at a second evaluation
+    assert min(st["fp32_iterations"]) >= 1 and max(st["fp32_iterations"]) <= 30, st
+    # counting leaves the arithmetic unchanged
+    ref.step(wl.dt, steps)
+    ref.check()
+    assert np.array_equal(g.cons(), ref.cons())
+    # the read cleared the counts; a stopped counter stays empty
+    g.set_solver_stats(False)
+    g.step(wl.dt, 1)
+    assert g.solver_stats() == {"fp32_iterations": {}, "fp64_passes": {}}
+
+
+def test_solver_stats_batch(Sim):
+    runs = WL.batch_tubes(count=6, seed=4, nmin=50, nmax=120)
+    b = Sim.batch(runs, precision=1)
+    b.set_solver_stats(True)
+    b.step(0.0, 4)
+    b.check()
+    st = b.solver_stats()
+    cells = sum(r.nx for r in runs)
+    assert sum(st["fp64_passes"].values()) == 2 * 4 * cells, st
+
+
+@pytest.mark.parametrize("make", [lambda: WL.khi(n=16, seed=0), lambda: WL.tf_sheet(n=12, seed=1)],
+                         ids=["khi", "tf_sheet"])
+def test_refinement_cap_injects_a_solver_failure(Sim, make):
+    wl = make()
+    g = Sim.from_workload(wl)
+    g.set_refinement_cap(1)
+    with pytest.raises(RmhdError) as ei:
+        g.step(wl.dt, 1)
+        g.check()
+    # the report names the first failing cell of the grid
+    m = re.search(r"i=(\d+), j=(\d+)", str(ei.value))
+    assert ei.value.code == -3 and m, str(ei.value)
+    assert int(m.group(1)) < wl.nx and int(m.group(2)) < wl.ny
+    # the context stays usable and reproduces an undisturbed run
+    g.set_refinement_cap(0)
+    g.set_prims(wl.prims)
+    g.step(wl.dt, 2)
+    g.check()
+    ref = Sim.from_workload(wl)
+    ref.step(wl.dt, 2)
+    ref.check()
+    assert np.array_equal(g.cons(), ref.cons())
+    with pytest.raises(RmhdError) as ei:
+        g.set_refinement_cap(9)
+    assert ei.value.code == -1
