@@ -118,6 +118,20 @@ int rmhd_get_prims(rmhd_ctx *ctx, double *prims, int where);
 int rmhd_get_cons(rmhd_ctx *ctx, double *cons, int where);
 int rmhd_set_cons(rmhd_ctx *ctx, const double *cons, int where);
 
+/* Full-state checkpoint for bitwise restarts: the conserved state and the
+ * primitives the next stage solve starts from, [N_c + N_w][ny][nx] (N_w = 5,
+ * one fluid: v_x, v_y, v_z, p, W; N_w = 10, two fluids: v, p, rho h W^2 per
+ * species, electrons first). A context restored with rmhd_set_state (same
+ * configuration) continues bit for bit as the saved one would have;
+ * rmhd_set_cons restores the same conserved state but recovers fresh
+ * primitives, so a continued run agrees only to round-off. The simulation
+ * time is not part of the state. rmhd_state_doubles gives the array length.
+ * Synchronous. Errors: RMHD_ERR_INVALID, RMHD_ERR_STATE (get before any
+ * state), RMHD_ERR_CUDA. */
+int rmhd_state_doubles(const rmhd_ctx *ctx, size_t *n);
+int rmhd_get_state(rmhd_ctx *ctx, double *state, int where);
+int rmhd_set_state(rmhd_ctx *ctx, const double *state, int where);
+
 /* Advance `nsteps` SSP2(222) IMEX steps (Sec. 2.2.1, Table 1) with fluxes from
  * Lax-Friedrichs splitting + WENO3 (Sec. 2.2.2). dt <= 0 selects
  * dt = cfl * min(dx, dy). Async: enqueued on the context's stream. A failed

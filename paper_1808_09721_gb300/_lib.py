@@ -27,7 +27,8 @@ EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_err
            "rmhd_diagnostics", "rmhd_recording_bytes", "rmhd_record", "rmhd_adjoint_step",
            "rmhd_batch_workspace_bytes", "rmhd_create_batch", "rmhd_autotune",
            "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc", "rmhd_version",
-           "rmhd_set_solver_stats", "rmhd_solver_stats", "rmhd_set_refinement_cap")
+           "rmhd_set_solver_stats", "rmhd_solver_stats", "rmhd_set_refinement_cap",
+           "rmhd_state_doubles", "rmhd_get_state", "rmhd_set_state")
 
 
 class Config(C.Structure):
@@ -85,6 +86,9 @@ def load(path: str | None = None):
     L.rmhd_set_solver_stats.argtypes = [_P, C.c_int]
     L.rmhd_solver_stats.argtypes = [_P, C.POINTER(C.c_ulonglong)]
     L.rmhd_set_refinement_cap.argtypes = [_P, C.c_int]
+    L.rmhd_state_doubles.argtypes = [_P, C.POINTER(C.c_size_t)]
+    L.rmhd_get_state.argtypes = [_P, _P, C.c_int]
+    L.rmhd_set_state.argtypes = [_P, _P, C.c_int]
     L.rmhd_diagnostics_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, _P, _P]
     L.rmhd_version.restype = C.c_char_p
     _lib = L

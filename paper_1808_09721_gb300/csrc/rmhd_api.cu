@@ -435,6 +435,41 @@ int rmhd_set_cons(rmhd_ctx *c, const double *cons, int where) {
     return RMHD_OK;
 }
 
+int rmhd_state_doubles(const rmhd_ctx *c, size_t *n) {
+    if (!c || !n) return RMHD_ERR_INVALID;
+    *n = (size_t)(model_nc(c->cfg.model) + model_nw(c->cfg.model)) * (size_t)c->g.ncell;
+    return RMHD_OK;
+}
+
+int rmhd_get_state(rmhd_ctx *c, double *state, int where) {
+    if (!c || !state || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_state: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_state: no state (call rmhd_set_prims first)");
+    const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    CK(c, launch_unpack(c->g, nc, c->Q, c->stage_buf, c->stream));
+    int st = stage_out(c, state, nc, where);
+    if (st) return st;
+    CK(c, launch_unpack(c->g, nw, c->W, c->stage_buf, c->stream));
+    return stage_out(c, state + (size_t)nc * c->g.ncell, nw, where);
+}
+
+int rmhd_set_state(rmhd_ctx *c, const double *state, int where) {
+    if (!c || !state || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_state: bad argument");
+    const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    int st = stage_in(c, state, nc, where);
+    if (st) return st;
+    CK(c, launch_pack(c->g, nc, c->stage_buf, c->Q, c->stream));
+    st = stage_in(c, state + (size_t)nc * c->g.ncell, nw, where);  // same stream: after the pack above
+    if (st) return st;
+    CK(c, launch_pack(c->g, nw, c->stage_buf, c->W, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->has_state = true;
+    c->fresh_prims = false;
+    c->w_stale = true;  // W is a warm start; output calls recover the primitives of Q
+    c->recording = false;
+    c->rec_done = 0;
+    return RMHD_OK;
+}
+
 // Event bracket around one launch when profiling (no-op otherwise).
 static int tic(rmhd_ctx *c, int kind) {
     if (!c->profiling) return RMHD_OK;

@@ -110,6 +110,25 @@ class Sim:
         p, where, _keep = self._ptr(cons, self.nc, False)
         self._check(self.lib.rmhd_set_cons(self.h, p, where), "set_cons")
 
+    @property
+    def nw(self):
+        return 5 if self.model == L.RESISTIVE else 10
+
+    def get_state(self, out=None):
+        """Checkpoint for a bitwise restart: N_c + N_w planes (the conserved
+        state, then the primitives the next stage solve starts from)."""
+        if out is None:
+            out = np.empty((self.nc + self.nw,) + self.shape)
+        p, where, _keep = self._ptr(out, self.nc + self.nw, True)
+        self._check(self.lib.rmhd_get_state(self.h, p, where), "get_state")
+        return out
+
+    def set_state(self, state):
+        if isinstance(state, np.ndarray):
+            state = np.ascontiguousarray(state, dtype=np.float64)
+        p, where, _keep = self._ptr(state, self.nc + self.nw, False)
+        self._check(self.lib.rmhd_set_state(self.h, p, where), "set_state")
+
     def prims(self, out=None):
         if out is None:
             out = np.empty((self.np,) + self.shape)
