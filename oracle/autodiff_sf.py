@@ -328,3 +328,17 @@ def gradient(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, lam, kappa=1.0):
     J = (torch.tensor(lam, dtype=F64) * q).sum()
     gP, gs = torch.autograd.grad(J, (P, s))
     return float(J.detach()), gP.numpy(), float(gs), q.detach().numpy()
+
+
+def jvp(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, v_prims, v_sigma, kappa=1.0):
+    """Directional derivative of q^n along (v_prims, v_sigma): reverse mode
+    applied twice. g(u) = d<u, q^n>/d(prims, sigma) is linear in u, so the
+    derivative of <g(u), v> with respect to u is J v at any u."""
+    P = torch.tensor(prims, dtype=F64, requires_grad=True)
+    s = torch.tensor(float(sigma), dtype=F64, requires_grad=True)
+    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa)
+    u = torch.zeros_like(q, requires_grad=True)
+    gP, gs = torch.autograd.grad((u * q).sum(), (P, s), create_graph=True)
+    inner = (gP * torch.tensor(v_prims, dtype=F64)).sum() + gs * float(v_sigma)
+    (Jv,) = torch.autograd.grad(inner, u)
+    return Jv.numpy()

@@ -237,3 +237,30 @@ def test_adjoint_matches_autodiff_oracle(env, name, make, nsteps, ckpt):
     print(name, "entrywise relative error", err, "dJ/dsigma", gs, gso)
     assert err <= 1e-9, (name, err)
     assert abs(gs - gso) <= 1e-9 * abs(gso) + 1e-12 * np.abs(go).max(), (name, gs, gso)
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", TINY)
+def test_adjoint_dot_product(env, name, make, nsteps, ckpt):
+    """<J v, w> = <v, J^T w>: the GPU adjoint (reverse mode, J^T w for a random
+    w) against the differentiable oracle's forward-mode derivative J v (its
+    reverse mode applied twice) along a random direction v of the initial
+    primitives and sigma."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = make()
+    rng = np.random.default_rng(17)
+    w = rng.normal(size=(14,) + wl.prims.shape[1:])
+    vp = rng.normal(size=wl.prims.shape) * np.abs(wl.prims).reshape(11, -1).max(axis=1).clip(1e-2)[
+        (slice(None),) + (None,) * (wl.prims.ndim - 1)]
+    vs = 0.1 * wl.sigma
+    s = Sim.from_workload(wl)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(w))
+    Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs)
+    lhs = float((Jv * w).sum())
+    rhs = float((gp * vp).sum() + gs * vs)
+    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    print(name, "dot-product relative difference", rel)
+    assert rel <= 1e-12, (name, lhs, rhs, rel)

@@ -69,3 +69,25 @@ def test_gradient_matches_c_oracle_differences():
     d2 = (J(wl.prims, wl.sigma + h / 2) - J(wl.prims, wl.sigma - h / 2)) / h
     fs = (4 * d2 - d1) / 3
     assert abs(gs - fs) <= 1e-6 * abs(fs), (gs, fs)
+
+
+def test_jvp_matches_c_oracle_differences():
+    """The forward-mode derivative (reverse mode applied twice) along a random
+    direction of the primitives and sigma, against Richardson-extrapolated
+    central differences of the C oracle's final state."""
+    wl = WL.field_loop(n=6, nsteps=3)
+    nsteps = 3
+    rng = np.random.default_rng(7)
+    vp = rng.normal(size=wl.prims.shape) * np.abs(wl.prims).reshape(11, -1).max(axis=1).clip(1e-2)[:, None, None]
+    vs = 0.1 * wl.sigma
+    Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs)
+
+    def q(h):
+        return c_oracle(wl, wl.prims + h * vp, nsteps, wl.sigma + h * vs)
+    # h = 1e-6: the field loop's near-constant fields make the WENO3 weights
+    # vary fast (1e-5 leaves a 3e-6 truncation error); 1e-7 reaches round-off
+    h = 1e-6
+    d1 = (q(h) - q(-h)) / (2 * h)
+    d2 = (q(h / 2) - q(-h / 2)) / h
+    fd = (4 * d2 - d1) / 3
+    assert np.abs(Jv - fd).max() <= 1e-7 * np.abs(fd).max(), np.abs(Jv - fd).max() / np.abs(fd).max()
