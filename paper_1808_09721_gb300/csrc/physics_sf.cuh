@@ -16,8 +16,9 @@
 //      (one FP64 Newton step of the pressure root per pass, started from a
 //      first-order prediction) and correct E with the FP32 inverse Jacobian.
 //      Each pass gains ~6-7 digits. The first evaluation point (from the
-//      second on) where |G| is at round-off of the magnitude of G's terms is
-//      returned with its own primitives, so E and v are consistent.
+//      second on) where |G| is at round-off of the magnitude of G's terms
+//      (relative 1e-12, tighter in stiff cells) is returned with its own
+//      primitives, so E and v are consistent.
 #pragma once
 #include "device_math.cuh"
 
@@ -283,6 +284,12 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     // NREF-th) is the result, with its own primitives (J amplifies any E/v
     // mismatch by sigma). Cells that need it take extra passes (up to 8).
     const float gs = resid_scale(E, rEf, v, Bf, W, rhoef, adtf, sigf);  // round-off scale of G
+    // Acceptance |G| <= tol gs. The explicit stages evaluate J = sigma W (E + v x B
+    // - (v.E) v) at the accepted E, which multiplies an E error by ~sigma dt W,
+    // while G's own terms carry a dt sigma W: for stiff cells (a dt sigma W >> 1)
+    // the tolerance shrinks by that factor, down to a few units of FP64
+    // round-off of G's terms. Non-stiff cells keep 1e-12.
+    const double tolg = f64_of(fmaxf(1e-12f / (1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
     // FP64 inputs, read again (the stores above keep the compiler from reusing
     // the first loads' registers)
     const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
@@ -300,7 +307,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
         pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
         gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
-        if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
+        if (pass >= NREF - 1 && gres <= tolg) break;
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];

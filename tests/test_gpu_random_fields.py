@@ -77,3 +77,42 @@ def test_random_fields_mixed(Sim, name, shape, model, bc):
     mu_ref = 1e3 if model == 1 else 1.0
     l1 = np.abs(got - want).reshape(got.shape[0], -1).mean(axis=1) / parity_scale(model, want, mu_ref)
     assert np.all(l1 <= 1e-4), (name, l1)
+
+
+@pytest.mark.parametrize("name,shape,model,sigma", [
+    ("1d_weakly_coupled", (70,), 0, 1e-2), ("2d_weakly_coupled", (33, 45), 0, 1e-2),
+    ("1d_very_stiff", (70,), 0, 1e7), ("2d_very_stiff", (33, 45), 0, 1e7),
+    ("3d_very_stiff", (8, 10, 12), 0, 1e7), ("tf_2d_very_stiff", (24, 40), 1, 1e7),
+], ids=lambda x: x if isinstance(x, str) else None)
+def test_random_fields_conductivity_limits(Sim, name, shape, model, sigma):
+    """The weakly coupled (sigma dt << 1: Maxwell nearly decoupled from the
+    fluid) and very stiff (sigma dt >> 1: near the ideal limit, where the
+    explicit stages' J = sigma W (E + v x B - ...) multiplies any error of the
+    stage's E by ~sigma dt) regimes of the implicit stage, with every field
+    component of order one. (Two fluids at sigma <= 1 with these O(1) species
+    currents are left out: there the oracle's stage solve finds no root either.)"""
+    wl = WL.random_smooth(shape, seed=21, model=model, sigma=sigma)
+    got, want = run_pair(Sim, wl, 3)
+    err = parity_errors(model, got, want, 1e3 if model == 1 else 1.0)
+    assert np.all(err <= TOL), (name, sigma, err)
+
+
+@pytest.mark.parametrize("name,model,shape", [("sf_2d", 0, (12, 40)), ("sf_3d", 0, (6, 8, 40)),
+                                              ("tf_2d", 1, (12, 40))])
+def test_uniform_state_stays_uniform(Sim, name, model, shape):
+    """Degenerate case: a uniform state (ideal E = -v x B, no current) on a
+    periodic grid stays uniform -- every cell bit for bit equal to every other,
+    the same arithmetic in every tile and at every tile edge -- and equal to
+    the oracle's."""
+    wl = WL.random_smooth(shape, seed=23, model=model)
+    p = wl.prims.reshape(wl.prims.shape[0], -1)
+    p[:] = p[:, [137]]  # the primitives of one cell everywhere
+    nv = 14 if model == 0 else 18
+    if model == 0:
+        v, B = p[1:4, 0], p[5:8, 0]
+        p[8:11] = -np.cross(v, B)[:, None]
+    got, want = run_pair(Sim, wl, 4)
+    assert np.all(got == got[:, :1, :]), name  # bitwise uniform
+    err = parity_errors(model, got, want, 1e3 if model == 1 else 1.0)
+    assert np.all(err <= TOL), (name, err)
+    assert got.shape[0] == nv
