@@ -71,7 +71,7 @@ typedef struct rmhd_config {
     double sigma;     /* conductivity (one fluid, Ohm's law of Sec. 2.1.1); eta = 1/sigma for two fluids */
     double mu_e, mu_p;/* charge-to-mass ratios (two fluids only), mu_e != mu_p */
     double kappa;     /* divergence-cleaning rate, 1 in the paper (Sec. 2.1.1) */
-    double cfl;       /* dt = cfl * min(dx, dy) when rmhd_imex_step gets dt <= 0 */
+    double cfl;       /* dt = cfl * min(dx, dy, dz) when rmhd_imex_step gets dt <= 0 */
     int bc_x, bc_y;   /* RMHD_OUTFLOW or RMHD_PERIODIC */
     int precision;    /* RMHD_FP64 or RMHD_MIXED */
     int scheme;       /* RMHD_SSP2 (0, Table 1) or RMHD_SSP3 (1, Table 2); batches: RMHD_SSP2 */
@@ -84,7 +84,9 @@ typedef struct rmhd_config {
 typedef struct rmhd_ctx rmhd_ctx;
 
 /* Bytes of device workspace a context with this configuration needs.
- * Errors: RMHD_ERR_INVALID for a bad configuration. */
+ * Errors: RMHD_ERR_INVALID for a bad configuration: any field out of range,
+ * nx*ny*nz above 2^31 - 1 cells, or above the flux kernel's launch grid
+ * (ny > 524280 in 2-D; nz or ny > 65535 in 3-D). */
 int rmhd_workspace_bytes(const rmhd_config *cfg, size_t *bytes);
 
 /* Create a context on the device of `cuda_stream` (a cudaStream_t; NULL means

@@ -119,10 +119,16 @@ static int validate(const rmhd_config *cfg) {
     if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED) return RMHD_ERR_INVALID;
     if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
     if (cfg->nz < 0) return RMHD_ERR_INVALID;
+    // launch limits of the flux kernel's grid: tiles of 8 rows along y in
+    // gridDim.y; in 3-D the z planes (x-y pass) and the y rows (z pass) in
+    // gridDim.z, z in tiles of 8 rows in gridDim.y
+    constexpr int kMaxGridYZ = 65535;
+    if (cfg->ny > 1 && (cfg->ny + 7) / 8 > kMaxGridYZ) return RMHD_ERR_INVALID;
     if (cfg->nz > 1) {
         if (cfg->ny < 2 || !(cfg->zlen > 0.0)) return RMHD_ERR_INVALID;
         if (cfg->bc_z != RMHD_OUTFLOW && cfg->bc_z != RMHD_PERIODIC) return RMHD_ERR_INVALID;
         if ((long long)cfg->nx * cfg->ny * cfg->nz > (1LL << 31) - 1) return RMHD_ERR_INVALID;
+        if (cfg->nz > kMaxGridYZ || cfg->ny > kMaxGridYZ) return RMHD_ERR_INVALID;
     }
     return RMHD_OK;
 }

@@ -52,8 +52,9 @@ def test_workspace_bytes_and_validation(lib):
     assert n.value >= (4 * 14 + 2 * 5) * plane and n.value % 256 == 0
     n2 = C.c_size_t()
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(model=1)), C.byref(n2)) == 0 and n2.value > n.value
-    for bad in (dict(model=7), dict(nx=0), dict(gamma=2.5), dict(gamma=1.0), dict(sigma=0.0), dict(bc_x=3),
-                dict(precision=2), dict(model=1, mu_e=1.0, mu_p=1.0), dict(xmax=-1.0)):
+    for bad in (dict(model=7), dict(nx=0), dict(ny=0), dict(gamma=2.5), dict(gamma=1.0), dict(sigma=0.0), dict(bc_x=3),
+                dict(precision=2), dict(model=1, mu_e=1.0, mu_p=1.0), dict(xmax=-1.0),
+                dict(nx=1, ny=600000)):  # more rows than the flux kernel's grid can hold
         assert lib.rmhd_workspace_bytes(C.byref(_cfg(**bad)), C.byref(n)) == -1, bad
 
 
@@ -103,7 +104,8 @@ def test_3d_configuration(lib):
     n4 = C.c_size_t()
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(nz=4, zlen=1.0, model=1)), C.byref(n4)) == 0
     for bad in (dict(nz=4, zlen=0.0), dict(nz=4, zlen=1.0, ny=1),
-                dict(nz=4, zlen=1.0, bc_z=5), dict(nz=-2)):
+                dict(nz=4, zlen=1.0, bc_z=5), dict(nz=-2),
+                dict(nz=70000, zlen=1.0, ny=2, nx=2), dict(nz=2, zlen=1.0, ny=70000, nx=2)):
         assert lib.rmhd_workspace_bytes(C.byref(_cfg(**bad)), C.byref(n3)) == -1, bad
     nx = (C.c_int * 2)(100, 200)
     assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1, nz=3, zlen=1.0)), 2, nx, C.byref(n3)) == -1
