@@ -134,9 +134,12 @@ int rmhd_state_doubles(const rmhd_ctx *ctx, size_t *n);
 int rmhd_get_state(rmhd_ctx *ctx, double *state, int where);
 int rmhd_set_state(rmhd_ctx *ctx, const double *state, int where);
 
-/* Advance `nsteps` SSP2(222) IMEX steps (Sec. 2.2.1, Table 1) with fluxes from
- * Lax-Friedrichs splitting + WENO3 (Sec. 2.2.2). dt <= 0 selects
- * dt = cfl * min(dx, dy). Async: enqueued on the context's stream. A failed
+/* Advance `nsteps` IMEX steps of the configured scheme (SSP2(222), Table 1,
+ * or SSP3(332), Table 2; Sec. 2.2.1) with fluxes from Lax-Friedrichs
+ * splitting + WENO3 (Sec. 2.2.2). dt <= 0 selects dt = cfl * min(dx, dy, dz)
+ * over the grid's directions (batches: each run's own cfl * dx). Steps of one
+ * dt are replayed from one captured CUDA graph. Async: enqueued on the
+ * context's stream. A failed
  * implicit solve or recovery is recorded on the device and reported by the
  * next synchronous call (or rmhd_check). If t_out is not NULL it receives the
  * simulation time after the steps (host bookkeeping, no synchronisation). */
