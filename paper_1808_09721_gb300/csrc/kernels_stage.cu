@@ -115,13 +115,18 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
 // user primitives are dense [np][nz][ny][nx]; the state uses padded planes.
 __global__ void k_set_prims_sf(Grid g, Phys ph, const double *U, double *q, double *w, int *status) {
     using namespace sf;
-    const long long n = g.ncell, nxy = (long long)g.nx * g.ny;
+    // cell counts are below 2^31 (validated), so 32-bit index arithmetic
+    const long long n = g.ncell;
+    const unsigned nxy = (unsigned)g.nx * (unsigned)g.ny;
+    const double r2x = 2.0 * g.rdx4, r2y = 2.0 * g.rdy4, r2z = 2.0 * g.rdz4;  // 1 / (2 dx) ...
+    const double hfac = ph.gamma / (ph.gamma - 1.0);
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(cell / nxy);
-        const long long c2 = cell - kz * nxy;  // index within the x-y plane
-        int j = (int)(c2 / g.nx), i = (int)(c2 - (long long)j * g.nx);
-        const long long pz = kz * nxy;         // first cell of the plane
+        const unsigned c32 = (unsigned)cell;
+        const int kz = (int)(c32 / nxy);
+        const unsigned c2 = c32 - (unsigned)kz * nxy;  // index within the x-y plane
+        const int j = (int)(c2 / (unsigned)g.nx), i = (int)(c2 - (unsigned)j * (unsigned)g.nx);
+        const long long pz = (long long)kz * nxy;      // first cell of the plane
         double rho = U[0 * n + cell], v[3] = {U[1 * n + cell], U[2 * n + cell], U[3 * n + cell]}, p = U[4 * n + cell];
         double B[3] = {U[5 * n + cell], U[6 * n + cell], U[7 * n + cell]};
         double E[3] = {U[8 * n + cell], U[9 * n + cell], U[10 * n + cell]};
@@ -130,17 +135,17 @@ __global__ void k_set_prims_sf(Grid g, Phys ph, const double *U, double *q, doub
         if (!ok) { record(status, -1, cell); continue; }
         // Gauss's law varrho = div E, central differences with the boundary map
         int il = wrap(i - 1, g.nx, g.bcx), ir = wrap(i + 1, g.nx, g.bcx);
-        double divE = (U[8 * n + pz + (long long)j * g.nx + ir] - U[8 * n + pz + (long long)j * g.nx + il]) / (2.0 * g.dx);
+        double divE = (U[8 * n + pz + (long long)j * g.nx + ir] - U[8 * n + pz + (long long)j * g.nx + il]) * r2x;
         if (g.ny > 1) {
             int jl = wrap(j - 1, g.ny, g.bcy), jr = wrap(j + 1, g.ny, g.bcy);
-            divE += (U[9 * n + pz + (long long)jr * g.nx + i] - U[9 * n + pz + (long long)jl * g.nx + i]) / (2.0 * g.dy);
+            divE += (U[9 * n + pz + (long long)jr * g.nx + i] - U[9 * n + pz + (long long)jl * g.nx + i]) * r2y;
         }
         if (g.nz > 1) {
             int kl = wrap(kz - 1, g.nz, g.bcz), kr = wrap(kz + 1, g.nz, g.bcz);
-            divE += (U[10 * n + kr * nxy + c2] - U[10 * n + kl * nxy + c2]) / (2.0 * g.dz);
+            divE += (U[10 * n + (long long)kr * nxy + c2] - U[10 * n + (long long)kl * nxy + c2]) * r2z;
         }
-        double W = 1.0 / sqrt(1.0 - v2);
-        double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
+        double W = s_rsqrt(1.0 - v2);
+        double h = fma(hfac * p, s_rcp(rho), 1.0);
         double Z = rho * h * W * W;
         double ExB[3];
         cross(E, B, ExB);
@@ -180,8 +185,8 @@ __global__ void k_set_prims_tf(Grid g, Phys ph, const double *U, double *q, doub
             double v[3] = {U[(5 * s + 1) * n + cell], U[(5 * s + 2) * n + cell], U[(5 * s + 3) * n + cell]};
             double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
             ok = ok && rho > 0.0 && p > 0.0 && v2 < 1.0 && isfinite(rho + p + v2);
-            double W = 1.0 / sqrt(1.0 - v2);
-            double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
+            double W = s_rsqrt(1.0 - v2);  // inadmissible states are flagged by ok
+            double h = fma(ph.gamma / (ph.gamma - 1.0) * p, s_rcp(rho), 1.0);
             double Z = rho * h * W * W;
             qc[D] += rho * W;
             qc[DB] += mu[s] * rho * W;
@@ -224,9 +229,9 @@ __global__ void k_set_prims_batch_sf(Grid g, Phys ph, BatchArgs b, const double 
         bool ok = rho > 0.0 && p > 0.0 && v2 < 1.0 && isfinite(rho + p + v2 + B[0] + B[1] + B[2] + E[0] + E[1] + E[2]);
         if (!ok) { record(status, -1, cell); continue; }
         int il = wrap(i - 1, nx, g.bcx), ir = wrap(i + 1, nx, g.bcx);
-        double divE = (U[8 * n + o + ir] - U[8 * n + o + il]) / (2.0 * b.dx[run]);
-        double W = 1.0 / sqrt(1.0 - v2);
-        double h = 1.0 + ph.gamma * p / (rho * (ph.gamma - 1.0));
+        double divE = (U[8 * n + o + ir] - U[8 * n + o + il]) * (2.0 * b.rdx4[run]);
+        double W = s_rsqrt(1.0 - v2);  // inadmissible states are flagged by ok
+        double h = fma(ph.gamma / (ph.gamma - 1.0) * p, s_rcp(rho), 1.0);
         double Z = rho * h * W * W;
         double ExB[3];
         cross(E, B, ExB);
@@ -273,7 +278,7 @@ __global__ void k_get_prims_sf(Grid g, const double *q, const double *w, double 
     const long long n = g.ncell;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
-        U[0 * n + cell] = q[D * g.plane + cell] / w[LOR * g.plane + cell];
+        U[0 * n + cell] = q[D * g.plane + cell] * s_rcp(w[LOR * g.plane + cell]);
         U[1 * n + cell] = w[VX * g.plane + cell];
         U[2 * n + cell] = w[VY * g.plane + cell];
         U[3 * n + cell] = w[VZ * g.plane + cell];
@@ -288,11 +293,11 @@ __global__ void k_get_prims_tf(Grid g, Phys ph, const double *q, const double *w
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
         double Dt = q[D * g.plane + cell], Db = q[DB * g.plane + cell];
-        double Ds[2] = {(Db - ph.mu_p * Dt) / (ph.mu_e - ph.mu_p), (ph.mu_e * Dt - Db) / (ph.mu_e - ph.mu_p)};
+        double Ds[2] = {(Db - ph.mu_p * Dt) * ph.inv_dmu, (ph.mu_e * Dt - Db) * ph.inv_dmu};
         for (int s = 0; s < 2; ++s) {
             double v[3] = {w[(5 * s) * g.plane + cell], w[(5 * s + 1) * g.plane + cell], w[(5 * s + 2) * g.plane + cell]};
-            double W = 1.0 / sqrt(1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
-            U[(5 * s) * n + cell] = Ds[s] / W;
+            const double om = 1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            U[(5 * s) * n + cell] = Ds[s] * (om * s_rsqrt(om));  // rho_s = D_s / W_s
             for (int k = 0; k < 3; ++k) U[(5 * s + 1 + k) * n + cell] = v[k];
             U[(5 * s + 4) * n + cell] = w[(5 * s + P) * g.plane + cell];
         }
