@@ -412,41 +412,43 @@ def main():
     adjoint = None
     if args.adjoint:
         fl = WL.field_loop(n=256, seed=3, nsteps=50)
-        fs = Sim.from_workload(fl, device=f"cuda:{local}")
-        fs.step(fl.dt, 3)
-        fs.set_prims(fl.prims)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        fs.step(fl.dt, 50)
-        fs.check()
-        torch.cuda.synchronize()
-        t_fwd = time.perf_counter() - t0
-        fs.set_prims(fl.prims)
-        fs.record(50, 10)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        fs.step(fl.dt, 50)
-        fs.check()
-        torch.cuda.synchronize()
-        t_rec = time.perf_counter() - t0
-        qN = fs.cons()
-        dv = fl.dx * fl.dy
-        lam = np.zeros_like(qN)
-        lam[5] = 2.0 * qN[5] * dv
-        lam[6] = 2.0 * qN[6] * dv
-        lam[7] = 4.0 * qN[7] * dv
-        fs.adjoint(lam)  # warm-up (kernel set-up)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        gp, gsig = fs.adjoint(lam)
-        torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
-        adjoint = {"fwd_s": t_fwd, "recorded_fwd_s": t_rec, "adjoint_s": t_adj,
-                   "adjoint_over_fwd": t_adj / t_fwd, "total_over_fwd": (t_rec + t_adj) / t_fwd,
-                   "dJ_dsigma": gsig, "sigma": fl.sigma,
-                   "workload": "field loop 256x256 periodic, 50 SSP2(222) steps FP64, checkpoints every 10, "
-                               "J = sum(Bx^2 + By^2 + 2 Bz^2) dV"}
-        del fs
+
+        def adjoint_cost(scheme):
+            fs = Sim.from_workload(fl, device=f"cuda:{local}", scheme=scheme)
+            fs.step(fl.dt, 3)
+            fs.set_prims(fl.prims)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fs.step(fl.dt, 50)
+            fs.check()
+            torch.cuda.synchronize()
+            t_fwd = time.perf_counter() - t0
+            fs.set_prims(fl.prims)
+            fs.record(50, 10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fs.step(fl.dt, 50)
+            fs.check()
+            torch.cuda.synchronize()
+            t_rec = time.perf_counter() - t0
+            qN = fs.cons()
+            dv = fl.dx * fl.dy
+            lam = np.zeros_like(qN)
+            lam[5] = 2.0 * qN[5] * dv
+            lam[6] = 2.0 * qN[6] * dv
+            lam[7] = 4.0 * qN[7] * dv
+            fs.adjoint(lam)  # warm-up (kernel set-up)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gp, gsig = fs.adjoint(lam)
+            torch.cuda.synchronize()
+            t_adj = time.perf_counter() - t0
+            return {"fwd_s": t_fwd, "recorded_fwd_s": t_rec, "adjoint_s": t_adj,
+                    "adjoint_over_fwd": t_adj / t_fwd, "total_over_fwd": (t_rec + t_adj) / t_fwd, "dJ_dsigma": gsig}
+        adjoint = adjoint_cost(0)
+        adjoint.update({"sigma": fl.sigma, "ssp3": adjoint_cost(1),
+                        "workload": "field loop 256x256 periodic, 50 SSP2(222) steps FP64 (and SSP3(332) in "
+                                    "'ssp3'), checkpoints every 10, J = sum(Bx^2 + By^2 + 2 Bz^2) dV"})
 
     # e2e through the C ABI with host buffers: upload prims, one step, read prims back
     pin = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)

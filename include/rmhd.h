@@ -177,8 +177,9 @@ int rmhd_set_refinement_cap(rmhd_ctx *ctx, int passes);
  * directions. Synchronous. */
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
-/* Discrete adjoint of the SSP2(222) step (single fluid, FP64, single grid with
- * at least 3 cells per direction): gradients of a functional of the final
+/* Discrete adjoint of the IMEX step, SSP2(222) or SSP3(332) (single fluid,
+ * FP64, 1-D or 2-D single grid with at least 3 cells per direction): gradients
+ * of a functional of the final
  * conserved state with respect to the initial primitives and sigma.
  *   rmhd_record arms recording of the next `nsteps` steps; it must follow
  *   rmhd_set_prims directly (the gradient is w.r.t. those primitives, with

@@ -28,8 +28,9 @@ Wright & Hawke, arXiv:1808.09721, in plain tensor operations over all cells:
     gamma = 1 - 1/sqrt(2):
       q1 = q^n + gamma dt Psi(q1),
       q2 = q^n + dt L(q1) + dt [(1 - 2 gamma) Psi(q1) + gamma Psi(q2)],
-      q^{n+1} = q^n + dt/2 [L(q1) + L(q2)] + dt/2 [Psi(q1) + Psi(q2)].
-    Each implicit stage: components without a source equal r; psi, phi in
+      q^{n+1} = q^n + dt/2 [L(q1) + L(q2)] + dt/2 [Psi(q1) + Psi(q2)];
+    and Table 2, SSP3(332) (ssp3_step: three implicit stages, weights 1/6,
+    1/6, 2/3). Each implicit stage: components without a source equal r; psi, phi in
     closed form; E solves G(E) = E - r_E + a dt J(q(E)) = 0.
   - Boundary conditions: two ghost cells per side, outflow (copy the nearest
     interior cell) or periodic (wrap).
@@ -312,31 +313,50 @@ def ssp2_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy):
     return q + 0.5 * dt * (L1 + L2) + 0.5 * dt * (P1 + P2)
 
 
-def run(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa=1.0):
-    """prims (11, ny, nx) and sigma (0-d) as tensors (may require grad) -> q^n."""
+# ---- Table 2: one SSP3(332) step --------------------------------------------
+def ssp3_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy):
+    """Implicit rows (g, 0, 0), (1 - 2g, g, 0), (1/2 - g, 0, g); explicit rows
+    (0, 0, 0), (1, 0, 0), (1/4, 1/4, 0); weights (1/6, 1/6, 2/3) for both parts."""
+    g = GAMMA_SSP2
+    q1, w1 = stage(q, g * dt, sigma, gamma, kappa)
+    L1 = divergence(q1, *w1, sigma, bcx, bcy, dx, dy)
+    P1 = source(q1, w1[0], w1[2], sigma, kappa)
+    q2, w2 = stage(q + dt * L1 + (1.0 - 2.0 * g) * dt * P1, g * dt, sigma, gamma, kappa)
+    L2 = divergence(q2, *w2, sigma, bcx, bcy, dx, dy)
+    P2 = source(q2, w2[0], w2[2], sigma, kappa)
+    q3, w3 = stage(q + 0.25 * dt * (L1 + L2) + (0.5 - g) * dt * P1, g * dt, sigma, gamma, kappa)
+    L3 = divergence(q3, *w3, sigma, bcx, bcy, dx, dy)
+    P3 = source(q3, w3[0], w3[2], sigma, kappa)
+    return q + dt / 6.0 * (L1 + P1) + dt / 6.0 * (L2 + P2) + 2.0 * dt / 3.0 * (L3 + P3)
+
+
+def run(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa=1.0, scheme=0):
+    """prims (11, ny, nx) and sigma (0-d) as tensors (may require grad) -> q^n;
+    scheme 0: SSP2(222), 1: SSP3(332)."""
+    step = ssp3_step if scheme == 1 else ssp2_step
     q = prims_to_cons(prims, gamma, bcx, bcy, dx, dy)
     for _ in range(nsteps):
-        q = ssp2_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy)
+        q = step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy)
     return q
 
 
-def gradient(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, lam, kappa=1.0):
+def gradient(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, lam, kappa=1.0, scheme=0):
     """J = sum(lam * q^n): returns (J, dJ/dprims, dJ/dsigma) as NumPy/float."""
     P = torch.tensor(prims, dtype=F64, requires_grad=True)
     s = torch.tensor(float(sigma), dtype=F64, requires_grad=True)
-    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa)
+    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme)
     J = (torch.tensor(lam, dtype=F64) * q).sum()
     gP, gs = torch.autograd.grad(J, (P, s))
     return float(J.detach()), gP.numpy(), float(gs), q.detach().numpy()
 
 
-def jvp(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, v_prims, v_sigma, kappa=1.0):
+def jvp(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, v_prims, v_sigma, kappa=1.0, scheme=0):
     """Directional derivative of q^n along (v_prims, v_sigma): reverse mode
     applied twice. g(u) = d<u, q^n>/d(prims, sigma) is linear in u, so the
     derivative of <g(u), v> with respect to u is J v at any u."""
     P = torch.tensor(prims, dtype=F64, requires_grad=True)
     s = torch.tensor(float(sigma), dtype=F64, requires_grad=True)
-    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa)
+    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme)
     u = torch.zeros_like(q, requires_grad=True)
     gP, gs = torch.autograd.grad((u * q).sum(), (P, s), create_graph=True)
     inner = (gP * torch.tensor(v_prims, dtype=F64)).sum() + gs * float(v_sigma)

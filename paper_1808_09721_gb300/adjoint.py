@@ -1,6 +1,6 @@
-"""Gradients through SSP2(222) IMEX runs as a torch.autograd.Function.
+"""Gradients through SSP2(222) or SSP3(332) IMEX runs as a torch.autograd.Function.
 
-`ImexSteps.apply(prims0, sigma, workload, nsteps, ckpt_every)` advances the
+`ImexSteps.apply(prims0, sigma, workload, nsteps, ckpt_every, scheme)` advances the
 resistive model from the primitives `prims0` ([11][ny][nx] float64 CUDA
 tensor) with conductivity `sigma` (0-d float64 tensor) and returns the final
 conserved state [14][ny][nx]. Its backward runs the library's discrete
@@ -20,10 +20,10 @@ from .sim import Sim
 
 class ImexSteps(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, prims0, sigma, workload, nsteps: int, ckpt_every: int = 10):
+    def forward(ctx, prims0, sigma, workload, nsteps: int, ckpt_every: int = 10, scheme: int = 0):
         wl = dataclasses.replace(workload, sigma=float(sigma))
         sim = Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, wl.cfl,
-                  wl.mu_e, wl.mu_p, wl.kappa, device=prims0.device)
+                  wl.mu_e, wl.mu_p, wl.kappa, device=prims0.device, scheme=scheme)
         sim.set_prims(prims0.detach().contiguous())
         sim.record(nsteps, ckpt_every)
         sim.step(wl.dt, nsteps)
@@ -38,4 +38,4 @@ class ImexSteps(torch.autograd.Function):
         sim = ctx.sim
         gp = torch.empty((11, sim.ny, sim.nx), dtype=torch.float64, device=grad_out.device)
         _, gs = sim.adjoint(grad_out.contiguous(), out=gp)
-        return gp, torch.tensor(gs, dtype=torch.float64, device=grad_out.device), None, None, None
+        return gp, torch.tensor(gs, dtype=torch.float64, device=grad_out.device), None, None, None, None

@@ -2,13 +2,22 @@
 // fluid, FP64) of Wright & Hawke, arXiv:1808.09721 (Sec. 2.2.1, Table 1;
 // Sec. 2.2.2 fluxes; Sec. 2.1.1 model).
 //
-// Reverse of one step, with lambda the adjoint of q^{n+1}, (q_i, w_i) the
-// stored stage states and g = 1 - 1/sqrt(2):
+// Reverse of one SSP2(222) step, with lambda the adjoint of q^{n+1}, (q_i, w_i)
+// the stored stage states and g = 1 - 1/sqrt(2):
 //   lambda_q2 = (dL/dq)^T (dt/2 lambda) + (dPsi/dq)^T (dt/2 lambda)    at q2
 //   lambda_r2 = (I - g dt dPsi/dq)^{-T} lambda_q2                       at q2
 //   lambda_q1 = (dL/dq)^T (dt lambda_r2 + dt/2 lambda)
 //             + (dPsi/dq)^T ((1 - 2g) dt lambda_r2 + dt/2 lambda)       at q1
 //   lambda^n  = (I - g dt dPsi/dq)^{-T} lambda_q1 + lambda_r2 + lambda  at q1
+// SSP3(332) (Table 2: R = q^n + dt L1 + (1 - 2g) dt Psi1, R3 = q^n + dt/4 (L1 +
+// L2) + (1/2 - g) dt Psi1, q^{n+1} = q^n + dt/6 (L1 + Psi1 + L2 + Psi2) + 2 dt/3
+// (L3 + Psi3)) reverses the same way, stage 3 first:
+//   lambda_R3 = S3^T [(dL/dq)^T + (dPsi/dq)^T] (2 dt/3 lambda)              at q3
+//   lambda_R  = S2^T [(dL/dq)^T (dt/6 lambda + dt/4 lambda_R3) + (dPsi/dq)^T (dt/6 lambda)]   at q2
+//   lambda^n  = S1^T [(dL/dq)^T (dt/6 lambda + dt/4 lambda_R3 + dt lambda_R)
+//             + (dPsi/dq)^T (dt/6 lambda + (1/2 - g) dt lambda_R3 + (1 - 2g) dt lambda_R)]
+//             + lambda_R + lambda_R3 + lambda                               at q1
+// with S_i^T = (I - g dt dPsi/dq)^{-T} at q_i.
 // The stage solves are differentiated by the implicit-function theorem, the
 // primitive recovery inside every map likewise (adjoint_sf.cuh). The flux
 // divergence is transposed face by face: each face's WENO3/LF value depends on
@@ -33,6 +42,18 @@ __device__ __forceinline__ int amap(int i, int n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// A weighted sum of up to three adjoint fields: sum a[k] p[k][i] (null p[k] skipped).
+struct Lin {
+    const double *p[3];
+    double a[3];
+    __device__ __forceinline__ double at(long long i) const {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k)
+            if (p[k]) s += a[k] * p[k][i];
+        return s;
+    }
+};
+
 // Physical fluxes f_x, f_y (14 each) of every cell of a stage state.
 __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, double *fx, double *fy) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
@@ -54,9 +75,8 @@ __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, do
 // faces k = -1 .. n-1 along dir (the face after cell k) for every line.
 // Consecutive threads take neighbouring faces along x (dir 0) or neighbouring
 // lines (dir 1), so a warp's loads and atomics fall on consecutive cells of
-// one variable plane. lambda_L of a cell = aL * LA + bL * LB (LB may be null).
-__global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, const double *LA, double aL,
-                           const double *LB, double bL, double *fbar, double *qbar) {
+// one variable plane. lamL_ = the adjoint of L (a weighted sum of adjoint fields).
+__global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, Lin lamL_, double *fbar, double *qbar) {
     const int n = dir == 0 ? g.nx : g.ny, m = dir == 0 ? g.ny : g.nx, bc = dir == 0 ? g.bcx : g.bcy;
     const double h4 = dir == 0 ? g.rdx4 : g.rdy4;
     const long long nf = (long long)(n + 1) * m * sf::NC;
@@ -78,11 +98,7 @@ __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, co
             int im = amap(i, n, bc);
             return dir == 0 ? (long long)line * g.nx + im : (long long)im * g.nx + line;
         };
-        auto lamL = [&](long long cc) -> double {
-            double l = aL * LA[c * g.plane + cc];
-            if (LB) l += bL * LB[c * g.plane + cc];
-            return l;
-        };
+        auto lamL = [&](long long cc) -> double { return lamL_.at(c * g.plane + cc); };
         // 4F at this face enters L of cell k (- 1/(4h)) and of cell k+1 (+ 1/(4h)), real cells only
         double Fb = 0.0;
         if (k >= 0) Fb -= h4 * lamL(cell(k));
@@ -139,10 +155,10 @@ __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, co
 }
 
 // Per cell: lambda_q = qbar (direct, from the splitting) + cell_vjp(fbar_x, fbar_y, sbar),
-// sbar = aP * LA[src] + bP * LB[src]. Adds the sigma adjoint into sig[cell].
+// sbar = the adjoint of Psi (a weighted sum of adjoint fields) at the source
+// components. Adds the sigma adjoint into sig[cell].
 __global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, const double *fbx, const double *fby,
-                           const double *qbd, const double *LA, double aP, const double *LB, double bP,
-                           double *lamq, double *sig) {
+                           const double *qbd, Lin psib, double *lamq, double *sig) {
     const int src[5] = {sf::EX, sf::EY, sf::EZ, sf::PSI, sf::PHI};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
@@ -153,11 +169,7 @@ __global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, co
             fb[0][v] = fbx[v * g.plane + c];
             fb[1][v] = g.ny > 1 ? fby[v * g.plane + c] : 0.0;
         }
-        for (int k = 0; k < 5; ++k) {
-            double s = aP * LA[src[k] * g.plane + c];
-            if (LB) s += bP * LB[src[k] * g.plane + c];
-            sb[k] = s;
-        }
+        for (int k = 0; k < 5; ++k) sb[k] = psib.at(src[k] * g.plane + c);
         double sigb = 0.0;
         sf::cell_vjp(qc, w[sf::P * g.plane + c], ph.gamma, ph.sigma, ph.kappa, g.ny > 1 ? 2 : 1, fb, sb, qb, &sigb);
         for (int v = 0; v < sf::NC; ++v) lamq[v * g.plane + c] = qb[v];
@@ -168,9 +180,10 @@ __global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, co
 // Implicit-stage adjoint at the stage state q: mu = (I - adt dPsi/dq)^{-T} lambda.
 // Psi has nonzero rows only for (E, psi, phi): the E block (3x3) is solved
 // exactly, psi and phi scale by 1/(1 + adt kappa), the other components are
-// mu_n = lambda_n + adt [(dPsi/dq)^T mu_src]_n. out = mu (+ P1 + P2 if given).
+// mu_n = lambda_n + adt [(dPsi/dq)^T mu_src]_n. out = mu + the fields of add
+// (weights 1; null entries skipped).
 __global__ void k_stage_adj(Grid g, Phys ph, double adt, const double *q, const double *w, const double *lam,
-                            const double *P1, const double *P2, double *out, double *sig) {
+                            Lin add, double *out, double *sig) {
     const double nofb[2][sf::NC] = {};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
@@ -211,12 +224,7 @@ __global__ void k_stage_adj(Grid g, Phys ph, double adt, const double *q, const 
         o[sf::EZ] = mu[2];
         o[sf::PSI] = mu[3];
         o[sf::PHI] = mu[4];
-        for (int v = 0; v < sf::NC; ++v) {
-            double x = o[v];
-            if (P1) x += P1[v * g.plane + c];
-            if (P2) x += P2[v * g.plane + c];
-            out[v * g.plane + c] = x;
-        }
+        for (int v = 0; v < sf::NC; ++v) out[v * g.plane + c] = o[v] + add.at(v * g.plane + c);
         sig[c] += adt * sgb;
     }
 }
@@ -271,39 +279,66 @@ int blocks_for(long long n, int t) {
 
 } // namespace
 
-// One reverse step; see the file comment. Buffers: lam (in), out (lambda^n),
-// S1q/S1w, S2q/S2w the stage states, scratch planes fx, fy, fbx, fby, qbd, lq, lr2,
-// sig (per-cell sigma adjoint, accumulated).
-cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, double dt, const double *lam, double *out,
-                                const double *S1q, const double *S1w, const double *S2q, const double *S2w,
-                                double *fx, double *fy, double *fbx, double *fby, double *qbd, double *lq,
-                                double *lr2, double *sig, cudaStream_t s) {
-    const double gam = 1.0 - 0.70710678118654752440;
+// Reverse of one stage at the stored stage state (q, w): lambda_q from the
+// transposed flux divergence (adjoint of L: lamL) and the source VJP
+// (adjoint of Psi: psib), then out = S^T lambda_q + the fields of add.
+static cudaError_t reverse_stage(const Grid &g, const Phys &ph, double adt, const double *q, const double *w,
+                                 Lin lamL, Lin psib, Lin add, double *out, double *fx, double *fy, double *fbx,
+                                 double *fby, double *qbd, double *lq, double *sig, cudaStream_t s) {
     const size_t pb = (size_t)g.plane * sf::NC * sizeof(double);
     const int T = 256;
     const int cb = blocks_for(g.ncell, T);
     const int ndir = g.ny > 1 ? 2 : 1;
-    for (int stage = 2; stage >= 1; --stage) {
-        const double *q = stage == 2 ? S2q : S1q, *w = stage == 2 ? S2w : S1w;
-        cudaMemsetAsync(fbx, 0, pb, s);
-        if (ndir > 1) cudaMemsetAsync(fby, 0, pb, s);
-        cudaMemsetAsync(qbd, 0, pb, s);
-        k_cellflux<<<cb, T, 0, s>>>(g, ph, q, w, fx, fy);
-        // lambda_L and Psi-bar: stage 2 -> dt/2 lam ; stage 1 -> dt lr2 + dt/2 lam, (1-2g) dt lr2 + dt/2 lam
-        const double *LA = stage == 2 ? lam : lr2, *LB = stage == 2 ? nullptr : lam;
-        const double aL = stage == 2 ? 0.5 * dt : dt, bL = 0.5 * dt;
-        const double aP = stage == 2 ? 0.5 * dt : (1.0 - 2.0 * gam) * dt, bP = 0.5 * dt;
-        for (int d = 0; d < ndir; ++d) {
-            long long nf = (long long)((d == 0 ? g.nx : g.ny) + 1) * (d == 0 ? g.ny : g.nx) * sf::NC;
-            k_face_adj<<<blocks_for(nf, T), T, 0, s>>>(g, d, q, d == 0 ? fx : fy, LA, aL, LB, bL, d == 0 ? fbx : fby, qbd);
-        }
-        k_cell_adj<<<cb, T, 0, s>>>(g, ph, q, w, fbx, fby, qbd, LA, aP, LB, bP, lq, sig);
-        if (stage == 2)
-            k_stage_adj<<<cb, T, 0, s>>>(g, ph, gam * dt, q, w, lq, nullptr, nullptr, lr2, sig);
-        else
-            k_stage_adj<<<cb, T, 0, s>>>(g, ph, gam * dt, q, w, lq, lr2, lam, out, sig);
+    cudaMemsetAsync(fbx, 0, pb, s);
+    if (ndir > 1) cudaMemsetAsync(fby, 0, pb, s);
+    cudaMemsetAsync(qbd, 0, pb, s);
+    k_cellflux<<<cb, T, 0, s>>>(g, ph, q, w, fx, fy);
+    for (int d = 0; d < ndir; ++d) {
+        long long nf = (long long)((d == 0 ? g.nx : g.ny) + 1) * (d == 0 ? g.ny : g.nx) * sf::NC;
+        k_face_adj<<<blocks_for(nf, T), T, 0, s>>>(g, d, q, d == 0 ? fx : fy, lamL, d == 0 ? fbx : fby, qbd);
     }
+    k_cell_adj<<<cb, T, 0, s>>>(g, ph, q, w, fbx, fby, qbd, psib, lq, sig);
+    k_stage_adj<<<cb, T, 0, s>>>(g, ph, adt, q, w, lq, add, out, sig);
     return cudaGetLastError();
+}
+
+// One reverse step; see the file comment. lam (in) -> out (lambda^n); Sq/Sw the
+// stage states (2 for SSP2(222), 3 for SSP3(332)); scratch planes fx, fy, fbx,
+// fby, qbd, lq, lr2, lr3 (SSP3 only); sig the per-cell sigma adjoint (accumulated).
+cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, int scheme, double dt, const double *lam, double *out,
+                                const double *const *Sq, const double *const *Sw, double *fx, double *fy,
+                                double *fbx, double *fby, double *qbd, double *lq, double *lr2, double *lr3,
+                                double *sig, cudaStream_t s) {
+    const double gam = 1.0 - 0.70710678118654752440;
+    const double adt = gam * dt;
+    const Lin none{{nullptr, nullptr, nullptr}, {0.0, 0.0, 0.0}};
+    cudaError_t e;
+    if (scheme == 0) {
+        // stage 2: L2 and Psi2 enter q^{n+1} with dt/2
+        const Lin l2{{lam, nullptr, nullptr}, {0.5 * dt, 0.0, 0.0}};
+        e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, l2, none, lr2, fx, fy, fbx, fby, qbd, lq, sig, s);
+        if (e != cudaSuccess) return e;
+        // stage 1: L1 enters r2 (dt) and q^{n+1} (dt/2); Psi1 with (1 - 2g) dt and dt/2
+        const Lin l1{{lr2, lam, nullptr}, {dt, 0.5 * dt, 0.0}};
+        const Lin p1{{lr2, lam, nullptr}, {(1.0 - 2.0 * gam) * dt, 0.5 * dt, 0.0}};
+        const Lin a1{{lr2, lam, nullptr}, {1.0, 1.0, 0.0}};
+        return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, fx, fy, fbx, fby, qbd, lq, sig, s);
+    }
+    // SSP3(332), stage 3: L3 and Psi3 enter q^{n+1} with 2 dt/3
+    const Lin l3{{lam, nullptr, nullptr}, {2.0 * dt / 3.0, 0.0, 0.0}};
+    e = reverse_stage(g, ph, adt, Sq[2], Sw[2], l3, l3, none, lr3, fx, fy, fbx, fby, qbd, lq, sig, s);
+    if (e != cudaSuccess) return e;
+    // stage 2: L2 enters q^{n+1} (dt/6) and R3 (dt/4); Psi2 only q^{n+1} (dt/6)
+    const Lin l2{{lam, lr3, nullptr}, {dt / 6.0, 0.25 * dt, 0.0}};
+    const Lin p2{{lam, nullptr, nullptr}, {dt / 6.0, 0.0, 0.0}};
+    e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, p2, none, lr2, fx, fy, fbx, fby, qbd, lq, sig, s);
+    if (e != cudaSuccess) return e;
+    // stage 1: L1 enters q^{n+1} (dt/6), R3 (dt/4) and R (dt); Psi1 with dt/6,
+    // (1/2 - g) dt and (1 - 2g) dt; q^n enters all three with weight 1
+    const Lin l1{{lam, lr3, lr2}, {dt / 6.0, 0.25 * dt, dt}};
+    const Lin p1{{lam, lr3, lr2}, {dt / 6.0, (0.5 - gam) * dt, (1.0 - 2.0 * gam) * dt}};
+    const Lin a1{{lam, lr3, lr2}, {1.0, 1.0, 1.0}};
+    return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, fx, fy, fbx, fby, qbd, lq, sig, s);
 }
 
 cudaError_t launch_adjoint_prims(const Grid &g, const Phys &ph, const double *q, const double *w, const double *lam,

@@ -75,7 +75,7 @@ struct rmhd_ctx {
     double rec_dt;
     char *rec_ws;
     bool rec_own;
-    double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_fx, *rec_fy, *rec_fbx, *rec_fby,
+    double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_lr3, *rec_fx, *rec_fy, *rec_fbx, *rec_fby,
         *rec_qbd, *rec_sig, *rec_pbar, *rec_fin, *rec_sum;
     struct Timed { int kind; cudaEvent_t a, b; };
     std::vector<Timed> timed;
@@ -949,8 +949,11 @@ int rmhd_autotune(rmhd_ctx *c, int *choice) {
 
 // ---------------------------------------------------------------- discrete adjoint
 struct RecLayout {
-    size_t ck, seg, lam, lamn, lq, lr2, fx, fy, fbx, fby, qbd, sig, pbar, fin, sum, total;
+    size_t ck, seg, lam, lamn, lq, lr2, lr3, fx, fy, fbx, fby, qbd, sig, pbar, fin, sum, total;
 };
+
+// implicit stages per step of the context's scheme
+static int scheme_stages(const rmhd_ctx *c) { return c->cfg.scheme == RMHD_SSP3 ? 3 : 2; }
 
 static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
     const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
@@ -959,11 +962,12 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
     RecLayout L;
     size_t o = 0;
     L.ck = o; o += align256((size_t)nck * (nc + nw) * pl);
-    L.seg = o; o += align256((size_t)K * 2 * (nc + nw) * pl);
+    L.seg = o; o += align256((size_t)K * scheme_stages(c) * (nc + nw) * pl);
     L.lam = o; o += align256(nc * pl);
     L.lamn = o; o += align256(nc * pl);
     L.lq = o; o += align256(nc * pl);
     L.lr2 = o; o += align256(nc * pl);
+    L.lr3 = o; o += align256(nc * pl);
     L.fx = o; o += align256(nc * pl);
     L.fy = o; o += align256(nc * pl);
     L.fbx = o; o += align256(nc * pl);
@@ -978,9 +982,8 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->cfg.scheme != RMHD_SSP2 ||
-        c->g.nz > 1)
-        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 SSP2(222) 1-D/2-D single-grid contexts only");
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->g.nz > 1)
+        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 1-D/2-D single-grid contexts only");
     if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
     return RMHD_OK;
@@ -1016,6 +1019,7 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
     c->rec_lamn = (double *)(c->rec_ws + L.lamn);
     c->rec_lq = (double *)(c->rec_ws + L.lq);
     c->rec_lr2 = (double *)(c->rec_ws + L.lr2);
+    c->rec_lr3 = (double *)(c->rec_ws + L.lr3);
     c->rec_fx = (double *)(c->rec_ws + L.fx);
     c->rec_fy = (double *)(c->rec_ws + L.fy);
     c->rec_fbx = (double *)(c->rec_ws + L.fbx);
@@ -1035,20 +1039,42 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
 }
 
 // One forward step writing the stage states into caller buffers (same kernels
-// and arithmetic as enqueue_step, so the recomputation reproduces the run).
-static int enqueue_step_into(rmhd_ctx *c, double dt, double *q1, double *w1, double *q2, double *w2) {
+// and arithmetic as enqueue_step, so the recomputation reproduces the run):
+// stage i into (Sq[i], Sw[i]).
+static int enqueue_step_into(rmhd_ctx *c, double dt, double *const *Sq, double *const *Sw) {
     const int m = c->cfg.model;
     FluxArgs f;
-    StageArgs s1 = stage_args(c, c->Q, c->W, q1, w1, kGamma * dt);
+    if (c->cfg.scheme == RMHD_SSP3) {
+        // as enqueue_step_ssp3; stage 2 starts from stage 1's primitives, stage 3 from stage 2's
+        StageArgs s1 = stage_args(c, c->Q, c->W, Sq[0], Sw[0], kGamma * dt);
+        CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
+        f = flux_args(Sq[0], Sw[0]);
+        int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
+        n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma, dt);
+        n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
+        CK(c, flux_pass(c, n, f));
+        StageArgs s2 = stage_args(c, c->R, Sw[0], Sq[1], Sw[1], kGamma * dt);
+        CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
+        f = flux_args(Sq[1], Sw[1]);
+        n = add_out(f, 0, c->R3, c->R, 0.25, 0.0, dt);
+        n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
+        CK(c, flux_pass(c, n, f));
+        StageArgs s3 = stage_args(c, c->R, Sw[1], Sq[2], Sw[2], kGamma * dt);
+        CK(c, launch_stage(m, c->g, c->ph, s3, c->stream));
+        f = flux_args(Sq[2], Sw[2]);
+        f.wcarry = c->W;
+        n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0, dt);
+        CK(c, flux_pass(c, n, f));
+        return RMHD_OK;
+    }
+    StageArgs s1 = stage_args(c, c->Q, c->W, Sq[0], Sw[0], kGamma * dt);
     CK(c, launch_stage(m, c->g, c->ph, s1, c->stream));
-    int n = ssp2_pass1(c, q1, w1, dt, f);
-    f.srcg = c->SRCG;
-    CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
-    StageArgs s2 = stage_args(c, c->R, w1, q2, w2, kGamma * dt);
+    int n = ssp2_pass1(c, Sq[0], Sw[0], dt, f);
+    CK(c, flux_pass(c, n, f));
+    StageArgs s2 = stage_args(c, c->R, Sw[0], Sq[1], Sw[1], kGamma * dt);
     CK(c, launch_stage(m, c->g, c->ph, s2, c->stream));
-    n = ssp2_pass2(c, q2, w2, dt, f);
-    f.srcg = c->SRCG;
-    CK(c, launch_flux(m, c->cfg.precision, n, c->g, c->ph, f, c->stream));
+    n = ssp2_pass2(c, Sq[1], Sw[1], dt, f);
+    CK(c, flux_pass(c, n, f));
     return RMHD_OK;
 }
 
@@ -1079,16 +1105,29 @@ int rmhd_adjoint_step(rmhd_ctx *c, const double *dJ_dcons, int where_in, double 
         const double *ck = c->rec_ck + (size_t)seg * (nc + nw) * P;
         CK(c, cudaMemcpyAsync(c->Q, ck, nc * pl, cudaMemcpyDeviceToDevice, c->stream));
         CK(c, cudaMemcpyAsync(c->W, ck + (size_t)nc * P, nw * pl, cudaMemcpyDeviceToDevice, c->stream));
+        const int S = scheme_stages(c);
+        // stage i of step s: q at b + i (nc + nw) P, w right after it
+        auto stage_ptrs = [&](int s, double **Sq, double **Sw) {
+            double *b = c->rec_seg + (size_t)s * S * (nc + nw) * P;
+            for (int k = 0; k < S; ++k) {
+                Sq[k] = b + (size_t)k * (nc + nw) * P;
+                Sw[k] = Sq[k] + (size_t)nc * P;
+            }
+        };
         for (int s = 0; s < len; ++s) {
-            double *b = c->rec_seg + (size_t)s * 2 * (nc + nw) * P;
-            st = enqueue_step_into(c, dt, b, b + (size_t)nc * P, b + (size_t)(nc + nw) * P, b + (size_t)(2 * nc + nw) * P);
+            double *Sq[3], *Sw[3];
+            stage_ptrs(s, Sq, Sw);
+            st = enqueue_step_into(c, dt, Sq, Sw);
             if (st) return st;
         }
         for (int s = len - 1; s >= 0; --s) {
-            double *b = c->rec_seg + (size_t)s * 2 * (nc + nw) * P;
-            CK(c, launch_adjoint_step(c->g, c->ph, dt, lam, lamn, b, b + (size_t)nc * P, b + (size_t)(nc + nw) * P,
-                                      b + (size_t)(2 * nc + nw) * P, c->rec_fx, c->rec_fy, c->rec_fbx, c->rec_fby,
-                                      c->rec_qbd, c->rec_lq, c->rec_lr2, c->rec_sig, c->stream));
+            double *Sq[3], *Sw[3];
+            stage_ptrs(s, Sq, Sw);
+            const double *cq[3] = {Sq[0], Sq[1], S > 2 ? Sq[2] : nullptr};
+            const double *cw[3] = {Sw[0], Sw[1], S > 2 ? Sw[2] : nullptr};
+            CK(c, launch_adjoint_step(c->g, c->ph, S > 2 ? 1 : 0, dt, lam, lamn, cq, cw, c->rec_fx, c->rec_fy,
+                                      c->rec_fbx, c->rec_fby, c->rec_qbd, c->rec_lq, c->rec_lr2, c->rec_lr3,
+                                      c->rec_sig, c->stream));
             std::swap(lam, lamn);
         }
     }

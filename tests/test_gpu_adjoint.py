@@ -264,3 +264,82 @@ def test_adjoint_dot_product(env, name, make, nsteps, ckpt):
     rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
     print(name, "dot-product relative difference", rel)
     assert rel <= 1e-12, (name, lhs, rhs, rel)
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", TINY)
+def test_adjoint_ssp3_matches_autodiff_oracle(env, name, make, nsteps, ckpt):
+    """SSP3(332) (Table 2; three implicit stages reversed from the third): every
+    entry of the GPU gradient and dJ/dsigma against the differentiable oracle's
+    SSP3 gradient (pinned to the C oracle's SSP3 step)."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = make()
+    lam = np.random.default_rng(15).normal(size=(14,) + wl.prims.shape[1:])
+    s = Sim.from_workload(wl, scheme=1)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(lam))
+    _, go, gso, _ = A.gradient(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y,
+                               wl.dx, wl.dy, lam, scheme=1)
+    err = np.abs(gp - go).max() / np.abs(go).max()
+    print(name, "SSP3 entrywise relative error", err, "dJ/dsigma", gs, gso)
+    assert err <= 1e-9, (name, err)
+    assert abs(gs - gso) <= 1e-9 * abs(gso) + 1e-12 * np.abs(go).max(), (name, gs, gso)
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt", TINY)
+def test_adjoint_ssp3_dot_product(env, name, make, nsteps, ckpt):
+    """<J v, w> = <v, J^T w> for SSP3(332): GPU reverse mode against the
+    differentiable oracle's forward-mode derivative."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = make()
+    rng = np.random.default_rng(27)
+    w = rng.normal(size=(14,) + wl.prims.shape[1:])
+    vp = rng.normal(size=wl.prims.shape) * np.abs(wl.prims).reshape(11, -1).max(axis=1).clip(1e-2)[
+        (slice(None),) + (None,) * (wl.prims.ndim - 1)]
+    vs = 0.1 * wl.sigma
+    s = Sim.from_workload(wl, scheme=1)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(w))
+    Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs, scheme=1)
+    lhs = float((Jv * w).sum())
+    rhs = float((gp * vp).sum() + gs * vs)
+    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    print(name, "SSP3 dot-product relative difference", rel)
+    assert rel <= 1e-12, (name, lhs, rhs, rel)
+
+
+def test_adjoint_ssp3_finite_differences(env):
+    """SSP3(332) through the torch.autograd.Function: directional central
+    differences of the GPU forward (field loop 24^2, 12 steps, checkpoints
+    every 5) along random directions of the primitives and sigma."""
+    torch, Sim, ImexSteps = env
+    wl = WL.field_loop(n=24, nsteps=12)
+    nsteps = 12
+    p0 = torch.tensor(wl.prims, dtype=torch.float64, device="cuda", requires_grad=True)
+    sig = torch.tensor(wl.sigma, dtype=torch.float64, requires_grad=True)
+    q = ImexSteps.apply(p0, sig, wl, nsteps, 5, 1)
+    dv = wl.dx * wl.dy
+    J = (q[5] ** 2 + q[6] ** 2 + 2.0 * q[7] ** 2).sum() * dv
+    J.backward()
+    gp, gs = p0.grad.cpu().numpy(), sig.grad.item()
+
+    def gJ(prims, sigma):
+        s = Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, sigma, wl.bc_x, wl.bc_y, wl.cfl, scheme=1)
+        s.set_prims(np.ascontiguousarray(prims))
+        s.step(wl.dt, nsteps)
+        s.check()
+        return functional_np(s.cons(), wl)
+    assert abs(J.item() - gJ(wl.prims, wl.sigma)) <= 1e-14 * abs(J.item())
+    rng = np.random.default_rng(33)
+    for seed in (41, 42, 43):
+        d = direction(wl, seed)
+        ds = float(rng.uniform(-1.0, 1.0)) * 1e-2 * wl.sigma
+        h = 1e-6
+        fd = (gJ(wl.prims + h * d, wl.sigma + h * ds) - gJ(wl.prims - h * d, wl.sigma - h * ds)) / (2 * h)
+        ad = float((gp * d).sum()) + gs * ds
+        assert abs(ad - fd) <= 1e-5 * abs(fd), (seed, ad, fd)

@@ -91,3 +91,37 @@ def test_jvp_matches_c_oracle_differences():
     d2 = (q(h / 2) - q(-h / 2)) / h
     fd = (4 * d2 - d1) / 3
     assert np.abs(Jv - fd).max() <= 1e-7 * np.abs(fd).max(), np.abs(Jv - fd).max() / np.abs(fd).max()
+
+
+def test_ssp3_forward_and_gradient_match_c_oracle():
+    """SSP3(332) (Table 2): the differentiable oracle's forward run agrees with
+    the C oracle's SSP3 step to round-off, and its gradient with central
+    differences of the C oracle (Brio-Wu, 10 cells, 3 steps)."""
+    wl = WL.brio_wu(nx=10)
+    nsteps = 3
+
+    def c3(prims, sigma=None):
+        o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma if sigma is None else sigma,
+                  wl.bc_x, wl.bc_y, scheme=1)
+        o.set_prims(np.ascontiguousarray(prims))
+        o.step(wl.dt, nsteps)
+        return o.cons()
+    lam = np.random.default_rng(6).normal(size=(14,) + wl.prims.shape[1:])
+    _, g, gs, q = A.gradient(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, lam,
+                             scheme=1)
+    assert np.all(parity_errors(0, q, c3(wl.prims)) <= 1e-12)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        d = rng.normal(size=wl.prims.shape) * np.abs(wl.prims).reshape(11, -1).max(axis=1).clip(1e-2)[:, None, None]
+        h = 1e-6
+        J = lambda t: float((lam * c3(wl.prims + t * d)).sum())
+        d1 = (J(h) - J(-h)) / (2 * h)
+        d2 = (J(h / 2) - J(-h / 2)) / h
+        fd = (4 * d2 - d1) / 3
+        assert abs(float((g * d).sum()) - fd) <= 1e-6 * abs(fd), (float((g * d).sum()), fd)
+    h = 1e-4 * wl.sigma
+    Js = lambda sg: float((lam * c3(wl.prims, sg)).sum())
+    d1 = (Js(wl.sigma + h) - Js(wl.sigma - h)) / (2 * h)
+    d2 = (Js(wl.sigma + h / 2) - Js(wl.sigma - h / 2)) / h
+    fs = (4 * d2 - d1) / 3
+    assert abs(gs - fs) <= 1e-6 * abs(fs), (gs, fs)
