@@ -178,7 +178,7 @@ int rmhd_set_refinement_cap(rmhd_ctx *ctx, int passes);
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
 /* Discrete adjoint of the IMEX step, SSP2(222) or SSP3(332) (single fluid,
- * FP64, 1-D or 2-D single grid with at least 3 cells per direction): gradients
+ * FP64, 1-D, 2-D or 3-D single grid with at least 3 cells per direction): gradients
  * of a functional of the final
  * conserved state with respect to the initial primitives and sigma.
  *   rmhd_record arms recording of the next `nsteps` steps; it must follow

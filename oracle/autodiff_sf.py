@@ -71,17 +71,21 @@ def _ghost_index(n, bc, g=2):
     return i.remainder(n) if bc == PERIODIC else i.clamp(0, n - 1)
 
 
-def pad(u, bcx, bcy):
-    """u: (..., ny, nx) -> (..., ny + 4, nx + 4) (ny == 1: no ghosts along y)."""
+def pad(u, bcx, bcy, bcz=None):
+    """u: (..., ny, nx) -> (..., ny + 4, nx + 4) (ny == 1: no ghosts along y);
+    with bcz given, u: (..., nz, ny, nx) and ghosts along z too."""
     ny, nx = u.shape[-2], u.shape[-1]
     u = u.index_select(-1, _ghost_index(nx, bcx))
     if ny > 1:
         u = u.index_select(-2, _ghost_index(ny, bcy))
+    if bcz is not None:
+        u = u.index_select(-3, _ghost_index(u.shape[-3], bcz))
     return u
 
 
 # ---- Eq. (resistive prims) -------------------------------------------------
-def prims_to_cons(P, gamma, bcx, bcy, dx, dy):
+def prims_to_cons(P, gamma, bcx, bcy, dx, dy, bcz=1, dz=1.0):
+    """P: (11, ny, nx), or (11, nz, ny, nx) for a 3-D grid."""
     rho, v, p, B, E = P[0], P[1:4], P[4], P[5:8], P[8:11]
     W = 1.0 / torch.sqrt(1.0 - dot(v, v))
     rhohW2 = (rho + gamma / (gamma - 1.0) * p) * W * W
@@ -89,6 +93,13 @@ def prims_to_cons(P, gamma, bcx, bcy, dx, dy):
     S = rhohW2 * v + cross(E, B)
     tau = rhohW2 - p + 0.5 * (dot(E, E) + dot(B, B)) - Dd
     # Gauss's law, second-order central differences
+    if P.dim() == 4:  # 3-D
+        Eg = pad(E, bcx, bcy, bcz)
+        divE = ((Eg[0, 2:-2, 2:-2, 3:-1] - Eg[0, 2:-2, 2:-2, 1:-3]) / (2.0 * dx)
+                + (Eg[1, 2:-2, 3:-1, 2:-2] - Eg[1, 2:-2, 1:-3, 2:-2]) / (2.0 * dy)
+                + (Eg[2, 3:-1, 2:-2, 2:-2] - Eg[2, 1:-3, 2:-2, 2:-2]) / (2.0 * dz))
+        z = torch.zeros_like(Dd)
+        return torch.cat([Dd[None], S, tau[None], B, E, divE[None], z[None], z[None]])
     Eg = pad(E, bcx, bcy)
     ny = P.shape[1]
     divE = (Eg[0, :, 3:-1] - Eg[0, :, 1:-3]) / (2.0 * dx)
@@ -224,7 +235,18 @@ def _divergence_1d(qg, fg, h):
     return -(F[..., 1:] - F[..., :-1]) / h
 
 
-def divergence(q, v, p, W, sigma, bcx, bcy, dx, dy):
+def divergence(q, v, p, W, sigma, bcx, bcy, dx, dy, bcz=1, dz=1.0):
+    if q.dim() == 4:  # 3-D: (14, nz, ny, nx)
+        qg, vg = pad(q, bcx, bcy, bcz), pad(v, bcx, bcy, bcz)
+        pg, Wg = pad(p, bcx, bcy, bcz), pad(W, bcx, bcy, bcz)
+        s_ = slice(2, -2)
+        Lx = _divergence_1d(qg[:, s_, s_, :], flux(qg[:, s_, s_, :], vg[:, s_, s_, :], pg[s_, s_, :],
+                                                   Wg[s_, s_, :], sigma, 0), dx)
+        qy, fy = qg[:, s_, :, s_], flux(qg[:, s_, :, s_], vg[:, s_, :, s_], pg[s_, :, s_], Wg[s_, :, s_], sigma, 1)
+        Ly = _divergence_1d(qy.transpose(2, 3), fy.transpose(2, 3), dy).transpose(2, 3)
+        qz, fz = qg[:, :, s_, s_], flux(qg[:, :, s_, s_], vg[:, :, s_, s_], pg[:, s_, s_], Wg[:, s_, s_], sigma, 2)
+        Lz = _divergence_1d(qz.permute(0, 2, 3, 1), fz.permute(0, 2, 3, 1), dz).permute(0, 3, 1, 2)
+        return Lx + Ly + Lz
     ny = q.shape[1]
     qg = pad(q, bcx, bcy)
     vg, pg, Wg = pad(v, bcx, bcy), pad(p, bcx, bcy), pad(W, bcx, bcy)
@@ -301,62 +323,62 @@ def stage(r, adt, sigma, gamma, kappa):
 GAMMA_SSP2 = 1.0 - 1.0 / math.sqrt(2.0)
 
 
-def ssp2_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy):
+def ssp2_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy, bcz=1, dz=1.0):
     g = GAMMA_SSP2
     q1, w1 = stage(q, g * dt, sigma, gamma, kappa)
-    L1 = divergence(q1, *w1, sigma, bcx, bcy, dx, dy)
+    L1 = divergence(q1, *w1, sigma, bcx, bcy, dx, dy, bcz, dz)
     P1 = source(q1, w1[0], w1[2], sigma, kappa)
     r2 = q + dt * L1 + (1.0 - 2.0 * g) * dt * P1
     q2, w2 = stage(r2, g * dt, sigma, gamma, kappa)
-    L2 = divergence(q2, *w2, sigma, bcx, bcy, dx, dy)
+    L2 = divergence(q2, *w2, sigma, bcx, bcy, dx, dy, bcz, dz)
     P2 = source(q2, w2[0], w2[2], sigma, kappa)
     return q + 0.5 * dt * (L1 + L2) + 0.5 * dt * (P1 + P2)
 
 
 # ---- Table 2: one SSP3(332) step --------------------------------------------
-def ssp3_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy):
+def ssp3_step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy, bcz=1, dz=1.0):
     """Implicit rows (g, 0, 0), (1 - 2g, g, 0), (1/2 - g, 0, g); explicit rows
     (0, 0, 0), (1, 0, 0), (1/4, 1/4, 0); weights (1/6, 1/6, 2/3) for both parts."""
     g = GAMMA_SSP2
     q1, w1 = stage(q, g * dt, sigma, gamma, kappa)
-    L1 = divergence(q1, *w1, sigma, bcx, bcy, dx, dy)
+    L1 = divergence(q1, *w1, sigma, bcx, bcy, dx, dy, bcz, dz)
     P1 = source(q1, w1[0], w1[2], sigma, kappa)
     q2, w2 = stage(q + dt * L1 + (1.0 - 2.0 * g) * dt * P1, g * dt, sigma, gamma, kappa)
-    L2 = divergence(q2, *w2, sigma, bcx, bcy, dx, dy)
+    L2 = divergence(q2, *w2, sigma, bcx, bcy, dx, dy, bcz, dz)
     P2 = source(q2, w2[0], w2[2], sigma, kappa)
     q3, w3 = stage(q + 0.25 * dt * (L1 + L2) + (0.5 - g) * dt * P1, g * dt, sigma, gamma, kappa)
-    L3 = divergence(q3, *w3, sigma, bcx, bcy, dx, dy)
+    L3 = divergence(q3, *w3, sigma, bcx, bcy, dx, dy, bcz, dz)
     P3 = source(q3, w3[0], w3[2], sigma, kappa)
     return q + dt / 6.0 * (L1 + P1) + dt / 6.0 * (L2 + P2) + 2.0 * dt / 3.0 * (L3 + P3)
 
 
-def run(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa=1.0, scheme=0):
-    """prims (11, ny, nx) and sigma (0-d) as tensors (may require grad) -> q^n;
-    scheme 0: SSP2(222), 1: SSP3(332)."""
+def run(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa=1.0, scheme=0, bcz=1, dz=1.0):
+    """prims (11, ny, nx), or (11, nz, ny, nx) for a 3-D grid, and sigma (0-d)
+    as tensors (may require grad) -> q^n; scheme 0: SSP2(222), 1: SSP3(332)."""
     step = ssp3_step if scheme == 1 else ssp2_step
-    q = prims_to_cons(prims, gamma, bcx, bcy, dx, dy)
+    q = prims_to_cons(prims, gamma, bcx, bcy, dx, dy, bcz, dz)
     for _ in range(nsteps):
-        q = step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy)
+        q = step(q, dt, sigma, gamma, kappa, bcx, bcy, dx, dy, bcz, dz)
     return q
 
 
-def gradient(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, lam, kappa=1.0, scheme=0):
+def gradient(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, lam, kappa=1.0, scheme=0, bcz=1, dz=1.0):
     """J = sum(lam * q^n): returns (J, dJ/dprims, dJ/dsigma) as NumPy/float."""
     P = torch.tensor(prims, dtype=F64, requires_grad=True)
     s = torch.tensor(float(sigma), dtype=F64, requires_grad=True)
-    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme)
+    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme, bcz, dz)
     J = (torch.tensor(lam, dtype=F64) * q).sum()
     gP, gs = torch.autograd.grad(J, (P, s))
     return float(J.detach()), gP.numpy(), float(gs), q.detach().numpy()
 
 
-def jvp(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, v_prims, v_sigma, kappa=1.0, scheme=0):
+def jvp(prims, sigma, dt, nsteps, gamma, bcx, bcy, dx, dy, v_prims, v_sigma, kappa=1.0, scheme=0, bcz=1, dz=1.0):
     """Directional derivative of q^n along (v_prims, v_sigma): reverse mode
     applied twice. g(u) = d<u, q^n>/d(prims, sigma) is linear in u, so the
     derivative of <g(u), v> with respect to u is J v at any u."""
     P = torch.tensor(prims, dtype=F64, requires_grad=True)
     s = torch.tensor(float(sigma), dtype=F64, requires_grad=True)
-    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme)
+    q = run(P, s, dt, nsteps, gamma, bcx, bcy, dx, dy, kappa, scheme, bcz, dz)
     u = torch.zeros_like(q, requires_grad=True)
     gP, gs = torch.autograd.grad((u * q).sum(), (P, s), create_graph=True)
     inner = (gP * torch.tensor(v_prims, dtype=F64)).sum() + gs * float(v_sigma)

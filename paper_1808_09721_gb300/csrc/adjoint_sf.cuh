@@ -27,11 +27,11 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// Adjoints flowing in: fbar[dir][14] for dir < ndir (may be null when ndir = 0),
+// Adjoints flowing in: fbar[dir][14] for dir < ndir (x, y, z; may be null when ndir = 0),
 // sbar[5] for the source entries (E_x, E_y, E_z, psi, phi). Adds into qbar[14]
 // and *sigbar. p is the converged pressure of q.
 __device__ __forceinline__ void cell_vjp(const double q[NC], double p, double gamma, double sigma, double kappa,
-                                         int ndir, const double fbar[2][NC], const double sbar[5], double qbar[NC],
+                                         int ndir, const double fbar[3][NC], const double sbar[5], double qbar[NC],
                                          double *sigbar) {
     const double gm1 = gamma - 1.0;
     const double Dd = q[D], rho_e = q[RHOE];
@@ -60,7 +60,8 @@ __device__ __forceinline__ void cell_vjp(const double q[NC], double p, double ga
     psib -= kappa * sbar[3];
     phib -= kappa * sbar[4];
     // fluxes f_d: D v_d; Z v_i v_d + delta_id p_em - E_i E_d - B_i B_d; S_d - D v_d;
-    // B: (phi, -E_z, E_y) / (E_z, phi, -E_x); E: (psi, B_z, -B_y) / (-B_z, psi, B_x); J_d; E_d; B_d
+    // B: (phi, -E_z, E_y) / (E_z, phi, -E_x) / (-E_y, E_x, phi);
+    // E: (psi, B_z, -B_y) / (-B_z, psi, B_x) / (B_y, -B_x, psi); J_d; E_d; B_d
     for (int d = 0; d < ndir; ++d) {
         const double *m = fbar[d];
         Db += (m[D] - m[TAU]) * v[d];
@@ -80,9 +81,12 @@ __device__ __forceinline__ void cell_vjp(const double q[NC], double p, double ga
         if (d == 0) {
             phib += m[BX]; Eb[2] -= m[BY]; Eb[1] += m[BZ];
             psib += m[EX]; Bb[2] += m[EY]; Bb[1] -= m[EZ];
-        } else {
+        } else if (d == 1) {
             Eb[2] += m[BX]; phib += m[BY]; Eb[0] -= m[BZ];
             Bb[2] -= m[EX]; psib += m[EY]; Bb[0] += m[EZ];
+        } else {
+            Eb[1] -= m[BX]; Eb[0] += m[BY]; phib += m[BZ];
+            Bb[1] += m[EX]; Bb[0] -= m[EY]; psib += m[EZ];
         }
         Jb[d] += m[RHOE];
         Eb[d] += m[PSI];

@@ -54,8 +54,9 @@ struct Lin {
     }
 };
 
-// Physical fluxes f_x, f_y (14 each) of every cell of a stage state.
-__global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, double *fx, double *fy) {
+// Physical fluxes f_x, f_y, f_z (14 each; y, z where the grid has them) of
+// every cell of a stage state.
+__global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, double *fx, double *fy, double *fz) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
         double qc[sf::NC], wc[sf::NW], J[3], f[sf::NC];
@@ -68,6 +69,10 @@ __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, do
             sf::flux(qc, wc, J, 1, f);
             for (int v = 0; v < sf::NC; ++v) fy[v * g.plane + c] = f[v];
         }
+        if (g.nz > 1) {
+            sf::flux(qc, wc, J, 2, f);
+            for (int v = 0; v < sf::NC; ++v) fz[v * g.plane + c] = f[v];
+        }
     }
 }
 
@@ -77,26 +82,34 @@ __global__ void k_cellflux(Grid g, Phys ph, const double *q, const double *w, do
 // lines (dir 1), so a warp's loads and atomics fall on consecutive cells of
 // one variable plane. lamL_ = the adjoint of L (a weighted sum of adjoint fields).
 __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, Lin lamL_, double *fbar, double *qbar) {
-    const int n = dir == 0 ? g.nx : g.ny, m = dir == 0 ? g.ny : g.nx, bc = dir == 0 ? g.bcx : g.bcy;
-    const double h4 = dir == 0 ? g.rdx4 : g.rdy4;
+    const int nz = g.nz > 1 ? g.nz : 1;
+    const long long nxy = (long long)g.nx * g.ny;
+    // cells along dir, lines across it
+    const int n = dir == 0 ? g.nx : (dir == 1 ? g.ny : nz);
+    const long long m = dir == 0 ? (long long)g.ny * nz : (dir == 1 ? (long long)g.nx * nz : nxy);
+    const int bc = dir == 0 ? g.bcx : (dir == 1 ? g.bcy : g.bcz);
+    const double h4 = dir == 0 ? g.rdx4 : (dir == 1 ? g.rdy4 : g.rdz4);
     const long long nf = (long long)(n + 1) * m * sf::NC;
     const double eps4 = 4e-6;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
-        int c, k, line;  // component, face after cell k, line
+        int c, k;        // component, face after cell k
+        long long line;  // dir 0: (z, y) row; dir 1: (z, x) column; dir 2: (y, x) pillar
         if (dir == 0) {
             k = (int)(t % (n + 1)) - 1;
             const long long r = t / (n + 1);
-            line = (int)(r % m);
+            line = r % m;
             c = (int)(r / m);
         } else {
-            line = (int)(t % m);
+            line = t % m;
             const long long r = t / m;
             k = (int)(r % (n + 1)) - 1;
             c = (int)(r / (n + 1));
         }
         auto cell = [&](int i) -> long long {
-            int im = amap(i, n, bc);
-            return dir == 0 ? (long long)line * g.nx + im : (long long)im * g.nx + line;
+            const long long im = amap(i, n, bc);
+            if (dir == 0) return line * g.nx + im;
+            if (dir == 1) return (line / g.nx) * nxy + im * g.nx + line % g.nx;
+            return im * nxy + line;
         };
         auto lamL = [&](long long cc) -> double { return lamL_.at(c * g.plane + cc); };
         // 4F at this face enters L of cell k (- 1/(4h)) and of cell k+1 (+ 1/(4h)), real cells only
@@ -158,20 +171,22 @@ __global__ void k_face_adj(Grid g, int dir, const double *q, const double *f, Li
 // sbar = the adjoint of Psi (a weighted sum of adjoint fields) at the source
 // components. Adds the sigma adjoint into sig[cell].
 __global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, const double *fbx, const double *fby,
-                           const double *qbd, Lin psib, double *lamq, double *sig) {
+                           const double *fbz, const double *qbd, Lin psib, double *lamq, double *sig) {
+    const int ndir = g.nz > 1 ? 3 : (g.ny > 1 ? 2 : 1);
     const int src[5] = {sf::EX, sf::EY, sf::EZ, sf::PSI, sf::PHI};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        double qc[sf::NC], qb[sf::NC], fb[2][sf::NC], sb[5];
+        double qc[sf::NC], qb[sf::NC], fb[3][sf::NC], sb[5];
         for (int v = 0; v < sf::NC; ++v) {
             qc[v] = q[v * g.plane + c];
             qb[v] = qbd[v * g.plane + c];
             fb[0][v] = fbx[v * g.plane + c];
-            fb[1][v] = g.ny > 1 ? fby[v * g.plane + c] : 0.0;
+            fb[1][v] = ndir > 1 ? fby[v * g.plane + c] : 0.0;
+            fb[2][v] = ndir > 2 ? fbz[v * g.plane + c] : 0.0;
         }
         for (int k = 0; k < 5; ++k) sb[k] = psib.at(src[k] * g.plane + c);
         double sigb = 0.0;
-        sf::cell_vjp(qc, w[sf::P * g.plane + c], ph.gamma, ph.sigma, ph.kappa, g.ny > 1 ? 2 : 1, fb, sb, qb, &sigb);
+        sf::cell_vjp(qc, w[sf::P * g.plane + c], ph.gamma, ph.sigma, ph.kappa, ndir, fb, sb, qb, &sigb);
         for (int v = 0; v < sf::NC; ++v) lamq[v * g.plane + c] = qb[v];
         sig[c] += sigb;
     }
@@ -184,7 +199,7 @@ __global__ void k_cell_adj(Grid g, Phys ph, const double *q, const double *w, co
 // (weights 1; null entries skipped).
 __global__ void k_stage_adj(Grid g, Phys ph, double adt, const double *q, const double *w, const double *lam,
                             Lin add, double *out, double *sig) {
-    const double nofb[2][sf::NC] = {};
+    const double nofb[3][sf::NC] = {};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
         double qc[sf::NC], la[sf::NC];
@@ -245,15 +260,24 @@ __global__ void k_prims_adj(Grid g, Phys ph, const double *q, const double *w, c
         sf::p2c_vjp(prim, ph.gamma, qb, pb);
         for (int k = 0; k < 11; ++k) atomicAdd(&pbar[k * g.plane + c], pb[k]);
         // varrho_c = (E_x[i+1] - E_x[i-1]) / (2 dx) + (E_y[j+1] - E_y[j-1]) / (2 dy)
+        //          + (E_z[k+1] - E_z[k-1]) / (2 dz)
         const double lr = qb[sf::RHOE];
-        const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
+        const long long nxy = (long long)g.nx * g.ny;
+        const int kz = (int)(c / nxy);
+        const long long rem = c - kz * nxy, pz = kz * nxy;
+        const int j = (int)(rem / g.nx), i = (int)(rem - (long long)j * g.nx);
         const double hx = lr / (2.0 * g.dx);
-        atomicAdd(&pbar[8 * g.plane + (long long)j * g.nx + amap(i + 1, g.nx, g.bcx)], hx);
-        atomicAdd(&pbar[8 * g.plane + (long long)j * g.nx + amap(i - 1, g.nx, g.bcx)], -hx);
+        atomicAdd(&pbar[8 * g.plane + pz + (long long)j * g.nx + amap(i + 1, g.nx, g.bcx)], hx);
+        atomicAdd(&pbar[8 * g.plane + pz + (long long)j * g.nx + amap(i - 1, g.nx, g.bcx)], -hx);
         if (g.ny > 1) {
             const double hy = lr / (2.0 * g.dy);
-            atomicAdd(&pbar[9 * g.plane + (long long)amap(j + 1, g.ny, g.bcy) * g.nx + i], hy);
-            atomicAdd(&pbar[9 * g.plane + (long long)amap(j - 1, g.ny, g.bcy) * g.nx + i], -hy);
+            atomicAdd(&pbar[9 * g.plane + pz + (long long)amap(j + 1, g.ny, g.bcy) * g.nx + i], hy);
+            atomicAdd(&pbar[9 * g.plane + pz + (long long)amap(j - 1, g.ny, g.bcy) * g.nx + i], -hy);
+        }
+        if (g.nz > 1) {
+            const double hz = lr / (2.0 * g.dz);
+            atomicAdd(&pbar[10 * g.plane + (long long)amap(kz + 1, g.nz, g.bcz) * nxy + rem], hz);
+            atomicAdd(&pbar[10 * g.plane + (long long)amap(kz - 1, g.nz, g.bcz) * nxy + rem], -hz);
         }
     }
 }
@@ -283,31 +307,35 @@ int blocks_for(long long n, int t) {
 // transposed flux divergence (adjoint of L: lamL) and the source VJP
 // (adjoint of Psi: psib), then out = S^T lambda_q + the fields of add.
 static cudaError_t reverse_stage(const Grid &g, const Phys &ph, double adt, const double *q, const double *w,
-                                 Lin lamL, Lin psib, Lin add, double *out, double *fx, double *fy, double *fbx,
-                                 double *fby, double *qbd, double *lq, double *sig, cudaStream_t s) {
+                                 Lin lamL, Lin psib, Lin add, double *out, double *const *f, double *const *fb,
+                                 double *qbd, double *lq, double *sig, cudaStream_t s) {
     const size_t pb = (size_t)g.plane * sf::NC * sizeof(double);
     const int T = 256;
     const int cb = blocks_for(g.ncell, T);
-    const int ndir = g.ny > 1 ? 2 : 1;
-    cudaMemsetAsync(fbx, 0, pb, s);
-    if (ndir > 1) cudaMemsetAsync(fby, 0, pb, s);
+    const int ndir = g.nz > 1 ? 3 : (g.ny > 1 ? 2 : 1);
+    const long long nz = g.nz > 1 ? g.nz : 1;
+    for (int d = 0; d < ndir; ++d) cudaMemsetAsync(fb[d], 0, pb, s);
     cudaMemsetAsync(qbd, 0, pb, s);
-    k_cellflux<<<cb, T, 0, s>>>(g, ph, q, w, fx, fy);
+    k_cellflux<<<cb, T, 0, s>>>(g, ph, q, w, f[0], f[1], f[2]);
     for (int d = 0; d < ndir; ++d) {
-        long long nf = (long long)((d == 0 ? g.nx : g.ny) + 1) * (d == 0 ? g.ny : g.nx) * sf::NC;
-        k_face_adj<<<blocks_for(nf, T), T, 0, s>>>(g, d, q, d == 0 ? fx : fy, lamL, d == 0 ? fbx : fby, qbd);
+        // (cells along d + 1 faces) x lines across d x components
+        const long long n = d == 0 ? g.nx : (d == 1 ? g.ny : nz);
+        const long long lines = g.ncell / n;
+        const long long nf = (n + 1) * lines * sf::NC;
+        k_face_adj<<<blocks_for(nf, T), T, 0, s>>>(g, d, q, f[d], lamL, fb[d], qbd);
     }
-    k_cell_adj<<<cb, T, 0, s>>>(g, ph, q, w, fbx, fby, qbd, psib, lq, sig);
+    k_cell_adj<<<cb, T, 0, s>>>(g, ph, q, w, fb[0], fb[1], fb[2], qbd, psib, lq, sig);
     k_stage_adj<<<cb, T, 0, s>>>(g, ph, adt, q, w, lq, add, out, sig);
     return cudaGetLastError();
 }
 
 // One reverse step; see the file comment. lam (in) -> out (lambda^n); Sq/Sw the
-// stage states (2 for SSP2(222), 3 for SSP3(332)); scratch planes fx, fy, fbx,
-// fby, qbd, lq, lr2, lr3 (SSP3 only); sig the per-cell sigma adjoint (accumulated).
+// stage states (2 for SSP2(222), 3 for SSP3(332)); scratch planes: f[3] cell
+// fluxes and fb[3] their adjoints (x, y, z; those the grid has), qbd, lq, lr2,
+// lr3 (SSP3 only); sig the per-cell sigma adjoint (accumulated).
 cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, int scheme, double dt, const double *lam, double *out,
-                                const double *const *Sq, const double *const *Sw, double *fx, double *fy,
-                                double *fbx, double *fby, double *qbd, double *lq, double *lr2, double *lr3,
+                                const double *const *Sq, const double *const *Sw, double *const *f,
+                                double *const *fb, double *qbd, double *lq, double *lr2, double *lr3,
                                 double *sig, cudaStream_t s) {
     const double gam = 1.0 - 0.70710678118654752440;
     const double adt = gam * dt;
@@ -316,29 +344,29 @@ cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, int scheme, doubl
     if (scheme == 0) {
         // stage 2: L2 and Psi2 enter q^{n+1} with dt/2
         const Lin l2{{lam, nullptr, nullptr}, {0.5 * dt, 0.0, 0.0}};
-        e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, l2, none, lr2, fx, fy, fbx, fby, qbd, lq, sig, s);
+        e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, l2, none, lr2, f, fb, qbd, lq, sig, s);
         if (e != cudaSuccess) return e;
         // stage 1: L1 enters r2 (dt) and q^{n+1} (dt/2); Psi1 with (1 - 2g) dt and dt/2
         const Lin l1{{lr2, lam, nullptr}, {dt, 0.5 * dt, 0.0}};
         const Lin p1{{lr2, lam, nullptr}, {(1.0 - 2.0 * gam) * dt, 0.5 * dt, 0.0}};
         const Lin a1{{lr2, lam, nullptr}, {1.0, 1.0, 0.0}};
-        return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, fx, fy, fbx, fby, qbd, lq, sig, s);
+        return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, f, fb, qbd, lq, sig, s);
     }
     // SSP3(332), stage 3: L3 and Psi3 enter q^{n+1} with 2 dt/3
     const Lin l3{{lam, nullptr, nullptr}, {2.0 * dt / 3.0, 0.0, 0.0}};
-    e = reverse_stage(g, ph, adt, Sq[2], Sw[2], l3, l3, none, lr3, fx, fy, fbx, fby, qbd, lq, sig, s);
+    e = reverse_stage(g, ph, adt, Sq[2], Sw[2], l3, l3, none, lr3, f, fb, qbd, lq, sig, s);
     if (e != cudaSuccess) return e;
     // stage 2: L2 enters q^{n+1} (dt/6) and R3 (dt/4); Psi2 only q^{n+1} (dt/6)
     const Lin l2{{lam, lr3, nullptr}, {dt / 6.0, 0.25 * dt, 0.0}};
     const Lin p2{{lam, nullptr, nullptr}, {dt / 6.0, 0.0, 0.0}};
-    e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, p2, none, lr2, fx, fy, fbx, fby, qbd, lq, sig, s);
+    e = reverse_stage(g, ph, adt, Sq[1], Sw[1], l2, p2, none, lr2, f, fb, qbd, lq, sig, s);
     if (e != cudaSuccess) return e;
     // stage 1: L1 enters q^{n+1} (dt/6), R3 (dt/4) and R (dt); Psi1 with dt/6,
     // (1/2 - g) dt and (1 - 2g) dt; q^n enters all three with weight 1
     const Lin l1{{lam, lr3, lr2}, {dt / 6.0, 0.25 * dt, dt}};
     const Lin p1{{lam, lr3, lr2}, {dt / 6.0, (0.5 - gam) * dt, (1.0 - 2.0 * gam) * dt}};
     const Lin a1{{lam, lr3, lr2}, {1.0, 1.0, 1.0}};
-    return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, fx, fy, fbx, fby, qbd, lq, sig, s);
+    return reverse_stage(g, ph, adt, Sq[0], Sw[0], l1, p1, a1, out, f, fb, qbd, lq, sig, s);
 }
 
 cudaError_t launch_adjoint_prims(const Grid &g, const Phys &ph, const double *q, const double *w, const double *lam,

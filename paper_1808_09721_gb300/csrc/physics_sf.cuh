@@ -365,7 +365,7 @@ __device__ __forceinline__ void current(const double *q, const double *w, double
     for (int i = 0; i < 3; ++i) J[i] = q[RHOE] * v[i] + Ws * (E[i] + vxB[i] - vE * v[i]);
 }
 
-// Flux along direction `dir` (0 = x, 1 = y) of Eq. (resistive RMHD):
+// Flux along direction `dir` (0 = x, 1 = y, 2 = z) of Eq. (resistive RMHD):
 //   D v_d; Z v_i v_d + [p + (E^2+B^2)/2] delta_id - E_i E_d - B_i B_d; S_d - D v_d;
 //   B: -eps_ijd E_j + delta_id phi; E: eps_ijd B_j + delta_id psi; J_d; E_d; B_d,
 // with Z = rho h W^2 = tau - (E^2+B^2)/2 + D + p (no division needed).
@@ -376,22 +376,26 @@ __device__ __forceinline__ void flux(const T q[NC], const T w[NW], const T J[3],
     const T pem = w[P] + T(0.5) * E2B2;
     const T Z = (q[TAU] - T(0.5) * E2B2) + q[D] + w[P];
     // selects instead of indices computed from dir keep the arrays in registers
-    const T vd = dir == 0 ? w[VX] : w[VY], Ed = dir == 0 ? q[EX] : q[EY], Bd = dir == 0 ? q[BX] : q[BY];
+    const T vd = dir == 0 ? w[VX] : (dir == 1 ? w[VY] : w[VZ]);
+    const T Ed = dir == 0 ? q[EX] : (dir == 1 ? q[EY] : q[EZ]), Bd = dir == 0 ? q[BX] : (dir == 1 ? q[BY] : q[BZ]);
     const T Zv = Z * vd;
     f[D] = q[D] * vd;
     f[SX] = Zv * w[VX] - q[EX] * Ed - q[BX] * Bd;
     f[SY] = Zv * w[VY] - q[EY] * Ed - q[BY] * Bd;
     f[SZ] = Zv * w[VZ] - q[EZ] * Ed - q[BZ] * Bd;
-    if (dir == 0) f[SX] += pem; else f[SY] += pem;
-    f[TAU] = (dir == 0 ? q[SX] : q[SY]) - q[D] * vd;
+    if (dir == 0) f[SX] += pem; else if (dir == 1) f[SY] += pem; else f[SZ] += pem;
+    f[TAU] = (dir == 0 ? q[SX] : (dir == 1 ? q[SY] : q[SZ])) - q[D] * vd;
     if (dir == 0) {
         f[BX] = q[PHI]; f[BY] = -q[EZ]; f[BZ] = q[EY];
         f[EX] = q[PSI]; f[EY] = q[BZ]; f[EZ] = -q[BY];
-    } else {
+    } else if (dir == 1) {
         f[BX] = q[EZ]; f[BY] = q[PHI]; f[BZ] = -q[EX];
         f[EX] = -q[BZ]; f[EY] = q[PSI]; f[EZ] = q[BX];
+    } else {
+        f[BX] = -q[EY]; f[BY] = q[EX]; f[BZ] = q[PHI];
+        f[EX] = q[BY]; f[EY] = -q[BX]; f[EZ] = q[PSI];
     }
-    f[RHOE] = dir == 0 ? J[0] : J[1];
+    f[RHOE] = dir == 0 ? J[0] : (dir == 1 ? J[1] : J[2]);
     f[PSI] = Ed;
     f[PHI] = Bd;
 }

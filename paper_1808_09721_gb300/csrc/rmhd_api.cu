@@ -75,7 +75,8 @@ struct rmhd_ctx {
     double rec_dt;
     char *rec_ws;
     bool rec_own;
-    double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_lr3, *rec_fx, *rec_fy, *rec_fbx, *rec_fby,
+    double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_lr3, *rec_fx, *rec_fy, *rec_fz, *rec_fbx,
+        *rec_fby, *rec_fbz,
         *rec_qbd, *rec_sig, *rec_pbar, *rec_fin, *rec_sum;
     struct Timed { int kind; cudaEvent_t a, b; };
     std::vector<Timed> timed;
@@ -949,7 +950,7 @@ int rmhd_autotune(rmhd_ctx *c, int *choice) {
 
 // ---------------------------------------------------------------- discrete adjoint
 struct RecLayout {
-    size_t ck, seg, lam, lamn, lq, lr2, lr3, fx, fy, fbx, fby, qbd, sig, pbar, fin, sum, total;
+    size_t ck, seg, lam, lamn, lq, lr2, lr3, fx, fy, fz, fbx, fby, fbz, qbd, sig, pbar, fin, sum, total;
 };
 
 // implicit stages per step of the context's scheme
@@ -968,10 +969,13 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
     L.lq = o; o += align256(nc * pl);
     L.lr2 = o; o += align256(nc * pl);
     L.lr3 = o; o += align256(nc * pl);
+    const size_t zpl = c->g.nz > 1 ? nc * pl : 0;  // z fluxes: 3-D grids only
     L.fx = o; o += align256(nc * pl);
     L.fy = o; o += align256(nc * pl);
+    L.fz = o; o += align256(zpl);
     L.fbx = o; o += align256(nc * pl);
     L.fby = o; o += align256(nc * pl);
+    L.fbz = o; o += align256(zpl);
     L.qbd = o; o += align256(nc * pl);
     L.sig = o; o += align256(pl);
     L.pbar = o; o += align256(11 * pl);
@@ -982,9 +986,9 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->g.nz > 1)
-        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 1-D/2-D single-grid contexts only");
-    if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3))
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch)
+        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 single-grid contexts only");
+    if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3) || (c->g.nz > 1 && c->g.nz < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
     return RMHD_OK;
 }
@@ -1022,8 +1026,10 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
     c->rec_lr3 = (double *)(c->rec_ws + L.lr3);
     c->rec_fx = (double *)(c->rec_ws + L.fx);
     c->rec_fy = (double *)(c->rec_ws + L.fy);
+    c->rec_fz = (double *)(c->rec_ws + L.fz);
     c->rec_fbx = (double *)(c->rec_ws + L.fbx);
     c->rec_fby = (double *)(c->rec_ws + L.fby);
+    c->rec_fbz = (double *)(c->rec_ws + L.fbz);
     c->rec_qbd = (double *)(c->rec_ws + L.qbd);
     c->rec_sig = (double *)(c->rec_ws + L.sig);
     c->rec_pbar = (double *)(c->rec_ws + L.pbar);
@@ -1125,9 +1131,9 @@ int rmhd_adjoint_step(rmhd_ctx *c, const double *dJ_dcons, int where_in, double 
             stage_ptrs(s, Sq, Sw);
             const double *cq[3] = {Sq[0], Sq[1], S > 2 ? Sq[2] : nullptr};
             const double *cw[3] = {Sw[0], Sw[1], S > 2 ? Sw[2] : nullptr};
-            CK(c, launch_adjoint_step(c->g, c->ph, S > 2 ? 1 : 0, dt, lam, lamn, cq, cw, c->rec_fx, c->rec_fy,
-                                      c->rec_fbx, c->rec_fby, c->rec_qbd, c->rec_lq, c->rec_lr2, c->rec_lr3,
-                                      c->rec_sig, c->stream));
+            double *fl[3] = {c->rec_fx, c->rec_fy, c->rec_fz}, *fbl[3] = {c->rec_fbx, c->rec_fby, c->rec_fbz};
+            CK(c, launch_adjoint_step(c->g, c->ph, S > 2 ? 1 : 0, dt, lam, lamn, cq, cw, fl, fbl, c->rec_qbd,
+                                      c->rec_lq, c->rec_lr2, c->rec_lr3, c->rec_sig, c->stream));
             std::swap(lam, lamn);
         }
     }

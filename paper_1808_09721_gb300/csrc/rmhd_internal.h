@@ -115,8 +115,8 @@ int flux_batch_occupancy(int model, int precision, int tile_x);
 // discrete adjoint (single fluid, FP64): one reverse step, the initial-map
 // adjoint, and a deterministic plane sum
 cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, int scheme, double dt, const double *lam, double *out,
-                                const double *const *Sq, const double *const *Sw, double *fx, double *fy,
-                                double *fbx, double *fby, double *qbd, double *lq, double *lr2, double *lr3,
+                                const double *const *Sq, const double *const *Sw, double *const *f,
+                                double *const *fb, double *qbd, double *lq, double *lr2, double *lr3,
                                 double *sig, cudaStream_t s);
 cudaError_t launch_adjoint_prims(const Grid &g, const Phys &ph, const double *q, const double *w, const double *lam,
                                  double *pbar, cudaStream_t s);

@@ -261,7 +261,9 @@ def test_adjoint_dot_product(env, name, make, nsteps, ckpt):
     Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs)
     lhs = float((Jv * w).sum())
     rhs = float((gp * vp).sum() + gs * vs)
-    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    # round-off of an inner product is relative to the magnitude of its terms
+    mag = max(float(np.abs(Jv * w).sum()), float(np.abs(gp * vp).sum() + abs(gs * vs)))
+    rel = abs(lhs - rhs) / mag
     print(name, "dot-product relative difference", rel)
     assert rel <= 1e-12, (name, lhs, rhs, rel)
 
@@ -308,7 +310,9 @@ def test_adjoint_ssp3_dot_product(env, name, make, nsteps, ckpt):
     Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs, scheme=1)
     lhs = float((Jv * w).sum())
     rhs = float((gp * vp).sum() + gs * vs)
-    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    # round-off of an inner product is relative to the magnitude of its terms
+    mag = max(float(np.abs(Jv * w).sum()), float(np.abs(gp * vp).sum() + abs(gs * vs)))
+    rel = abs(lhs - rhs) / mag
     print(name, "SSP3 dot-product relative difference", rel)
     assert rel <= 1e-12, (name, lhs, rhs, rel)
 
@@ -343,3 +347,59 @@ def test_adjoint_ssp3_finite_differences(env):
         fd = (gJ(wl.prims + h * d, wl.sigma + h * ds) - gJ(wl.prims - h * d, wl.sigma - h * ds)) / (2 * h)
         ad = float((gp * d).sum()) + gs * ds
         assert abs(ad - fd) <= 1e-5 * abs(fd), (seed, ad, fd)
+
+
+TINY3D = [
+    ("random_3d", lambda: WL.random_smooth((4, 5, 6), seed=5, sigma=30.0), 2, 1, 0),
+    ("khi3d", lambda: WL.khi3d(shape=(4, 5, 6), seed=3), 2, 1, 0),
+    ("random_3d_ssp3", lambda: WL.random_smooth((4, 5, 6), seed=6, sigma=30.0), 2, 1, 1),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt,scheme", TINY3D, ids=[c[0] for c in TINY3D])
+def test_adjoint_3d_matches_autodiff_oracle(env, name, make, nsteps, ckpt, scheme):
+    """3-D grids (z fluxes transposed face by face, Gauss's law along z in the
+    initial map): every entry of the GPU gradient and dJ/dsigma against the
+    differentiable oracle's 3-D gradient (pinned to the C oracle's 3-D step)."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = make()
+    lam = np.random.default_rng(25).normal(size=(14,) + wl.prims.shape[1:])
+    s = Sim.from_workload(wl, scheme=scheme)
+    s.record(nsteps, ckpt)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(lam))
+    _, go, gso, _ = A.gradient(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, lam,
+                               scheme=scheme, bcz=wl.bc_z, dz=wl.dz)
+    err = np.abs(gp - go).max() / np.abs(go).max()
+    print(name, "3-D entrywise relative error", err, "dJ/dsigma", gs, gso)
+    assert err <= 1e-9, (name, err)
+    assert abs(gs - gso) <= 1e-9 * abs(gso) + 1e-12 * np.abs(go).max(), (name, gs, gso)
+
+
+def test_adjoint_3d_dot_product(env):
+    """<J v, w> = <v, J^T w> on a 3-D grid."""
+    A = pytest.importorskip("oracle.autodiff_sf")
+    torch, Sim, _ = env
+    wl = WL.random_smooth((4, 5, 6), seed=7, sigma=30.0)
+    nsteps = 2
+    rng = np.random.default_rng(37)
+    w = rng.normal(size=(14,) + wl.prims.shape[1:])
+    vp = rng.normal(size=wl.prims.shape) * np.abs(wl.prims).reshape(11, -1).max(axis=1).clip(1e-2)[
+        (slice(None),) + (None,) * (wl.prims.ndim - 1)]
+    vs = 0.1 * wl.sigma
+    s = Sim.from_workload(wl)
+    s.record(nsteps, 1)
+    s.step(wl.dt, nsteps)
+    s.check()
+    gp, gs = s.adjoint(np.ascontiguousarray(w))
+    Jv = A.jvp(wl.prims, wl.sigma, wl.dt, nsteps, wl.gamma, wl.bc_x, wl.bc_y, wl.dx, wl.dy, vp, vs,
+               bcz=wl.bc_z, dz=wl.dz)
+    lhs = float((Jv * w).sum())
+    rhs = float((gp * vp).sum() + gs * vs)
+    # round-off of an inner product is relative to the magnitude of its terms
+    mag = max(float(np.abs(Jv * w).sum()), float(np.abs(gp * vp).sum() + abs(gs * vs)))
+    rel = abs(lhs - rhs) / mag
+    print("3-D dot-product relative difference", rel)
+    assert rel <= 1e-12, (lhs, rhs, rel)

@@ -72,13 +72,14 @@ def test_ssp3_mixed_precision(Sim):
     assert np.all(l1 <= 1e-4), l1
 
 
-def test_ssp3_adjoint_refused(Sim):
-    """The discrete adjoint reverses SSP2(222) steps only: arming it on an
-    SSP3(332) context is an error, and the context stays usable."""
+def test_adjoint_refused_outside_its_scope(Sim):
+    """The discrete adjoint covers the single-fluid FP64 step (both schemes):
+    arming it on a mixed-precision or two-fluid SSP3(332) context is an error,
+    and the context stays usable."""
     from paper_1808_09721_gb300 import _lib as L
-    wl = WL.field_loop(n=8, nsteps=2)
-    s = Sim.from_workload(wl, scheme=1)
-    with pytest.raises(L.RmhdError):
-        s.record(2, 1)
-    s.step(wl.dt, 1)
-    s.check()
+    for wl, prec in ((WL.field_loop(n=8, nsteps=2), 1), (WL.tf_sheet(n=8, seed=1), 0)):
+        s = Sim.from_workload(wl, scheme=1, precision=prec)
+        with pytest.raises(L.RmhdError):
+            s.record(2, 1)
+        s.step(wl.dt, 1)
+        s.check()
