@@ -30,13 +30,15 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
 // ---------------------------------------------------------------- stage
 // 5 blocks per SM (at most 96 registers): the solve is latency-bound, and
 // 20 warps per SM hide more of its FP64 and MUFU latency than 16 (no spills)
+// STATS: instantiation that also fills the iteration histogram a.hist
+template <bool STATS>
 __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace sf;
     sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const double pw = a.wwarm[P * g.plane + cell];
-        const int st = stage_solve<kNRef>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
+        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
         record(a.status, st, cell);
     }
 }
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, 
 static constexpr int kStageThreadsTF = 64;
 // 8 blocks per SM (at most 128 registers, a 32-byte spill): 16 warps per SM
 // instead of 8 hide the latency of the 7-unknown solve (measured 18% faster)
+template <bool STATS>
 __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace tf;
     __shared__ float sJ[49 * kStageThreadsTF], sM[49 * kStageThreadsTF];
@@ -54,7 +57,8 @@ __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph
     tf::StageConst k{a.adt, cpsi, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
-        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm, Minv);
+        const int st =
+            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm, Minv);
         record(a.status, st, cell);
     }
 }
@@ -67,8 +71,14 @@ static int grid_for(long long n, int threads) {
 cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageArgs &a, cudaStream_t s) {
     double cpsi = 1.0 / (1.0 + a.adt * ph.kappa);
     int blocks = grid_for(g.ncell, kStageThreads);
-    if (model == 0) k_stage_sf<<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
-    else k_stage_tf<<<grid_for(g.ncell, kStageThreadsTF), kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
+    const int btf = grid_for(g.ncell, kStageThreadsTF);
+    if (model == 0) {
+        if (a.hist) k_stage_sf<true><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+        else k_stage_sf<false><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+    } else {
+        if (a.hist) k_stage_tf<true><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
+        else k_stage_tf<false><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
+    }
     return cudaGetLastError();
 }
 
@@ -76,17 +86,20 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
 // One thread per packed cell; the run's a_ii dt, 1/(1 + a_ii dt kappa) and
 // conductivity come from the per-run tables.
 // the block size is the autotuner's choice: cap registers as k_stage_sf's bounds do
+template <bool STATS>
 __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
     using namespace sf;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const int run = b.run_of[cell];
         sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
+        const int st =
+            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
         record(a.status, st, cell);
     }
 }
 
+template <bool STATS>
 __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
     using namespace tf;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
@@ -97,8 +110,8 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
         pr.eta = b.eta[run];
         tf::StageConst k{b.adt[run], b.cpsi[run], a.maxpass > 0 ? a.maxpass : 8, a.hist};
         float jl[49], ml[49];
-        const int st = stage_solve<kNRef>(a.r + cell, g.plane, a.wwarm + cell, k, pr, a.q + cell, a.w + cell,
-                                          tf::Mat{jl, 1}, tf::Mat{ml, 1});
+        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm + cell, k, pr, a.q + cell, a.w + cell,
+                                                 tf::Mat{jl, 1}, tf::Mat{ml, 1});
         record(a.status, st, cell);
     }
 }
@@ -106,8 +119,13 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
 cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const StageArgs &a, const BatchArgs &b,
                                int threads, cudaStream_t s) {
     int blocks = grid_for(g.ncell, threads);
-    if (model == 0) k_stage_batch_sf<<<blocks, threads, 0, s>>>(g, ph, a, b);
-    else k_stage_batch_tf<<<blocks, threads, 0, s>>>(g, ph, a, b);
+    if (model == 0) {
+        if (a.hist) k_stage_batch_sf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
+        else k_stage_batch_sf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
+    } else {
+        if (a.hist) k_stage_batch_tf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
+        else k_stage_batch_tf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
+    }
     return cudaGetLastError();
 }
 

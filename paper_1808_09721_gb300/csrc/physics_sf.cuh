@@ -176,8 +176,11 @@ __device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, i
 // through qp) and w = (v, p, W) (through wp), ps apart. NREF FP64 passes.
 // The FP64 inputs of the refinement passes are read again after the FP32
 // Newton phase instead of being held in registers through it (they are in
-// L1), which keeps the kernel at a higher occupancy.
-template <int NREF>
+// L1), which keeps the kernel at a higher occupancy. STATS adds the solve to
+// the iteration histogram k.hist; it is a template switch rather than a null
+// test because the live counters lengthen the latency-bound code even when
+// nothing is counted.
+template <int NREF, bool STATS = false>
 __device__ int stage_solve(const double *rp, long long ps, double p_warm, const StageConst &k, double *qp,
                            double *wp) {
     const double gm1 = k.gamma - 1.0, gam = k.gamma;
@@ -289,7 +292,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     // while G's own terms carry a dt sigma W: for stiff cells (a dt sigma W >> 1)
     // the tolerance shrinks by that factor, down to a few units of FP64
     // round-off of G's terms. Non-stiff cells keep 1e-12.
-    const double tolg = f64_of(fmaxf(1e-12f / (1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
+    const double tolg = f64_of(fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
     // FP64 inputs, read again (the stores above keep the compiler from reusing
     // the first loads' registers)
     const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
@@ -302,7 +305,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     double St64[3], a64, S264, G64[3], v64[3], W64;
     double gres = 0.0;
     int pass = 0;
-    for (; pass < k.maxpass; ++pass) {
+    for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
         em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
         pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
@@ -311,7 +314,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
-        if (pass == k.maxpass - 1) break;
+        if (pass == 7 || pass == k.maxpass - 1) break;
         // first-order prediction of the pressure at the corrected E
         pdd -= f64_of(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
         Ed[0] -= f64_of(dE[0]);
@@ -326,7 +329,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
-    count_solve(k.hist, nit, pass + 1);
+    if constexpr (STATS) count_solve(k.hist, nit, pass + 1);
     if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
     return ST_OK;
 }

@@ -322,7 +322,7 @@ __device__ __forceinline__ void load_cell(Cell<double> &c, const double *rp, lon
 // are the caller's 7 x 7 FP32 scratch for the Jacobian and its inverse. The
 // FP64 cell data are built again after the FP32 Newton phase rather than held
 // in registers through it.
-template <int NREF>
+template <int NREF, bool STATS = false>
 __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, const StageConst &k,
                            const Phys &ph, double *qp, double *wp, Mat Jm, Mat Minv) {
     const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
@@ -433,14 +433,14 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
     double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
     double gres = 0.0;
     int pass = 0;
-    for (; pass < k.maxpass; ++pass) {
+    for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
         split_x(c, xd, St64, a64, S264);
         for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
         stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
         gres = 0.0;
         for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
         if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
-        if (pass == k.maxpass - 1) break;
+        if (pass == 7 || pass == k.maxpass - 1) break;
         float Gf[7], dx[7];
         for (int i = 0; i < 7; ++i) Gf[i] = f32_of(G64[i]);
         for (int i = 0; i < 7; ++i) {
@@ -469,7 +469,7 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
         qp[(EX + i) * ps] = xd[4 + i];
     }
     qp[TAUB * ps] = xd[3] * c.mur;
-    sf::count_solve(k.hist, nit, pass + 1);
+    if constexpr (STATS) sf::count_solve(k.hist, nit, pass + 1);
     if (!ok || !(gres <= 1e-9 * f64_of(gs))) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
