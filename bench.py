@@ -37,16 +37,18 @@ if ROOT not in sys.path:
 
 METRIC = "cell-updates/s per IMEX step, FP64 vs mixed, % HBM roofline; adjoint/fwd cost"
 UNIT = "cell-updates/s"
-WORKLOAD = "khi-2d-1024x1024 (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=4/3, sigma=1e3, SSP2(222), WENO3+LF)"
+def workload_name(n: int = 1024) -> str:
+    return (f"khi-2d-{n}x{n} (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=4/3, sigma=1e3, SSP2(222), "
+            "WENO3+LF)")
 
 # FP64 arithmetic instructions (add, mul, fma; one op each) per interior cell
 # for each kernel of the FP64 form on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
 # The FP64 pipe issues 2 of them per clock per SM, which sets the ALU peak.
-FP64_OPS_PER_CELL = {"stage": 174.0, "flux1": 738.4, "flux2": 710.4}
+FP64_OPS_PER_CELL = {"stage": 173.0, "flux1": 738.4, "flux2": 710.4}
 # DRAM bytes (read + write) per cell and launch of the same kernels, from the
 # ncu launch list of the KHI 1024^2 bench (dram__bytes_read.sum + write.sum).
-DRAM_BYTES_PER_CELL = {"stage": 223.1, "flux1": 448.0, "flux2": 386.9}
+DRAM_BYTES_PER_CELL = {"stage": 223.1, "flux1": 448.0, "flux2": 387.1}
 # Algorithmic HBM bytes per cell for each kernel (read once + written once).
 BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
 
@@ -213,7 +215,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "96x96 window of the same recipe per step"},
+            "config": {"workload": workload_name(), "sample": "96x96 window of the same recipe per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
                              "sample": f"KHI recipe 96x96 periodic, one SSP2(222) step per bench step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -517,7 +519,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms64 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "cells_per_gpu": wl.cells, "parallelism": f"replicas x{world}",
+                "config": {"workload": workload_name(args.n), "cells_per_gpu": wl.cells, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2: state+workspace %.2f GB > 129 MB" %
                                  (sim64.workspace.numel() / 1e9)},
                 "mixed": {"value": value_mx, "ms_per_step": msmx / K, "dtype": "f32 flux / f64 source",
