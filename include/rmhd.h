@@ -12,7 +12,13 @@
  *     a[v][j][i] at a[(v * ny + j) * nx + i], interior cells only (no ghosts).
  *   - `where` selects RMHD_HOST (pageable or pinned host memory) or
  *     RMHD_DEVICE (memory of the context's GPU). The caller keeps ownership of
- *     every array it passes; the library copies and never keeps the pointer.
+ *     every array it passes; the library never keeps the pointer. The state
+ *     and primitive calls (set/get prims, cons, state) read and write device
+ *     arrays and page-locked host arrays (cudaHostAlloc, cudaHostRegister,
+ *     pinned torch tensors) in place from their kernels, host arrays over the
+ *     host-GPU link; pageable host arrays go through a staging copy. A
+ *     RMHD_DEVICE pointer that is not device memory of the context's device
+ *     fails with RMHD_ERR_INVALID.
  *   - All device work is issued on the CUDA stream given to rmhd_create. Calls
  *     marked "async" return after enqueueing; the calls that read results back
  *     synchronise that stream first.
@@ -112,7 +118,11 @@ const char *rmhd_last_error(const rmhd_ctx *ctx);
  * Errors: RMHD_ERR_INVALID (inadmissible state; message names the first cell). */
 int rmhd_set_prims(rmhd_ctx *ctx, const double *prims, int where);
 
-/* Primitives of the current state in the same layout. Synchronous. */
+/* Primitives of the current state in the same layout. After a step they are
+ * recovered from the conserved state (Sec. 2.1.3) in the same pass that
+ * writes the output. Synchronous. Errors: RMHD_ERR_STATE (no state),
+ * RMHD_ERR_C2P (some cell has no primitives; message names the first one;
+ * the contents of `prims` are then unspecified), RMHD_ERR_INVALID, RMHD_ERR_CUDA. */
 int rmhd_get_prims(rmhd_ctx *ctx, double *prims, int where);
 
 /* Conserved state [N_c][ny][nx]; set_cons recovers the primitives

@@ -291,35 +291,49 @@ cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const dou
 }
 
 // ---------------------------------------------------------------- state -> user primitives
-__global__ void k_get_prims_sf(Grid g, const double *q, const double *w, double *U) {
+// User primitives of one cell from its conserved values q(v) and stored
+// primitives w(v) (accessors), written to the dense layout U[var * n + cell].
+template <class QF, class WF>
+__device__ __forceinline__ void emit_prims_sf(QF q, WF w, double *U, long long n, long long cell) {
     using namespace sf;
+    U[0 * n + cell] = q(D) * s_rcp(w(LOR));  // rho = D / W
+    U[1 * n + cell] = w(VX);
+    U[2 * n + cell] = w(VY);
+    U[3 * n + cell] = w(VZ);
+    U[4 * n + cell] = w(P);
+    for (int k = 0; k < 6; ++k) U[(5 + k) * n + cell] = q(BX + k);
+}
+
+template <class QF, class WF>
+__device__ __forceinline__ void emit_prims_tf(QF q, WF w, const Phys &ph, double *U, long long n, long long cell) {
+    using namespace tf;
+    const double Dt = q(D), Db = q(DB);
+    const double Ds[2] = {(Db - ph.mu_p * Dt) * ph.inv_dmu, (ph.mu_e * Dt - Db) * ph.inv_dmu};
+    for (int s = 0; s < 2; ++s) {
+        const double v[3] = {w(5 * s), w(5 * s + 1), w(5 * s + 2)};
+        const double om = 1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        U[(5 * s) * n + cell] = Ds[s] * (om * s_rsqrt(om));  // rho_s = D_s / W_s
+        for (int k = 0; k < 3; ++k) U[(5 * s + 1 + k) * n + cell] = v[k];
+        U[(5 * s + 4) * n + cell] = w(5 * s + P);
+    }
+    for (int k = 0; k < 6; ++k) U[(10 + k) * n + cell] = q(BX + k);
+}
+
+__global__ void k_get_prims_sf(Grid g, const double *q, const double *w, double *U) {
     const long long n = g.ncell;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
-        U[0 * n + cell] = q[D * g.plane + cell] * s_rcp(w[LOR * g.plane + cell]);
-        U[1 * n + cell] = w[VX * g.plane + cell];
-        U[2 * n + cell] = w[VY * g.plane + cell];
-        U[3 * n + cell] = w[VZ * g.plane + cell];
-        U[4 * n + cell] = w[P * g.plane + cell];
-        for (int k = 0; k < 6; ++k) U[(5 + k) * n + cell] = q[(BX + k) * g.plane + cell];
+        emit_prims_sf([&](int v) { return q[v * g.plane + cell]; }, [&](int v) { return w[v * g.plane + cell]; }, U,
+                      n, cell);
     }
 }
 
 __global__ void k_get_prims_tf(Grid g, Phys ph, const double *q, const double *w, double *U) {
-    using namespace tf;
     const long long n = g.ncell;
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
-        double Dt = q[D * g.plane + cell], Db = q[DB * g.plane + cell];
-        double Ds[2] = {(Db - ph.mu_p * Dt) * ph.inv_dmu, (ph.mu_e * Dt - Db) * ph.inv_dmu};
-        for (int s = 0; s < 2; ++s) {
-            double v[3] = {w[(5 * s) * g.plane + cell], w[(5 * s + 1) * g.plane + cell], w[(5 * s + 2) * g.plane + cell]};
-            const double om = 1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            U[(5 * s) * n + cell] = Ds[s] * (om * s_rsqrt(om));  // rho_s = D_s / W_s
-            for (int k = 0; k < 3; ++k) U[(5 * s + 1 + k) * n + cell] = v[k];
-            U[(5 * s + 4) * n + cell] = w[(5 * s + P) * g.plane + cell];
-        }
-        for (int k = 0; k < 6; ++k) U[(10 + k) * n + cell] = q[(BX + k) * g.plane + cell];
+        emit_prims_tf([&](int v) { return q[v * g.plane + cell]; }, [&](int v) { return w[v * g.plane + cell]; }, ph,
+                      U, n, cell);
     }
 }
 
@@ -332,8 +346,12 @@ cudaError_t launch_get_prims(int model, const Grid &g, const Phys &ph, const dou
 }
 
 // ---------------------------------------------------------------- recovery
-__global__ void k_recover(int model, Grid g, Phys ph, const double *q, double *w, int *status) {
-    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
+// Primitives of q (cold start) into w; with U set, the user primitives of the
+// recovered state too (the output of get_prims in one pass, so the recovery
+// overlaps the writes when U is host memory).
+__global__ void k_recover(int model, Grid g, Phys ph, const double *q, double *w, double *U, int *status) {
+    const long long n = g.ncell;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
          cell += (long long)gridDim.x * blockDim.x) {
         if (model == 0) {
             double qc[sf::NC], wc[sf::NW];
@@ -342,6 +360,7 @@ __global__ void k_recover(int model, Grid g, Phys ph, const double *q, double *w
             int st = sf::recover(qc, -1.0, ph.gamma, wc);
             record(status, st, cell);
             for (int v = 0; v < sf::NW; ++v) w[v * g.plane + cell] = wc[v];
+            if (U) emit_prims_sf([&](int v) { return qc[v]; }, [&](int v) { return wc[v]; }, U, n, cell);
         } else {
             double qc[tf::NC], wc[tf::NW], wo[tf::NW];
             for (int v = 0; v < tf::NC; ++v) qc[v] = q[v * g.plane + cell];
@@ -349,13 +368,14 @@ __global__ void k_recover(int model, Grid g, Phys ph, const double *q, double *w
             int st = tf::recover(qc, wo, ph, wc);
             record(status, st, cell);
             for (int v = 0; v < tf::NW; ++v) w[v * g.plane + cell] = wc[v];
+            if (U) emit_prims_tf([&](int v) { return qc[v]; }, [&](int v) { return wc[v]; }, ph, U, n, cell);
         }
     }
 }
 
 cudaError_t launch_recover(int model, const Grid &g, const Phys &ph, const double *q, double *w, int *status,
-                           cudaStream_t s) {
-    k_recover<<<grid_for(g.ncell, 128), 128, 0, s>>>(model, g, ph, q, w, status);
+                           cudaStream_t s, double *prims) {
+    k_recover<<<grid_for(g.ncell, 128), 128, 0, s>>>(model, g, ph, q, w, prims, status);
     return cudaGetLastError();
 }
 

@@ -380,15 +380,76 @@ static int stage_out(rmhd_ctx *c, double *dst, int nvar, int where) {
     return RMHD_OK;
 }
 
+// Address at which this context's kernels can read or write a caller's buffer
+// in place: a device buffer on the context's device as it is; page-locked
+// host memory (cudaHostAlloc, cudaHostRegister, torch pinned tensors) through
+// its mapping into the device's address space, so the kernels stream it over
+// the host link with no staging copy. Null for pageable host memory, which
+// goes through the staging buffer. A RMHD_DEVICE pointer that is not device
+// memory of this device is an error (*bad set).
+static void *device_view(const rmhd_ctx *c, const void *p, int where, bool *bad) {
+    *bad = false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        *bad = where == RMHD_DEVICE;
+        return nullptr;
+    }
+    if (where == RMHD_DEVICE) {
+        if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != c->device) {
+            *bad = true;
+            return nullptr;
+        }
+        return const_cast<void *>(p);
+    }
+    // page-locked memory is mapped at its host address under unified
+    // addressing; anything else is staged
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p ? a.devicePointer : nullptr;
+}
+
+// Device-readable view of a caller's input [nvar][cells]: the buffer itself
+// where the device can address it, else the staging buffer after a copy.
+static int input_view(rmhd_ctx *c, const double *src, int nvar, int where, const double **view, const char *what) {
+    bool bad;
+    if (void *d = device_view(c, src, where, &bad)) {
+        *view = static_cast<const double *>(d);
+        return RMHD_OK;
+    }
+    if (bad) return fail(c, RMHD_ERR_INVALID, "%s: RMHD_DEVICE pointer is not device memory of this context's device", what);
+    int st = stage_in(c, src, nvar, where);
+    *view = c->stage_buf;
+    return st;
+}
+
+// Where an output kernel writes a caller's buffer: in place where the device
+// can address it, else the staging buffer (finish_output copies it out).
+static int output_view(rmhd_ctx *c, double *dst, int where, double **view, const char *what) {
+    bool bad;
+    void *d = device_view(c, dst, where, &bad);
+    if (bad) return fail(c, RMHD_ERR_INVALID, "%s: RMHD_DEVICE pointer is not device memory of this context's device", what);
+    *view = d ? static_cast<double *>(d) : c->stage_buf;
+    return RMHD_OK;
+}
+// Completes an output written through output_view: the copy out of the
+// staging buffer if one was used, then the stream is synchronised.
+static int finish_output(rmhd_ctx *c, double *dst, const double *view, int nvar) {
+    if (view == c->stage_buf)
+        CK(c, cudaMemcpyAsync(dst, c->stage_buf, (size_t)nvar * c->g.ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return RMHD_OK;
+}
+
 int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_prims: bad argument");
     int np = model_np(c->cfg.model);
-    int st = stage_in(c, prims, np, where);
+    const double *src;
+    int st = input_view(c, prims, np, where, &src, "set_prims");
     if (st) return st;
     if (c->batch)
-        CK(c, launch_set_prims_batch(c->cfg.model, c->g, c->ph, c->bargs, c->stage_buf, c->Q, c->W, c->status, c->stream));
+        CK(c, launch_set_prims_batch(c->cfg.model, c->g, c->ph, c->bargs, src, c->Q, c->W, c->status, c->stream));
     else
-        CK(c, launch_set_prims(c->cfg.model, c->g, c->ph, c->stage_buf, c->Q, c->W, c->status, c->stream));
+        CK(c, launch_set_prims(c->cfg.model, c->g, c->ph, src, c->Q, c->W, c->status, c->stream));
     st = read_status(c, "set_prims");
     if (st) return st;
     c->has_state = true;
@@ -414,26 +475,43 @@ static int ensure_prims(rmhd_ctx *c, const char *what) {
 int rmhd_get_prims(rmhd_ctx *c, double *prims, int where) {
     if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_prims: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_prims: no state (call rmhd_set_prims first)");
-    int st0 = ensure_prims(c, "get_prims");
-    if (st0) return st0;
-    CK(c, launch_get_prims(c->cfg.model, c->g, c->ph, c->Q, c->W, c->stage_buf, c->stream));
-    return stage_out(c, prims, model_np(c->cfg.model), where);
+    const int np = model_np(c->cfg.model);
+    double *out;
+    int st = output_view(c, prims, where, &out, "get_prims");
+    if (st) return st;
+    if (!c->w_stale) {
+        CK(c, launch_get_prims(c->cfg.model, c->g, c->ph, c->Q, c->W, out, c->stream));
+        return finish_output(c, prims, out, np);
+    }
+    // recovery and output in one kernel; the status is read after the copy
+    CK(c, launch_recover(c->cfg.model, c->g, c->ph, c->Q, c->W, c->status, c->stream, out));
+    if (out == c->stage_buf)
+        CK(c, cudaMemcpyAsync(prims, c->stage_buf, (size_t)np * c->g.ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+    st = read_status(c, "get_prims");
+    if (st) return st;
+    c->w_stale = false;
+    return RMHD_OK;
 }
 
 int rmhd_get_cons(rmhd_ctx *c, double *cons, int where) {
     if (!c || !cons || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_cons: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_cons: no state (call rmhd_set_prims first)");
     int nc = model_nc(c->cfg.model);
-    CK(c, launch_unpack(c->g, nc, c->Q, c->stage_buf, c->stream));
-    return stage_out(c, cons, nc, where);
+    double *out;
+    int st = output_view(c, cons, where, &out, "get_cons");
+    if (st) return st;
+    CK(c, launch_unpack(c->g, nc, c->Q, out, c->stream));
+    return finish_output(c, cons, out, nc);
 }
 
 int rmhd_set_cons(rmhd_ctx *c, const double *cons, int where) {
     if (!c || !cons || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_cons: bad argument");
     int nc = model_nc(c->cfg.model);
-    int st = stage_in(c, cons, nc, where);
+    const double *src;
+    int st = input_view(c, cons, nc, where, &src, "set_cons");
     if (st) return st;
-    CK(c, launch_pack(c->g, nc, c->stage_buf, c->Q, c->stream));
+    CK(c, launch_pack(c->g, nc, src, c->Q, c->stream));
     CK(c, launch_recover(c->cfg.model, c->g, c->ph, c->Q, c->W, c->status, c->stream));
     st = read_status(c, "set_cons");
     if (st) return st;
@@ -452,22 +530,33 @@ int rmhd_get_state(rmhd_ctx *c, double *state, int where) {
     if (!c || !state || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "get_state: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "get_state: no state (call rmhd_set_prims first)");
     const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    double *out;
+    int st = output_view(c, state, where, &out, "get_state");
+    if (st) return st;
+    if (out != c->stage_buf) {  // both parts in place
+        CK(c, launch_unpack(c->g, nc, c->Q, out, c->stream));
+        CK(c, launch_unpack(c->g, nw, c->W, out + (size_t)nc * c->g.ncell, c->stream));
+        return finish_output(c, state, out, nc + nw);
+    }
+    // the staging buffer holds one part at a time
     CK(c, launch_unpack(c->g, nc, c->Q, c->stage_buf, c->stream));
-    int st = stage_out(c, state, nc, where);
+    st = finish_output(c, state, c->stage_buf, nc);
     if (st) return st;
     CK(c, launch_unpack(c->g, nw, c->W, c->stage_buf, c->stream));
-    return stage_out(c, state + (size_t)nc * c->g.ncell, nw, where);
+    return finish_output(c, state + (size_t)nc * c->g.ncell, c->stage_buf, nw);
 }
 
 int rmhd_set_state(rmhd_ctx *c, const double *state, int where) {
     if (!c || !state || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_state: bad argument");
     const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
-    int st = stage_in(c, state, nc, where);
+    const double *src;
+    int st = input_view(c, state, nc, where, &src, "set_state");
     if (st) return st;
-    CK(c, launch_pack(c->g, nc, c->stage_buf, c->Q, c->stream));
-    st = stage_in(c, state + (size_t)nc * c->g.ncell, nw, where);  // same stream: after the pack above
+    CK(c, launch_pack(c->g, nc, src, c->Q, c->stream));
+    // same stream: a staged second part overwrites the staging buffer after the pack above
+    st = input_view(c, state + (size_t)nc * c->g.ncell, nw, where, &src, "set_state");
     if (st) return st;
-    CK(c, launch_pack(c->g, nw, c->stage_buf, c->W, c->stream));
+    CK(c, launch_pack(c->g, nw, src, c->W, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->has_state = true;
     c->fresh_prims = false;

@@ -90,9 +90,10 @@ cudaError_t launch_set_prims(int model, const Grid &g, const Phys &ph, const dou
 // internal state -> primitives in the user layout
 cudaError_t launch_get_prims(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
                              double *prims, cudaStream_t s);
-// conserved -> internal primitives (recovery), warm-started from w
+// conserved -> internal primitives (recovery, cold start) into w; with prims
+// set, also the primitives in the user layout (as launch_get_prims writes them)
 cudaError_t launch_recover(int model, const Grid &g, const Phys &ph, const double *q, double *w, int *status,
-                           cudaStream_t s);
+                           cudaStream_t s, double *prims = nullptr);
 // copy between the user layout [v][ny][nx] and the padded device layout
 cudaError_t launch_pack(const Grid &g, int nvar, const double *user, double *dev, cudaStream_t s);
 cudaError_t launch_unpack(const Grid &g, int nvar, const double *dev, double *user, cudaStream_t s);
