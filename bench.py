@@ -256,7 +256,7 @@ def main():
     if world > 1:
         dist.barrier()
     B.build()
-    from paper_1808_09721_gb300 import FP64, MIXED, HOST
+    from paper_1808_09721_gb300 import FP64, MIXED, FLOATFLOAT, HOST
     from paper_1808_09721_gb300 import workloads as WL
     from paper_1808_09721_gb300.sim import Sim
 
@@ -306,10 +306,18 @@ def main():
     q64, qmx = sim64.cons(), simmx.cons()
     rel_l1_mixed = float(np.max(np.abs(qmx - q64).reshape(14, -1).mean(axis=1) / natural_scale(0, q64)))
     del simmx
+    # float-float flux form: FP64-class accuracy from the FP32 pipes
+    simff, msff, ktff = timed_run(FLOATFLOAT, True)
+    qff = simff.cons()
+    dff = np.abs(qff - q64).reshape(14, -1)
+    rel_linf_ff = float(np.max(dff.max(axis=1) / natural_scale(0, q64)))
+    rel_l1_ff = float(np.max(dff.mean(axis=1) / natural_scale(0, q64)))
+    del simff
 
     total_cells = world * wl.cells
     value = total_cells * K / (ms64 * 1e-3)
     value_mx = total_cells * K / (msmx * 1e-3)
+    value_ff = total_cells * K / (msff * 1e-3)
 
     # the other single-grid workloads: two-fluid current sheet 512^2 (FP64 and
     # mixed) and the 1-D Brio-Wu tube (400 cells, launch-bound, 100 steps)
@@ -510,6 +518,7 @@ def main():
     step_bytes = 1056.0  # algorithmic HBM bytes per cell-update of the whole step
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt64.items()}
     kernels_mx = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in ktmx.items()}
+    kernels_ff = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in ktff.items()}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -524,6 +533,9 @@ def main():
                                  (sim64.workspace.numel() / 1e9)},
                 "mixed": {"value": value_mx, "ms_per_step": msmx / K, "dtype": "f32 flux / f64 source",
                           "rel_l1_vs_fp64": rel_l1_mixed, "speedup_vs_fp64": value_mx / value, "kernels": kernels_mx},
+                "floatfloat": {"value": value_ff, "ms_per_step": msff / K, "dtype": "f32x2 flux / f64 source",
+                               "rel_linf_vs_fp64": rel_linf_ff, "rel_l1_vs_fp64": rel_l1_ff,
+                               "speedup_vs_fp64": value_ff / value, "kernels": kernels_ff},
                 "hbm_roofline_step": {"bytes_per_cell_update": step_bytes,
                                       "achieved_gbs": step_bytes * value / world / 1e9,
                                       "frac": step_bytes * value / world / 1e9 / hbm_gbs},

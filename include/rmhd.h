@@ -59,6 +59,10 @@ extern "C" {
 #define RMHD_FP64 0  /* everything in FP64 */
 #define RMHD_MIXED 1 /* WENO3/flux arithmetic in FP32 with FP64 accumulation of the update;
                         the implicit source solve, primitive recovery and current J stay FP64 */
+#define RMHD_FLOATFLOAT 2 /* WENO3/flux arithmetic in float-float (pairs of FP32 numbers, ~48
+                             significant bits, on the FP32 pipes), the rest as RMHD_MIXED; one
+                             fluid, single grids (1-D, 2-D, 3-D) only. Agrees with RMHD_FP64 to
+                             ~1e-13 relative while the state stays inside FP32's range */
 
 /* memory kinds for `where` */
 #define RMHD_HOST 0
@@ -79,7 +83,7 @@ typedef struct rmhd_config {
     double kappa;     /* divergence-cleaning rate, 1 in the paper (Sec. 2.1.1) */
     double cfl;       /* dt = cfl * min(dx, dy, dz) when rmhd_imex_step gets dt <= 0 */
     int bc_x, bc_y;   /* RMHD_OUTFLOW or RMHD_PERIODIC */
-    int precision;    /* RMHD_FP64 or RMHD_MIXED */
+    int precision;    /* RMHD_FP64, RMHD_MIXED or RMHD_FLOATFLOAT */
     int scheme;       /* RMHD_SSP2 (0, Table 1) or RMHD_SSP3 (1, Table 2); batches: RMHD_SSP2 */
     int nz;           /* cells along z; 0 or 1: a 1-D or 2-D grid. nz > 1 (3-D) needs ny > 1 and a
                          single grid (not a batch); arrays are then [n_var][nz][ny][nx] */

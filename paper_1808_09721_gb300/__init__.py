@@ -5,7 +5,7 @@ The compute path is the CUDA library librmhd.so (C ABI in include/rmhd.h);
 this package only builds it, marshals arguments (`_lib`, `sim.Sim`) and
 provides seeded synthetic workloads (`workloads`).
 """
-from ._lib import (DEVICE, FP64, HOST, MIXED, OUTFLOW, PERIODIC, RESISTIVE, SSP2, SSP3, TWO_FLUID,  # noqa: F401
+from ._lib import (DEVICE, FLOATFLOAT, FP64, HOST, MIXED, OUTFLOW, PERIODIC, RESISTIVE, SSP2, SSP3, TWO_FLUID,  # noqa: F401
                    RmhdError)
 
 

@@ -17,7 +17,7 @@ ERRORS = {-1: "RMHD_ERR_INVALID", -2: "RMHD_ERR_CUDA", -3: "RMHD_ERR_NEWTON", -4
           -5: "RMHD_ERR_STATE", -6: "RMHD_ERR_NOMEM"}
 RESISTIVE, TWO_FLUID = 0, 1
 OUTFLOW, PERIODIC = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, FLOATFLOAT = 0, 1, 2
 SSP2, SSP3 = 0, 1  # IMEX integrators of Tables 1 and 2
 HOST, DEVICE = 0, 1
 

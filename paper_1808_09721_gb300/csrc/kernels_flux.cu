@@ -40,6 +40,7 @@
 #include "rmhd_internal.h"
 #include "physics_sf.cuh"
 #include "physics_tf.cuh"
+#include "ffloat.cuh"
 
 namespace rmhd {
 
@@ -238,17 +239,18 @@ template <class M, int TX, int TY, int G, class FT, int NOUT>
 struct FluxSmem {
     static constexpr int NC = M::NC, NW = M::NW, NV = NC + NW;
     static constexpr int SW = TX + 4, SH = TY > 1 ? TY + 4 : 1, SN = SW * SH, NL = TX * TY;
-    // FP32 form: only an FP32 copy of the staged state is kept (converted once
-    // per staged value); the FP64 current and sources are computed from the
-    // loaded doubles while staging, and the auxiliaries are kept in FP32
-    static constexpr bool SHADOW = sizeof(FT) < sizeof(double);
+    // FP32 and float-float forms: only a copy of the staged state in FT is
+    // kept (converted once per staged value); the FP64 current and sources are
+    // computed from the loaded doubles while staging, and the auxiliaries are
+    // kept in FT
+    static constexpr bool SHADOW = !std::is_same<FT, double>::value;
     // interior cells' sources through global scratch (FluxArgs::srcg) instead of shared memory
     static constexpr bool SRCG = M::SRCG && !SHADOW && TY > 1;
     // byte offsets
     static constexpr size_t st = 0;
     static constexpr size_t st32 = st + (SHADOW ? 0 : sizeof(double) * NV * SN);
-    static constexpr size_t aux = st32 + (SHADOW ? sizeof(float) * NV * SN : 0);
-    static constexpr size_t src = aux + (SHADOW ? sizeof(float) : sizeof(double)) * M::NAUX * SN;
+    static constexpr size_t aux = st32 + (SHADOW ? sizeof(FT) * NV * SN : 0);
+    static constexpr size_t src = aux + (SHADOW ? sizeof(FT) : sizeof(double)) * M::NAUX * SN;
     static constexpr size_t fl = src + (SRCG ? 0 : sizeof(double) * M::NS * NL);
     static constexpr size_t hp = fl + sizeof(FT) * M::NGEN * SN;
     static constexpr size_t fc = hp + sizeof(FT) * 4 * G * SN;
@@ -609,8 +611,10 @@ static cudaError_t launch_flux_n(int nout, const Grid &g, const Phys &ph, const 
 cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                         cudaStream_t s) {
     if (model == 0)
-        return precision == 0 ? launch_flux_n<SFModel, double>(nout, g, ph, a, s)
-                              : launch_flux_n<SFModel, float>(nout, g, ph, a, s);
+        return precision == 0   ? launch_flux_n<SFModel, double>(nout, g, ph, a, s)
+               : precision == 2 ? launch_flux_n<SFModel, ff>(nout, g, ph, a, s)
+                                : launch_flux_n<SFModel, float>(nout, g, ph, a, s);
+    if (precision == 2) return cudaErrorInvalidValue;  // float-float: one fluid only
     return precision == 0 ? launch_flux_n<TFModel, double>(nout, g, ph, a, s)
                           : launch_flux_n<TFModel, float>(nout, g, ph, a, s);
 }
@@ -676,8 +680,10 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
 cudaError_t launch_flux_3d(int model, int precision, int nout, const Grid &g, const Phys &ph, const FluxArgs &a,
                            double *lbuf, cudaStream_t s) {
     if (model == 0)
-        return precision == 0 ? launch_flux_3d_t<SFModel, double>(nout, g, ph, a, lbuf, s)
-                              : launch_flux_3d_t<SFModel, float>(nout, g, ph, a, lbuf, s);
+        return precision == 0   ? launch_flux_3d_t<SFModel, double>(nout, g, ph, a, lbuf, s)
+               : precision == 2 ? launch_flux_3d_t<SFModel, ff>(nout, g, ph, a, lbuf, s)
+                                : launch_flux_3d_t<SFModel, float>(nout, g, ph, a, lbuf, s);
+    if (precision == 2) return cudaErrorInvalidValue;
     return precision == 0 ? launch_flux_3d_t<TFModel, double>(nout, g, ph, a, lbuf, s)
                           : launch_flux_3d_t<TFModel, float>(nout, g, ph, a, lbuf, s);
 }

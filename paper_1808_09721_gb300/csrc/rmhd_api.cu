@@ -117,7 +117,9 @@ static int validate(const rmhd_config *cfg) {
     if (cfg->model == RMHD_TWO_FLUID && !(cfg->mu_e != cfg->mu_p)) return RMHD_ERR_INVALID;
     if ((cfg->bc_x != RMHD_OUTFLOW && cfg->bc_x != RMHD_PERIODIC) || (cfg->bc_y != RMHD_OUTFLOW && cfg->bc_y != RMHD_PERIODIC))
         return RMHD_ERR_INVALID;
-    if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED) return RMHD_ERR_INVALID;
+    if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED && cfg->precision != RMHD_FLOATFLOAT)
+        return RMHD_ERR_INVALID;
+    if (cfg->precision == RMHD_FLOATFLOAT && cfg->model != RMHD_RESISTIVE) return RMHD_ERR_INVALID;
     if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
     if (cfg->nz < 0) return RMHD_ERR_INVALID;
     // launch limits of the flux kernel's grid: tiles of 8 rows along y in
@@ -821,6 +823,7 @@ static int validate_batch(const rmhd_config *base, int nruns, const int *nx, con
     }
     if (tot > (1LL << 31) - 1) return RMHD_ERR_INVALID;
     if (base->scheme != RMHD_SSP2 || base->nz > 1) return RMHD_ERR_INVALID;
+    if (base->precision == RMHD_FLOATFLOAT) return RMHD_ERR_INVALID;  // batches: FP64 or mixed
     one.nx = (int)std::min<long long>(tot, 1 << 30);
     return validate(&one);
 }
