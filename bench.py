@@ -326,10 +326,13 @@ def main():
         tfw = WL.tf_sheet(n=512, seed=1)
         tf64, ms_tf64, kt_tf64 = timed_run(FP64, True, tfw)
         tfmx, ms_tfmx, kt_tfmx = timed_run(MIXED, True, tfw)
-        qa, qb = tf64.cons(), tfmx.cons()
+        tfff, ms_tfff, kt_tfff = timed_run(FLOATFLOAT, True, tfw)
+        qa, qb, qc = tf64.cons(), tfmx.cons(), tfff.cons()
         l1_tf = float(np.max(np.abs(qb - qa).reshape(qa.shape[0], -1).mean(axis=1) /
                              natural_scale(1, qa, abs(tfw.mu_p))))
-        del tf64, tfmx
+        linf_tf_ff = float(np.max(np.abs(qc - qa).reshape(qa.shape[0], -1).max(axis=1) /
+                                  natural_scale(1, qa, abs(tfw.mu_p))))
+        del tf64, tfmx, tfff
         bw = WL.brio_wu()
         bws, ms_bw, _ = timed_run(FP64, False, bw, 100)
         del bws
@@ -347,7 +350,10 @@ def main():
         del s3, s3m
         extra = {"two_fluid_512": {"fp64": world * tfw.cells * K / (ms_tf64 * 1e-3),
                                    "mixed": world * tfw.cells * K / (ms_tfmx * 1e-3),
+                                   "floatfloat": world * tfw.cells * K / (ms_tfff * 1e-3),
                                    "ms_per_step_fp64": ms_tf64 / K, "ms_per_step_mixed": ms_tfmx / K,
+                                   "ms_per_step_floatfloat": ms_tfff / K, "rel_linf_floatfloat_vs_fp64": linf_tf_ff,
+                                   "kernels_ms_per_launch_floatfloat": {k: v[0] / max(v[1], 1) for k, v in kt_tfff.items()},
                                    "rel_l1_mixed_vs_fp64": l1_tf, "unit": UNIT,
                                    "kernels_ms_per_launch_fp64": {k: v[0] / max(v[1], 1) for k, v in kt_tf64.items()},
                                    "kernels_ms_per_launch_mixed": {k: v[0] / max(v[1], 1) for k, v in kt_tfmx.items()},

@@ -56,6 +56,7 @@ __device__ __forceinline__ ff operator+(ff a, ff b) {
 }
 __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
 __device__ __forceinline__ ff &operator+=(ff &a, ff b) { return a = a + b; }
+__device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
 
 // a b = p + e with p = fl(a_hi b_hi); e collects the exact product error and
 // the cross terms

@@ -244,8 +244,9 @@ struct FluxSmem {
     // computed from the loaded doubles while staging, and the auxiliaries are
     // kept in FT
     static constexpr bool SHADOW = !std::is_same<FT, double>::value;
-    // interior cells' sources through global scratch (FluxArgs::srcg) instead of shared memory
-    static constexpr bool SRCG = M::SRCG && !SHADOW && TY > 1;
+    // interior cells' sources through global scratch (FluxArgs::srcg) instead of
+    // shared memory: the 8-byte forms (FP64, float-float) of 2-D tiles
+    static constexpr bool SRCG = M::SRCG && sizeof(FT) == sizeof(double) && TY > 1;
     // byte offsets
     static constexpr size_t st = 0;
     static constexpr size_t st32 = st + (SHADOW ? 0 : sizeof(double) * NV * SN);
@@ -312,8 +313,17 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             double s[M::NS];
             M::template stage_cell<FT>(x, ph, aux32, SN, e, interior && NOUT > 0 ? s : nullptr);
             if (interior && NOUT > 0) {
+                if constexpr (L_::SRCG) {
+                    const int si = i0 + tx, sj = j0 + ty;
+                    if (si < g.nx && sj < g.ny) {
+                        const long long sc = base + (long long)sj * g.row + si;
 #pragma unroll
-                for (int k = 0; k < M::NS; ++k) src[k * NL + ty * TX + tx] = s[k];
+                        for (int k = 0; k < M::NS; ++k) a.srcg[(long long)k * g.plane + sc] = s[k];
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < M::NS; ++k) src[k * NL + ty * TX + tx] = s[k];
+                }
             }
         }
         __syncthreads();
@@ -614,9 +624,9 @@ cudaError_t launch_flux(int model, int precision, int nout, const Grid &g, const
         return precision == 0   ? launch_flux_n<SFModel, double>(nout, g, ph, a, s)
                : precision == 2 ? launch_flux_n<SFModel, ff>(nout, g, ph, a, s)
                                 : launch_flux_n<SFModel, float>(nout, g, ph, a, s);
-    if (precision == 2) return cudaErrorInvalidValue;  // float-float: one fluid only
-    return precision == 0 ? launch_flux_n<TFModel, double>(nout, g, ph, a, s)
-                          : launch_flux_n<TFModel, float>(nout, g, ph, a, s);
+    return precision == 0   ? launch_flux_n<TFModel, double>(nout, g, ph, a, s)
+           : precision == 2 ? launch_flux_n<TFModel, ff>(nout, g, ph, a, s)
+                            : launch_flux_n<TFModel, float>(nout, g, ph, a, s);
 }
 
 // ---- batched ensemble ------------------------------------------------------
@@ -683,9 +693,9 @@ cudaError_t launch_flux_3d(int model, int precision, int nout, const Grid &g, co
         return precision == 0   ? launch_flux_3d_t<SFModel, double>(nout, g, ph, a, lbuf, s)
                : precision == 2 ? launch_flux_3d_t<SFModel, ff>(nout, g, ph, a, lbuf, s)
                                 : launch_flux_3d_t<SFModel, float>(nout, g, ph, a, lbuf, s);
-    if (precision == 2) return cudaErrorInvalidValue;
-    return precision == 0 ? launch_flux_3d_t<TFModel, double>(nout, g, ph, a, lbuf, s)
-                          : launch_flux_3d_t<TFModel, float>(nout, g, ph, a, lbuf, s);
+    return precision == 0   ? launch_flux_3d_t<TFModel, double>(nout, g, ph, a, lbuf, s)
+           : precision == 2 ? launch_flux_3d_t<TFModel, ff>(nout, g, ph, a, lbuf, s)
+                            : launch_flux_3d_t<TFModel, float>(nout, g, ph, a, lbuf, s);
 }
 
 // Batches run SSP2(222): passes with two outputs (r2, acc) and one (q^{n+1}).

@@ -119,7 +119,6 @@ static int validate(const rmhd_config *cfg) {
         return RMHD_ERR_INVALID;
     if (cfg->precision != RMHD_FP64 && cfg->precision != RMHD_MIXED && cfg->precision != RMHD_FLOATFLOAT)
         return RMHD_ERR_INVALID;
-    if (cfg->precision == RMHD_FLOATFLOAT && cfg->model != RMHD_RESISTIVE) return RMHD_ERR_INVALID;
     if (cfg->scheme != RMHD_SSP2 && cfg->scheme != RMHD_SSP3) return RMHD_ERR_INVALID;
     if (cfg->nz < 0) return RMHD_ERR_INVALID;
     // launch limits of the flux kernel's grid: tiles of 8 rows along y in

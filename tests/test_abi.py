@@ -52,10 +52,11 @@ def test_workspace_bytes_and_validation(lib):
     assert n.value >= (4 * 14 + 2 * 5) * plane and n.value % 256 == 0
     n2 = C.c_size_t()
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(model=1)), C.byref(n2)) == 0 and n2.value > n.value
-    # float-float flux form: one fluid only
+    # float-float flux form, both models
     assert lib.rmhd_workspace_bytes(C.byref(_cfg(precision=2)), C.byref(n2)) == 0
+    assert lib.rmhd_workspace_bytes(C.byref(_cfg(precision=2, model=1)), C.byref(n2)) == 0
     for bad in (dict(model=7), dict(nx=0), dict(ny=0), dict(gamma=2.5), dict(gamma=1.0), dict(sigma=0.0), dict(bc_x=3),
-                dict(precision=3), dict(precision=2, model=1), dict(model=1, mu_e=1.0, mu_p=1.0), dict(xmax=-1.0),
+                dict(precision=3), dict(model=1, mu_e=1.0, mu_p=1.0), dict(xmax=-1.0),
                 dict(nx=1, ny=600000)):  # more rows than the flux kernel's grid can hold
         assert lib.rmhd_workspace_bytes(C.byref(_cfg(**bad)), C.byref(n)) == -1, bad
 

@@ -6,8 +6,9 @@ implicit stage solves stay FP64. The bar is the FP64 one: relative L-infinity
 <= 1e-9 per conserved variable (conftest.parity_scale), on the same cases as
 the FP64 parity tests -- 1-D shocks and stiff tubes, 2-D periodic and outflow
 grids, SSP3(332), 3-D, and the 1024^2 benchmark grid on sampled cells -- plus
-agreement with the GPU's own FP64 form to 1e-11. The mode is one-fluid,
-single-grid only; the rest is refused."""
+agreement with the GPU's own FP64 form to 1e-11; the two-fluid model on the
+current sheet (2-D) and the pair / electron-proton Brio-Wu tubes. Batches and
+the adjoint refuse the mode."""
 import numpy as np
 import pytest
 
@@ -50,6 +51,10 @@ def gpu_run(Sim, wl, nsteps, precision=FF, scheme=0):
 
 def err(got, want):
     return parity_errors(0, got.reshape(14, -1, 1), want.reshape(14, -1, 1))
+
+
+def err_tf(got, want, wl):
+    return parity_errors(1, got, want, max(abs(wl.mu_e), abs(wl.mu_p)))
 
 
 @pytest.mark.parametrize("name,make,steps,scheme", [
@@ -109,9 +114,26 @@ def test_floatfloat_full_size_khi(Sim):
         assert np.all(np.abs(got[:, j0, i0] - want) <= TOL * scale), (j0, i0)
 
 
+@pytest.mark.parametrize("name,make,steps", [
+    ("tf_sheet_40", lambda: WL.tf_sheet(n=40, seed=2), 4),
+    ("tf_brio_wu_pair", lambda: WL.tf_brio_wu(nx=400), None),
+    ("tf_brio_wu_ep", lambda: WL.tf_brio_wu(nx=200, mass_ratio=100.0), None),
+])
+def test_floatfloat_two_fluid_parity(Sim, name, make, steps):
+    wl = make()
+    steps = wl.nsteps if steps is None else steps
+    e = err_tf(gpu_run(Sim, wl, steps), oracle_run(wl, steps), wl)
+    assert np.all(e <= TOL), e
+
+
+def test_floatfloat_two_fluid_512_agrees_with_fp64(Sim):
+    """The two-fluid sheet 512^2 the bench times: 2 steps against the FP64 form."""
+    wl = WL.tf_sheet(n=512, seed=1)
+    e = err_tf(gpu_run(Sim, wl, 2), gpu_run(Sim, wl, 2, precision=0), wl)
+    assert np.all(e <= 1e-11), e
+
+
 def test_floatfloat_scope_is_refused(Sim):
-    with pytest.raises(RmhdError):
-        Sim.from_workload(WL.tf_sheet(n=16, seed=1), precision=FF)
     with pytest.raises(RmhdError):
         Sim.batch(WL.batch_tubes(count=2, seed=3, nmin=40, nmax=60), precision=FF)
     wl = WL.field_loop(n=16)
