@@ -131,6 +131,9 @@ template <class T> __device__ __forceinline__ T value(Dual<T> a) { return a.v; }
 // fused multiply-add that also works for duals
 __device__ __forceinline__ double s_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float s_fma(float a, float b, float c) { return fmaf(a, b, c); }
+// 2 a + b (one rounding in FP64 and FP32)
+__device__ __forceinline__ double s_fma2(double a, double b) { return fma(2.0, a, b); }
+__device__ __forceinline__ float s_fma2(float a, float b) { return fmaf(2.f, a, b); }
 template <class T> __device__ __forceinline__ Dual<T> s_fma(Dual<T> a, Dual<T> b, Dual<T> c) { return a * b + c; }
 
 } // namespace rmhd

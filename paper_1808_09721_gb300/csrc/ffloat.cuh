@@ -76,6 +76,8 @@ __device__ __forceinline__ ff s_fma(ff a, ff b, ff c) {
     const ff s = two_sum(p, c.hi);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
+// 2 a + b: the doubling is exact, so one float-float sum
+__device__ __forceinline__ ff s_fma2(ff a, ff b) { return ff(2.f * a.hi, 2.f * a.lo) + b; }
 // a / x (x > 0 and normal in FP32 where this is used)
 __device__ __forceinline__ ff s_div1(ff a, ff x) {
     const float y = s_rcp(x.hi);

@@ -368,6 +368,9 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     for (int k = 0; k < NSLOT; ++k) L[k] = FT(0);
 
     const FT eps4 = FT(4e-6);
+    // float-float: 2 a + b as an exact doubling and one sum, and the pairs'
+    // signs as negations (the FP64 and FP32 forms keep their FMAs)
+    constexpr bool FFT = std::is_same<FT, ff>::value;
     FT *hpw = hp + grp * 4 * SN;  // this group's half-point and face buffers
     FT *fcw = fc + grp * 2 * SN;
     // component c of the staged state in the flux arithmetic type
@@ -427,11 +430,19 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                 const int idx = (fy0 + fy) * SW + fx0 + fx;
                 const int il = idx - sstep, ir = idx + sstep;
                 const FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
-                const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
-                const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
-                const FT Xp = hpw[il] - hpw[idx];
-                const FT Xm = hpw[SN + idx] - hpw[SN + ir];
-                fcw[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+                if constexpr (FFT) {
+                    const FT wp = s_div1(Ap, s_fma2(hpw[2 * SN + il], Ap));
+                    const FT wm = s_div1(Am, s_fma2(hpw[3 * SN + ir], Am));
+                    const FT Xp = hpw[il] - hpw[idx];
+                    const FT Xm = hpw[SN + idx] - hpw[SN + ir];
+                    fcw[idx] = s_fma2(fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+                } else {
+                    const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
+                    const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
+                    const FT Xp = hpw[il] - hpw[idx];
+                    const FT Xm = hpw[SN + idx] - hpw[SN + ir];
+                    fcw[idx] = s_fma(FT(2), fv[idx] + fv[ir], s_fma(wp, Xp, wm * Xm));
+                }
             }
             group_sync<NL>(grp);
             return fcw[own - sstep] - fcw[own];
@@ -446,7 +457,15 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                 const int idx = (hy0 + hy) * SW + hx0 + hx;
                 const FT d_a = qa[idx + sstep] - qa[idx];
                 const FT d_b = qb[idx + sstep] - qb[idx];
-                const FT ep = s_fma(sg, d_b, d_a), em = s_fma(sg, d_b, -d_a);  // e+-_a
+                FT ep, em;  // e+-_a
+                if constexpr (FFT) {
+                    const FT sd_b = sg.hi < 0.f ? -d_b : d_b;
+                    ep = d_a + sd_b;
+                    em = sd_b - d_a;
+                } else {
+                    ep = s_fma(sg, d_b, d_a);
+                    em = s_fma(sg, d_b, -d_a);
+                }
                 const FT ap = s_fma(ep, ep, eps4), am = s_fma(em, em, eps4);
                 hpw[idx] = ep;
                 hpw[SN + idx] = em;
@@ -459,12 +478,22 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                 const int idx = (fy0 + fy) * SW + fx0 + fx;
                 const int il = idx - sstep, ir = idx + sstep;
                 const FT Ap = hpw[2 * SN + idx], Am = hpw[3 * SN + idx];
-                const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
-                const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
-                const FT Xp = hpw[il] - hpw[idx];
-                const FT M_ = wm * (hpw[SN + idx] - hpw[SN + ir]);
-                fcw[idx] = s_fma(FT(2) * sg, qb[idx] + qb[ir], s_fma(wp, Xp, M_));
-                fcw[SN + idx] = s_fma(FT(2), qa[idx] + qa[ir], s_fma(wp, Xp, -M_));
+                if constexpr (FFT) {
+                    const FT wp = s_div1(Ap, s_fma2(hpw[2 * SN + il], Ap));
+                    const FT wm = s_div1(Am, s_fma2(hpw[3 * SN + ir], Am));
+                    const FT Xp = hpw[il] - hpw[idx];
+                    const FT M_ = wm * (hpw[SN + idx] - hpw[SN + ir]);
+                    const FT qbs = qb[idx] + qb[ir];
+                    fcw[idx] = s_fma2(sg.hi < 0.f ? -qbs : qbs, s_fma(wp, Xp, M_));
+                    fcw[SN + idx] = s_fma2(qa[idx] + qa[ir], s_fma(wp, Xp, -M_));
+                } else {
+                    const FT wp = s_div1(Ap, s_fma(FT(2), hpw[2 * SN + il], Ap));
+                    const FT wm = s_div1(Am, s_fma(FT(2), hpw[3 * SN + ir], Am));
+                    const FT Xp = hpw[il] - hpw[idx];
+                    const FT M_ = wm * (hpw[SN + idx] - hpw[SN + ir]);
+                    fcw[idx] = s_fma(FT(2) * sg, qb[idx] + qb[ir], s_fma(wp, Xp, M_));
+                    fcw[SN + idx] = s_fma(FT(2), qa[idx] + qa[ir], s_fma(wp, Xp, -M_));
+                }
             }
             group_sync<NL>(grp);
             da = fcw[own - sstep] - fcw[own];
@@ -482,7 +511,8 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
                 const FT sg = neg ? FT(-1) : FT(1);
                 FT da, db;
                 pair(em_comp<M, ZP>(grp, sa), em_comp<M, ZP>(grp, 3 - k), sg, da, db);
-                L[3 - k] = s_fma(db, sg * inv4h, L[3 - k]);
+                if constexpr (FFT) L[3 - k] = s_fma(db, neg ? -inv4h : inv4h, L[3 - k]);
+                else L[3 - k] = s_fma(db, sg * inv4h, L[3 - k]);
                 if (sa == 0) L[0] = s_fma(da, inv4h, L[0]);
                 else L[1] = s_fma(da, inv4h, L[1]);
             }
