@@ -8,8 +8,9 @@ implicit per-cell stage solves, two WENO3/LF flux passes, stage combine and
 recovery) over all cells. Metric: cell-updates/s.
 
 Printed JSON line: the FP64 form is `value`; the mixed form (FP32 flux
-arithmetic, FP64 source solve) is under "mixed" with its error against the
-FP64 result; "e2e" is the same metric through the C ABI with host buffers
+arithmetic, FP64 source solve) is under "mixed" and the float-float form
+(flux arithmetic in pairs of FP32 numbers, FP64 source solve) under
+"floatfloat", each with its error against the FP64 result; "e2e" is the same metric through the C ABI with host buffers
 (prims uploaded and read back every step); "roofline" is for the dominant
 kernel, timed with CUDA events inside the timed region; "cpu_baseline" is the
 FP64 CPU oracle on the host cores on a bounded sample of the same workload.
