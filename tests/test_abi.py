@@ -81,6 +81,9 @@ def test_batch_workspace_bytes(lib):
     bad = (C.c_int * 2)(10, 0)
     assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 2, bad, C.byref(n)) == -1
     assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1)), 0, nx, C.byref(n)) == -1
+    # batches take the FP64 and mixed forms; the float-float form is single-grid only
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1, precision=1)), 3, nx, C.byref(n)) == 0
+    assert lib.rmhd_batch_workspace_bytes(C.byref(_cfg(ny=1, precision=2)), 3, nx, C.byref(n)) == -1
 
 
 def test_scheme_selection(lib):
