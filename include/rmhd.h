@@ -61,9 +61,9 @@ extern "C" {
                         the implicit source solve, primitive recovery and current J stay FP64 */
 #define RMHD_FLOATFLOAT 2 /* WENO3/flux arithmetic in float-float (pairs of FP32 numbers, ~48
                              significant bits, on the FP32 pipes), the rest as RMHD_MIXED; both
-                             models on single grids (1-D, 2-D, 3-D), not batches. Agrees with
-                             RMHD_FP64 to ~1e-13 relative while the state stays inside FP32's
-                             range */
+                             models on single grids (1-D, 2-D, 3-D), not batches. Differs from
+                             RMHD_FP64 by ~1e-13 relative per step (unstable flows amplify it like
+                             any round-off) while the state stays inside FP32's range */
 
 /* memory kinds for `where` */
 #define RMHD_HOST 0
