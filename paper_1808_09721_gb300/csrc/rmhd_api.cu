@@ -344,6 +344,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->hist = (unsigned long long *)(c->ws + L.hist);
     if (cudaMallocHost(&c->h_status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->h_diag, 8 * sizeof(double)) != cudaSuccess) {
+        if (c->h_status) cudaFreeHost(c->h_status);  // the first may have succeeded
         if (c->own_ws) cudaFree(c->ws);
         delete c;
         return RMHD_ERR_NOMEM;
