@@ -202,6 +202,8 @@ int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
  *   armed, rmhd_imex_step stores a checkpoint every `ckpt_every` steps and
  *   all recorded steps must use one dt. `workspace` (device, 256-byte
  *   aligned, >= rmhd_recording_bytes) may be NULL: the library allocates.
+ *   Arming again drops the earlier recording (and frees the library's own
+ *   workspace) first; if the new arming fails, the context is left unarmed.
  *   rmhd_adjoint_step reverses every recorded step: from dJ/dq at the final
  *   state ([14][ny][nx]) it writes dJ/d(prims) ([11][ny][nx], may be NULL) and
  *   dJ/dsigma (may be NULL). Each segment of ckpt_every steps is recomputed from its

@@ -795,7 +795,10 @@ int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
         CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         st = enqueue_step(c, dt);
         cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
-        if (st) return st;
+        if (st) {
+            if (e == cudaSuccess) cudaGraphDestroy(gr);
+            return st;
+        }
         if (e != cudaSuccess) return fail(c, RMHD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&c->graph, gr, 0);
         cudaGraphDestroy(gr);
@@ -1100,6 +1103,10 @@ int rmhd_record(rmhd_ctx *c, int nsteps, int ckpt_every, void *workspace, size_t
     if (!c->has_state || !c->fresh_prims)
         return fail(c, RMHD_ERR_STATE, "record: arm right after rmhd_set_prims (the gradient is w.r.t. those primitives)");
     RecLayout L = rec_layout(c, nsteps, ckpt_every);
+    // disarm any earlier recording first: a failure below must not leave the
+    // context recording into a workspace that is gone
+    c->recording = false;
+    c->rec_done = 0;
     if (c->rec_own && c->rec_ws) { cudaFree(c->rec_ws); c->rec_ws = nullptr; c->rec_own = false; }
     if (workspace) {
         if (bytes < L.total || ((uintptr_t)workspace & 255)) return fail(c, RMHD_ERR_NOMEM, "record: workspace too small");

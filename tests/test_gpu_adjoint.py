@@ -164,6 +164,29 @@ def test_adjoint_restores_state_and_repeats(env):
     assert abs(s2 - s1) <= 1e-10 * abs(s1)
 
 
+def test_failed_rearm_leaves_context_unarmed(env):
+    """Arming again drops the earlier recording first; when the new arming
+    fails (here: a caller workspace that is too small, refused on the host
+    before any device work) the context is left unarmed: steps run without
+    recording, bit for bit as an unrecorded run, and the adjoint is refused."""
+    import ctypes as C
+    from paper_1808_09721_gb300 import _lib as L
+    torch, Sim, _ = env
+    wl = WL.field_loop(n=12, nsteps=4)
+    s = Sim.from_workload(wl)
+    s.record(4, 2)
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    code = s.lib.rmhd_record(s.h, 4, 2, C.c_void_p(small.data_ptr()), 256)
+    assert L.ERRORS.get(code) == "RMHD_ERR_NOMEM", code
+    ref = Sim.from_workload(wl)
+    s.step(wl.dt, 4)
+    ref.step(wl.dt, 4)
+    s.check()
+    np.testing.assert_array_equal(s.cons(), ref.cons())
+    with pytest.raises(L.RmhdError):
+        s.adjoint(np.zeros((14,) + s.shape))
+
+
 def oracle_lin_J(wl, prims, lam, nsteps):
     o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y)
     o.set_prims(np.ascontiguousarray(prims))
