@@ -66,6 +66,8 @@ def lib():
         L.orc_step.restype = C.c_int
         L.orc_stage_solve.argtypes = [C.c_void_p, C.c_double, _D, _D]
         L.orc_stage_solve.restype = C.c_int
+        L.orc_get_padded.argtypes = [C.c_void_p, C.c_int, _D, C.POINTER(C.c_int)]
+        L.orc_get_padded.restype = C.c_int
         L.orc_time.argtypes = [C.c_void_p]
         L.orc_time.restype = C.c_double
         L.orc_fail_cell.argtypes = [C.c_void_p]
@@ -278,6 +280,17 @@ class Sim:
         w = np.zeros((NW[self.model],) + self.shape)
         self._check(lib().orc_stage_solve(self.h, adt, _p(q), _p(w)), "stage_solve")
         return q, w
+
+    def padded(self, which="cons"):
+        """The padded array with its ghost cells: [var][NZ][NY][NX] (NZ = 1 for
+        1-D and 2-D grids; 2 ghost layers per side in every active direction)."""
+        dims = (C.c_int * 3)()
+        w = 0 if which == "cons" else 1
+        lib().orc_get_padded(self.h, w, None, dims)
+        nv = self.nc if w == 0 else NW[self.model]
+        out = np.zeros((nv, dims[2], dims[1], dims[0]))
+        lib().orc_get_padded(self.h, w, _p(out), dims)
+        return out
 
     @property
     def t(self):

@@ -850,6 +850,19 @@ int orc_get_prims(const orc_sim *s, double *out)
     return ORC_OK;
 }
 
+/* The whole padded array (ghost cells included) of the conserved state
+ * (which = 0, [nc][NZ][NY][NX]) or of the recovered primitives (which = 1,
+ * [nw][NZ][NY][NX]); dims[3] receives (NX, NY, NZ). Exposes the ghost cells
+ * that fill_ghosts wrote, for tests of the boundary conditions. */
+int orc_get_padded(const orc_sim *s, int which, double *out, int *dims)
+{
+    const double *a = which == 0 ? s->q : s->w;
+    int nv = which == 0 ? s->nc : s->nw;
+    if (dims) { dims[0] = s->NX; dims[1] = s->NY; dims[2] = s->NZ; }
+    if (out) memcpy(out, a, cells(s) * nv * sizeof(double));
+    return ORC_OK;
+}
+
 double orc_time(const orc_sim *s) { return s->t; }
 int orc_fail_cell(const orc_sim *s) { return s->fail_cell; }
 
