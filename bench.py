@@ -42,11 +42,17 @@ def workload_name(n: int = 1024) -> str:
     return (f"khi-2d-{n}x{n} (resistive SRMHD Kelvin-Helmholtz, periodic, Gamma=4/3, sigma=1e3, SSP2(222), "
             "WENO3+LF)")
 
-# FP64 arithmetic instructions (add, mul, fma; one op each) per interior cell
-# for each kernel of the FP64 form on a 2-D grid, counted by ncu's
+# Algorithmic FP64 operations (+, -, x, /, sqrt; one flop each) per interior
+# cell of the flux passes of a 2-D periodic grid, counted by the op-counting
+# build of the CPU oracle (oracle/opcount.py: each cell's flux once per
+# direction, each face's two WENO3 reconstructions once per component, the
+# source and the stage combinations; a test recomputes them): pass 1 has two
+# outputs (r2, acc), pass 2 one (q^{n+1}).
+ALG_FP64_FLOPS_PER_CELL = {"flux1": 1918, "flux2": 1880, "tf_flux1": 2556, "tf_flux2": 2502}
+# FP64 arithmetic instructions the kernels themselves issue (dadd, dmul, dfma;
+# one each) per interior cell on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
-# The FP64 pipe issues 2 of them per clock per SM, which sets the ALU peak.
-FP64_OPS_PER_CELL = {"stage": 173.0, "flux1": 738.4, "flux2": 710.4}
+FP64_INST_PER_CELL = {"stage": 173.0, "flux1": 738.4, "flux2": 710.4}
 # DRAM bytes (read + write) per cell and launch of the same kernels, from the
 # ncu launch list of the KHI 1024^2 bench (dram__bytes_read.sum + write.sum).
 DRAM_BYTES_PER_CELL = {"stage": 223.1, "flux1": 448.0, "flux2": 387.1}
@@ -216,9 +222,12 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(), "sample": "96x96 window of the same recipe per step"},
+            "config": {"workload": workload_name(args.n), "cells_per_gpu": args.n * args.n,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: state+workspace > 129 MB"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-                             "sample": f"KHI recipe 96x96 periodic, one SSP2(222) step per bench step"},
+                             "sample": "KHI recipe 96x96 periodic (a window of the workload), one SSP2(222) "
+                                       "step per bench step, all host cores"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -259,7 +268,7 @@ def main():
     B.build()
     from paper_1808_09721_gb300 import FP64, MIXED, FLOATFLOAT, HOST
     from paper_1808_09721_gb300 import workloads as WL
-    from paper_1808_09721_gb300.sim import Sim
+    from paper_1808_09721_gb300.sim import Sim, fp64_fma_rate
 
     wl = WL.khi(n=args.n, seed=0)
     K, W = args.steps, args.warmup
@@ -507,19 +516,29 @@ def main():
               "fp64_passes": {str(k): v for k, v in hist["fp64_passes"].items()},
               "note": "one FP64 step of the benchmark workload, both implicit stages, counted after timing"}
 
-    # roofline of the dominant kernel (FP64 form)
+    # roofline of the dominant kernel (FP64 form): FP64-pipe bound. Peak = the
+    # FP64 FMA rate measured now on this GPU by the library's own probe
+    # (independent FMA chains on every SM), x2 for FLOP/s; achieved = the
+    # oracle-counted algorithmic flops of the kernel per cell x cells / its
+    # CUDA-event time per launch
     hbm_gbs, peak_src, smax = _peaks()
     dom = max(kt64, key=lambda k: kt64[k][0])
     dom_ms, dom_n = kt64[dom]
     per_launch_ms = dom_ms / dom_n
-    fp64_peak = 2.0 * 152 * smax * 1e6 / 1e12  # TOP/s: 2 FP64 lanes/clk/SM x 152 SMs x max clock
-    achieved = FP64_OPS_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3) / 1e12
+    fma_rate, n_sm = fp64_fma_rate(f"cuda:{local}")
+    fp64_peak = 2.0 * fma_rate / 1e12
+    alg = ALG_FP64_FLOPS_PER_CELL.get(dom)
+    achieved = alg * wl.cells / (per_launch_ms * 1e-3) / 1e12 if alg else None
+    issued = FP64_INST_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3)
     hbm_achieved = BYTES_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak,
+                "frac": achieved / fp64_peak if achieved else None,
                 "traffic": DRAM_BYTES_PER_CELL[dom] * wl.cells if args.n == 1024 else None, "kernel": dom,
                 "kernel_ms_per_launch": per_launch_ms,
-                "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
+                "peak_source": f"measured: FP64 FMA chains on all {n_sm} SMs, CUDA events (rmhd_fp64_fma_rate), x2",
+                "alg_flops_per_cell": alg,
+                "fp64_inst_per_cell": FP64_INST_PER_CELL[dom],
+                "issue_frac": issued / fma_rate,
                 "hbm_gbs": hbm_achieved, "hbm_frac": hbm_achieved / hbm_gbs,
                 "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": peak_src}
     step_bytes = 1056.0  # algorithmic HBM bytes per cell-update of the whole step
@@ -532,12 +551,19 @@ def main():
         cpu = cpu_baseline()
 
     if rank == 0:
+        # verbose sections first; the standard keys and a compact summary of
+        # every form and workload at the end of the line
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms64 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": workload_name(args.n), "cells_per_gpu": wl.cells, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2: state+workspace %.2f GB > 129 MB" %
                                  (sim64.workspace.numel() / 1e9)},
+                "other_workloads": extra,
+                "batch": batch,
+                "adjoint": adjoint,
+                "solver_stats": solver,
+                "kernels": kernels,
                 "mixed": {"value": value_mx, "ms_per_step": msmx / K, "dtype": "f32 flux / f64 source",
                           "rel_l1_vs_fp64": rel_l1_mixed, "speedup_vs_fp64": value_mx / value, "kernels": kernels_mx},
                 "floatfloat": {"value": value_ff, "ms_per_step": msff / K, "dtype": "f32x2 flux / f64 source",
@@ -546,17 +572,28 @@ def main():
                 "hbm_roofline_step": {"bytes_per_cell_update": step_bytes,
                                       "achieved_gbs": step_bytes * value / world / 1e9,
                                       "frac": step_bytes * value / world / 1e9 / hbm_gbs},
-                "batch": batch,
-                "other_workloads": extra,
-                "adjoint": adjoint,
+                "cpu_baseline": cpu,
+                "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                         "d2h_bytes_per_step": io_bytes},
                 "gpu_launches": 4 * K,
-                "roofline": roofline,
-                "kernels": kernels,
-                "solver_stats": solver,
-                "cpu_baseline": cpu,
-                "clocks": clocks}
+                "roofline": roofline}
+        summ = {"fp64": round(value / 1e6, 1), "mixed": round(value_mx / 1e6, 1),
+                "mixed_speedup": round(value_mx / value, 2), "mixed_rel_l1": float(f"{rel_l1_mixed:.2e}"),
+                "ff": round(value_ff / 1e6, 1), "ff_rel_linf": float(f"{rel_linf_ff:.2e}")}
+        if extra:
+            tfx = extra["two_fluid_512"]
+            summ.update({"tf512_fp64": round(tfx["fp64"] / 1e6, 1), "tf512_mixed": round(tfx["mixed"] / 1e6, 1),
+                         "ssp3_fp64": round(extra["khi_1024_ssp3"]["fp64"] / 1e6, 1),
+                         "khi3d_fp64": round(extra["khi3d_128"]["fp64"] / 1e6, 1)})
+        if batch:
+            summ.update({"batch_mixed": round(batch["value"] / 1e6, 1),
+                         "batch_rel_l1": float(f"{batch['rel_l1_mixed_vs_fp64_max_over_tubes']:.2e}")})
+        if adjoint:
+            summ.update({"adjoint_over_fwd": round(adjoint["adjoint_over_fwd"], 2)})
+        summ.update({"alu_frac": round(roofline["frac"], 3) if roofline["frac"] else None,
+                     "hbm_frac_kernel": round(roofline["hbm_frac"], 4)})
+        line["summary_Mcell_updates_per_s"] = summ
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

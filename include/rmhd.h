@@ -255,23 +255,41 @@ int rmhd_autotune(rmhd_ctx *ctx, int *choice);
 int rmhd_set_profiling(rmhd_ctx *ctx, int enable);
 int rmhd_kernel_times(rmhd_ctx *ctx, double *ms, int *counts);
 
+/* Measured FP64 fused multiply-add rate of the current device (no
+ * counterpart in the paper; the peak against which the FP64-bound kernels of
+ * the step are judged). Launches, on `cuda_stream`, independent FMA chains on
+ * every SM (8 blocks of 256 threads per SM, 8 chains per thread), times them
+ * with CUDA events and writes the best of three timed launches to
+ * *fma_per_s (lane FMAs per second; x2 for FLOP/s) and the number of SMs to
+ * *sm_count (may be NULL). Allocates no device memory. Synchronous, about
+ * 0.1 s. Errors: RMHD_ERR_INVALID (fma_per_s NULL), RMHD_ERR_CUDA (a CUDA
+ * error was pending on entry, or a launch or event call failed). */
+int rmhd_fp64_fma_rate(void *cuda_stream, double *fma_per_s, int *sm_count);
+
 /* Diagnostics without any allocation (the paper has no counterpart). For
  * callers that cannot call cudaMalloc -- e.g. code running while a memory
  * pool or arena owns the device, or a framework that forbids allocation after
  * start-up -- this computes the same 7 numbers as out[0..6] of
  * rmhd_diagnostics from caller-owned device arrays, with no context:
- *   cons  [N_c][ny][nx] and prims [n_prim][ny][nx] (dense, device, FP64),
+ *   cons  [N_c][nz][ny][nx] and prims [n_prim][nz][ny][nx] (dense, device,
+ *         FP64; nz = 1 for 1-D and 2-D grids, ny = 1 for 1-D),
+ *   dx, dy, dz  cell widths (dy is used when ny > 1, dz when nz > 1; the
+ *         sums are multiplied by the cell volume dx [dy] [dz]),
  *   out   7 doubles in device memory (written asynchronously on cuda_stream).
  * Partial sums live in a file-scope device array of 512 KiB that every GPU
  * loading the library keeps until exit; it limits inputs to 16,777,216 cells.
  * The first call on a device looks up that array's address with
- * cudaGetSymbolAddress (once per device, that device current); make that
- * first call before any stream capture. Calls share the array: two calls
- * whose kernels overlap on the GPU race. Calls no cudaMalloc/cudaFree.
- * Errors: RMHD_ERR_INVALID (bad argument), RMHD_ERR_NOMEM (more cells than
- * the static array holds), RMHD_ERR_CUDA. */
-int rmhd_diagnostics_noalloc(int model, int nx, int ny, double dx, double dy, const double *cons,
-                             const double *prims, double *out, void *cuda_stream);
+ * cudaGetSymbolAddress (once per device, that device current) and caches it
+ * for the life of the process; make that first call before any stream
+ * capture, and do not use this call on a device after cudaDeviceReset. Calls
+ * share the array: two calls whose kernels overlap on the GPU race. Calls no
+ * cudaMalloc/cudaFree.
+ * Errors: RMHD_ERR_INVALID (bad argument; nz > 1 needs ny > 1),
+ * RMHD_ERR_NOMEM (more cells than the static array holds), RMHD_ERR_CUDA (a
+ * CUDA error was already pending on entry -- it is left pending and nothing
+ * is launched -- or one of this call's launches failed). */
+int rmhd_diagnostics_noalloc(int model, int nx, int ny, int nz, double dx, double dy, double dz,
+                             const double *cons, const double *prims, double *out, void *cuda_stream);
 
 /* Library version string. */
 const char *rmhd_version(void);

@@ -54,48 +54,53 @@ _D = C.POINTER(C.c_double)
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(_Cfg)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        for name in ("orc_set_prims", "orc_set_cons", "orc_get_cons", "orc_get_prims", "orc_current_L"):
-            getattr(L, name).argtypes = [C.c_void_p, _D]
-            getattr(L, name).restype = C.c_int
-        L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
-        L.orc_step.restype = C.c_int
-        L.orc_stage_solve.argtypes = [C.c_void_p, C.c_double, _D, _D]
-        L.orc_stage_solve.restype = C.c_int
-        L.orc_get_padded.argtypes = [C.c_void_p, C.c_int, _D, C.POINTER(C.c_int)]
-        L.orc_get_padded.restype = C.c_int
-        L.orc_time.argtypes = [C.c_void_p]
-        L.orc_time.restype = C.c_double
-        L.orc_fail_cell.argtypes = [C.c_void_p]
-        L.orc_fail_cell.restype = C.c_int
-        L.orc_sf_p2c.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
-        L.orc_tf_p2c.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _D]
-        L.orc_sf_c2p.argtypes = [_D, C.c_double, _D]
-        L.orc_tf_c2p.argtypes = [_D, C.c_double, C.c_double, C.c_double, _D]
-        L.orc_hydro_c2p.argtypes = [C.c_double, _D, C.c_double, C.c_double, _D]
-        L.orc_sf_flux.argtypes = [_D, _D, C.c_double, C.c_double, C.c_int, _D]
-        L.orc_sf_flux.restype = None
-        L.orc_tf_flux.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, C.c_int, _D]
-        L.orc_tf_flux.restype = None
-        L.orc_sf_source.argtypes = [_D, _D, C.c_double, C.c_double, _D]
-        L.orc_sf_source.restype = None
-        L.orc_tf_source.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
-        L.orc_tf_source.restype = None
-        L.orc_sf_current.argtypes = [_D, _D, C.c_double, _D]
-        L.orc_sf_current.restype = None
-        L.orc_sf_implicit.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D, _D]
-        L.orc_tf_implicit.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                      C.c_double, _D, _D]
-        L.orc_weno3.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.orc_weno3.restype = C.c_double
-        L.orc_set_threads.argtypes = [C.c_int]
-        L.orc_set_threads.restype = None
-        L.orc_get_threads.restype = C.c_int
+        _lib = declare(C.CDLL(build()))
     return _lib
+
+
+def declare(L):
+    """ctypes signatures of the oracle's exported functions on a loaded library
+    (the plain build, or the op-counting build of ``oracle/opcount.py``)."""
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(_Cfg)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    for name in ("orc_set_prims", "orc_set_cons", "orc_get_cons", "orc_get_prims", "orc_current_L"):
+        getattr(L, name).argtypes = [C.c_void_p, _D]
+        getattr(L, name).restype = C.c_int
+    L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+    L.orc_step.restype = C.c_int
+    L.orc_stage_solve.argtypes = [C.c_void_p, C.c_double, _D, _D]
+    L.orc_stage_solve.restype = C.c_int
+    L.orc_get_padded.argtypes = [C.c_void_p, C.c_int, _D, C.POINTER(C.c_int)]
+    L.orc_get_padded.restype = C.c_int
+    L.orc_time.argtypes = [C.c_void_p]
+    L.orc_time.restype = C.c_double
+    L.orc_fail_cell.argtypes = [C.c_void_p]
+    L.orc_fail_cell.restype = C.c_int
+    L.orc_sf_p2c.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
+    L.orc_tf_p2c.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _D]
+    L.orc_sf_c2p.argtypes = [_D, C.c_double, _D]
+    L.orc_tf_c2p.argtypes = [_D, C.c_double, C.c_double, C.c_double, _D]
+    L.orc_hydro_c2p.argtypes = [C.c_double, _D, C.c_double, C.c_double, _D]
+    L.orc_sf_flux.argtypes = [_D, _D, C.c_double, C.c_double, C.c_int, _D]
+    L.orc_sf_flux.restype = None
+    L.orc_tf_flux.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, C.c_int, _D]
+    L.orc_tf_flux.restype = None
+    L.orc_sf_source.argtypes = [_D, _D, C.c_double, C.c_double, _D]
+    L.orc_sf_source.restype = None
+    L.orc_tf_source.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
+    L.orc_tf_source.restype = None
+    L.orc_sf_current.argtypes = [_D, _D, C.c_double, _D]
+    L.orc_sf_current.restype = None
+    L.orc_sf_implicit.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D, _D]
+    L.orc_tf_implicit.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, _D, _D]
+    L.orc_weno3.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.orc_weno3.restype = C.c_double
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_threads.restype = None
+    L.orc_get_threads.restype = C.c_int
+    return L
 
 
 def _p(a: np.ndarray):

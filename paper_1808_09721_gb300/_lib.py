@@ -28,7 +28,7 @@ EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_err
            "rmhd_batch_workspace_bytes", "rmhd_create_batch", "rmhd_autotune",
            "rmhd_set_profiling", "rmhd_kernel_times", "rmhd_diagnostics_noalloc", "rmhd_version",
            "rmhd_set_solver_stats", "rmhd_solver_stats", "rmhd_set_refinement_cap",
-           "rmhd_state_doubles", "rmhd_get_state", "rmhd_set_state")
+           "rmhd_state_doubles", "rmhd_get_state", "rmhd_set_state", "rmhd_fp64_fma_rate")
 
 
 class Config(C.Structure):
@@ -89,7 +89,9 @@ def load(path: str | None = None):
     L.rmhd_state_doubles.argtypes = [_P, C.POINTER(C.c_size_t)]
     L.rmhd_get_state.argtypes = [_P, _P, C.c_int]
     L.rmhd_set_state.argtypes = [_P, _P, C.c_int]
-    L.rmhd_diagnostics_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, _P, _P]
+    L.rmhd_diagnostics_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                            _P, _P, _P, _P]
+    L.rmhd_fp64_fma_rate.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.rmhd_version.restype = C.c_char_p
     _lib = L
     return L

@@ -6,8 +6,9 @@
 // device. rmhd_diagnostics_noalloc serves them: it computes the same numbers
 // as rmhd_diagnostics (cell sums of D, tau, S_x, B_x and the charge variable
 // times the cell volume, max |v|, count of non-finite conserved values) from
-// caller-provided device arrays, and keeps its partial sums in the file-scope
-// device array below instead of in any allocated workspace.
+// caller-provided device arrays of a 1-D, 2-D or 3-D grid, and keeps its
+// partial sums in the file-scope device array below instead of in any
+// allocated workspace.
 //
 // The scratch array is a device global: every GPU that loads this library
 // holds its 512 KiB until the process exits. It holds one 8-double partial per
@@ -15,6 +16,9 @@
 // All calls share it and it keeps the last call's contents; each call writes
 // every partial it later reads, so nothing needs clearing, but two calls whose
 // kernels overlap on the GPU (different streams, no ordering) race on it.
+// The device address of the array is looked up once per device and cached for
+// the life of the process; a cudaDeviceReset reloads the module (possibly at
+// another address), so this call must not be used on a device after a reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -114,18 +118,24 @@ __global__ void __launch_bounds__(kThreads) k_combine(int nblocks, double vol, c
 
 } // namespace
 
-extern "C" int rmhd_diagnostics_noalloc(int model, int nx, int ny, double dx, double dy, const double *cons,
-                                        const double *prims, double *out, void *cuda_stream) {
-    if ((model != RMHD_RESISTIVE && model != RMHD_TWO_FLUID) || nx < 1 || ny < 1 || !cons || !prims || !out ||
-        !(dx > 0.0) || (ny > 1 && !(dy > 0.0)))
+extern "C" int rmhd_diagnostics_noalloc(int model, int nx, int ny, int nz, double dx, double dy, double dz,
+                                        const double *cons, const double *prims, double *out, void *cuda_stream) {
+    if ((model != RMHD_RESISTIVE && model != RMHD_TWO_FLUID) || nx < 1 || ny < 1 || nz < 1 || !cons || !prims ||
+        !out || !(dx > 0.0) || (ny > 1 && !(dy > 0.0)) || (nz > 1 && (ny < 2 || !(dz > 0.0))))
         return RMHD_ERR_INVALID;
-    const long long ncell = (long long)nx * ny;
+    const long long ncell = (long long)nx * ny * nz;
     if (ncell > kMaxCells) return RMHD_ERR_NOMEM;  // beyond the static scratch
+    // an error left pending by earlier work on this thread is not this call's:
+    // report it without clearing it and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return RMHD_ERR_CUDA;
     double *partials = nullptr;
     if (scratch_ptr(&partials) != cudaSuccess) return RMHD_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nblocks = (int)((ncell + kCellsPerBlock - 1) / kCellsPerBlock);
+    const double vol = dx * (ny > 1 ? dy : 1.0) * (nz > 1 ? dz : 1.0);
     k_partials<<<nblocks, kThreads, 0, s>>>(model, ncell, cons, prims, partials);
-    k_combine<<<1, kThreads, 0, s>>>(nblocks, dx * (ny > 1 ? dy : 1.0), partials, out);
-    return cudaGetLastError() == cudaSuccess ? RMHD_OK : RMHD_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return RMHD_ERR_CUDA;  // this launch's own error
+    k_combine<<<1, kThreads, 0, s>>>(nblocks, vol, partials, out);
+    if (cudaGetLastError() != cudaSuccess) return RMHD_ERR_CUDA;
+    return RMHD_OK;
 }

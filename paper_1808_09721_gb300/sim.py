@@ -18,6 +18,21 @@ def _torch():
     return torch
 
 
+def fp64_fma_rate(device=None):
+    """(lane FP64 FMAs per second, SM count) of the device, measured by the
+    library's probe (rmhd_fp64_fma_rate) on a stream of its own."""
+    torch = _torch()
+    lib = L.load()
+    dev = torch.device("cuda" if device is None else device)
+    with torch.cuda.device(dev):
+        st = torch.cuda.Stream(dev)
+        rate, sms = C.c_double(), C.c_int()
+        code = lib.rmhd_fp64_fma_rate(C.c_void_p(st.cuda_stream), C.byref(rate), C.byref(sms))
+    if code != L.RMHD_OK:
+        raise L.RmhdError(code, "rmhd_fp64_fma_rate")
+    return rate.value, sms.value
+
+
 class Sim:
     """One resistive (N_c = 14) or two-fluid (N_c = 18) SRMHD run."""
 

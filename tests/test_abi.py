@@ -21,7 +21,7 @@ def lib():
 def declared_functions():
     txt = open(os.path.join(ROOT, "include", "rmhd.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rmhd_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rmhd_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_and_binding_agree():
