@@ -220,6 +220,55 @@ int rmhd_record(rmhd_ctx *ctx, int nsteps, int ckpt_every, void *workspace, size
 int rmhd_adjoint_step(rmhd_ctx *ctx, const double *dJ_dcons, int where_in, double *dJ_dprims0, int where_out,
                       double *dJ_dsigma);
 
+/* Phase-by-phase stepping (the building block of domain decomposition). One
+ * IMEX step of the configured scheme is 4 phases (SSP2(222), Table 1) or 6
+ * (SSP3(332), Table 2), run in order 0, 1, ...: an even phase 2k is the
+ * implicit stage solve of stage k + 1 (Sec. 2.2.1, Eq. implicit stage), an odd
+ * phase 2k + 1 the flux pass that follows it (WENO3/LF divergence of the
+ * stage state, Sec. 2.2.2, fused with the stage combinations of the tableau).
+ * dt <= 0 in phase 0 selects the CFL step; later phases take the same dt (pass
+ * it again or pass 0). The phases of a step give exactly the results of
+ * rmhd_imex_step. Async (enqueued on the context's stream, no CUDA graph).
+ * If t_out is not NULL it receives the simulation time (advanced after the
+ * last phase). rmhd_imex_step is refused while a step is half done.
+ * Errors: RMHD_ERR_STATE (no state, batch, armed recording, phase out of
+ * order), RMHD_ERR_INVALID, RMHD_ERR_CUDA. */
+int rmhd_step_phase(rmhd_ctx *ctx, double dt, int phase, double *t_out);
+
+/* Domain decomposition along y (the paper names multi-GPU runs as future
+ * work, Sec. 3.1 and Sec. 5). A slab context holds rows [j0, j0 + ny_local)
+ * of the 2-D grid described by `global` (ny_local >= 2; 1-D and 3-D grids
+ * are not decomposed); its arrays are [n_var][ny_local][nx]. A side of the
+ * slab is a halo side unless it is a global boundary with RMHD_OUTFLOW (a
+ * periodic global grid has halo sides everywhere, also a single slab that
+ * covers it all, which is then its own neighbour).
+ *   Before every flux pass (odd phase of rmhd_step_phase) each halo side needs
+ *   the neighbour's two rows next to it, of the neighbour's current stage
+ *   state: after the even phase, rmhd_halo_pack writes a slab's first two rows
+ *   (lo) and last two rows (hi) of all N_c conserved and N_w internal
+ *   primitive variables to caller device buffers [N_c + N_w][2][nx]
+ *   (rmhd_halo_doubles gives the length); the caller moves them (a device copy
+ *   on one GPU, NCCL or peer copies across GPUs): slab s receives into its lo
+ *   side the hi rows of slab s - 1 and into its hi side the lo rows of slab
+ *   s + 1 (periodic: cyclically); rmhd_halo_unpack copies them into the slab
+ *   (a NULL pointer, or a side without a neighbour, is skipped). pack and
+ *   unpack are async on the context's stream; the caller orders the stream of
+ *   a neighbour's pack before its own unpack. With exchanged halos every phase
+ *   gives bit for bit the rows of the undecomposed run.
+ *   A slab with a halo side is stepped only through rmhd_step_phase, takes its
+ *   state from rmhd_set_cons or rmhd_set_state (rmhd_set_prims is refused:
+ *   Gauss's law at its edge needs the neighbour's field) and has no adjoint.
+ *   Diagnostics sum over the slab's own cells.
+ * Errors: RMHD_ERR_INVALID (bad configuration or rows), RMHD_ERR_STATE (pack,
+ * unpack or halo_doubles on a context that is not a slab), RMHD_ERR_NOMEM,
+ * RMHD_ERR_CUDA. */
+int rmhd_slab_workspace_bytes(const rmhd_config *global, int j0, int ny_local, size_t *bytes);
+int rmhd_create_slab(rmhd_ctx **out, const rmhd_config *global, int j0, int ny_local, void *cuda_stream,
+                     void *workspace, size_t workspace_bytes);
+int rmhd_halo_doubles(const rmhd_ctx *ctx, size_t *n);
+int rmhd_halo_pack(rmhd_ctx *ctx, double *lo, double *hi);
+int rmhd_halo_unpack(rmhd_ctx *ctx, const double *lo, const double *hi);
+
 /* Batched ensemble of independent 1-D runs (many tests of Sec. 4.1 at once).
  * All runs share `base` (model, x-range, Gamma, kappa, cfl, boundary
  * conditions, precision; base->ny is ignored and taken as 1); run r has

@@ -52,6 +52,23 @@ __device__ __forceinline__ int map_index(int i, int n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// Halo buffer that holds row jj of a slab (jj < 0: the rows below, jj >= ny:
+// the rows above), or null when the row comes from the field itself (interior
+// rows, and the sides where the boundary condition applies). *hr is the row
+// within the buffer; tile rows past ny + 1 only feed cells outside the grid,
+// which are never written, and read the last halo row.
+__device__ __forceinline__ const double *halo_of(const Grid &g, int jj, int *hr) {
+    if (jj < 0 && g.hlo) {
+        *hr = jj + 2;
+        return g.hlo;
+    }
+    if (jj >= g.ny && g.hhi) {
+        *hr = jj - g.ny < 1 ? jj - g.ny : 1;
+        return g.hhi;
+    }
+    return nullptr;
+}
+
 // Barrier over the NTHR threads of component group grp (named barrier 1 + grp;
 // barrier 0 is __syncthreads). The half-point and face buffers are private to
 // a group, so the rounds of the reconstruction only synchronise the group.
@@ -299,13 +316,20 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
         for (int e = tid; e < SN; e += NT) {
             const int sy = e / SW, sx = e - sy * SW;
             const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
-            const int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
-            const long long gc = base + (long long)gj * g.row + gi;
+            int hr = 0;
+            const double *hb = TWO_D ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
             double x[NV];
+            if (hb) {
 #pragma unroll
-            for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
+                for (int v = 0; v < NV; ++v) x[v] = hb[((long long)v * 2 + hr) * g.nx + gi];
+            } else {
+                const int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
+                const long long gc = base + (long long)gj * g.row + gi;
 #pragma unroll
-            for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
+                for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
+#pragma unroll
+                for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) st32[v * SN + e] = to_t<FT>(x[v]);
             const int tx = sx - 2, ty = sy - OY;
@@ -333,9 +357,15 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int v = e / SN, r = e - v * SN;
             int sy = r / SW, sx = r - sy * SW;
             int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
-            int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
-            const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-            st[e] = srcp[base + (long long)gj * g.row + gi];
+            int hr = 0;
+            const double *hb = TWO_D ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
+            if (hb) {
+                st[e] = hb[((long long)v * 2 + hr) * g.nx + gi];
+            } else {
+                int gj = TWO_D ? map_index(j0 + sy - 2, g.ny, g.bcy) : 0;
+                const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
+                st[e] = srcp[base + (long long)gj * g.row + gi];
+            }
         }
         __syncthreads();
         // 2. per-cell auxiliaries of every staged cell, then sources of interior cells

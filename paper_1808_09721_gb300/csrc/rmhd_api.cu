@@ -78,6 +78,13 @@ struct rmhd_ctx {
     double *rec_ck, *rec_seg, *rec_lam, *rec_lamn, *rec_lq, *rec_lr2, *rec_lr3, *rec_fx, *rec_fy, *rec_fz, *rec_fbx,
         *rec_fby, *rec_fbz,
         *rec_qbd, *rec_sig, *rec_pbar, *rec_fin, *rec_sum;
+    // slab of a domain decomposed along y (rmhd_create_slab)
+    bool slab;
+    int slab_j0, slab_ny;   // first global row, global rows
+    double *HLO, *HHI;      // halo rows below / above ([NC + NW][2][nx] each)
+    // phase-by-phase stepping (rmhd_step_phase)
+    int phase_next;         // next phase of the current step (0: between steps)
+    double phase_dt;
     struct Timed { int kind; cudaEvent_t a, b; };
     std::vector<Timed> timed;
     std::string err;
@@ -153,11 +160,12 @@ static Grid make_grid(const rmhd_config *cfg) {
     g.rdz4 = 0.25 / g.dz;
     g.row = cfg->nx;
     g.zoff = (long long)cfg->nx * cfg->ny;
+    g.hlo = g.hhi = nullptr;
     return g;
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status, hist;
+    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status, hist, HLO, HHI;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -184,11 +192,11 @@ static Grid make_grid_n(const rmhd_config *cfg, long long ncell) {
     return g;
 }
 
-static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork);
+static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork, bool halo = false);
 
-static Layout layout(const rmhd_config *cfg) { return layout_g(cfg, make_grid(cfg), 0, 0); }
+static Layout layout(const rmhd_config *cfg, bool halo = false) { return layout_g(cfg, make_grid(cfg), 0, 0, halo); }
 
-static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork) {
+static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork, bool halo) {
     int nc = model_nc(cfg->model), nw = model_nw(cfg->model), np = model_np(cfg->model);
     size_t pl = (size_t)g.plane * sizeof(double);
     Layout L;
@@ -210,6 +218,12 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
     L.hist = o; o += align256(40 * sizeof(unsigned long long));
+    L.HLO = L.HHI = 0;
+    if (halo) {  // slab: two halo rows of every staged variable below and above
+        const size_t hb = (size_t)(nc + nw) * 2 * g.nx * sizeof(double);
+        L.HLO = o; o += align256(hb);
+        L.HHI = o; o += align256(hb);
+    }
     L.nx = L.off = L.dx = L.rdx4 = L.dt = L.sigma = L.eta = L.adt = L.cpsi = L.work = L.run_of = L.Qsave = L.Wsave = 0;
     if (nruns > 0) {
         L.nx = o; o += align256((size_t)nruns * sizeof(int));
@@ -278,12 +292,19 @@ static int read_status(rmhd_ctx *c, const char *what) {
     return fail(c, code, "%s: %s in cell (i=%d, j=%d)", what, kind, i, j);
 }
 
-int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void *workspace, size_t workspace_bytes) {
+static int create_impl(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void *workspace,
+                       size_t workspace_bytes, bool halo) {
     if (!out) return RMHD_ERR_INVALID;
     *out = nullptr;
     int v = validate(cfg);
     if (v) return v;
     rmhd_ctx *c = new rmhd_ctx();
+    c->slab = false;
+    c->slab_j0 = 0;
+    c->slab_ny = cfg->ny;
+    c->HLO = c->HHI = nullptr;
+    c->phase_next = 0;
+    c->phase_dt = 0.0;
     c->cfg = *cfg;
     c->g = make_grid(cfg);
     c->ph.gamma = cfg->gamma;
@@ -318,7 +339,7 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->fresh_prims = false;
     c->w_stale = false;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return RMHD_ERR_CUDA; }
-    Layout L = layout(cfg);
+    Layout L = layout(cfg, halo);
     if (workspace) {
         if (workspace_bytes < L.total || ((uintptr_t)workspace & 255)) { delete c; return RMHD_ERR_NOMEM; }
         c->ws = (char *)workspace;
@@ -342,6 +363,10 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     c->diag = (double *)(c->ws + L.diag);
     c->status = (int *)(c->ws + L.status);
     c->hist = (unsigned long long *)(c->ws + L.hist);
+    if (halo) {
+        c->HLO = (double *)(c->ws + L.HLO);
+        c->HHI = (double *)(c->ws + L.HHI);
+    }
     if (cudaMallocHost(&c->h_status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&c->h_diag, 8 * sizeof(double)) != cudaSuccess) {
         if (c->h_status) cudaFreeHost(c->h_status);  // the first may have succeeded
@@ -351,6 +376,101 @@ int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void 
     }
     if (reset_status(c)) { rmhd_destroy(c); return RMHD_ERR_CUDA; }
     *out = c;
+    return RMHD_OK;
+}
+
+int rmhd_create(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream, void *workspace, size_t workspace_bytes) {
+    return create_impl(out, cfg, cuda_stream, workspace, workspace_bytes, false);
+}
+
+// ---------------------------------------------------------------- slabs
+// Configuration of the slab [j0, j0 + ny_local) of the global 2-D grid: the
+// global x-range and cell widths, ny_local rows.
+static int slab_config(const rmhd_config *global, int j0, int ny_local, rmhd_config *local) {
+    int v = validate(global);
+    if (v) return v;
+    if (global->nz > 1 || global->ny < 2 || ny_local < 2 || j0 < 0 || j0 + ny_local > global->ny)
+        return RMHD_ERR_INVALID;
+    const double dy = (global->ymax - global->ymin) / global->ny;
+    *local = *global;
+    local->ny = ny_local;
+    local->ymin = global->ymin + j0 * dy;
+    local->ymax = global->ymin + (j0 + ny_local) * dy;
+    return validate(local);
+}
+
+int rmhd_slab_workspace_bytes(const rmhd_config *global, int j0, int ny_local, size_t *bytes) {
+    if (!bytes) return RMHD_ERR_INVALID;
+    rmhd_config local;
+    int v = slab_config(global, j0, ny_local, &local);
+    if (v) return v;
+    *bytes = layout(&local, true).total;
+    return RMHD_OK;
+}
+
+int rmhd_create_slab(rmhd_ctx **out, const rmhd_config *global, int j0, int ny_local, void *cuda_stream,
+                     void *workspace, size_t workspace_bytes) {
+    if (!out) return RMHD_ERR_INVALID;
+    *out = nullptr;
+    rmhd_config local;
+    int v = slab_config(global, j0, ny_local, &local);
+    if (v) return v;
+    rmhd_ctx *c = nullptr;
+    v = create_impl(&c, &local, cuda_stream, workspace, workspace_bytes, true);
+    if (v) return v;
+    c->slab = true;
+    c->slab_j0 = j0;
+    c->slab_ny = global->ny;
+    // the global cell height (the slab's own extent / ny_local may differ in the last bit)
+    c->g.dy = (global->ymax - global->ymin) / global->ny;
+    c->g.rdy4 = 0.25 / c->g.dy;
+    // a side has a neighbour unless it is the global boundary with outflow
+    const bool per = global->bc_y == RMHD_PERIODIC;
+    c->g.hlo = (j0 > 0 || per) ? c->HLO : nullptr;
+    c->g.hhi = (j0 + ny_local < global->ny || per) ? c->HHI : nullptr;
+    c->g.bcy = RMHD_OUTFLOW;  // a side without a neighbour is a global outflow boundary
+    c->cfg.bc_y = RMHD_OUTFLOW;
+    *out = c;
+    return RMHD_OK;
+}
+
+static bool has_halo(const rmhd_ctx *c) { return c->g.hlo || c->g.hhi; }
+
+int rmhd_halo_doubles(const rmhd_ctx *c, size_t *n) {
+    if (!c || !n) return RMHD_ERR_INVALID;
+    if (!c->slab) return RMHD_ERR_STATE;
+    *n = (size_t)(model_nc(c->cfg.model) + model_nw(c->cfg.model)) * 2 * c->g.nx;
+    return RMHD_OK;
+}
+
+// The first two rows (lo) and the last two rows (hi) of the current stage
+// state -- the state the next flux pass reads -- as [NC + NW][2][nx].
+int rmhd_halo_pack(rmhd_ctx *c, double *lo, double *hi) {
+    if (!c) return RMHD_ERR_INVALID;
+    if (!c->slab) return fail(c, RMHD_ERR_STATE, "halo_pack: not a slab context");
+    const int nc = model_nc(c->cfg.model), nw = model_nw(c->cfg.model);
+    const size_t w2 = 2 * (size_t)c->g.nx * sizeof(double), pl = (size_t)c->g.plane * sizeof(double);
+    const size_t hi_off = (size_t)(c->g.ny - 2) * c->g.nx;
+    const double *q = c->Q1, *w = c->W1;
+    if (lo) {
+        CK(c, cudaMemcpy2DAsync(lo, w2, q, pl, w2, nc, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemcpy2DAsync(lo + (size_t)nc * 2 * c->g.nx, w2, w, pl, w2, nw, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (hi) {
+        CK(c, cudaMemcpy2DAsync(hi, w2, q + hi_off, pl, w2, nc, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemcpy2DAsync(hi + (size_t)nc * 2 * c->g.nx, w2, w + hi_off, pl, w2, nw, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    }
+    return RMHD_OK;
+}
+
+int rmhd_halo_unpack(rmhd_ctx *c, const double *lo, const double *hi) {
+    if (!c) return RMHD_ERR_INVALID;
+    if (!c->slab) return fail(c, RMHD_ERR_STATE, "halo_unpack: not a slab context");
+    size_t n = 0;
+    rmhd_halo_doubles(c, &n);
+    if (lo && c->g.hlo) CK(c, cudaMemcpyAsync(c->HLO, lo, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (hi && c->g.hhi) CK(c, cudaMemcpyAsync(c->HHI, hi, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     return RMHD_OK;
 }
 
@@ -444,6 +564,9 @@ static int finish_output(rmhd_ctx *c, double *dst, const double *view, int nvar)
 
 int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     if (!c || !prims || (where != RMHD_HOST && where != RMHD_DEVICE)) return fail(c, RMHD_ERR_INVALID, "set_prims: bad argument");
+    if (has_halo(c))
+        return fail(c, RMHD_ERR_STATE, "set_prims: Gauss's law at a slab's edge needs the neighbour's field; "
+                                       "set a slab's state with rmhd_set_cons or rmhd_set_state");
     int np = model_np(c->cfg.model);
     const double *src;
     int st = input_view(c, prims, np, where, &src, "set_prims");
@@ -455,6 +578,7 @@ int rmhd_set_prims(rmhd_ctx *c, const double *prims, int where) {
     st = read_status(c, "set_prims");
     if (st) return st;
     c->has_state = true;
+    c->phase_next = 0;
     c->t = 0.0;
     c->recording = false;
     c->rec_done = 0;
@@ -518,6 +642,7 @@ int rmhd_set_cons(rmhd_ctx *c, const double *cons, int where) {
     st = read_status(c, "set_cons");
     if (st) return st;
     c->has_state = true;
+    c->phase_next = 0;
     c->w_stale = false;
     return RMHD_OK;
 }
@@ -561,6 +686,7 @@ int rmhd_set_state(rmhd_ctx *c, const double *state, int where) {
     CK(c, launch_pack(c->g, nw, src, c->W, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->has_state = true;
+    c->phase_next = 0;
     c->fresh_prims = false;
     c->w_stale = true;  // W is a warm start; output calls recover the primitives of Q
     c->recording = false;
@@ -687,57 +813,95 @@ static double min_width(const rmhd_ctx *c) {
     return h;
 }
 
-// SSP3(332) step (Table 2): three implicit stages (each in place in Q1/W1)
+// Phases of one IMEX step: the implicit stage solves (even phases) and the
+// flux passes (odd phases), in order. SSP2(222) (Table 1), 4 phases:
+//   0: q1 = q^n + g dt Psi(q1)                       (stage solve into Q1/W1)
+//   1: r2 = q^n + dt L1 + (1 - 2g) dt Psi1,  acc = q^n + dt/2 (L1 + Psi1)
+//   2: q2 = r2 + g dt Psi(q2)                        (in place in Q1/W1)
+//   3: q^{n+1} = acc + dt/2 (L2 + Psi2)              (stage-2 primitives kept as the warm start)
+// SSP3(332) (Table 2), 6 phases: three stage solves (each in place in Q1/W1)
 // and three flux passes:
 //   pass 1: r2 = q^n + dt L1 + (1 - 2g) dt Psi1,  r3' = q^n + dt/4 L1 + (1/2 - g) dt Psi1,
 //           acc = q^n + dt/6 (L1 + Psi1)
 //   pass 2: r3 = r3' + dt/4 L2,  acc += dt/6 (L2 + Psi2)
 //   pass 3: q^{n+1} = acc + 2 dt/3 (L3 + Psi3)
-static int enqueue_step_ssp3(rmhd_ctx *c, double dt) {
+static int step_phases(const rmhd_ctx *c) { return c->cfg.scheme == RMHD_SSP3 ? 6 : 4; }
+
+static int enqueue_phase(rmhd_ctx *c, double dt, int phase) {
     const int m = c->cfg.model;
+    const bool ssp3 = c->cfg.scheme == RMHD_SSP3;
+    const bool last = phase == step_phases(c) - 1;
+    if ((phase & 1) == 0) {  // implicit stage solve: stage 1 from q^n, later stages from R
+        StageArgs s = phase == 0 ? stage_args(c, c->Q, c->W, c->Q1, c->W1, kGamma * dt)
+                                 : stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
+        LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s, c->stream));
+        return RMHD_OK;
+    }
     FluxArgs f;
-    StageArgs s1 = stage_args(c, c->Q, c->W, c->Q1, c->W1, kGamma * dt);
-    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
-    f = flux_args(c->Q1, c->W1);
-    int n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
-    n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma, dt);
-    n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
-    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s2 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
-    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
-    f = flux_args(c->Q1, c->W1);
-    n = add_out(f, 0, c->R3, c->R, 0.25, 0.0, dt);
-    n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
-    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s3 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
-    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s3, c->stream));
-    f = flux_args(c->Q1, c->W1);
-    f.wcarry = c->W;
-    n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0, dt);
-    LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
+    int n = 0;
+    if (!ssp3) {
+        n = phase == 1 ? ssp2_pass1(c, c->Q1, c->W1, dt, f) : ssp2_pass2(c, c->Q1, c->W1, dt, f);
+    } else {
+        f = flux_args(c->Q1, c->W1);
+        if (phase == 1) {
+            n = add_out(f, 0, c->Q, c->R, 1.0, 1.0 - 2.0 * kGamma, dt);
+            n = add_out(f, n, c->Q, c->R3, 0.25, 0.5 - kGamma, dt);
+            n = add_out(f, n, c->Q, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
+        } else if (phase == 3) {
+            n = add_out(f, 0, c->R3, c->R, 0.25, 0.0, dt);
+            n = add_out(f, n, c->ACC, c->ACC, 1.0 / 6.0, 1.0 / 6.0, dt);
+        } else {
+            f.wcarry = c->W;
+            n = add_out(f, 0, c->ACC, c->Q, 2.0 / 3.0, 2.0 / 3.0, dt);
+        }
+    }
+    LAUNCH(c, last ? RMHD_K_FLUX2 : RMHD_K_FLUX1, flux_pass(c, n, f));
     return RMHD_OK;
 }
 
 // Enqueue one IMEX step with time step dt.
 static int enqueue_step(rmhd_ctx *c, double dt) {
     if (c->batch) return enqueue_step_batch(c);
-    if (c->cfg.scheme == RMHD_SSP3) return enqueue_step_ssp3(c, dt);
-    const int m = c->cfg.model;
-    FluxArgs f;
-    StageArgs s1 = stage_args(c, c->Q, c->W, c->Q1, c->W1, kGamma * dt);
-    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s1, c->stream));
-    int n = ssp2_pass1(c, c->Q1, c->W1, dt, f);
-    LAUNCH(c, RMHD_K_FLUX1, flux_pass(c, n, f));
-    StageArgs s2 = stage_args(c, c->R, c->W1, c->Q1, c->W1, kGamma * dt);
-    LAUNCH(c, RMHD_K_STAGE, launch_stage(m, c->g, c->ph, s2, c->stream));
-    n = ssp2_pass2(c, c->Q1, c->W1, dt, f);
-    LAUNCH(c, RMHD_K_FLUX2, flux_pass(c, n, f));
+    for (int p = 0; p < step_phases(c); ++p) {
+        int st = enqueue_phase(c, dt, p);
+        if (st) return st;
+    }
+    return RMHD_OK;
+}
+
+int rmhd_step_phase(rmhd_ctx *c, double dt, int phase, double *t_out) {
+    if (!c || phase < 0) return fail(c, RMHD_ERR_INVALID, "step_phase: bad argument");
+    if (!c->has_state) return fail(c, RMHD_ERR_STATE, "step_phase: no state");
+    if (c->batch || c->recording)
+        return fail(c, RMHD_ERR_STATE, "step_phase: single grids without an armed recording only");
+    if (phase >= step_phases(c)) return fail(c, RMHD_ERR_INVALID, "step_phase: phase %d of %d", phase, step_phases(c));
+    if (phase != c->phase_next)
+        return fail(c, RMHD_ERR_STATE, "step_phase: expected phase %d, got %d", c->phase_next, phase);
+    if (phase == 0) {
+        if (!(dt > 0.0)) dt = c->cfg.cfl * min_width(c);
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RMHD_ERR_INVALID, "step_phase: dt must be positive");
+        c->phase_dt = dt;
+        c->fresh_prims = false;
+    } else if (dt > 0.0 && dt != c->phase_dt) {
+        return fail(c, RMHD_ERR_INVALID, "step_phase: the phases of a step take one dt (%g, got %g)", c->phase_dt, dt);
+    }
+    int st = enqueue_phase(c, c->phase_dt, phase);
+    if (st) return st;
+    c->phase_next = (phase + 1) % step_phases(c);
+    if (c->phase_next == 0) {
+        c->t += c->phase_dt;
+        c->w_stale = true;
+    }
+    if (t_out) *t_out = c->t;
     return RMHD_OK;
 }
 
 int rmhd_imex_step(rmhd_ctx *c, double dt, int nsteps, double *t_out) {
     if (!c || nsteps < 0) return fail(c, RMHD_ERR_INVALID, "imex_step: bad argument");
     if (!c->has_state) return fail(c, RMHD_ERR_STATE, "imex_step: no state (call rmhd_set_prims first)");
+    if (has_halo(c))
+        return fail(c, RMHD_ERR_STATE, "imex_step: a slab with neighbours steps by rmhd_step_phase with halo exchange");
+    if (c->phase_next != 0) return fail(c, RMHD_ERR_STATE, "imex_step: a phase-by-phase step is not finished");
     if (c->batch) {
         if (!(c->cfg.cfl > 0.0) && !(dt > 0.0)) return fail(c, RMHD_ERR_INVALID, "imex_step: dt <= 0 needs cfl > 0");
         int st = upload_dt_tables(c, dt > 0.0 ? dt : 0.0);
@@ -1081,7 +1245,7 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch)
+    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->slab)
         return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 single-grid contexts only");
     if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3) || (c->g.nz > 1 && c->g.nz < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");

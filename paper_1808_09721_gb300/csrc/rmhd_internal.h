@@ -22,6 +22,12 @@ struct Grid {
     // zoff * blockIdx.z + j * row + i (x-y planes: row = nx, zoff = nx ny;
     // x-z slabs of a 3-D grid: row = nx ny, zoff = nx).
     long long row, zoff;
+    // Slab of a domain decomposed along y (2-D grids): the two rows below row
+    // 0 (hlo) and above row ny - 1 (hhi) of every staged variable (the N_c
+    // conserved, then the N_w internal primitives), [NC + NW][2][nx] each,
+    // filled by halo exchange with the neighbouring slabs. Null on a side
+    // without a neighbour: the boundary condition bcy applies there.
+    const double *hlo, *hhi;
 };
 
 // Physical constants of a run plus host-precomputed reciprocals (the device
