@@ -315,6 +315,29 @@ int rmhd_kernel_times(rmhd_ctx *ctx, double *ms, int *counts);
  * error was pending on entry, or a launch or event call failed). */
 int rmhd_fp64_fma_rate(void *cuda_stream, double *fma_per_s, int *sm_count);
 
+/* Elementwise evaluation of the device arithmetic helpers the kernels use
+ * (tests of their error bounds; no counterpart in the paper). For i < n,
+ * out[i] = (device arrays, async on cuda_stream)
+ *   RMHD_MATH_RCP    1/x[i]: approximate reciprocal refined by the series
+ *                    y0 (1 + e + e^2), e = 1 - x y0; relative error ~2^-57
+ *                    plus the last rounding, for 2^-1022 <= |x| <= 2^1021
+ *                    (the approximation flushes subnormal inputs and results);
+ *   RMHD_MATH_RSQRT  1/sqrt(x[i]): y0 (1 + e/2 + 3 e^2/8), e = 1 - x y0^2;
+ *                    same accuracy, 2^-1022 <= x < 2^1024;
+ *   RMHD_MATH_DIV1   a[i]/x[i] with one Newton step, t (1 + e), t = a y0:
+ *                    relative error ~2^-38 (used only for WENO3 weights);
+ *   RMHD_MATH_F32    x[i] rounded to FP32 on the integer pipes (nearest,
+ *                    ties away from zero; FP32 subnormals included), as double;
+ *   RMHD_MATH_F64    x[i] (an FP32 value held in a double) converted back by
+ *                    the integer-pipe conversion (exact).
+ * Errors: RMHD_ERR_INVALID (bad which, n < 0, NULL array), RMHD_ERR_CUDA. */
+#define RMHD_MATH_RCP 0
+#define RMHD_MATH_RSQRT 1
+#define RMHD_MATH_DIV1 2
+#define RMHD_MATH_F32 3
+#define RMHD_MATH_F64 4
+int rmhd_eval_math(int which, long long n, const double *x, const double *a, double *out, void *cuda_stream);
+
 /* Diagnostics without any allocation (the paper has no counterpart). For
  * callers that cannot call cudaMalloc -- e.g. code running while a memory
  * pool or arena owns the device, or a framework that forbids allocation after

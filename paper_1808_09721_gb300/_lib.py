@@ -30,7 +30,7 @@ EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_err
            "rmhd_set_solver_stats", "rmhd_solver_stats", "rmhd_set_refinement_cap",
            "rmhd_state_doubles", "rmhd_get_state", "rmhd_set_state", "rmhd_fp64_fma_rate",
            "rmhd_step_phase", "rmhd_slab_workspace_bytes", "rmhd_create_slab", "rmhd_halo_doubles",
-           "rmhd_halo_pack", "rmhd_halo_unpack")
+           "rmhd_halo_pack", "rmhd_halo_unpack", "rmhd_eval_math")
 
 
 class Config(C.Structure):
@@ -95,6 +95,7 @@ def load(path: str | None = None):
                                             _P, _P, _P, _P]
     L.rmhd_fp64_fma_rate.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.rmhd_step_phase.argtypes = [_P, C.c_double, C.c_int, C.POINTER(C.c_double)]
+    L.rmhd_eval_math.argtypes = [C.c_int, C.c_longlong, _P, _P, _P, _P]
     L.rmhd_slab_workspace_bytes.argtypes = [C.POINTER(Config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]
     L.rmhd_create_slab.argtypes = [C.POINTER(_P), C.POINTER(Config), C.c_int, C.c_int, _P, _P, C.c_size_t]
     L.rmhd_halo_doubles.argtypes = [_P, C.POINTER(C.c_size_t)]

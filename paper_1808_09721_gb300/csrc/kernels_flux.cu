@@ -308,6 +308,9 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
     const int grp = tid / NL, lid = tid - grp * NL;
 
     __syncthreads();  // the previous tile of a persistent CTA is done with shared memory
+    // a slab's tile whose staged rows reach past its edge reads halo rows
+    // (uniform over the CTA; false for all other grids)
+    const bool halo_tile = TWO_D && ((g.hlo && j0 < 2) || (g.hhi && j0 + SH - 2 > g.ny));
     if constexpr (L_::SHADOW) {
         // 1-2 (FP32 form). One thread per staged cell (boundary conditions by
         // index map): its FP32 copy, its FP64 current and auxiliaries, and the
@@ -317,7 +320,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             const int sy = e / SW, sx = e - sy * SW;
             const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
             int hr = 0;
-            const double *hb = TWO_D ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
+            const double *hb = halo_tile ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
             double x[NV];
             if (hb) {
 #pragma unroll
@@ -358,7 +361,7 @@ __device__ __forceinline__ void flux_tile(const Grid &g, const Phys &ph, const F
             int sy = r / SW, sx = r - sy * SW;
             int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
             int hr = 0;
-            const double *hb = TWO_D ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
+            const double *hb = halo_tile ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
             if (hb) {
                 st[e] = hb[((long long)v * 2 + hr) * g.nx + gi];
             } else {
