@@ -99,8 +99,8 @@ def test_integer_pipe_conversions(ev):
         want = x.astype(np.float32).astype(np.float64)
     assert np.array_equal(got, want)
     # exact ties (a float plus half an ulp) round away from zero
-    f = rng.uniform(1.0, 2.0, 1000).astype(np.float32).astype(np.float64) * rng.choice([-1.0, 1.0], 1000)
-    half = np.abs(f) * 2.0 ** -24
+    f = rng.uniform(1.0, 1.99, 1000).astype(np.float32).astype(np.float64) * rng.choice([-1.0, 1.0], 1000)
+    half = 2.0 ** -24  # half an FP32 ulp in [1, 2)
     tie = f + np.sign(f) * half
     got = ev(F32, tie)
     away = (np.abs(f) + 2 * half) * np.sign(f)
