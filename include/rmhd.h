@@ -166,13 +166,17 @@ int rmhd_imex_step(rmhd_ctx *ctx, double dt, int nsteps, double *t_out);
 int rmhd_check(rmhd_ctx *ctx);
 
 /* Solver statistics (tracing; off by default). While enabled, every stage
- * solve adds one count to two device histograms: by the number of FP32
- * Newton iterations it took (hist[k], k = 1..30; hist[31]: 31 or more) and
- * by the number of FP64 refinement passes (hist[32 + k - 1], k = 1..8).
- * Counting uses device atomics and slows the stage kernels: it is for
+ * solve adds one count to three device histograms: by the number of FP32
+ * Newton iterations it took (hist[k], k = 1..30; hist[31]: 31 or more), by
+ * the number of FP64 refinement passes (hist[32 + k - 1], k = 1..8), and by
+ * the start that converged (hist[40]: the explicit part's E; hist[41]: the
+ * ideal-MHD limit E = -v x B after the first start failed; hist[42]: the
+ * continuation in a dt after both failed; hist[43]: no start converged --
+ * the cell is then reported as RMHD_ERR_NEWTON; two-fluid solves count 40
+ * or 43). Counting uses device atomics and slows the stage kernels: it is for
  * diagnostics, not for timed runs. rmhd_set_solver_stats(ctx, 1) clears the
  * histograms and starts counting, 0 stops it; rmhd_solver_stats copies the
- * 40 counts into the caller's host array `hist` and clears them.
+ * 44 counts into the caller's host array `hist` and clears them.
  * Synchronous. Errors: RMHD_ERR_INVALID, RMHD_ERR_CUDA. */
 int rmhd_set_solver_stats(rmhd_ctx *ctx, int enable);
 int rmhd_solver_stats(rmhd_ctx *ctx, unsigned long long *hist);
@@ -184,6 +188,17 @@ int rmhd_solver_stats(rmhd_ctx *ctx, unsigned long long *hist);
  * the first failing cell (reported by rmhd_check), and the context stays
  * usable. Errors: RMHD_ERR_INVALID (passes outside 0..8). */
 int rmhd_set_refinement_cap(rmhd_ctx *ctx, int passes);
+
+/* Test control of the stage-solve restarts (single fluid). Every implicit
+ * stage solve (Sec. 2.2.1, Eq. implicit stage) tries up to three starts: 0,
+ * the explicit part's E; 1, the ideal-MHD limit E = -v x B (Sec. 2.1.1); 2,
+ * a continuation in a dt; a cell whose start fails goes on to the next. The
+ * root is the same whichever start converges. rmhd_set_first_start(ctx, s)
+ * makes every solve begin at start s (1 or 2; 0, the default, restores all
+ * starts), which exercises the restart path on any state; all cells must fit
+ * the restart list (2^18 cells). Errors: RMHD_ERR_INVALID (s outside 0..2,
+ * grid too large), RMHD_ERR_STATE (two-fluid context). */
+int rmhd_set_first_start(rmhd_ctx *ctx, int start);
 
 /* Diagnostics of the current state (Sec. 2.1 invariants), written to out[8]:
  * sum D, sum tau, sum S_x, sum B_x, sum varrho (Dbar for two fluids)

@@ -30,7 +30,8 @@ EXPORTS = ("rmhd_workspace_bytes", "rmhd_create", "rmhd_destroy", "rmhd_last_err
            "rmhd_set_solver_stats", "rmhd_solver_stats", "rmhd_set_refinement_cap",
            "rmhd_state_doubles", "rmhd_get_state", "rmhd_set_state", "rmhd_fp64_fma_rate",
            "rmhd_step_phase", "rmhd_slab_workspace_bytes", "rmhd_create_slab", "rmhd_halo_doubles",
-           "rmhd_halo_pack", "rmhd_halo_unpack", "rmhd_eval_math")
+           "rmhd_halo_pack", "rmhd_halo_unpack", "rmhd_eval_math",
+           "rmhd_set_first_start")
 
 
 class Config(C.Structure):
@@ -88,6 +89,7 @@ def load(path: str | None = None):
     L.rmhd_set_solver_stats.argtypes = [_P, C.c_int]
     L.rmhd_solver_stats.argtypes = [_P, C.POINTER(C.c_ulonglong)]
     L.rmhd_set_refinement_cap.argtypes = [_P, C.c_int]
+    L.rmhd_set_first_start.argtypes = [_P, C.c_int]
     L.rmhd_state_doubles.argtypes = [_P, C.POINTER(C.c_size_t)]
     L.rmhd_get_state.argtypes = [_P, _P, C.c_int]
     L.rmhd_set_state.argtypes = [_P, _P, C.c_int]

@@ -27,6 +27,19 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// A cell whose first start failed goes to the restart list (or, beyond its
+// capacity, is reported as failed).
+__device__ __forceinline__ void defer_or_record(const StageArgs &a, int st, long long cell) {
+    if (st == sf::ST_NEWTON && a.rlist) {
+        const int slot = atomicAdd(a.rlist, 1);
+        if (slot < a.rcap) {
+            a.rlist[1 + slot] = (int)cell;
+            return;
+        }
+    }
+    record(a.status, st, cell);
+}
+
 // ---------------------------------------------------------------- stage
 // 5 blocks per SM (at most 96 registers): the solve is latency-bound, and
 // 20 warps per SM hide more of its FP64 and MUFU latency than 16 (no spills)
@@ -38,8 +51,25 @@ __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, 
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const double pw = a.wwarm[P * g.plane + cell];
-        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
-        record(a.status, st, cell);
+        const int st = a.first_start == 0 ? stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell)
+                                          : (int)sf::ST_NEWTON;
+        defer_or_record(a, st, cell);
+    }
+}
+
+// The listed cells again, from the ideal-limit start and then along a
+// continuation in a dt (physics_sf.cuh: stage_restarts). Launched after every
+// single-fluid stage kernel; with an empty list every thread exits at once.
+template <bool STATS>
+__global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
+    using namespace sf;
+    const int n = min(a.rlist[0], a.rcap);
+    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long cell = a.rlist[1 + e];
+        const double pw = a.wwarm[P * g.plane + cell];
+        record(a.status, stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start),
+               cell);
     }
 }
 
@@ -63,6 +93,9 @@ __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph
     }
 }
 
+// restart kernels: a small fixed grid (the list is short: cells whose first start failed)
+static constexpr int kRestartBlocks = 64;
+
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > (1 << 30) ? (1 << 30) : b));
@@ -73,8 +106,16 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
     int blocks = grid_for(g.ncell, kStageThreads);
     const int btf = grid_for(g.ncell, kStageThreadsTF);
     if (model == 0) {
+        if (a.rlist) {
+            cudaError_t e = cudaMemsetAsync(a.rlist, 0, sizeof(int), s);
+            if (e != cudaSuccess) return e;
+        }
         if (a.hist) k_stage_sf<true><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
         else k_stage_sf<false><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+        if (a.rlist) {
+            if (a.hist) k_restart_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
+            else k_restart_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
+        }
     } else {
         if (a.hist) k_stage_tf<true><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
         else k_stage_tf<false><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
@@ -93,9 +134,26 @@ __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, B
          cell += (long long)gridDim.x * blockDim.x) {
         const int run = b.run_of[cell];
         sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        const int st =
-            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
-        record(a.status, st, cell);
+        const int st = a.first_start == 0
+                           ? stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell,
+                                                       a.w + cell)
+                           : (int)sf::ST_NEWTON;
+        defer_or_record(a, st, cell);
+    }
+}
+
+template <bool STATS>
+__global__ void k_restart_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
+    using namespace sf;
+    const int n = min(a.rlist[0], a.rcap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long cell = a.rlist[1 + e];
+        const int run = b.run_of[cell];
+        sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
+        record(a.status,
+               stage_restarts<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell,
+                                            a.first_start),
+               cell);
     }
 }
 
@@ -120,8 +178,16 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
                                int threads, cudaStream_t s) {
     int blocks = grid_for(g.ncell, threads);
     if (model == 0) {
+        if (a.rlist) {
+            cudaError_t e = cudaMemsetAsync(a.rlist, 0, sizeof(int), s);
+            if (e != cudaSuccess) return e;
+        }
         if (a.hist) k_stage_batch_sf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_sf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
+        if (a.rlist) {
+            if (a.hist) k_restart_batch_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
+            else k_restart_batch_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
+        }
     } else {
         if (a.hist) k_stage_batch_tf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_tf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);

@@ -164,11 +164,13 @@ struct StageConst {
     unsigned long long *hist;   // if not null: histograms of FP32 iterations [32] and FP64 passes [8]
 };
 
-// Adds one solve to the histograms: by FP32 Newton iterations and by FP64 passes.
-__device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, int npass) {
+// Adds one solve to the histograms: by FP32 Newton iterations, by FP64
+// passes, and by the start that converged (start 0, 1, 2; 3: none did).
+__device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, int npass, int start) {
     if (!hist) return;
     atomicAdd(&hist[nit < 31 ? nit : 31], 1ULL);
     atomicAdd(&hist[32 + npass - 1], 1ULL);
+    atomicAdd(&hist[40 + start], 1ULL);
 }
 
 // Solve one implicit stage for one cell. rp: the cell's explicit part (14
@@ -180,9 +182,21 @@ __device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, i
 // the iteration histogram k.hist; it is a template switch rather than a null
 // test because the live counters lengthen the latency-bound code even when
 // nothing is counted.
+//
+// Starts (the root is the same whichever converges; only the path differs):
+//   0. E = r_E;
+//   1. the ideal-MHD limit E = -v x B with v recovered at E = r_E (the
+//      sigma -> infinity root, Sec. 2.1.1), if start 0 fails;
+//   2. continuation in a dt: the stage solved for a dt / 64, a dt / 32, ...,
+//      a dt in FP32, each from the previous root, if start 1 fails too.
+// A start fails on a singular FP32 Jacobian, an FP32 pressure root that does
+// not exist, or FP64 passes that do not reach the acceptance test.
+// stage_solve runs start 0 and returns ST_NEWTON when it fails; the kernels
+// then hand the cell to stage_restarts (starts 1 and 2) in a separate launch,
+// which keeps the register allocation of the common path unchanged.
 template <int NREF, bool STATS = false>
-__device__ int stage_solve(const double *rp, long long ps, double p_warm, const StageConst &k, double *qp,
-                           double *wp) {
+__device__ __forceinline__ int stage_solve(const double *rp, long long ps, double p_warm, const StageConst &k,
+                                           double *qp, double *wp) {
     const double gm1 = k.gamma - 1.0, gam = k.gamma;
     double tauB;
     float Bf[3], Sf[3], rEf[3], tauBf, Df, rhoef;
@@ -265,7 +279,7 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
             if (pres_solve_f32(pt, at, S2t, Df, gm1f, gamf, dft)) {
                 stage_resid(Et, pt, Stt, at, Bf, rEf, rhoef, adtf, sigf, Gt, vt, Wt);
                 float gt = fmaxf(fmaxf(fabsf(Gt[0]), fabsf(Gt[1])), fabsf(Gt[2]));
-                if (gt < gn || t < 0.02f) {
+                if (gt < gn || (t < 0.02f && gt <= 1.5f * gn)) {
                     E[0] = Et[0]; E[1] = Et[1]; E[2] = Et[2];
                     p = pt; dfdp = dft; G[0] = Gt[0]; G[1] = Gt[1]; G[2] = Gt[2];
                     v[0] = vt[0]; v[1] = vt[1]; v[2] = vt[2]; W = Wt;
@@ -304,13 +318,16 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     const double rdf = f64_of(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
     double gres = 0.0;
+    bool pconv = false;
     int pass = 0;
     for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
         em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
-        pdd -= pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
+        const double dp = pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
+        pdd -= dp;
+        pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
         gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
-        if (pass >= NREF - 1 && gres <= tolg) break;
+        if (pass >= NREF - 1 && gres <= tolg && pconv) break;
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
@@ -329,9 +346,204 @@ __device__ int stage_solve(const double *rp, long long ps, double p_warm, const 
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
-    if constexpr (STATS) count_solve(k.hist, nit, pass + 1);
-    if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64)) return ST_NEWTON;
+    if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
+        return ST_NEWTON;  // counted by the restart (stage_restarts)
+    if constexpr (STATS) count_solve(k.hist, nit, pass + 1, 0);
     return ST_OK;
+}
+
+// One restart of the solve (starts 1 and 2 above): the same FP32 Newton phase
+// and FP64 passes, from the ideal-limit E (START = 1) or along a continuation
+// in a dt (START = 2). Used only after start 0 failed.
+template <int NREF, bool STATS, int START>
+__device__ __forceinline__ int stage_attempt(const double *rp, long long ps, double p_warm, const StageConst &k,
+                                             double *qp, double *wp) {
+    constexpr int start = START;
+    const double gm1 = k.gamma - 1.0, gam = k.gamma;
+    double tauB;
+    float Bf[3], Sf[3], rEf[3], tauBf, Df, rhoef;
+    {
+        const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
+        const double Sv[3] = {rp[SX * ps], rp[SY * ps], rp[SZ * ps]};
+        const double tau = rp[TAU * ps], Dd = rp[D * ps], rhoe = rp[RHOE * ps];
+        tauB = tau - 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        for (int i = 0; i < 3; ++i) {
+            const double rEi = rp[(EX + i) * ps];
+            Bf[i] = f32_of(B[i]);
+            Sf[i] = f32_of(Sv[i]);
+            rEf[i] = f32_of(rEi);
+            qp[(EX + i) * ps] = rEi;  // replaced by the root; left as r_E if the solve fails
+        }
+        tauBf = f32_of(tauB);
+        Df = f32_of(Dd);
+        rhoef = f32_of(rhoe);
+        // source-free components equal r; psi and phi in closed form
+        qp[D * ps] = Dd;
+        qp[TAU * ps] = tau;
+        qp[RHOE * ps] = rhoe;
+        for (int i = 0; i < 3; ++i) {
+            qp[(SX + i) * ps] = Sv[i];
+            qp[(BX + i) * ps] = B[i];
+        }
+        qp[PSI * ps] = (rp[PSI * ps] + k.adt * rhoe) * k.cpsi;
+        qp[PHI * ps] = rp[PHI * ps] * k.cpsi;
+    }
+
+    const float adtf = f32_of(k.adt), sigf = f32_of(k.sigma), gm1f = f32_of(gm1), gamf = f32_of(gam);
+    const float scale = fmaxf(fmaxf(fabsf(rEf[0]), fabsf(rEf[1])), fmaxf(fabsf(rEf[2]), 1e-30f));
+    int nit = 0, pass = 0;
+    {
+        // ---- FP32 Newton (start 2: a continuation of 7 levels in a dt)
+        float E[3] = {rEf[0], rEf[1], rEf[2]};
+        float p = f32_of(p_warm), dfdp = -1.f;
+        float G[3], v[3], W, St[3], a, S2;
+        float Minv[9], dpdE[3];
+        bool have_jac = false, ok = true;
+        if constexpr (start == 1) {  // the ideal-MHD limit E = -v x B, v recovered at E = r_E
+            em_split(E, Sf, Bf, tauBf, Df, St, a, S2);
+            if (!pres_solve_f32(p, a, S2, Df, gm1f, gamf, dfdp)) return ST_NEWTON;
+            stage_resid(E, p, St, a, Bf, rEf, rhoef, adtf, sigf, G, v, W);
+            cross(v, Bf, E);
+            E[0] = -E[0]; E[1] = -E[1]; E[2] = -E[2];
+        }
+        constexpr int nlev = start == 2 ? 7 : 1;
+        nit = 0;
+        for (int lev = 0; lev < nlev && ok; ++lev) {
+            // a dt 2^-(nlev-1-lev)
+            const float adtl = nlev == 1 ? adtf : adtf * __int_as_float((127 - (nlev - 1 - lev)) << 23);
+            em_split(E, Sf, Bf, tauBf, Df, St, a, S2);
+            if (!pres_solve_f32(p, a, S2, Df, gm1f, gamf, dfdp)) {
+                if (start == 0) return ST_C2P;  // r admits no primitives: no start can help
+                ok = false;
+                break;
+            }
+            stage_resid(E, p, St, a, Bf, rEf, rhoef, adtl, sigf, G, v, W);
+            float gn = fmaxf(fmaxf(fabsf(G[0]), fabsf(G[1])), fabsf(G[2]));
+            for (int it = 0; it < 24; ++it) {
+                ++nit;
+                // Jacobian columns dG/dE_k with duals; dp/dE_k by the implicit-function theorem
+                float Jm[9];
+                for (int kc = 0; kc < 3; ++kc) {
+                    Dual<float> Ed[3] = {Dual<float>(E[0], kc == 0), Dual<float>(E[1], kc == 1),
+                                         Dual<float>(E[2], kc == 2)};
+                    Dual<float> Std[3], ad, S2d;
+                    em_split(Ed, Sf, Bf, tauBf, Df, Std, ad, S2d);
+                    Dual<float> pd(p);
+                    Dual<float> fd = pres_resid(pd, ad, S2d, Df, gm1f, gamf);
+                    pd = Dual<float>(p, -fd.d / dfdp);
+                    dpdE[kc] = pd.d;
+                    Dual<float> Gd[3], vd[3], Wd;
+                    stage_resid(Ed, pd, Std, ad, Bf, rEf, rhoef, adtl, sigf, Gd, vd, Wd);
+                    Jm[0 + kc] = Gd[0].d;
+                    Jm[3 + kc] = Gd[1].d;
+                    Jm[6 + kc] = Gd[2].d;
+                }
+                if (!inv3(Jm, Minv)) { ok = false; break; }
+                have_jac = true;
+                float dE[3];
+                for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * G[0] + Minv[3 * i + 1] * G[1] + Minv[3 * i + 2] * G[2];
+                float dn = fmaxf(fmaxf(fabsf(dE[0]), fabsf(dE[1])), fabsf(dE[2]));
+                if (dn <= 2e-7f * fmaxf(scale, fmaxf(fmaxf(fabsf(E[0]), fabsf(E[1])), fabsf(E[2])))) break;
+                // |G| at the FP32 noise floor (p and v carry ~2e-7 relative error):
+                // further FP32 steps cannot improve E; the FP64 passes take over
+                if (gn <= 1e-6f * resid_scale(E, rEf, v, Bf, W, rhoef, adtl, sigf)) break;
+                // backtracking on |G|_inf; the shortest steps may raise |G| by at
+                // most half (a way out of FP32 noise), never more
+                float t = 1.f;
+                bool accepted = false;
+                for (int ls = 0; ls < 8; ++ls) {
+                    float Et[3] = {E[0] - t * dE[0], E[1] - t * dE[1], E[2] - t * dE[2]};
+                    float pt = p, dft = dfdp, Gt[3], vt[3], Wt, Stt[3], at, S2t;
+                    em_split(Et, Sf, Bf, tauBf, Df, Stt, at, S2t);
+                    if (pres_solve_f32(pt, at, S2t, Df, gm1f, gamf, dft)) {
+                        stage_resid(Et, pt, Stt, at, Bf, rEf, rhoef, adtl, sigf, Gt, vt, Wt);
+                        float gt = fmaxf(fmaxf(fabsf(Gt[0]), fabsf(Gt[1])), fabsf(Gt[2]));
+                        if (gt < gn || (t < 0.02f && gt <= 1.5f * gn)) {
+                            E[0] = Et[0]; E[1] = Et[1]; E[2] = Et[2];
+                            p = pt; dfdp = dft; G[0] = Gt[0]; G[1] = Gt[1]; G[2] = Gt[2];
+                            v[0] = vt[0]; v[1] = vt[1]; v[2] = vt[2]; W = Wt;
+                            gn = gt;
+                            accepted = true;
+                            break;
+                        }
+                    }
+                    t *= 0.5f;
+                }
+                if (!accepted) break;  // FP32 noise floor: hand over to the FP64 passes
+            }
+        }
+        if (!ok || !have_jac) return ST_NEWTON;
+
+        // ---- FP64 refinement passes. Pass k evaluates G in FP64 at E_k (one FP64
+        // pressure step, started from a first-order prediction) and forms the
+        // correction dE_k with the FP32 inverse Jacobian. The evaluation point at
+        // which |G| reaches round-off of the magnitude of G's terms and the
+        // pressure step is at FP64 round-off (at least the NREF-th) is the
+        // result, with its own primitives (J amplifies any E/v mismatch by
+        // sigma). Cells that need it take extra passes (up to 8).
+        const float gs = resid_scale(E, rEf, v, Bf, W, rhoef, adtf, sigf);  // round-off scale of G
+        // Acceptance |G| <= tol gs. The explicit stages evaluate J = sigma W (E + v x B
+        // - (v.E) v) at the accepted E, which multiplies an E error by ~sigma dt W,
+        // while G's own terms carry a dt sigma W: for stiff cells (a dt sigma W >> 1)
+        // the tolerance shrinks by that factor, down to a few units of FP64
+        // round-off of G's terms. Non-stiff cells keep 1e-12.
+        const double tolg = f64_of(fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
+        // FP64 inputs, read again (the stores above keep the compiler from reusing
+        // the first loads' registers)
+        const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
+        const double Sv[3] = {rp[SX * ps], rp[SY * ps], rp[SZ * ps]};
+        const double rE[3] = {rp[EX * ps], rp[EY * ps], rp[EZ * ps]};
+        const double Dd = rp[D * ps], rhoe = rp[RHOE * ps];
+        double Ed[3] = {f64_of(E[0]), f64_of(E[1]), f64_of(E[2])};
+        double pdd = f64_of(p);
+        const double rdf = f64_of(1.f / dfdp);
+        double St64[3], a64, S264, G64[3], v64[3], W64;
+        double gres = 0.0;
+        bool pconv = false;
+        for (pass = 0; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
+            em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
+            const double dp = pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
+            pdd -= dp;
+            // the pressure step is at round-off: with the FP32 slope each step
+            // gains ~7 digits, so the error left after this one is below 1e-13 p
+            pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
+            stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
+            gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
+            if (pass >= NREF - 1 && gres <= tolg && pconv) break;
+            float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
+            float dE[3];
+            for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
+            if (pass == 7 || pass == k.maxpass - 1) break;
+            // first-order prediction of the pressure at the corrected E
+            pdd -= f64_of(dpdE[0] * dE[0] + dpdE[1] * dE[1] + dpdE[2] * dE[2]);
+            Ed[0] -= f64_of(dE[0]);
+            Ed[1] -= f64_of(dE[1]);
+            Ed[2] -= f64_of(dE[2]);
+        }
+        if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
+            return ST_NEWTON;
+        wp[VX * ps] = v64[0];
+        wp[VY * ps] = v64[1];
+        wp[VZ * ps] = v64[2];
+        wp[P * ps] = pdd;
+        wp[LOR * ps] = W64;
+        qp[EX * ps] = Ed[0];
+        qp[EY * ps] = Ed[1];
+        qp[EZ * ps] = Ed[2];
+        if constexpr (STATS) count_solve(k.hist, nit, pass + 1, start);
+        return ST_OK;
+    }
+}
+
+// Starts 1 and 2 after start 0 failed. A solve that no start converges is
+// counted as start 3.
+template <int NREF, bool STATS>
+__device__ int stage_restarts(const double *rp, long long ps, double p_warm, const StageConst &k, double *qp,
+                              double *wp, int first = 1) {
+    if (first <= 1 && stage_attempt<NREF, STATS, 1>(rp, ps, p_warm, k, qp, wp) == ST_OK) return ST_OK;
+    if (stage_attempt<NREF, STATS, 2>(rp, ps, p_warm, k, qp, wp) == ST_OK) return ST_OK;
+    if constexpr (STATS) count_solve(k.hist, 24, 8, 3);
+    return ST_NEWTON;
 }
 
 // Primitive recovery of a conserved state (no source solve): FP32 root, then

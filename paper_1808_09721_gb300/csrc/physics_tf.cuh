@@ -469,8 +469,9 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
         qp[(EX + i) * ps] = xd[4 + i];
     }
     qp[TAUB * ps] = xd[3] * c.mur;
-    if constexpr (STATS) sf::count_solve(k.hist, nit, pass + 1);
-    if (!ok || !(gres <= 1e-9 * f64_of(gs))) return sf::ST_NEWTON;
+    ok = ok && gres <= 1e-9 * f64_of(gs);
+    if constexpr (STATS) sf::count_solve(k.hist, nit, pass + 1, ok ? 0 : 3);
+    if (!ok) return sf::ST_NEWTON;
     return sf::ST_OK;
 }
 

@@ -42,7 +42,10 @@ struct rmhd_ctx {
     double *LBUF;  // 3-D grids: L_x + L_y of the current flux pass (null otherwise)
     double *SRCG;  // two fluids: source scratch of the FP64 flux kernel (null otherwise)
     int *status;       // device [2]
-    unsigned long long *hist;  // device [40]: solver statistics (FP32 iterations, FP64 passes)
+    unsigned long long *hist;  // device [44]: solver statistics (FP32 iterations, FP64 passes, starts)
+    int *rlist;                // device [1 + rcap]: cells whose first stage-solve start failed
+    int rcap;
+    int first_start;           // rmhd_set_first_start (tests of the restart path)
     bool stats_on;             // count stage solves into hist
     int maxpass;               // cap on the FP64 refinement passes (0: the kernels' default)
     int *h_status;     // pinned host copy of the 64-bit status key
@@ -165,7 +168,7 @@ static Grid make_grid(const rmhd_config *cfg) {
 }
 
 struct Layout {
-    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status, hist, HLO, HHI;
+    size_t Q, W, Q1, W1, R, ACC, R3, LBUF, SRCG, stage, scratch, diag, status, hist, HLO, HHI, rlist;
     size_t nx, off, dx, rdx4, dt, sigma, eta, adt, cpsi, work, run_of, Qsave, Wsave;
     size_t total;
 };
@@ -194,6 +197,10 @@ static Grid make_grid_n(const rmhd_config *cfg, long long ncell) {
 
 static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork, bool halo = false);
 
+// Cells of one stage whose first solve start may fail and be restarted in
+// the restart kernel (more are reported as failed).
+static int restart_capacity(long long ncell) { return (int)std::min<long long>(ncell, 1 << 18); }
+
 static Layout layout(const rmhd_config *cfg, bool halo = false) { return layout_g(cfg, make_grid(cfg), 0, 0, halo); }
 
 static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long long maxwork, bool halo) {
@@ -217,7 +224,8 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
-    L.hist = o; o += align256(40 * sizeof(unsigned long long));
+    L.hist = o; o += align256(44 * sizeof(unsigned long long));
+    L.rlist = o; o += align256((1 + (size_t)restart_capacity(g.ncell)) * sizeof(int));
     L.HLO = L.HHI = 0;
     if (halo) {  // slab: two halo rows of every staged variable below and above
         const size_t hb = (size_t)(nc + nw) * 2 * g.nx * sizeof(double);
@@ -363,6 +371,8 @@ static int create_impl(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream
     c->diag = (double *)(c->ws + L.diag);
     c->status = (int *)(c->ws + L.status);
     c->hist = (unsigned long long *)(c->ws + L.hist);
+    c->rlist = (int *)(c->ws + L.rlist);
+    c->rcap = restart_capacity(c->g.ncell);
     if (halo) {
         c->HLO = (double *)(c->ws + L.HLO);
         c->HHI = (double *)(c->ws + L.HHI);
@@ -727,7 +737,8 @@ static int toc(rmhd_ctx *c) {
 // Stage-solve arguments with the context's statistics and refinement settings.
 static StageArgs stage_args(const rmhd_ctx *c, const double *r, const double *wwarm, double *q, double *w,
                             double adt) {
-    StageArgs a{r, wwarm, q, w, c->status, adt, c->stats_on ? c->hist : nullptr, c->maxpass};
+    StageArgs a{r, wwarm, q, w, c->status, adt, c->stats_on ? c->hist : nullptr, c->maxpass,
+                c->cfg.model == RMHD_RESISTIVE ? c->rlist : nullptr, c->rcap, c->first_start};
     return a;
 }
 
@@ -1076,6 +1087,8 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->diag = (double *)(c->ws + L.diag);
     c->status = (int *)(c->ws + L.status);
     c->hist = (unsigned long long *)(c->ws + L.hist);
+    c->rlist = (int *)(c->ws + L.rlist);
+    c->rcap = restart_capacity(c->g.ncell);
     c->d_nx = (int *)(c->ws + L.nx);
     c->d_off = (long long *)(c->ws + L.off);
     c->d_dx = (double *)(c->ws + L.dx);
@@ -1443,7 +1456,7 @@ int rmhd_kernel_times(rmhd_ctx *c, double *ms, int *counts) {
 
 int rmhd_set_solver_stats(rmhd_ctx *c, int enable) {
     if (!c) return RMHD_ERR_INVALID;
-    if (enable) CK(c, cudaMemsetAsync(c->hist, 0, 40 * sizeof(unsigned long long), c->stream));
+    if (enable) CK(c, cudaMemsetAsync(c->hist, 0, 44 * sizeof(unsigned long long), c->stream));
     c->stats_on = enable != 0;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // captured with the old arguments
     CK(c, cudaStreamSynchronize(c->stream));
@@ -1452,8 +1465,8 @@ int rmhd_set_solver_stats(rmhd_ctx *c, int enable) {
 
 int rmhd_solver_stats(rmhd_ctx *c, unsigned long long *hist) {
     if (!c || !hist) return fail(c, RMHD_ERR_INVALID, "solver_stats: bad argument");
-    CK(c, cudaMemcpyAsync(hist, c->hist, 40 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaMemsetAsync(c->hist, 0, 40 * sizeof(unsigned long long), c->stream));
+    CK(c, cudaMemcpyAsync(hist, c->hist, 44 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemsetAsync(c->hist, 0, 44 * sizeof(unsigned long long), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return RMHD_OK;
 }
@@ -1462,6 +1475,18 @@ int rmhd_set_refinement_cap(rmhd_ctx *c, int passes) {
     if (!c) return RMHD_ERR_INVALID;
     if (passes < 0 || passes > 8) return fail(c, RMHD_ERR_INVALID, "set_refinement_cap: passes must be 0..8");
     c->maxpass = passes;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // captured with the old arguments
+    return RMHD_OK;
+}
+
+int rmhd_set_first_start(rmhd_ctx *c, int start) {
+    if (!c || start < 0 || start > 2) return fail(c, RMHD_ERR_INVALID, "set_first_start: start must be 0, 1 or 2");
+    if (c->cfg.model != RMHD_RESISTIVE) return fail(c, RMHD_ERR_STATE, "set_first_start: single-fluid contexts only");
+    const long long cells = c->g.ncell;
+    if (start > 0 && cells > c->rcap)
+        return fail(c, RMHD_ERR_INVALID, "set_first_start: more cells (%lld) than the restart list holds (%d)", cells,
+                    c->rcap);
+    c->first_start = start;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // captured with the old arguments
     return RMHD_OK;
 }

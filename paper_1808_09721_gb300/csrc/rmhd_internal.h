@@ -64,8 +64,15 @@ struct StageArgs {
     double *w;           // its primitives, NW planes
     int *status;
     double adt;          // a_ii dt
-    unsigned long long *hist;  // if not null: per-solve histograms, FP32 Newton iterations [32] and FP64 passes [8]
+    unsigned long long *hist;  // if not null: per-solve histograms, FP32 Newton iterations [32], FP64 passes [8]
+                               // and converged starts [4]
     int maxpass;               // cap on the FP64 refinement passes (0: the default, 8)
+    // single fluid: cells whose first start failed, handed to the restart
+    // kernel (rlist[0]: count, rlist[1 .. rcap]: cells); a cell beyond the
+    // capacity is reported as failed. Null: no restarts.
+    int *rlist;
+    int rcap;
+    int first_start;  // tests of the restart path: 1 or 2 skips the earlier starts (0: all starts)
 };
 
 // Batched ensemble of independent 1-D runs packed one after another in every

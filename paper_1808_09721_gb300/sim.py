@@ -202,11 +202,18 @@ class Sim:
         self._check(self.lib.rmhd_set_solver_stats(self.h, int(bool(on))), "set_solver_stats")
 
     def solver_stats(self) -> dict:
-        """Histograms since the last read: {"fp32_iterations": {k: solves}, "fp64_passes": {k: solves}}."""
-        h = (C.c_ulonglong * 40)()
+        """Histograms since the last read: {"fp32_iterations": {k: solves}, "fp64_passes": {k: solves},
+        "starts": {"explicit": n, "ideal_limit": n, "continuation": n, "failed": n}}."""
+        h = (C.c_ulonglong * 44)()
         self._check(self.lib.rmhd_solver_stats(self.h, h), "solver_stats")
         return {"fp32_iterations": {k: int(h[k]) for k in range(1, 32) if h[k]},
-                "fp64_passes": {k: int(h[32 + k - 1]) for k in range(1, 9) if h[32 + k - 1]}}
+                "fp64_passes": {k: int(h[32 + k - 1]) for k in range(1, 9) if h[32 + k - 1]},
+                "starts": {k: int(h[40 + i]) for i, k in enumerate(("explicit", "ideal_limit", "continuation",
+                                                                    "failed"))}}
+
+    def set_first_start(self, start: int):
+        """Begin every stage solve at start 0 (default), 1 (ideal-MHD limit) or 2 (continuation)."""
+        self._check(self.lib.rmhd_set_first_start(self.h, int(start)), "set_first_start")
 
     def set_refinement_cap(self, passes: int):
         """Cap the FP64 refinement passes of the stage solves (0: default); 1 forces RMHD_ERR_NEWTON."""

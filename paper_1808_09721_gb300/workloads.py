@@ -231,6 +231,36 @@ def random_smooth(shape, seed: int = 0, model: int = RESISTIVE, sigma: float = 1
                     cfl, 10, np.ascontiguousarray(sp), mu_e=-mu, mu_p=mu, **kw)
 
 
+def relativistic_smooth(shape, seed: int = 0, sigma: float = 1e8, wmax: float = 10.0, gamma: float = 4.0 / 3.0,
+                        cfl: float = 0.4, bc: int = PERIODIC) -> Workload:
+    """Smooth random periodic single-fluid fields in relativistic bulk motion:
+    rho, p in [0.5, 1.5], B_i up to 1, a velocity of one random direction
+    (perturbed by up to 5% per component) with Lorentz factor W varying
+    smoothly by 10% around wmax (|v| = sqrt(1 - 1/W^2)), and E = -v x B + a
+    smooth |dE_i| <= 0.1 (a resistive current that stiff sigma damps)."""
+    shape = tuple(shape)
+    nd = len(shape)
+    nz, ny, nx = (1,) * (3 - nd) + shape
+    axes = [(np.arange(n) + 0.5) / n for n in (nz, ny, nx)]
+    Z, Y, X = np.meshgrid(*axes, indexing="ij")
+    coords = [X, Y, Z][:nd]
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + _smooth(rng, coords, 0.5)
+    p = 1.0 + _smooth(rng, coords, 0.5)
+    d0 = rng.standard_normal(3)
+    d = np.stack([d0[i] / np.linalg.norm(d0) + _smooth(rng, coords, 0.05) for i in range(3)])
+    d = d / np.sqrt((d * d).sum(axis=0))
+    W = wmax * (1.0 + _smooth(rng, coords, 0.1))
+    v = d * np.sqrt(1.0 - 1.0 / (W * W))
+    B = np.stack([_smooth(rng, coords, 1.0) for _ in range(3)])
+    E = _ideal_e(v, B) + np.stack([_smooth(rng, coords, 0.1) for _ in range(3)])
+    sq = (lambda a: a.reshape(a.shape[:-3] + (ny, nx))) if nz == 1 else (lambda a: a)
+    kw = dict(nz=nz, zlim=(0.0, 1.0), bc_z=bc) if nz > 1 else {}
+    prims = _sf_prims(sq(rho), sq(v), sq(p), sq(B), sq(E))
+    return Workload("relativistic_smooth", RESISTIVE, nx, ny, (0.0, 1.0), (0.0, 1.0), gamma, sigma, bc, bc,
+                    cfl, 10, prims, **kw)
+
+
 def tf_brio_wu(nx: int = 1600, mu_p: float = 1e3, mass_ratio: float = 1.0, sigma: float = 1e4,
                gamma: float = 2.0, cfl: float = 0.4) -> Workload:
     """Two-fluid Brio-Wu tube (Sec. 4.1): x in [0, 1], outflow, (rho, p, B_x, B_y) =
