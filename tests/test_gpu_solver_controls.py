@@ -47,6 +47,7 @@ def test_solver_stats_count_every_solve(Sim, name, make, scheme, stages):
     assert sum(st["fp64_passes"].values()) == n, st
     assert min(st["fp64_passes"]) >= 2, st  # convergence is confirmed at a second evaluation
     assert min(st["fp32_iterations"]) >= 1 and max(st["fp32_iterations"]) <= 30, st
+    assert sum(st["starts"].values()) == n and st["starts"]["failed"] == 0, st
     # counting leaves the arithmetic unchanged
     ref.step(wl.dt, steps)
     ref.check()
@@ -54,7 +55,8 @@ def test_solver_stats_count_every_solve(Sim, name, make, scheme, stages):
     # the read cleared the counts; a stopped counter stays empty
     g.set_solver_stats(False)
     g.step(wl.dt, 1)
-    assert g.solver_stats() == {"fp32_iterations": {}, "fp64_passes": {}}
+    zero = {"explicit": 0, "ideal_limit": 0, "continuation": 0, "failed": 0}
+    assert g.solver_stats() == {"fp32_iterations": {}, "fp64_passes": {}, "starts": zero}
 
 
 def test_solver_stats_batch(Sim):
