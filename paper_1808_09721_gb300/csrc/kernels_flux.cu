@@ -662,9 +662,15 @@ static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &
     return cudaGetLastError();
 }
 
+template <int NOUT, int DIRS>
+static cudaError_t launch_sweep_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz);
+
 template <class M, class FT, int NOUT>
 static cudaError_t launch_flux_m(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
     constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
+    // single fluid, FP64, 2-D: the line-sweep kernel
+    if constexpr (std::is_same<M, SFModel>::value && std::is_same<FT, double>::value)
+        if (g.ny > 1) return launch_sweep_t<NOUT, 3>(g, ph, a, s, 1);
     // 1-D: 32-cell tiles while one wave of them does not fill the 152 SMs
     // (short tubes are latency-bound on a few SMs), 128-cell tiles beyond
     if (g.ny == 1)
@@ -715,6 +721,266 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
     if (tile_x == 64) return launch_fb_t<M, 64, FT, NOUT>(g, ph, a, b, blocks, s);
     if (tile_x == 256) return launch_fb_t<M, 256, FT, NOUT>(g, ph, a, b, blocks, s);
     return launch_fb_t<M, 128, FT, NOUT>(g, ph, a, b, blocks, s);
+}
+
+// ---- single fluid, FP64, 2-D tiles by line sweeps -------------------------
+// The FP64 form is bound by the FP64 pipe. In the group kernel above the
+// half-point and face rounds of each component are separated by group
+// barriers and pass through shared memory; with every group at a barrier the
+// pipe idles. Here one thread reconstructs one component (or Maxwell pair)
+// along one line of a 16 x 16 tile from end to end: it walks the 20 staged
+// positions of its line, keeps the last three half points' e+-, A+- and the
+// last face value in registers, and emits the face difference of each
+// interior cell as soon as both of its faces exist. The arithmetic per half
+// point and face is the group kernel's (same formulas, same order), but no
+// barrier separates the sweeps and no half-point or face data goes through
+// shared memory, which leaves room for two CTAs per SM.
+//
+// Per tile (160 threads = 10 reconstructions x 16 lines): stage q, w with the
+// 2-cell halo (boundary conditions by index map, halo rows of a slab);
+// auxiliaries J, Z, p + (E^2 + B^2)/2 of every staged cell; the x sweeps
+// write 4 dt L_x / 4 dx ... into the L buffer; the y sweeps (or, in the z
+// pass of a 3-D grid, the z sweeps) add theirs; the epilogue forms the
+// pass's outputs from L and the sources. Reconstructions 0-3 are the four
+// Maxwell pairs of the direction, 4-9 the generic components D, tau, S_x,
+// S_y, S_z, varrho, so that each warp (two reconstructions) takes one code
+// path.
+namespace swp {
+constexpr int T = 16;                    // tile side (interior cells)
+constexpr int S = T + 4;                 // staged side (2-cell halo each way)
+constexpr int SP = S + 1;                // padded row stride: rows read by 16 lanes hit distinct banks
+constexpr int SN = S * SP;               // one staged plane
+constexpr int LP = T + 1;                // padded row stride of the L buffer
+constexpr int NREC = 10;                 // 4 Maxwell pairs + 6 generic components per direction
+constexpr int NTHR = NREC * T;           // 160 threads
+constexpr int NV = sf::NC + sf::NW;      // staged variables
+constexpr size_t OFF_AUX = sizeof(double) * NV * SN;
+constexpr size_t OFF_L = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
+constexpr size_t TOTAL = OFF_L + sizeof(double) * sf::NC * T * LP;
+
+// Maxwell pair k (a, b, s) along physical direction pdir: f_a = s q_b, f_b = s q_a.
+__device__ __forceinline__ void pair_of(int pdir, int k, int &a, int &b, double &sg) {
+    using namespace sf;
+    sg = 1.0;
+    if (pdir == 0) {
+        a = k == 0 ? BX : k == 1 ? EX : k == 2 ? BY : BZ;
+        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EZ : EY;
+        if (k == 2) sg = -1.0;
+    } else if (pdir == 1) {
+        a = k == 0 ? BY : k == 1 ? EY : k == 2 ? BZ : BX;
+        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EX : EZ;
+        if (k == 2) sg = -1.0;
+    } else {
+        a = k == 0 ? BZ : k == 1 ? EZ : k == 2 ? BX : BY;
+        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EY : EX;
+        if (k == 2) sg = -1.0;
+    }
+}
+// generic component of reconstruction r (4..9)
+__device__ __forceinline__ int gen_of(int r) {
+    using namespace sf;
+    return r == 4 ? D : r == 5 ? TAU : r == 6 ? SX : r == 7 ? SY : r == 8 ? SZ : RHOE;
+}
+
+// Physical flux along pdir of generic component c at staged cell idx
+// (Eq. resistive RMHD; the group kernel's expressions).
+__device__ __forceinline__ double gen_flux(const double *st, const double *aux, int c, int pdir, int idx) {
+    using namespace sf;
+    const double vd = st[(NC + VX + pdir) * SN + idx];
+    if (c == D) return st[D * SN + idx] * vd;
+    if (c == TAU) return st[(SX + pdir) * SN + idx] - st[D * SN + idx] * vd;
+    if (c == RHOE) return aux[pdir * SN + idx];
+    const int i = c - SX;
+    const double Zv = aux[3 * SN + idx] * vd;
+    double f = Zv * st[(NC + VX + i) * SN + idx] - st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] -
+               st[(BX + i) * SN + idx] * st[(BX + pdir) * SN + idx];
+    if (i == pdir) f += aux[4 * SN + idx];
+    return f;
+}
+
+// One line of reconstruction r along the tile's x (ALONG_X) or second
+// dimension, physical direction pdir; `line` is the interior row (ALONG_X) or
+// column. Writes (ACC: adds) the face differences times inv4h into L.
+template <bool ALONG_X, bool ACC>
+__device__ __forceinline__ void sweep_line(const double *st, const double *aux, double *Lb, int r, int line, int pdir,
+                                           double inv4h) {
+    constexpr int step = ALONG_X ? 1 : SP;
+    const int base = ALONG_X ? (2 + line) * SP : 2 + line;
+    const double eps4 = 4e-6;
+    auto lput = [&](int comp, int c, double v) {
+        double &d = Lb[comp * T * LP + (ALONG_X ? line * LP + c : c * LP + line)];
+        d = ACC ? fma(v, inv4h, d) : v * inv4h;
+    };
+    if (r < 4) {  // Maxwell pair
+        int a, b;
+        double sg;
+        pair_of(pdir, r, a, b, sg);
+        const double *qa = st + a * SN + base, *qb = st + b * SN + base;
+        double qa0 = qa[0], qb0 = qb[0];
+        double qa1 = 0.0, qb1 = 0.0;                      // positions h - 1 (valid from h = 1)
+        double ep1 = 0.0, em1 = 0.0, Ap1 = 0.0, Am1 = 0.0; // half point h - 1
+        double ep2 = 0.0, Ap2 = 0.0;                      // half point h - 2
+        double Fa = 0.0, Fb = 0.0;                        // faces h - 2 (previous)
+#pragma unroll
+        for (int h = 0; h < S - 1; ++h) {
+            const double qan = qa[(h + 1) * step], qbn = qb[(h + 1) * step];
+            const double d_a = qan - qa0, d_b = qbn - qb0;
+            const double ep = fma(sg, d_b, d_a), em = fma(sg, d_b, -d_a);
+            const double ap = fma(ep, ep, eps4), am = fma(em, em, eps4);
+            const double Ap = ap * ap, Am = am * am;
+            if (h >= 2) {  // face between positions h - 1 and h
+                const double wp = s_div1(Ap1, fma(2.0, Ap2, Ap1));
+                const double wm = s_div1(Am1, fma(2.0, Am, Am1));
+                const double Xp = ep2 - ep1;
+                const double M_ = wm * (em1 - em);
+                const double Fan = fma(2.0 * sg, qb1 + qb0, fma(wp, Xp, M_));
+                const double Fbn = fma(2.0, qa1 + qa0, fma(wp, Xp, -M_));
+                if (h >= 3) {
+                    lput(a, h - 3, Fa - Fan);
+                    lput(b, h - 3, (Fb - Fbn) * sg);
+                }
+                Fa = Fan;
+                Fb = Fbn;
+            }
+            ep2 = ep1; Ap2 = Ap1;
+            ep1 = ep; em1 = em; Ap1 = Ap; Am1 = Am;
+            qa1 = qa0; qb1 = qb0;
+            qa0 = qan; qb0 = qbn;
+        }
+    } else {  // generic component: its physical flux at each position
+        const int c = gen_of(r);
+        const double *qv = st + c * SN + base;
+        double q0 = qv[0], f0 = gen_flux(st, aux, c, pdir, base);
+        double f1 = 0.0;
+        double ep1 = 0.0, em1 = 0.0, Ap1 = 0.0, Am1 = 0.0, ep2 = 0.0, Ap2 = 0.0, F = 0.0;
+#pragma unroll
+        for (int h = 0; h < S - 1; ++h) {
+            const double qn = qv[(h + 1) * step], fn = gen_flux(st, aux, c, pdir, base + (h + 1) * step);
+            const double df = fn - f0, dq = qn - q0;
+            const double ep = df + dq, em = df - dq;
+            const double ap = fma(ep, ep, eps4), am = fma(em, em, eps4);
+            const double Ap = ap * ap, Am = am * am;
+            if (h >= 2) {
+                const double wp = s_div1(Ap1, fma(2.0, Ap2, Ap1));
+                const double wm = s_div1(Am1, fma(2.0, Am, Am1));
+                const double Xp = ep2 - ep1;
+                const double Xm = em1 - em;
+                const double Fn = fma(2.0, f1 + f0, fma(wp, Xp, wm * Xm));
+                if (h >= 3) lput(c, h - 3, F - Fn);
+                F = Fn;
+            }
+            ep2 = ep1; Ap2 = Ap1;
+            ep1 = ep; em1 = em; Ap1 = Ap; Am1 = Am;
+            f1 = f0; q0 = qn; f0 = fn;
+        }
+    }
+}
+} // namespace swp
+
+// DIRS = 3: x and y sweeps (2-D grids, and the x-y pass of a 3-D grid with
+// NOUT = 0); DIRS = 2: the z pass of a 3-D grid (tile's second dimension = z).
+template <int NOUT, int DIRS>
+__global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
+    using namespace swp;
+    using M = SFModel;
+    constexpr int NC = sf::NC, NW = sf::NW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *st = reinterpret_cast<double *>(smem_raw);
+    double *aux = reinterpret_cast<double *>(smem_raw + OFF_AUX);
+    double *Lb = reinterpret_cast<double *>(smem_raw + OFF_L);
+    const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
+    const long long base = (long long)blockIdx.z * g.zoff;
+    const int tid = threadIdx.x;
+
+    // 1. stage the tile + halo (boundary conditions by index map; halo rows of a slab)
+    const bool halo_tile = (g.hlo && j0 < 2) || (g.hhi && j0 + S - 2 > g.ny);
+    for (int e = tid; e < NV * S * S; e += NTHR) {
+        const int v = e / (S * S), rr = e - v * (S * S);
+        const int sy = rr / S, sx = rr - sy * S;
+        const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
+        int hr = 0;
+        const double *hb = halo_tile ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
+        double x;
+        if (hb) {
+            x = hb[((long long)v * 2 + hr) * g.nx + gi];
+        } else {
+            const int gj = map_index(j0 + sy - 2, g.ny, g.bcy);
+            const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
+            x = srcp[base + (long long)gj * g.row + gi];
+        }
+        st[v * SN + sy * SP + sx] = x;
+    }
+    __syncthreads();
+    // 2. auxiliaries (J, Z, p + (E^2 + B^2)/2) of every staged cell
+    for (int e = tid; e < S * S; e += NTHR) {
+        const int sy = e / S, sx = e - sy * S;
+        M::prep(st, SN, sy * SP + sx, ph, aux);
+    }
+    __syncthreads();
+    // 3. sweeps: thread = (reconstruction, line)
+    const int r = tid / T, line = tid - r * T;
+    if constexpr (DIRS == 3) {
+        swp::sweep_line<true, false>(st, aux, Lb, r, line, 0, g.rdx4);
+        __syncthreads();
+        swp::sweep_line<false, true>(st, aux, Lb, r, line, 1, g.rdy4);
+    } else {
+        swp::sweep_line<false, false>(st, aux, Lb, r, line, 2, g.rdy4);
+    }
+    __syncthreads();
+    // 4. epilogue: thread per (component, cell), cells of a row in consecutive threads
+    for (int e = tid; e < NC * T * T; e += NTHR) {
+        const int c = e / (T * T), cell = e - c * (T * T);
+        const int ty = cell / T, tx = cell - ty * T;
+        const int gi = i0 + tx, gj = j0 + ty;
+        if (gi >= g.nx || gj >= g.ny) continue;
+        const long long o = (long long)c * g.plane + base + (long long)gj * g.row + gi;
+        const double L = Lb[c * T * LP + ty * LP + tx];
+        if constexpr (NOUT == 0) {
+            a.lout[o] = L;
+        } else {
+            const int own = (ty + 2) * SP + tx + 2;
+            // nonzero source entries (Eq. resistive RMHD): E: -J, psi: varrho - kappa psi, phi: -kappa phi
+            const bool src = c >= sf::EX && c <= sf::EZ || c == sf::PSI || c == sf::PHI;
+            double sv = 0.0;
+            if (c >= sf::EX && c <= sf::EZ) sv = -aux[(c - sf::EX) * SN + own];
+            else if (c == sf::PSI) sv = fma(-ph.kappa, st[sf::PSI * SN + own], st[sf::RHOE * SN + own]);
+            else if (c == sf::PHI) sv = -ph.kappa * st[sf::PHI * SN + own];
+            const double Lv = a.lin ? L + a.lin[o] : L;
+            double b = a.base[0][o];
+#pragma unroll
+            for (int k = 0; k < NOUT; ++k) {
+                if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];
+                const double v0 = fma(a.cL[k], Lv, b);
+                a.out[k][o] = src ? fma(a.cS[k], sv, v0) : v0;
+            }
+        }
+    }
+    if constexpr (NOUT > 0) {
+        if (a.wcarry)
+            for (int e = tid; e < NW * T * T; e += NTHR) {
+                const int v = e / (T * T), cell = e - v * (T * T);
+                const int ty = cell / T, tx = cell - ty * T;
+                const int gi = i0 + tx, gj = j0 + ty;
+                if (gi >= g.nx || gj >= g.ny) continue;
+                a.wcarry[(long long)v * g.plane + base + (long long)gj * g.row + gi] =
+                    st[(NC + v) * SN + (ty + 2) * SP + tx + 2];
+            }
+    }
+}
+
+template <int NOUT, int DIRS>
+static cudaError_t launch_sweep_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz) {
+    static_assert(swp::TOTAL <= 113 * 1024, "two CTAs per SM");
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_flux_sweep<NOUT, DIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)swp::TOTAL);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((g.nx + swp::T - 1) / swp::T, (g.ny + swp::T - 1) / swp::T, gz);
+    k_flux_sweep<NOUT, DIRS><<<grid, swp::NTHR, swp::TOTAL, s>>>(g, ph, a);
+    return cudaGetLastError();
 }
 
 // 3-D grids. Pass 1: every x-y plane (blockIdx.z = k) with the
