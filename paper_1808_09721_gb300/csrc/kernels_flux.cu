@@ -752,7 +752,9 @@ constexpr int SP = S + 1;                // padded row stride: rows read by 16 l
 constexpr int SN = S * SP;               // one staged plane
 constexpr int LP = T + 1;                // padded row stride of the L buffer
 constexpr int NREC = 10;                 // 4 Maxwell pairs + 6 generic components per direction
-constexpr int NTHR = NREC * T;           // 160 threads
+constexpr int SEG = 2;                   // a line is swept in SEG segments of T / SEG cells
+constexpr int SL = T / SEG + 4;          // staged positions of one segment
+constexpr int NTHR = NREC * T * SEG;     // 320 threads
 constexpr int NV = sf::NC + sf::NW;      // staged variables
 constexpr size_t OFF_AUX = sizeof(double) * NV * SN;
 constexpr size_t OFF_L = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
@@ -798,16 +800,18 @@ __device__ __forceinline__ double gen_flux(const double *st, const double *aux, 
     return f;
 }
 
-// One line of reconstruction r along the tile's x (ALONG_X) or second
-// dimension, physical direction pdir; `line` is the interior row (ALONG_X) or
-// column. Writes (ACC: adds) the face differences times inv4h into L.
+// One segment (interior cells c0 .. c0 + T/SEG - 1) of line `line` of
+// reconstruction r along the tile's x (ALONG_X) or second dimension, physical
+// direction pdir; `line` is the interior row (ALONG_X) or column. Writes
+// (ACC: adds) the face differences times inv4h into L.
 template <bool ALONG_X, bool ACC>
-__device__ __forceinline__ void sweep_line(const double *st, const double *aux, double *Lb, int r, int line, int pdir,
-                                           double inv4h) {
+__device__ __forceinline__ void sweep_line(const double *st, const double *aux, double *Lb, int r, int line, int c0,
+                                           int pdir, double inv4h) {
     constexpr int step = ALONG_X ? 1 : SP;
-    const int base = ALONG_X ? (2 + line) * SP : 2 + line;
+    const int base = (ALONG_X ? (2 + line) * SP : 2 + line) + c0 * step;
     const double eps4 = 4e-6;
     auto lput = [&](int comp, int c, double v) {
+        c += c0;
         double &d = Lb[comp * T * LP + (ALONG_X ? line * LP + c : c * LP + line)];
         d = ACC ? fma(v, inv4h, d) : v * inv4h;
     };
@@ -822,7 +826,7 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
         double ep2 = 0.0, Ap2 = 0.0;                      // half point h - 2
         double Fa = 0.0, Fb = 0.0;                        // faces h - 2 (previous)
 #pragma unroll
-        for (int h = 0; h < S - 1; ++h) {
+        for (int h = 0; h < SL - 1; ++h) {
             const double qan = qa[(h + 1) * step], qbn = qb[(h + 1) * step];
             const double d_a = qan - qa0, d_b = qbn - qb0;
             const double ep = fma(sg, d_b, d_a), em = fma(sg, d_b, -d_a);
@@ -854,7 +858,7 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
         double f1 = 0.0;
         double ep1 = 0.0, em1 = 0.0, Ap1 = 0.0, Am1 = 0.0, ep2 = 0.0, Ap2 = 0.0, F = 0.0;
 #pragma unroll
-        for (int h = 0; h < S - 1; ++h) {
+        for (int h = 0; h < SL - 1; ++h) {
             const double qn = qv[(h + 1) * step], fn = gen_flux(st, aux, c, pdir, base + (h + 1) * step);
             const double df = fn - f0, dq = qn - q0;
             const double ep = df + dq, em = df - dq;
@@ -917,14 +921,15 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
         M::prep(st, SN, sy * SP + sx, ph, aux);
     }
     __syncthreads();
-    // 3. sweeps: thread = (reconstruction, line)
-    const int r = tid / T, line = tid - r * T;
+    // 3. sweeps: thread = (reconstruction, segment, line); a warp is one reconstruction
+    const int r = tid / (T * SEG), seg = (tid / T) % SEG, line = tid % T;
+    const int c0 = seg * (T / SEG);
     if constexpr (DIRS == 3) {
-        swp::sweep_line<true, false>(st, aux, Lb, r, line, 0, g.rdx4);
+        swp::sweep_line<true, false>(st, aux, Lb, r, line, c0, 0, g.rdx4);
         __syncthreads();
-        swp::sweep_line<false, true>(st, aux, Lb, r, line, 1, g.rdy4);
+        swp::sweep_line<false, true>(st, aux, Lb, r, line, c0, 1, g.rdy4);
     } else {
-        swp::sweep_line<false, false>(st, aux, Lb, r, line, 2, g.rdy4);
+        swp::sweep_line<false, false>(st, aux, Lb, r, line, c0, 2, g.rdy4);
     }
     __syncthreads();
     // 4. epilogue: thread per (component, cell), cells of a row in consecutive threads
