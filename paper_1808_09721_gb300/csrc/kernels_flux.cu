@@ -728,23 +728,25 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
 // half-point and face rounds of each component are separated by group
 // barriers and pass through shared memory; with every group at a barrier the
 // pipe idles. Here one thread reconstructs one component (or Maxwell pair)
-// along one line of a 16 x 16 tile from end to end: it walks the 20 staged
-// positions of its line, keeps the last three half points' e+-, A+- and the
-// last face value in registers, and emits the face difference of each
-// interior cell as soon as both of its faces exist. The arithmetic per half
-// point and face is the group kernel's (same formulas, same order), but no
-// barrier separates the sweeps and no half-point or face data goes through
-// shared memory, which leaves room for two CTAs per SM.
+// along one segment of a line of a 16 x 16 tile: it walks the segment's
+// staged positions, keeps the last three half points' e+-, A+- and the last
+// face value in registers, and emits the face difference of each interior
+// cell as soon as both of its faces exist. The arithmetic per half point and
+// face is the group kernel's (same formulas, same order), but no barrier
+// separates the rounds and no half-point or face data goes through shared
+// memory, which leaves room for two CTAs per SM. A line is swept in two
+// segments of 8 cells (each with its own 2-cell overlap), so that a CTA has
+// 320 threads: 20 warps per SM hide the FP64 latency that 10 did not.
 //
-// Per tile (160 threads = 10 reconstructions x 16 lines): stage q, w with the
-// 2-cell halo (boundary conditions by index map, halo rows of a slab);
-// auxiliaries J, Z, p + (E^2 + B^2)/2 of every staged cell; the x sweeps
-// write 4 dt L_x / 4 dx ... into the L buffer; the y sweeps (or, in the z
-// pass of a 3-D grid, the z sweeps) add theirs; the epilogue forms the
-// pass's outputs from L and the sources. Reconstructions 0-3 are the four
-// Maxwell pairs of the direction, 4-9 the generic components D, tau, S_x,
-// S_y, S_z, varrho, so that each warp (two reconstructions) takes one code
-// path.
+// Per tile three phases: (1) every staged cell (the tile and its 2-cell
+// halo; boundary conditions by index map, halo rows of a slab) is loaded by
+// one thread, which computes its auxiliaries J, Z, p + (E^2 + B^2)/2 and keeps
+// the 14 conserved variables and the velocity in shared memory; (2) the x
+// sweeps write their part of L into the L buffer; (3) the y sweeps (in the z
+// pass of a 3-D grid: the z sweeps) add theirs and form the pass's outputs
+// for their cells right away. Reconstructions 0-3 are the four Maxwell pairs
+// of the direction, 4-9 the generic components D, tau, S_x, S_y, S_z,
+// varrho, so that each warp (one reconstruction) takes one code path.
 namespace swp {
 constexpr int T = 16;                    // tile side (interior cells)
 constexpr int S = T + 4;                 // staged side (2-cell halo each way)
@@ -755,8 +757,8 @@ constexpr int NREC = 10;                 // 4 Maxwell pairs + 6 generic componen
 constexpr int SEG = 2;                   // a line is swept in SEG segments of T / SEG cells
 constexpr int SL = T / SEG + 4;          // staged positions of one segment
 constexpr int NTHR = NREC * T * SEG;     // 320 threads
-constexpr int NV = sf::NC + sf::NW;      // staged variables
-constexpr size_t OFF_AUX = sizeof(double) * NV * SN;
+constexpr int NST = sf::NC + 3;          // staged planes: the conserved variables and the velocity
+constexpr size_t OFF_AUX = sizeof(double) * NST * SN;
 constexpr size_t OFF_L = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
 constexpr size_t TOTAL = OFF_L + sizeof(double) * sf::NC * T * LP;
 
@@ -785,16 +787,17 @@ __device__ __forceinline__ int gen_of(int r) {
 }
 
 // Physical flux along pdir of generic component c at staged cell idx
-// (Eq. resistive RMHD; the group kernel's expressions).
+// (Eq. resistive RMHD; the group kernel's expressions). The velocity is
+// staged after the 14 conserved variables.
 __device__ __forceinline__ double gen_flux(const double *st, const double *aux, int c, int pdir, int idx) {
     using namespace sf;
-    const double vd = st[(NC + VX + pdir) * SN + idx];
+    const double vd = st[(NC + pdir) * SN + idx];
     if (c == D) return st[D * SN + idx] * vd;
     if (c == TAU) return st[(SX + pdir) * SN + idx] - st[D * SN + idx] * vd;
     if (c == RHOE) return aux[pdir * SN + idx];
     const int i = c - SX;
     const double Zv = aux[3 * SN + idx] * vd;
-    double f = Zv * st[(NC + VX + i) * SN + idx] - st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] -
+    double f = Zv * st[(NC + i) * SN + idx] - st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] -
                st[(BX + i) * SN + idx] * st[(BX + pdir) * SN + idx];
     if (i == pdir) f += aux[4 * SN + idx];
     return f;
@@ -802,18 +805,17 @@ __device__ __forceinline__ double gen_flux(const double *st, const double *aux, 
 
 // One segment (interior cells c0 .. c0 + T/SEG - 1) of line `line` of
 // reconstruction r along the tile's x (ALONG_X) or second dimension, physical
-// direction pdir; `line` is the interior row (ALONG_X) or column. Writes
-// (ACC: adds) the face differences times inv4h into L.
-template <bool ALONG_X, bool ACC>
-__device__ __forceinline__ void sweep_line(const double *st, const double *aux, double *Lb, int r, int line, int c0,
-                                           int pdir, double inv4h) {
+// direction pdir; `line` is the interior row (ALONG_X) or column. Hands each
+// cell's face difference 4 F_{c-1/2} - 4 F_{c+1/2} to put(component, cx, cy, d).
+template <bool ALONG_X, class PUT>
+__device__ __forceinline__ void sweep_line(const double *st, const double *aux, int r, int line, int c0, int pdir,
+                                           PUT &&put) {
     constexpr int step = ALONG_X ? 1 : SP;
     const int base = (ALONG_X ? (2 + line) * SP : 2 + line) + c0 * step;
     const double eps4 = 4e-6;
-    auto lput = [&](int comp, int c, double v) {
-        c += c0;
-        double &d = Lb[comp * T * LP + (ALONG_X ? line * LP + c : c * LP + line)];
-        d = ACC ? fma(v, inv4h, d) : v * inv4h;
+    auto cell = [&](int comp, int c, double d) {
+        if (ALONG_X) put(comp, c0 + c, line, d);
+        else put(comp, line, c0 + c, d);
     };
     if (r < 4) {  // Maxwell pair
         int a, b;
@@ -840,8 +842,8 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
                 const double Fan = fma(2.0 * sg, qb1 + qb0, fma(wp, Xp, M_));
                 const double Fbn = fma(2.0, qa1 + qa0, fma(wp, Xp, -M_));
                 if (h >= 3) {
-                    lput(a, h - 3, Fa - Fan);
-                    lput(b, h - 3, (Fb - Fbn) * sg);
+                    cell(a, h - 3, Fa - Fan);
+                    cell(b, h - 3, (Fb - Fbn) * sg);
                 }
                 Fa = Fan;
                 Fb = Fbn;
@@ -870,7 +872,7 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
                 const double Xp = ep2 - ep1;
                 const double Xm = em1 - em;
                 const double Fn = fma(2.0, f1 + f0, fma(wp, Xp, wm * Xm));
-                if (h >= 3) lput(c, h - 3, F - Fn);
+                if (h >= 3) cell(c, h - 3, F - Fn);
                 F = Fn;
             }
             ep2 = ep1; Ap2 = Ap1;
@@ -886,7 +888,6 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
 template <int NOUT, int DIRS>
 __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
     using namespace swp;
-    using M = SFModel;
     constexpr int NC = sf::NC, NW = sf::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *st = reinterpret_cast<double *>(smem_raw);
@@ -896,56 +897,63 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
     const long long base = (long long)blockIdx.z * g.zoff;
     const int tid = threadIdx.x;
 
-    // 1. stage the tile + halo (boundary conditions by index map; halo rows of a slab)
+    // 1. one thread per staged cell (boundary conditions by index map; halo
+    // rows of a slab): its conserved variables and velocity, and its
+    // auxiliaries J, Z = rho h W^2, p + (E^2 + B^2)/2; an interior cell's
+    // primitives go to the warm-start array of the step's last pass
     const bool halo_tile = (g.hlo && j0 < 2) || (g.hhi && j0 + S - 2 > g.ny);
-    for (int e = tid; e < NV * S * S; e += NTHR) {
-        const int v = e / (S * S), rr = e - v * (S * S);
-        const int sy = rr / S, sx = rr - sy * S;
+    for (int e = tid; e < S * S; e += NTHR) {
+        const int sy = e / S, sx = e - sy * S;
         const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
         int hr = 0;
         const double *hb = halo_tile ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
-        double x;
+        double x[NC + NW];
         if (hb) {
-            x = hb[((long long)v * 2 + hr) * g.nx + gi];
+#pragma unroll
+            for (int v = 0; v < NC + NW; ++v) x[v] = hb[((long long)v * 2 + hr) * g.nx + gi];
         } else {
             const int gj = map_index(j0 + sy - 2, g.ny, g.bcy);
-            const double *srcp = v < NC ? a.q + (long long)v * g.plane : a.w + (long long)(v - NC) * g.plane;
-            x = srcp[base + (long long)gj * g.row + gi];
+            const long long gc = base + (long long)gj * g.row + gi;
+#pragma unroll
+            for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
+#pragma unroll
+            for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
         }
-        st[v * SN + sy * SP + sx] = x;
+        const int idx = sy * SP + sx;
+#pragma unroll
+        for (int v = 0; v < NST; ++v) st[v * SN + idx] = x[v];
+        const double *q = x, *w = x + NC;
+        double J[3];
+        sf::current(q, w, ph.sigma, J);
+        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
+                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
+        aux[0 * SN + idx] = J[0];
+        aux[1 * SN + idx] = J[1];
+        aux[2 * SN + idx] = J[2];
+        aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
+        aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
+        if constexpr (NOUT > 0) {
+            const int gix = i0 + sx - 2, gjy = j0 + sy - 2;
+            if (a.wcarry && sx >= 2 && sx < T + 2 && sy >= 2 && sy < T + 2 && gix < g.nx && gjy < g.ny) {
+                const long long gc = base + (long long)gjy * g.row + gix;
+#pragma unroll
+                for (int v = 0; v < NW; ++v) a.wcarry[(long long)v * g.plane + gc] = w[v];
+            }
+        }
     }
     __syncthreads();
-    // 2. auxiliaries (J, Z, p + (E^2 + B^2)/2) of every staged cell
-    for (int e = tid; e < S * S; e += NTHR) {
-        const int sy = e / S, sx = e - sy * S;
-        M::prep(st, SN, sy * SP + sx, ph, aux);
-    }
-    __syncthreads();
-    // 3. sweeps: thread = (reconstruction, segment, line); a warp is one reconstruction
-    const int r = tid / (T * SEG), seg = (tid / T) % SEG, line = tid % T;
-    const int c0 = seg * (T / SEG);
-    if constexpr (DIRS == 3) {
-        swp::sweep_line<true, false>(st, aux, Lb, r, line, c0, 0, g.rdx4);
-        __syncthreads();
-        swp::sweep_line<false, true>(st, aux, Lb, r, line, c0, 1, g.rdy4);
-    } else {
-        swp::sweep_line<false, false>(st, aux, Lb, r, line, c0, 2, g.rdy4);
-    }
-    __syncthreads();
-    // 4. epilogue: thread per (component, cell), cells of a row in consecutive threads
-    for (int e = tid; e < NC * T * T; e += NTHR) {
-        const int c = e / (T * T), cell = e - c * (T * T);
-        const int ty = cell / T, tx = cell - ty * T;
+
+    // the pass's outputs of one component of one interior cell from its L
+    auto emit = [&](int c, int tx, int ty, double L) {
         const int gi = i0 + tx, gj = j0 + ty;
-        if (gi >= g.nx || gj >= g.ny) continue;
+        if (gi >= g.nx || gj >= g.ny) return;
         const long long o = (long long)c * g.plane + base + (long long)gj * g.row + gi;
-        const double L = Lb[c * T * LP + ty * LP + tx];
         if constexpr (NOUT == 0) {
             a.lout[o] = L;
         } else {
             const int own = (ty + 2) * SP + tx + 2;
             // nonzero source entries (Eq. resistive RMHD): E: -J, psi: varrho - kappa psi, phi: -kappa phi
-            const bool src = c >= sf::EX && c <= sf::EZ || c == sf::PSI || c == sf::PHI;
+            const bool src = (c >= sf::EX && c <= sf::EZ) || c == sf::PSI || c == sf::PHI;
             double sv = 0.0;
             if (c >= sf::EX && c <= sf::EZ) sv = -aux[(c - sf::EX) * SN + own];
             else if (c == sf::PSI) sv = fma(-ph.kappa, st[sf::PSI * SN + own], st[sf::RHOE * SN + own]);
@@ -959,18 +967,26 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
                 a.out[k][o] = src ? fma(a.cS[k], sv, v0) : v0;
             }
         }
+    };
+    // 2-3. sweeps: thread = (reconstruction, segment, line); a warp is one reconstruction
+    const int r = tid / (T * SEG), seg = (tid / T) % SEG, line = tid % T;
+    const int c0 = seg * (T / SEG);
+    if constexpr (DIRS == 3) {
+        const double ix = g.rdx4, iy = g.rdy4;
+        swp::sweep_line<true>(st, aux, r, line, c0, 0, [&](int c, int tx, int ty, double d) {
+            Lb[c * T * LP + ty * LP + tx] = d * ix;
+        });
+        __syncthreads();
+        swp::sweep_line<false>(st, aux, r, line, c0, 1, [&](int c, int tx, int ty, double d) {
+            emit(c, tx, ty, fma(d, iy, Lb[c * T * LP + ty * LP + tx]));
+        });
+    } else {
+        const double iz = g.rdy4;
+        swp::sweep_line<false>(st, aux, r, line, c0, 2, [&](int c, int tx, int ty, double d) {
+            emit(c, tx, ty, d * iz);
+        });
     }
-    if constexpr (NOUT > 0) {
-        if (a.wcarry)
-            for (int e = tid; e < NW * T * T; e += NTHR) {
-                const int v = e / (T * T), cell = e - v * (T * T);
-                const int ty = cell / T, tx = cell - ty * T;
-                const int gi = i0 + tx, gj = j0 + ty;
-                if (gi >= g.nx || gj >= g.ny) continue;
-                a.wcarry[(long long)v * g.plane + base + (long long)gj * g.row + gi] =
-                    st[(NC + v) * SN + (ty + 2) * SP + tx + 2];
-            }
-    }
+    (void)Lb;
 }
 
 template <int NOUT, int DIRS>
