@@ -734,17 +734,19 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
 // cell as soon as both of its faces exist. The arithmetic per half point and
 // face is the group kernel's (same formulas, same order), but no barrier
 // separates the rounds and no half-point or face data goes through shared
-// memory, which leaves room for two CTAs per SM. A line is swept in two
-// segments of 8 cells (each with its own 2-cell overlap), so that a CTA has
-// 320 threads: 20 warps per SM hide the FP64 latency that 10 did not.
+// memory: a CTA needs 74 KB, so three CTAs (30 warps) share an SM and hide
+// the FP64 latency. (An FP64 warp instruction takes the pipe for the same
+// time whatever its active lanes, so splitting lines into overlapping
+// segments for more threads would cost real FP64 throughput.)
 //
 // Per tile three phases: (1) every staged cell (the tile and its 2-cell
 // halo; boundary conditions by index map, halo rows of a slab) is loaded by
 // one thread, which computes its auxiliaries J, Z, p + (E^2 + B^2)/2 and keeps
 // the 14 conserved variables and the velocity in shared memory; (2) the x
-// sweeps write their part of L into the L buffer; (3) the y sweeps (in the z
-// pass of a 3-D grid: the z sweeps) add theirs and form the pass's outputs
-// for their cells right away. Reconstructions 0-3 are the four Maxwell pairs
+// sweeps write their part of L to a global scratch (FluxArgs::lscr; the x-y
+// pass of a 3-D grid writes L_x to lout); (3) the y sweeps (in the z pass of
+// a 3-D grid: the z sweeps) add theirs and form the pass's outputs for their
+// cells right away. Reconstructions 0-3 are the four Maxwell pairs
 // of the direction, 4-9 the generic components D, tau, S_x, S_y, S_z,
 // varrho, so that each warp (one reconstruction) takes one code path.
 namespace swp {
@@ -752,15 +754,13 @@ constexpr int T = 16;                    // tile side (interior cells)
 constexpr int S = T + 4;                 // staged side (2-cell halo each way)
 constexpr int SP = S + 1;                // padded row stride: rows read by 16 lanes hit distinct banks
 constexpr int SN = S * SP;               // one staged plane
-constexpr int LP = T + 1;                // padded row stride of the L buffer
 constexpr int NREC = 10;                 // 4 Maxwell pairs + 6 generic components per direction
-constexpr int SEG = 2;                   // a line is swept in SEG segments of T / SEG cells
+constexpr int SEG = 1;                   // a line is swept in SEG segments of T / SEG cells
 constexpr int SL = T / SEG + 4;          // staged positions of one segment
-constexpr int NTHR = NREC * T * SEG;     // 320 threads
+constexpr int NTHR = NREC * T * SEG;     // 160 threads
 constexpr int NST = sf::NC + 3;          // staged planes: the conserved variables and the velocity
 constexpr size_t OFF_AUX = sizeof(double) * NST * SN;
-constexpr size_t OFF_L = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
-constexpr size_t TOTAL = OFF_L + sizeof(double) * sf::NC * T * LP;
+constexpr size_t TOTAL = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
 
 // Maxwell pair k (a, b, s) along physical direction pdir: f_a = s q_b, f_b = s q_a.
 __device__ __forceinline__ void pair_of(int pdir, int k, int &a, int &b, double &sg) {
@@ -886,13 +886,12 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
 // DIRS = 3: x and y sweeps (2-D grids, and the x-y pass of a 3-D grid with
 // NOUT = 0); DIRS = 2: the z pass of a 3-D grid (tile's second dimension = z).
 template <int NOUT, int DIRS>
-__global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
+__global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
     using namespace swp;
     constexpr int NC = sf::NC, NW = sf::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *st = reinterpret_cast<double *>(smem_raw);
     double *aux = reinterpret_cast<double *>(smem_raw + OFF_AUX);
-    double *Lb = reinterpret_cast<double *>(smem_raw + OFF_L);
     const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
     const long long base = (long long)blockIdx.z * g.zoff;
     const int tid = threadIdx.x;
@@ -944,7 +943,10 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
     __syncthreads();
 
     // the pass's outputs of one component of one interior cell from its L
-    auto emit = [&](int c, int tx, int ty, double L) {
+    // (PART: a one-output pass whose output already holds base + c_L L_x, and
+    // L is the y part)
+    auto emit = [&](int c, int tx, int ty, double L, auto part_c) {
+        constexpr bool PART = decltype(part_c)::value;
         const int gi = i0 + tx, gj = j0 + ty;
         if (gi >= g.nx || gj >= g.ny) return;
         const long long o = (long long)c * g.plane + base + (long long)gj * g.row + gi;
@@ -959,7 +961,7 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
             else if (c == sf::PSI) sv = fma(-ph.kappa, st[sf::PSI * SN + own], st[sf::RHOE * SN + own]);
             else if (c == sf::PHI) sv = -ph.kappa * st[sf::PHI * SN + own];
             const double Lv = a.lin ? L + a.lin[o] : L;
-            double b = a.base[0][o];
+            double b = PART ? a.out[0][o] : a.base[0][o];
 #pragma unroll
             for (int k = 0; k < NOUT; ++k) {
                 if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];
@@ -968,30 +970,45 @@ __global__ void __launch_bounds__(swp::NTHR, 2) k_flux_sweep(Grid g, Phys ph, Fl
             }
         }
     };
-    // 2-3. sweeps: thread = (reconstruction, segment, line); a warp is one reconstruction
+    using Full = std::false_type;
+    using Part = std::true_type;
+    // 2-3. sweeps: thread = (reconstruction, line); a warp is two reconstructions
     const int r = tid / (T * SEG), seg = (tid / T) % SEG, line = tid % T;
     const int c0 = seg * (T / SEG);
     if constexpr (DIRS == 3) {
         const double ix = g.rdx4, iy = g.rdy4;
+        // The x part of L of interior cell (tx, ty), component c: in lout (x-y
+        // pass of a 3-D grid), folded into the output (one-output passes:
+        // out = base + c_L L_x), or in the scratch, plane c of ncell cells.
+        auto cell_of = [&](int tx, int ty) { return base + (long long)(j0 + ty) * g.row + i0 + tx; };
         swp::sweep_line<true>(st, aux, r, line, c0, 0, [&](int c, int tx, int ty, double d) {
-            Lb[c * T * LP + ty * LP + tx] = d * ix;
+            if (i0 + tx >= g.nx || j0 + ty >= g.ny) return;
+            const long long cx = cell_of(tx, ty);
+            if constexpr (NOUT == 0) a.lout[(long long)c * g.plane + cx] = d * ix;
+            else if constexpr (NOUT == 1) {
+                const long long o = (long long)c * g.plane + cx;
+                a.out[0][o] = fma(a.cL[0], d * ix, a.base[0][o]);
+            } else a.lscr[(long long)c * g.ncell + cx] = d * ix;
         });
         __syncthreads();
         swp::sweep_line<false>(st, aux, r, line, c0, 1, [&](int c, int tx, int ty, double d) {
-            emit(c, tx, ty, fma(d, iy, Lb[c * T * LP + ty * LP + tx]));
+            if (i0 + tx >= g.nx || j0 + ty >= g.ny) return;
+            const long long cx = cell_of(tx, ty);
+            if constexpr (NOUT == 0) a.lout[(long long)c * g.plane + cx] += d * iy;
+            else if constexpr (NOUT == 1) emit(c, tx, ty, d * iy, Part{});
+            else emit(c, tx, ty, fma(d, iy, a.lscr[(long long)c * g.ncell + cx]), Full{});
         });
     } else {
         const double iz = g.rdy4;
         swp::sweep_line<false>(st, aux, r, line, c0, 2, [&](int c, int tx, int ty, double d) {
-            emit(c, tx, ty, d * iz);
+            emit(c, tx, ty, d * iz, Full{});
         });
     }
-    (void)Lb;
 }
 
 template <int NOUT, int DIRS>
 static cudaError_t launch_sweep_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz) {
-    static_assert(swp::TOTAL <= 113 * 1024, "two CTAs per SM");
+    static_assert(swp::TOTAL <= 75 * 1024, "three CTAs per SM");
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_flux_sweep<NOUT, DIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,

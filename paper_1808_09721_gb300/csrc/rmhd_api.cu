@@ -812,6 +812,7 @@ static int upload_dt_tables(rmhd_ctx *c, double dt) {
 static cudaError_t flux_pass(rmhd_ctx *c, int nout, const FluxArgs &f0) {
     FluxArgs f = f0;
     f.srcg = c->SRCG;
+    f.lscr = c->stage_buf;  // idle during steps (it serves the host I/O calls only)
     if (c->g.nz > 1) return launch_flux_3d(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->LBUF, c->stream);
     return launch_flux(c->cfg.model, c->cfg.precision, nout, c->g, c->ph, f, c->stream);
 }

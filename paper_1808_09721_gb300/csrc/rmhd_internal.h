@@ -55,6 +55,8 @@ struct FluxArgs {
     const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
     double *srcg;           // two fluids, FP64, 2-D tiles: the interior cells' source entries (NS planes)
                             // go through this scratch instead of shared memory
+    double *lscr;           // single fluid, FP64, 2-D: the x part of L between the x and y sweeps
+                            // (NC planes of ncell cells)
 };
 
 struct StageArgs {
