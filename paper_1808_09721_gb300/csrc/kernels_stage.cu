@@ -27,17 +27,32 @@ __device__ __forceinline__ int wrap(int i, int n, int bc) {
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// A cell whose first start failed goes to the restart list (or, beyond its
-// capacity, is reported as failed).
+// Restart list: rlist[0] = number of cells, rlist[1] = restart blocks done,
+// rlist[2 ..] = cells. A cell whose first start failed goes to the list (or,
+// beyond its capacity, is reported as failed).
 __device__ __forceinline__ void defer_or_record(const StageArgs &a, int st, long long cell) {
     if (st == sf::ST_NEWTON && a.rlist) {
         const int slot = atomicAdd(a.rlist, 1);
         if (slot < a.rcap) {
-            a.rlist[1 + slot] = (int)cell;
+            a.rlist[2 + slot] = (int)cell;
             return;
         }
     }
     record(a.status, st, cell);
+}
+
+// End of a restart kernel: the last block to finish (every block has read
+// the count by then) empties the list for the next stage.
+__device__ __forceinline__ void restart_done(int *rlist) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&rlist[1], 1) == (int)gridDim.x - 1) {
+            rlist[0] = 0;
+            rlist[1] = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------- stage
@@ -63,14 +78,15 @@ __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, 
 template <bool STATS>
 __global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace sf;
-    const int n = min(a.rlist[0], a.rcap);
+    const int n = min(*(volatile int *)a.rlist, a.rcap);
     sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long cell = a.rlist[1 + e];
+        const long long cell = a.rlist[2 + e];
         const double pw = a.wwarm[P * g.plane + cell];
         record(a.status, stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start),
                cell);
     }
+    restart_done(a.rlist);
 }
 
 // Two fluids: the 7 x 7 Jacobian and its inverse of each thread live in a
@@ -106,10 +122,6 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
     int blocks = grid_for(g.ncell, kStageThreads);
     const int btf = grid_for(g.ncell, kStageThreadsTF);
     if (model == 0) {
-        if (a.rlist) {
-            cudaError_t e = cudaMemsetAsync(a.rlist, 0, sizeof(int), s);
-            if (e != cudaSuccess) return e;
-        }
         if (a.hist) k_stage_sf<true><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
         else k_stage_sf<false><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
         if (a.rlist) {
@@ -145,9 +157,9 @@ __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, B
 template <bool STATS>
 __global__ void k_restart_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
     using namespace sf;
-    const int n = min(a.rlist[0], a.rcap);
+    const int n = min(*(volatile int *)a.rlist, a.rcap);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long cell = a.rlist[1 + e];
+        const long long cell = a.rlist[2 + e];
         const int run = b.run_of[cell];
         sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
         record(a.status,
@@ -155,6 +167,7 @@ __global__ void k_restart_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
                                             a.first_start),
                cell);
     }
+    restart_done(a.rlist);
 }
 
 template <bool STATS>
@@ -178,10 +191,6 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
                                int threads, cudaStream_t s) {
     int blocks = grid_for(g.ncell, threads);
     if (model == 0) {
-        if (a.rlist) {
-            cudaError_t e = cudaMemsetAsync(a.rlist, 0, sizeof(int), s);
-            if (e != cudaSuccess) return e;
-        }
         if (a.hist) k_stage_batch_sf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_sf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
         if (a.rlist) {

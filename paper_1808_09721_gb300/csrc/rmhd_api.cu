@@ -43,7 +43,7 @@ struct rmhd_ctx {
     double *SRCG;  // two fluids: source scratch of the FP64 flux kernel (null otherwise)
     int *status;       // device [2]
     unsigned long long *hist;  // device [44]: solver statistics (FP32 iterations, FP64 passes, starts)
-    int *rlist;                // device [1 + rcap]: cells whose first stage-solve start failed
+    int *rlist;                // device [2 + rcap]: cells whose first stage-solve start failed
     int rcap;
     int first_start;           // rmhd_set_first_start (tests of the restart path)
     bool stats_on;             // count stage solves into hist
@@ -225,7 +225,7 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.diag = o; o += align256(8 * sizeof(double));
     L.status = o; o += align256(2 * sizeof(int));
     L.hist = o; o += align256(44 * sizeof(unsigned long long));
-    L.rlist = o; o += align256((1 + (size_t)restart_capacity(g.ncell)) * sizeof(int));
+    L.rlist = o; o += align256((2 + (size_t)restart_capacity(g.ncell)) * sizeof(int));
     L.HLO = L.HHI = 0;
     if (halo) {  // slab: two halo rows of every staged variable below and above
         const size_t hb = (size_t)(nc + nw) * 2 * g.nx * sizeof(double);
@@ -385,6 +385,10 @@ static int create_impl(rmhd_ctx **out, const rmhd_config *cfg, void *cuda_stream
         return RMHD_ERR_NOMEM;
     }
     if (reset_status(c)) { rmhd_destroy(c); return RMHD_ERR_CUDA; }
+    if (cudaMemsetAsync(c->rlist, 0, 2 * sizeof(int), c->stream) != cudaSuccess) {  // empty restart list
+        rmhd_destroy(c);
+        return RMHD_ERR_CUDA;
+    }
     *out = c;
     return RMHD_OK;
 }
@@ -1090,6 +1094,10 @@ int rmhd_create_batch(rmhd_ctx **out, const rmhd_config *base, int nruns, const 
     c->hist = (unsigned long long *)(c->ws + L.hist);
     c->rlist = (int *)(c->ws + L.rlist);
     c->rcap = restart_capacity(c->g.ncell);
+    if (cudaMemsetAsync(c->rlist, 0, 2 * sizeof(int), c->stream) != cudaSuccess) {  // empty restart list
+        rmhd_destroy(c);
+        return RMHD_ERR_CUDA;
+    }
     c->d_nx = (int *)(c->ws + L.nx);
     c->d_off = (long long *)(c->ws + L.off);
     c->d_dx = (double *)(c->ws + L.dx);

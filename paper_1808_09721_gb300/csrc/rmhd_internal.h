@@ -70,8 +70,9 @@ struct StageArgs {
                                // and converged starts [4]
     int maxpass;               // cap on the FP64 refinement passes (0: the default, 8)
     // single fluid: cells whose first start failed, handed to the restart
-    // kernel (rlist[0]: count, rlist[1 .. rcap]: cells); a cell beyond the
-    // capacity is reported as failed. Null: no restarts.
+    // kernel (rlist[0]: count, rlist[1]: restart blocks done, rlist[2 ..
+    // rcap + 1]: cells; zero at creation, emptied by each restart kernel); a
+    // cell beyond the capacity is reported as failed. Null: no restarts.
     int *rlist;
     int rcap;
     int first_start;  // tests of the restart path: 1 or 2 skips the earlier starts (0: all starts)
