@@ -1036,7 +1036,10 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     axy.lout = lbuf;
     axy.lin = nullptr;
     axy.wcarry = nullptr;
-    cudaError_t e = launch_flux_t<M, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
+    // single fluid, FP64: the line-sweep kernel for both passes
+    constexpr bool SWEEP = std::is_same<M, SFModel>::value && std::is_same<FT, double>::value;
+    cudaError_t e = SWEEP ? launch_sweep_t<0, 3>(gxy, ph, axy, s, g.nz)
+                          : launch_flux_t<M, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
     if (e != cudaSuccess) return e;
     Grid gz = g;
     gz.ny = g.nz;
@@ -1048,6 +1051,12 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     FluxArgs az = a;
     az.lout = nullptr;
     az.lin = lbuf;
+    if constexpr (SWEEP) {
+        if (nout == 1) return launch_sweep_t<1, 2>(gz, ph, az, s, g.ny);
+        if (nout == 2) return launch_sweep_t<2, 2>(gz, ph, az, s, g.ny);
+        if (nout == 3) return launch_sweep_t<3, 2>(gz, ph, az, s, g.ny);
+        return cudaErrorInvalidValue;
+    }
     if (nout == 1) return launch_flux_t<M, 32, 8, G, FT, 1, 2>(gz, ph, az, s, g.ny);
     if (nout == 2) return launch_flux_t<M, 32, 8, G, FT, 2, 2>(gz, ph, az, s, g.ny);
     if (nout == 3) return launch_flux_t<M, 32, 8, G, FT, 3, 2>(gz, ph, az, s, g.ny);
