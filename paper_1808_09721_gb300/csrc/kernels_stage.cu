@@ -41,17 +41,39 @@ __device__ __forceinline__ void defer_or_record(const StageArgs &a, int st, long
     record(a.status, st, cell);
 }
 
-// End of a restart kernel: the last block to finish (every block has read
-// the count by then) empties the list for the next stage.
-__device__ __forceinline__ void restart_done(int *rlist) {
+// After the whole stage: the last block of the stage kernel to finish (every
+// cell is solved or listed by then) solves the listed cells again from the
+// ideal-limit start and then along a continuation in a dt (physics_sf.cuh:
+// stage_restarts) and empties the list. With an empty list it only resets
+// the counters. Not inlined, so that the restart code does not raise the
+// register pressure of the kernel's main loop. `b` is null for a single grid
+// (a batch looks up each cell's run).
+template <bool STATS>
+__device__ __noinline__ void stage_tail_restarts(Grid g, Phys ph, StageArgs a, double cpsi, const BatchArgs *b) {
+    __shared__ int last;
+    __threadfence();  // this block's list entries, before its completion is counted
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&a.rlist[1], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int n = min(*(volatile int *)a.rlist, a.rcap);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const long long cell = ((volatile int *)a.rlist)[2 + e];
+        sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
+        if (b) {
+            const int run = b->run_of[cell];
+            k = sf::StageConst{b->adt[run], b->cpsi[run], b->sigma[run], ph.gamma, k.maxpass, a.hist};
+        }
+        const double pw = a.wwarm[sf::P * g.plane + cell];
+        record(a.status, sf::stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell,
+                                                           a.first_start),
+               cell);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&rlist[1], 1) == (int)gridDim.x - 1) {
-            rlist[0] = 0;
-            rlist[1] = 0;
-            __threadfence();
-        }
+        a.rlist[0] = 0;
+        a.rlist[1] = 0;
     }
 }
 
@@ -70,23 +92,7 @@ __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, 
                                           : (int)sf::ST_NEWTON;
         defer_or_record(a, st, cell);
     }
-}
-
-// The listed cells again, from the ideal-limit start and then along a
-// continuation in a dt (physics_sf.cuh: stage_restarts). Launched after every
-// single-fluid stage kernel; with an empty list every thread exits at once.
-template <bool STATS>
-__global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
-    using namespace sf;
-    const int n = min(*(volatile int *)a.rlist, a.rcap);
-    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long cell = a.rlist[2 + e];
-        const double pw = a.wwarm[P * g.plane + cell];
-        record(a.status, stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start),
-               cell);
-    }
-    restart_done(a.rlist);
+    if (a.rlist) stage_tail_restarts<STATS>(g, ph, a, cpsi, nullptr);
 }
 
 // Two fluids: the 7 x 7 Jacobian and its inverse of each thread live in a
@@ -109,9 +115,6 @@ __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph
     }
 }
 
-// restart kernels: a small fixed grid (the list is short: cells whose first start failed)
-static constexpr int kRestartBlocks = 64;
-
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > (1 << 30) ? (1 << 30) : b));
@@ -124,10 +127,6 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
     if (model == 0) {
         if (a.hist) k_stage_sf<true><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
         else k_stage_sf<false><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
-        if (a.rlist) {
-            if (a.hist) k_restart_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
-            else k_restart_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
-        }
     } else {
         if (a.hist) k_stage_tf<true><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
         else k_stage_tf<false><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
@@ -152,22 +151,7 @@ __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, B
                            : (int)sf::ST_NEWTON;
         defer_or_record(a, st, cell);
     }
-}
-
-template <bool STATS>
-__global__ void k_restart_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
-    using namespace sf;
-    const int n = min(*(volatile int *)a.rlist, a.rcap);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long cell = a.rlist[2 + e];
-        const int run = b.run_of[cell];
-        sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        record(a.status,
-               stage_restarts<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell,
-                                            a.first_start),
-               cell);
-    }
-    restart_done(a.rlist);
+    if (a.rlist) stage_tail_restarts<STATS>(g, ph, a, 0.0, &b);
 }
 
 template <bool STATS>
@@ -193,10 +177,6 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
     if (model == 0) {
         if (a.hist) k_stage_batch_sf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_sf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
-        if (a.rlist) {
-            if (a.hist) k_restart_batch_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
-            else k_restart_batch_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
-        }
     } else {
         if (a.hist) k_stage_batch_tf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_tf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
