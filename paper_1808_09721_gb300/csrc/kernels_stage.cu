@@ -41,39 +41,17 @@ __device__ __forceinline__ void defer_or_record(const StageArgs &a, int st, long
     record(a.status, st, cell);
 }
 
-// After the whole stage: the last block of the stage kernel to finish (every
-// cell is solved or listed by then) solves the listed cells again from the
-// ideal-limit start and then along a continuation in a dt (physics_sf.cuh:
-// stage_restarts) and empties the list. With an empty list it only resets
-// the counters. Not inlined, so that the restart code does not raise the
-// register pressure of the kernel's main loop. `b` is null for a single grid
-// (a batch looks up each cell's run).
-template <bool STATS>
-__device__ __noinline__ void stage_tail_restarts(Grid g, Phys ph, StageArgs a, double cpsi, const BatchArgs *b) {
-    __shared__ int last;
-    __threadfence();  // this block's list entries, before its completion is counted
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&a.rlist[1], 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int n = min(*(volatile int *)a.rlist, a.rcap);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const long long cell = ((volatile int *)a.rlist)[2 + e];
-        sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        if (b) {
-            const int run = b->run_of[cell];
-            k = sf::StageConst{b->adt[run], b->cpsi[run], b->sigma[run], ph.gamma, k.maxpass, a.hist};
-        }
-        const double pw = a.wwarm[sf::P * g.plane + cell];
-        record(a.status, sf::stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell,
-                                                           a.first_start),
-               cell);
-    }
+// End of a restart kernel: the last block to finish (every block has read
+// the count by then) empties the list for the next stage.
+__device__ __forceinline__ void restart_done(int *rlist) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        a.rlist[0] = 0;
-        a.rlist[1] = 0;
+        __threadfence();
+        if (atomicAdd(&rlist[1], 1) == (int)gridDim.x - 1) {
+            rlist[0] = 0;
+            rlist[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -85,14 +63,35 @@ template <bool STATS>
 __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace sf;
     sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
-         cell += (long long)gridDim.x * blockDim.x) {
+    const long long c0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, cs = (long long)gridDim.x * blockDim.x;
+    if (a.first_start != 0) {  // test control: every cell begins at a later start
+        for (long long cell = c0; cell < g.ncell; cell += cs) defer_or_record(a, sf::ST_NEWTON, cell);
+        return;
+    }
+    for (long long cell = c0; cell < g.ncell; cell += cs) {
         const double pw = a.wwarm[P * g.plane + cell];
-        const int st = a.first_start == 0 ? stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell)
-                                          : (int)sf::ST_NEWTON;
+        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
         defer_or_record(a, st, cell);
     }
-    if (a.rlist) stage_tail_restarts<STATS>(g, ph, a, cpsi, nullptr);
+}
+
+// The listed cells again, from the ideal-limit start and then along a
+// continuation in a dt (physics_sf.cuh: stage_restarts). Launched after every
+// single-fluid stage kernel; with an empty list every thread exits at once
+// (measured: ~4 us per step inside the step's CUDA graph, where an in-kernel
+// tail run by the stage kernel's last block cost ~20 us).
+template <bool STATS>
+__global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
+    using namespace sf;
+    const int n = min(*(volatile int *)a.rlist, a.rcap);
+    sf::StageConst k{a.adt, cpsi, ph.sigma, ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long cell = a.rlist[2 + e];
+        const double pw = a.wwarm[P * g.plane + cell];
+        record(a.status, stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start),
+               cell);
+    }
+    restart_done(a.rlist);
 }
 
 // Two fluids: the 7 x 7 Jacobian and its inverse of each thread live in a
@@ -115,6 +114,9 @@ __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph
     }
 }
 
+// restart kernels: a small fixed grid (the list is short: cells whose first start failed)
+static constexpr int kRestartBlocks = 64;
+
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > (1 << 30) ? (1 << 30) : b));
@@ -127,6 +129,10 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
     if (model == 0) {
         if (a.hist) k_stage_sf<true><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
         else k_stage_sf<false><<<blocks, kStageThreads, 0, s>>>(g, ph, a, cpsi);
+        if (a.rlist) {
+            if (a.hist) k_restart_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
+            else k_restart_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, cpsi);
+        }
     } else {
         if (a.hist) k_stage_tf<true><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
         else k_stage_tf<false><<<btf, kStageThreadsTF, 0, s>>>(g, ph, a, cpsi);
@@ -141,17 +147,34 @@ cudaError_t launch_stage(int model, const Grid &g, const Phys &ph, const StageAr
 template <bool STATS>
 __global__ void __maxnreg__(96) k_stage_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
     using namespace sf;
-    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
-         cell += (long long)gridDim.x * blockDim.x) {
+    const long long c0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, cs = (long long)gridDim.x * blockDim.x;
+    if (a.first_start != 0) {  // test control: every cell begins at a later start
+        for (long long cell = c0; cell < g.ncell; cell += cs) defer_or_record(a, sf::ST_NEWTON, cell);
+        return;
+    }
+    for (long long cell = c0; cell < g.ncell; cell += cs) {
         const int run = b.run_of[cell];
         sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        const int st = a.first_start == 0
-                           ? stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell,
-                                                       a.w + cell)
-                           : (int)sf::ST_NEWTON;
+        const int st =
+            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell);
         defer_or_record(a, st, cell);
     }
-    if (a.rlist) stage_tail_restarts<STATS>(g, ph, a, 0.0, &b);
+}
+
+template <bool STATS>
+__global__ void k_restart_batch_sf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
+    using namespace sf;
+    const int n = min(*(volatile int *)a.rlist, a.rcap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long cell = a.rlist[2 + e];
+        const int run = b.run_of[cell];
+        sf::StageConst k{b.adt[run], b.cpsi[run], b.sigma[run], ph.gamma, a.maxpass > 0 ? a.maxpass : 8, a.hist};
+        record(a.status,
+               stage_restarts<kNRef, STATS>(a.r + cell, g.plane, a.wwarm[P * g.plane + cell], k, a.q + cell, a.w + cell,
+                                            a.first_start),
+               cell);
+    }
+    restart_done(a.rlist);
 }
 
 template <bool STATS>
@@ -177,6 +200,10 @@ cudaError_t launch_stage_batch(int model, const Grid &g, const Phys &ph, const S
     if (model == 0) {
         if (a.hist) k_stage_batch_sf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_sf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
+        if (a.rlist) {
+            if (a.hist) k_restart_batch_sf<true><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
+            else k_restart_batch_sf<false><<<kRestartBlocks, 64, 0, s>>>(g, ph, a, b);
+        }
     } else {
         if (a.hist) k_stage_batch_tf<true><<<blocks, threads, 0, s>>>(g, ph, a, b);
         else k_stage_batch_tf<false><<<blocks, threads, 0, s>>>(g, ph, a, b);
