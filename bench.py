@@ -56,10 +56,12 @@ ALG_FP64_FLOPS_PER_CELL = {"flux1": 1918, "flux2": 1880, "tf_flux1": 2556, "tf_f
 # FP64 arithmetic instructions the kernels themselves issue (dadd, dmul, dfma;
 # one each) per interior cell on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
-FP64_INST_PER_CELL = {"stage": 173.0, "flux1": 738.4, "flux2": 710.4}
-# DRAM bytes (read + write) per cell and launch of the same kernels, from the
-# ncu launch list of the KHI 1024^2 bench (dram__bytes_read.sum + write.sum).
-DRAM_BYTES_PER_CELL = {"stage": 223.1, "flux1": 448.0, "flux2": 387.1}
+FP64_INST_PER_CELL = {"stage": 177.0, "flux1": 718.5, "flux2": 704.5}
+# DRAM bytes (read + write) per cell and launch of the same kernels, from an
+# ncu capture of the 512x512 KHI step (dram__bytes_read.sum + write.sum): the
+# reads scale with the cells; at that size part of the writes is still in L2
+# when a kernel ends, so the full-size writes are somewhat higher.
+DRAM_BYTES_PER_CELL = {"stage": 121.5, "flux1": 431.5, "flux2": 315.9}
 # Algorithmic HBM bytes per cell for each kernel (read once + written once).
 BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
 
@@ -544,6 +546,7 @@ def main():
               "fp64_passes_mean": _mean(hist["fp64_passes"]),
               "fp32_iterations": {str(k): v for k, v in hist["fp32_iterations"].items()},
               "fp64_passes": {str(k): v for k, v in hist["fp64_passes"].items()},
+              "converged_start": hist["starts"],
               "note": "one FP64 step of the benchmark workload, both implicit stages, counted after timing"}
 
     # roofline of the dominant kernel (FP64 form): FP64-pipe bound. Peak = the
@@ -563,7 +566,9 @@ def main():
     hbm_achieved = BYTES_PER_CELL[dom] * wl.cells / (per_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak if achieved else None,
-                "traffic": DRAM_BYTES_PER_CELL[dom] * wl.cells if args.n == 1024 else None, "kernel": dom,
+                "traffic": DRAM_BYTES_PER_CELL[dom] * wl.cells, "kernel": dom,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per cell on the 512^2 "
+                                  "step, times the cells of this launch",
                 "kernel_ms_per_launch": per_launch_ms,
                 "peak_source": f"measured: FP64 FMA chains on all {n_sm} SMs, CUDA events (rmhd_fp64_fma_rate), x2",
                 "alg_flops_per_cell": alg,
