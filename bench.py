@@ -471,30 +471,33 @@ def main():
     if args.adjoint:
         fl = WL.field_loop(n=256, seed=3, nsteps=50)
 
-        def adjoint_cost(scheme):
-            fs = Sim.from_workload(fl, device=f"cuda:{local}", scheme=scheme)
-            fs.step(fl.dt, 3)
-            fs.set_prims(fl.prims)
+        def adjoint_cost(wa, scheme, b0):
+            """Forward, recorded forward and adjoint wall times of 50 steps
+            (checkpoints every 10); J = sum(Bx^2 + By^2 + 2 Bz^2) dV with B at
+            conserved rows b0 .. b0 + 2."""
+            fs = Sim.from_workload(wa, device=f"cuda:{local}", scheme=scheme)
+            fs.step(wa.dt, 3)
+            fs.set_prims(wa.prims)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            fs.step(fl.dt, 50)
+            fs.step(wa.dt, 50)
             fs.check()
             torch.cuda.synchronize()
             t_fwd = time.perf_counter() - t0
-            fs.set_prims(fl.prims)
+            fs.set_prims(wa.prims)
             fs.record(50, 10)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            fs.step(fl.dt, 50)
+            fs.step(wa.dt, 50)
             fs.check()
             torch.cuda.synchronize()
             t_rec = time.perf_counter() - t0
             qN = fs.cons()
-            dv = fl.dx * fl.dy
+            dv = wa.dx * wa.dy
             lam = np.zeros_like(qN)
-            lam[5] = 2.0 * qN[5] * dv
-            lam[6] = 2.0 * qN[6] * dv
-            lam[7] = 4.0 * qN[7] * dv
+            lam[b0] = 2.0 * qN[b0] * dv
+            lam[b0 + 1] = 2.0 * qN[b0 + 1] * dv
+            lam[b0 + 2] = 4.0 * qN[b0 + 2] * dv
             fs.adjoint(lam)  # warm-up (kernel set-up)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -503,10 +506,14 @@ def main():
             t_adj = time.perf_counter() - t0
             return {"fwd_s": t_fwd, "recorded_fwd_s": t_rec, "adjoint_s": t_adj,
                     "adjoint_over_fwd": t_adj / t_fwd, "total_over_fwd": (t_rec + t_adj) / t_fwd, "dJ_dsigma": gsig}
-        adjoint = adjoint_cost(0)
-        adjoint.update({"sigma": fl.sigma, "ssp3": adjoint_cost(1),
+        adjoint = adjoint_cost(fl, 0, 5)
+        tfa = WL.tf_sheet(n=128, seed=1)
+        adjoint.update({"sigma": fl.sigma, "ssp3": adjoint_cost(fl, 1, 5),
                         "workload": "field loop 256x256 periodic, 50 SSP2(222) steps FP64 (and SSP3(332) in "
-                                    "'ssp3'), checkpoints every 10, J = sum(Bx^2 + By^2 + 2 Bz^2) dV"})
+                                    "'ssp3'), checkpoints every 10, J = sum(Bx^2 + By^2 + 2 Bz^2) dV",
+                        "two_fluid": dict(adjoint_cost(tfa, 0, 10), workload="two-fluid current sheet 128x128 "
+                                          "periodic (mu = -+1e3, sigma 1e4), 50 SSP2(222) steps FP64, "
+                                          "checkpoints every 10, J = sum(Bx^2 + By^2 + 2 Bz^2) dV")})
 
     # e2e through the C ABI with host buffers: upload prims, one step, read prims back
     pin = torch.empty(wl.prims.size, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.prims.shape)
@@ -627,7 +634,8 @@ def main():
             summ.update({"batch_mixed": round(batch["value"] / 1e6, 1),
                          "batch_rel_l1": float(f"{batch['rel_l1_mixed_vs_fp64_max_over_tubes']:.2e}")})
         if adjoint:
-            summ.update({"adjoint_over_fwd": round(adjoint["adjoint_over_fwd"], 2)})
+            summ.update({"adjoint_over_fwd": round(adjoint["adjoint_over_fwd"], 2),
+                         "tf_adjoint_over_fwd": round(adjoint["two_fluid"]["adjoint_over_fwd"], 2)})
         summ.update({"alu_frac": round(roofline["frac"], 3) if roofline["frac"] else None,
                      "hbm_frac_kernel": round(roofline["hbm_frac"], 4)})
         line["summary_Mcell_updates_per_s"] = summ

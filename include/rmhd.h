@@ -207,21 +207,27 @@ int rmhd_set_first_start(rmhd_ctx *ctx, int start);
  * directions. Synchronous. */
 int rmhd_diagnostics(rmhd_ctx *ctx, double *out);
 
-/* Discrete adjoint of the IMEX step, SSP2(222) or SSP3(332) (single fluid,
+/* Discrete adjoint of the IMEX step, SSP2(222) or SSP3(332) (either model,
  * FP64, 1-D, 2-D or 3-D single grid with at least 3 cells per direction): gradients
  * of a functional of the final
  * conserved state with respect to the initial primitives and sigma.
  *   rmhd_record arms recording of the next `nsteps` steps; it must follow
  *   rmhd_set_prims directly (the gradient is w.r.t. those primitives, with
- *   varrho = div E and psi = phi = 0 as rmhd_set_prims builds them). While
+ *   psi = phi = 0 and, for one fluid, varrho = div E as rmhd_set_prims
+ *   builds them; for two fluids the charge Dbar follows from the species
+ *   densities). While
  *   armed, rmhd_imex_step stores a checkpoint every `ckpt_every` steps and
  *   all recorded steps must use one dt. `workspace` (device, 256-byte
  *   aligned, >= rmhd_recording_bytes) may be NULL: the library allocates.
  *   Arming again drops the earlier recording (and frees the library's own
  *   workspace) first; if the new arming fails, the context is left unarmed.
  *   rmhd_adjoint_step reverses every recorded step: from dJ/dq at the final
- *   state ([14][ny][nx]) it writes dJ/d(prims) ([11][ny][nx], may be NULL) and
- *   dJ/dsigma (may be NULL). Each segment of ckpt_every steps is recomputed from its
+ *   state ([N_c][ny][nx], N_c = 14 or 18) it writes dJ/d(prims) ([n_prim][ny][nx],
+ *   n_prim = 11 or 16 in the layout of rmhd_set_prims, may be NULL) and
+ *   dJ/dsigma (may be NULL). Two fluids: the stiff unknowns of a stage are
+ *   (Sbar, taubar, E), whose transposed 7 x 7 system is solved per cell, and
+ *   the primitives come from the species split and one pressure root per
+ *   species (Sec. 2.1.3), both differentiated by the implicit-function theorem. Each segment of ckpt_every steps is recomputed from its
  *   checkpoint (same kernels, same results), the implicit stage solves and
  *   the primitive recovery are differentiated by the implicit-function
  *   theorem, and the WENO3/LF flux divergence is transposed face by face.

@@ -37,6 +37,6 @@ class ImexSteps(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         sim = ctx.sim
-        gp = torch.empty((11,) + sim.shape, dtype=torch.float64, device=grad_out.device)
+        gp = torch.empty((sim.np,) + sim.shape, dtype=torch.float64, device=grad_out.device)
         _, gs = sim.adjoint(grad_out.contiguous(), out=gp)
         return gp, torch.tensor(gs, dtype=torch.float64, device=grad_out.device), None, None, None, None

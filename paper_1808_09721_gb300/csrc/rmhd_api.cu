@@ -1259,7 +1259,7 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
     L.fbz = o; o += align256(zpl);
     L.qbd = o; o += align256(nc * pl);
     L.sig = o; o += align256(pl);
-    L.pbar = o; o += align256(11 * pl);
+    L.pbar = o; o += align256(model_np(c->cfg.model) * pl);
     L.fin = o; o += align256((size_t)(nc + nw) * pl);
     L.sum = o; o += align256(sizeof(double));
     L.total = o;
@@ -1267,8 +1267,8 @@ static RecLayout rec_layout(const rmhd_ctx *c, int nsteps, int K) {
 }
 
 static int adjoint_supported(rmhd_ctx *c) {
-    if (c->cfg.model != RMHD_RESISTIVE || c->cfg.precision != RMHD_FP64 || c->batch || c->slab)
-        return fail(c, RMHD_ERR_STATE, "adjoint: single-fluid FP64 single-grid contexts only");
+    if (c->cfg.precision != RMHD_FP64 || c->batch || c->slab)
+        return fail(c, RMHD_ERR_STATE, "adjoint: FP64 single-grid contexts only");
     if (c->cfg.nx < 3 || (c->cfg.ny > 1 && c->cfg.ny < 3) || (c->g.nz > 1 && c->g.nz < 3))
         return fail(c, RMHD_ERR_INVALID, "adjoint: grids need at least 3 cells per direction");
     return RMHD_OK;
@@ -1417,17 +1417,18 @@ int rmhd_adjoint_step(rmhd_ctx *c, const double *dJ_dcons, int where_in, double 
             const double *cq[3] = {Sq[0], Sq[1], S > 2 ? Sq[2] : nullptr};
             const double *cw[3] = {Sw[0], Sw[1], S > 2 ? Sw[2] : nullptr};
             double *fl[3] = {c->rec_fx, c->rec_fy, c->rec_fz}, *fbl[3] = {c->rec_fbx, c->rec_fby, c->rec_fbz};
-            CK(c, launch_adjoint_step(c->g, c->ph, S > 2 ? 1 : 0, dt, lam, lamn, cq, cw, fl, fbl, c->rec_qbd,
+            CK(c, launch_adjoint_step(c->cfg.model, c->g, c->ph, S > 2 ? 1 : 0, dt, lam, lamn, cq, cw, fl, fbl, c->rec_qbd,
                                       c->rec_lq, c->rec_lr2, c->rec_lr3, c->rec_sig, c->stream));
             std::swap(lam, lamn);
         }
     }
     // initial primitives: adjoint of the prims -> cons map at checkpoint 0
-    CK(c, launch_adjoint_prims(c->g, c->ph, c->rec_ck, c->rec_ck + (size_t)nc * P, lam, c->rec_pbar, c->stream));
+    CK(c, launch_adjoint_prims(c->cfg.model, c->g, c->ph, c->rec_ck, c->rec_ck + (size_t)nc * P, lam, c->rec_pbar, c->stream));
     CK(c, launch_sum(c->rec_sig, c->g.ncell, c->rec_sum, c->stream));
     if (dJ_dprims0) {
-        CK(c, launch_unpack(c->g, 11, c->rec_pbar, c->stage_buf, c->stream));
-        st = stage_out(c, dJ_dprims0, 11, where_out);
+        const int np = model_np(c->cfg.model);
+        CK(c, launch_unpack(c->g, np, c->rec_pbar, c->stage_buf, c->stream));
+        st = stage_out(c, dJ_dprims0, np, where_out);
         if (st) return st;
     }
     CK(c, cudaMemcpyAsync(c->h_diag, c->rec_sum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

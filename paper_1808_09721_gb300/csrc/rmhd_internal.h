@@ -129,14 +129,14 @@ cudaError_t launch_set_prims_batch(int model, const Grid &g, const Phys &ph, con
 // resident CTAs per SM of the batch flux kernel for a tile width (0 if unsupported)
 int flux_batch_occupancy(int model, int precision, int tile_x);
 
-// discrete adjoint (single fluid, FP64): one reverse step, the initial-map
-// adjoint, and a deterministic plane sum
-cudaError_t launch_adjoint_step(const Grid &g, const Phys &ph, int scheme, double dt, const double *lam, double *out,
-                                const double *const *Sq, const double *const *Sw, double *const *f,
-                                double *const *fb, double *qbd, double *lq, double *lr2, double *lr3,
-                                double *sig, cudaStream_t s);
-cudaError_t launch_adjoint_prims(const Grid &g, const Phys &ph, const double *q, const double *w, const double *lam,
-                                 double *pbar, cudaStream_t s);
+// discrete adjoint (FP64; model 0 single fluid, 1 two fluids): one reverse
+// step, the initial-map adjoint, and a deterministic plane sum
+cudaError_t launch_adjoint_step(int model, const Grid &g, const Phys &ph, int scheme, double dt, const double *lam,
+                                double *out, const double *const *Sq, const double *const *Sw, double *const *f,
+                                double *const *fb, double *qbd, double *lq, double *lr2, double *lr3, double *sig,
+                                cudaStream_t s);
+cudaError_t launch_adjoint_prims(int model, const Grid &g, const Phys &ph, const double *q, const double *w,
+                                 const double *lam, double *pbar, cudaStream_t s);
 cudaError_t launch_sum(const double *x, long long n, double *out, cudaStream_t s);
 
 inline int model_nc(int model) { return model == 0 ? 14 : 18; }

@@ -181,9 +181,9 @@ class Sim:
         if isinstance(dJ_dcons, np.ndarray):
             dJ_dcons = np.ascontiguousarray(dJ_dcons, dtype=np.float64)
         if out is None:
-            out = np.empty((11,) + self.shape)
+            out = np.empty((self.np,) + self.shape)
         pin, wi, _k1 = self._ptr(dJ_dcons, self.nc, False)
-        pout, wo, _k2 = self._ptr(out, 11, True)
+        pout, wo, _k2 = self._ptr(out, self.np, True)
         gs = C.c_double()
         self._check(self.lib.rmhd_adjoint_step(self.h, pin, wi, pout, wo, C.byref(gs)), "adjoint_step")
         return out, gs.value

@@ -73,11 +73,11 @@ def test_ssp3_mixed_precision(Sim):
 
 
 def test_adjoint_refused_outside_its_scope(Sim):
-    """The discrete adjoint covers the single-fluid FP64 step (both schemes):
-    arming it on a mixed-precision or two-fluid SSP3(332) context is an error,
-    and the context stays usable."""
+    """The discrete adjoint covers the FP64 step of either model (both schemes):
+    arming it on a mixed-precision SSP3(332) context, or on a grid with fewer
+    than 3 cells along a direction, is an error, and the context stays usable."""
     from paper_1808_09721_gb300 import _lib as L
-    for wl, prec in ((WL.field_loop(n=8, nsteps=2), 1), (WL.tf_sheet(n=8, seed=1), 0)):
+    for wl, prec in ((WL.field_loop(n=8, nsteps=2), 1), (WL.tf_sheet(n=8, seed=1, ny=2), 0)):
         s = Sim.from_workload(wl, scheme=1, precision=prec)
         with pytest.raises(L.RmhdError):
             s.record(2, 1)
