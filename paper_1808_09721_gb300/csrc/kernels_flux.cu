@@ -662,15 +662,19 @@ static cudaError_t launch_flux_t(const Grid &g, const Phys &ph, const FluxArgs &
     return cudaGetLastError();
 }
 
-template <int NOUT, int DIRS>
+namespace swp { struct SF; struct TF; }
+template <class M, int NOUT, int DIRS>
 static cudaError_t launch_sweep_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz);
 
 template <class M, class FT, int NOUT>
 static cudaError_t launch_flux_m(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s) {
     constexpr int G = sizeof(FT) == 8 ? M::G_FP64 : M::G_FP32;
-    // single fluid, FP64, 2-D: the line-sweep kernel
-    if constexpr (std::is_same<M, SFModel>::value && std::is_same<FT, double>::value)
-        if (g.ny > 1) return launch_sweep_t<NOUT, 3>(g, ph, a, s, 1);
+    // FP64, 2-D: the line-sweep kernel
+    if constexpr (std::is_same<FT, double>::value)
+        if (g.ny > 1) {
+            using SW = typename std::conditional<std::is_same<M, SFModel>::value, swp::SF, swp::TF>::type;
+            return launch_sweep_t<SW, NOUT, 3>(g, ph, a, s, 1);
+        }
     // 1-D: 32-cell tiles while one wave of them does not fill the 152 SMs
     // (short tubes are latency-bound on a few SMs), 128-cell tiles beyond
     if (g.ny == 1)
@@ -723,104 +727,207 @@ static cudaError_t launch_fb_m(const Grid &g, const Phys &ph, const FluxArgs &a,
     return launch_fb_t<M, 128, FT, NOUT>(g, ph, a, b, blocks, s);
 }
 
-// ---- single fluid, FP64, 2-D tiles by line sweeps -------------------------
+// ---- FP64, 2-D tiles by line sweeps (both models) ------------------------
 // The FP64 form is bound by the FP64 pipe. In the group kernel above the
 // half-point and face rounds of each component are separated by group
 // barriers and pass through shared memory; with every group at a barrier the
 // pipe idles. Here one thread reconstructs one component (or Maxwell pair)
-// along one segment of a line of a 16 x 16 tile: it walks the segment's
-// staged positions, keeps the last three half points' e+-, A+- and the last
-// face value in registers, and emits the face difference of each interior
-// cell as soon as both of its faces exist. The arithmetic per half point and
-// face is the group kernel's (same formulas, same order), but no barrier
-// separates the rounds and no half-point or face data goes through shared
-// memory: a CTA needs 74 KB, so three CTAs (30 warps) share an SM and hide
-// the FP64 latency. (An FP64 warp instruction takes the pipe for the same
-// time whatever its active lanes, so splitting lines into overlapping
+// along one line of a 16 x 16 tile: it walks the line's staged positions,
+// keeps the last three half points' e+-, A+- and the last face value in
+// registers, and emits the face difference of each interior cell as soon as
+// both of its faces exist. The arithmetic per half point and face is the
+// group kernel's (same formulas, same order), but no barrier separates the
+// rounds and no half-point or face data goes through shared memory. One fluid:
+// a CTA needs 74 KB, so three CTAs (30 warps) share an SM; two fluids: 99 KB
+// and two CTAs (28 warps). (An FP64 warp instruction takes the pipe for the
+// same time whatever its active lanes, so splitting lines into overlapping
 // segments for more threads would cost real FP64 throughput.)
 //
 // Per tile three phases: (1) every staged cell (the tile and its 2-cell
 // halo; boundary conditions by index map, halo rows of a slab) is loaded by
-// one thread, which computes its auxiliaries J, Z, p + (E^2 + B^2)/2 and keeps
-// the 14 conserved variables and the velocity in shared memory; (2) the x
-// sweeps write their part of L to a global scratch (FluxArgs::lscr; the x-y
-// pass of a 3-D grid writes L_x to lout); (3) the y sweeps (in the z pass of
-// a 3-D grid: the z sweeps) add theirs and form the pass's outputs for their
-// cells right away. Reconstructions 0-3 are the four Maxwell pairs
-// of the direction, 4-9 the generic components D, tau, S_x, S_y, S_z,
-// varrho, so that each warp (one reconstruction) takes one code path.
+// one thread, which keeps the conserved variables and the primitives the
+// fluxes need in shared memory, with the model's auxiliaries; (2) the x sweeps write
+// their part of L to a global scratch (FluxArgs::lscr; the x-y pass of a 3-D
+// grid writes L_x to lout); (3) the y sweeps (in the z pass of a 3-D grid:
+// the z sweeps) add theirs and form the pass's outputs for their cells right
+// away. Reconstructions 0-3 are the four Maxwell pairs of the direction, the
+// rest the components with their own flux, ordered so that the two
+// reconstructions of a warp (16 lines each) take one code path.
 namespace swp {
 constexpr int T = 16;                    // tile side (interior cells)
 constexpr int S = T + 4;                 // staged side (2-cell halo each way)
 constexpr int SP = S + 1;                // padded row stride: rows read by 16 lanes hit distinct banks
 constexpr int SN = S * SP;               // one staged plane
-constexpr int NREC = 10;                 // 4 Maxwell pairs + 6 generic components per direction
-constexpr int SEG = 1;                   // a line is swept in SEG segments of T / SEG cells
-constexpr int SL = T / SEG + 4;          // staged positions of one segment
-constexpr int NTHR = NREC * T * SEG;     // 160 threads
-constexpr int NST = sf::NC + 3;          // staged planes: the conserved variables and the velocity
-constexpr size_t OFF_AUX = sizeof(double) * NST * SN;
-constexpr size_t TOTAL = OFF_AUX + sizeof(double) * SFModel::NAUX * SN;
+constexpr int SL = T + 4;                // staged positions of one line
 
-// Maxwell pair k (a, b, s) along physical direction pdir: f_a = s q_b, f_b = s q_a.
-__device__ __forceinline__ void pair_of(int pdir, int k, int &a, int &b, double &sg) {
-    using namespace sf;
-    sg = 1.0;
-    if (pdir == 0) {
-        a = k == 0 ? BX : k == 1 ? EX : k == 2 ? BY : BZ;
-        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EZ : EY;
-        if (k == 2) sg = -1.0;
-    } else if (pdir == 1) {
-        a = k == 0 ? BY : k == 1 ? EY : k == 2 ? BZ : BX;
-        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EX : EZ;
-        if (k == 2) sg = -1.0;
-    } else {
-        a = k == 0 ? BZ : k == 1 ? EZ : k == 2 ? BX : BY;
-        b = k == 0 ? PHI : k == 1 ? PSI : k == 2 ? EY : EX;
-        if (k == 2) sg = -1.0;
+// Single fluid (Eq. resistive RMHD). Staged planes: the 14 conserved
+// variables and the velocity; auxiliaries J (3), Z = rho h W^2,
+// p + (E^2 + B^2)/2. Generic components D, tau, S_x, S_y, S_z, varrho.
+struct SF {
+    static constexpr int NC = sf::NC, NW = sf::NW;
+    static constexpr int NREC = 10, NST = NC + 3, NAUX = 5;
+    static constexpr int NTHR = NREC * T, MINB = 3;
+    static constexpr int BX = sf::BX, EX = sf::EX, PSI = sf::PSI, PHI = sf::PHI;
+    static __device__ __forceinline__ int gen_of(int r) {
+        using namespace sf;
+        return r == 4 ? D : r == 5 ? TAU : r == 6 ? SX : r == 7 ? SY : r == 8 ? SZ : RHOE;
     }
-}
-// generic component of reconstruction r (4..9)
-__device__ __forceinline__ int gen_of(int r) {
-    using namespace sf;
-    return r == 4 ? D : r == 5 ? TAU : r == 6 ? SX : r == 7 ? SY : r == 8 ? SZ : RHOE;
+    // physical flux along pdir of generic component c at staged cell idx
+    // (the group kernel's expressions)
+    static __device__ __forceinline__ double gen_flux(const double *st, const double *aux, const Phys &, int c,
+                                                      int pdir, int idx) {
+        using namespace sf;
+        const double vd = st[(NC + pdir) * SN + idx];
+        if (c == D) return st[D * SN + idx] * vd;
+        if (c == TAU) return st[(SX + pdir) * SN + idx] - st[D * SN + idx] * vd;
+        if (c == RHOE) return aux[pdir * SN + idx];
+        const int i = c - SX;
+        const double Zv = aux[3 * SN + idx] * vd;
+        double f = Zv * st[(NC + i) * SN + idx] - st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] -
+                   st[(BX + i) * SN + idx] * st[(BX + pdir) * SN + idx];
+        if (i == pdir) f += aux[4 * SN + idx];
+        return f;
+    }
+    // staged cell idx from its conserved variables and primitives x
+    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx) {
+#pragma unroll
+        for (int v = 0; v < NST; ++v) st[v * SN + idx] = x[v];
+        const double *q = x, *w = x + NC;
+        double J[3];
+        sf::current(q, w, ph.sigma, J);
+        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
+                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
+        aux[0 * SN + idx] = J[0];
+        aux[1 * SN + idx] = J[1];
+        aux[2 * SN + idx] = J[2];
+        aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
+        aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
+    }
+    // nonzero source entries: E: -J, psi: varrho - kappa psi, phi: -kappa phi
+    static __device__ __forceinline__ bool source(int c, const double *st, const double *aux, const FluxArgs &,
+                                                  const Grid &, int own, long long, const Phys &ph, double &sv) {
+        if (c >= sf::EX && c <= sf::EZ) { sv = -aux[(c - sf::EX) * SN + own]; return true; }
+        if (c == sf::PSI) { sv = fma(-ph.kappa, st[sf::PSI * SN + own], st[sf::RHOE * SN + own]); return true; }
+        if (c == sf::PHI) { sv = -ph.kappa * st[sf::PHI * SN + own]; return true; }
+        return false;
+    }
+};
+
+// Two fluids (Appendix A). Staged planes: the 18 conserved variables, the
+// species velocities v_e, v_p, Z_e, Z_p (Z_s = rho_s h_s W_s^2) and D_e, D_p
+// (the species split of (D, Dbar)); auxiliaries P = p_e + p_p + (E^2 + B^2)/2
+// and Pbar = mu_e p_e + mu_p p_p. The source entries Sbar (3), taubar and
+// E (3) = -J of the stage state come from the stage kernel
+// (FluxArgs::srcg), which evaluates them at its root. Generic components
+// D, tau | Dbar, taubar | S_x, S_y | S_z, Sbar_x | Sbar_y, Sbar_z: the two
+// reconstructions of a warp share one expression, its coefficients selected
+// per component.
+struct TF {
+    static constexpr int NC = tf::NC, NW = tf::NW;
+    static constexpr int NREC = 14, NST = NC + 10, NAUX = 2;
+    static constexpr int NTHR = NREC * T, MINB = 2;
+    static constexpr int VE = NC, VP = NC + 3, ZE = NC + 6, ZP = NC + 7, DE = NC + 8, DP = NC + 9;
+    static constexpr int BX = tf::BX, EX = tf::EX, PSI = tf::PSI, PHI = tf::PHI;
+    static __device__ __forceinline__ int gen_of(int r) {
+        using namespace tf;
+        return r == 4 ? D : r == 5 ? TAU : r == 6 ? DB : r == 7 ? TAUB : r == 8 ? SX : r == 9 ? SY : r == 10 ? SZ
+             : r == 11 ? SBX : r == 12 ? SBY : SBZ;
+    }
+    // Eq. (twoFluid flux) along pdir
+    static __device__ __forceinline__ double gen_flux(const double *st, const double *aux, const Phys &ph, int c,
+                                                      int pdir, int idx) {
+        using namespace tf;
+        const double ved = st[(VE + pdir) * SN + idx], vpd = st[(VP + pdir) * SN + idx];
+        const double De = st[DE * SN + idx], Dp = st[DP * SN + idx];
+        if (c == D || c == TAU) {  // D: sum D_s v_s; tau: S_d - sum D_s v_s
+            const double f = fma(De, ved, Dp * vpd);
+            return c == TAU ? st[(SX + pdir) * SN + idx] - f : f;
+        }
+        if (c == DB || c == TAUB) {  // Dbar: sum mu_s D_s v_s; taubar: sum mu_s (Z_s - D_s) v_s
+            const double xe = c == TAUB ? st[ZE * SN + idx] - De : De;
+            const double xp = c == TAUB ? st[ZP * SN + idx] - Dp : Dp;
+            return fma(ph.mu_e * xe, ved, ph.mu_p * xp * vpd);
+        }
+        // S_i: sum (Z_s v_s,d v_s,i + delta p_s) - E_i E_d - B_i B_d + delta (E^2 + B^2)/2;
+        // Sbar_i: sum mu_s (Z_s v_s,d v_s,i + delta p_s)
+        const bool bar = c >= SBX;
+        const double ce = bar ? ph.mu_e : 1.0, cp = bar ? ph.mu_p : 1.0;
+        const int i = c - (bar ? SBX : SX);
+        const double ze = ce * st[ZE * SN + idx] * ved, zp = cp * st[ZP * SN + idx] * vpd;
+        double f = fma(ze, st[(VE + i) * SN + idx], zp * st[(VP + i) * SN + idx]);
+        if (!bar)
+            f -= st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] + st[(BX + i) * SN + idx] * st[(BX + pdir) * SN + idx];
+        if (i == pdir) f += aux[(bar ? 1 : 0) * SN + idx];
+        return f;
+    }
+    // staged cell idx from its conserved variables and primitives x
+    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx) {
+        using namespace tf;
+        const double *q = x, *w = x + NC;
+#pragma unroll
+        for (int v = 0; v < NC; ++v) st[v * SN + idx] = q[v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            st[(VE + i) * SN + idx] = w[VX + i];
+            st[(VP + i) * SN + idx] = w[5 + VX + i];
+        }
+        st[ZE * SN + idx] = w[ZZ];
+        st[ZP * SN + idx] = w[5 + ZZ];
+        st[DE * SN + idx] = (q[DB] - ph.mu_p * q[D]) * ph.inv_dmu;
+        st[DP * SN + idx] = (ph.mu_e * q[D] - q[DB]) * ph.inv_dmu;
+        const double E2B2 = q[EX] * q[EX] + q[EY] * q[EY] + q[EZ] * q[EZ] + q[BX] * q[BX] + q[BY] * q[BY] +
+                            q[BZ] * q[BZ];
+        aux[0 * SN + idx] = fma(0.5, E2B2, w[P] + w[5 + P]);
+        aux[1 * SN + idx] = fma(ph.mu_e, w[P], ph.mu_p * w[5 + P]);
+    }
+    // nonzero source entries: Sbar, taubar, E (from the stage kernel), psi:
+    // Dbar - kappa psi (varrho = sum mu_s D_s = Dbar), phi: -kappa phi
+    static __device__ __forceinline__ bool source(int c, const double *st, const double *, const FluxArgs &a,
+                                                  const Grid &g, int own, long long cell, const Phys &ph,
+                                                  double &sv) {
+        using namespace tf;
+        if (c >= SBX && c <= TAUB) { sv = a.srcg[(long long)(c - SBX) * g.plane + cell]; return true; }
+        if (c >= EX && c <= EZ) { sv = a.srcg[(long long)(4 + c - EX) * g.plane + cell]; return true; }
+        if (c == PSI) { sv = fma(-ph.kappa, st[PSI * SN + own], st[DB * SN + own]); return true; }
+        if (c == PHI) { sv = -ph.kappa * st[PHI * SN + own]; return true; }
+        return false;
+    }
+};
+
+template <class M>
+constexpr size_t off_aux() { return sizeof(double) * M::NST * SN; }
+template <class M>
+constexpr size_t total() { return off_aux<M>() + sizeof(double) * M::NAUX * SN; }
+
+// Maxwell pair k (a, b, s) of model M along physical direction pdir:
+// f_a = s q_b, f_b = s q_a; with d1, d2 the other two directions in cyclic
+// order: (B_d, phi), (E_d, psi), (B_d1, E_d2) with s = -1, (B_d2, E_d1).
+template <class M>
+__device__ __forceinline__ void pair_of(int pdir, int k, int &a, int &b, double &sg) {
+    const int d1 = pdir == 2 ? 0 : pdir + 1, d2 = pdir == 0 ? 2 : pdir - 1;
+    sg = k == 2 ? -1.0 : 1.0;
+    a = k == 0 ? M::BX + pdir : k == 1 ? M::EX + pdir : k == 2 ? M::BX + d1 : M::BX + d2;
+    b = k == 0 ? M::PHI : k == 1 ? M::PSI : k == 2 ? M::EX + d2 : M::EX + d1;
 }
 
-// Physical flux along pdir of generic component c at staged cell idx
-// (Eq. resistive RMHD; the group kernel's expressions). The velocity is
-// staged after the 14 conserved variables.
-__device__ __forceinline__ double gen_flux(const double *st, const double *aux, int c, int pdir, int idx) {
-    using namespace sf;
-    const double vd = st[(NC + pdir) * SN + idx];
-    if (c == D) return st[D * SN + idx] * vd;
-    if (c == TAU) return st[(SX + pdir) * SN + idx] - st[D * SN + idx] * vd;
-    if (c == RHOE) return aux[pdir * SN + idx];
-    const int i = c - SX;
-    const double Zv = aux[3 * SN + idx] * vd;
-    double f = Zv * st[(NC + i) * SN + idx] - st[(EX + i) * SN + idx] * st[(EX + pdir) * SN + idx] -
-               st[(BX + i) * SN + idx] * st[(BX + pdir) * SN + idx];
-    if (i == pdir) f += aux[4 * SN + idx];
-    return f;
-}
-
-// One segment (interior cells c0 .. c0 + T/SEG - 1) of line `line` of
-// reconstruction r along the tile's x (ALONG_X) or second dimension, physical
-// direction pdir; `line` is the interior row (ALONG_X) or column. Hands each
-// cell's face difference 4 F_{c-1/2} - 4 F_{c+1/2} to put(component, cx, cy, d).
-template <bool ALONG_X, class PUT>
-__device__ __forceinline__ void sweep_line(const double *st, const double *aux, int r, int line, int c0, int pdir,
-                                           PUT &&put) {
+// One line `line` of reconstruction r of model M along the tile's x
+// (ALONG_X) or second dimension, physical direction pdir; `line` is the
+// interior row (ALONG_X) or column. Hands each interior cell's face
+// difference 4 F_{c-1/2} - 4 F_{c+1/2} to put(component, cx, cy, d).
+template <class M, bool ALONG_X, class PUT>
+__device__ __forceinline__ void sweep_line(const double *st, const double *aux, const Phys &ph, int r, int line,
+                                           int pdir, PUT &&put) {
     constexpr int step = ALONG_X ? 1 : SP;
-    const int base = (ALONG_X ? (2 + line) * SP : 2 + line) + c0 * step;
+    const int base = ALONG_X ? (2 + line) * SP : 2 + line;
     const double eps4 = 4e-6;
     auto cell = [&](int comp, int c, double d) {
-        if (ALONG_X) put(comp, c0 + c, line, d);
-        else put(comp, line, c0 + c, d);
+        if (ALONG_X) put(comp, c, line, d);
+        else put(comp, line, c, d);
     };
     if (r < 4) {  // Maxwell pair
         int a, b;
         double sg;
-        pair_of(pdir, r, a, b, sg);
+        pair_of<M>(pdir, r, a, b, sg);
         const double *qa = st + a * SN + base, *qb = st + b * SN + base;
         double qa0 = qa[0], qb0 = qb[0];
         double qa1 = 0.0, qb1 = 0.0;                      // positions h - 1 (valid from h = 1)
@@ -854,14 +961,14 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
             qa0 = qan; qb0 = qbn;
         }
     } else {  // generic component: its physical flux at each position
-        const int c = gen_of(r);
+        const int c = M::gen_of(r);
         const double *qv = st + c * SN + base;
-        double q0 = qv[0], f0 = gen_flux(st, aux, c, pdir, base);
+        double q0 = qv[0], f0 = M::gen_flux(st, aux, ph, c, pdir, base);
         double f1 = 0.0;
         double ep1 = 0.0, em1 = 0.0, Ap1 = 0.0, Am1 = 0.0, ep2 = 0.0, Ap2 = 0.0, F = 0.0;
 #pragma unroll
         for (int h = 0; h < SL - 1; ++h) {
-            const double qn = qv[(h + 1) * step], fn = gen_flux(st, aux, c, pdir, base + (h + 1) * step);
+            const double qn = qv[(h + 1) * step], fn = M::gen_flux(st, aux, ph, c, pdir, base + (h + 1) * step);
             const double df = fn - f0, dq = qn - q0;
             const double ep = df + dq, em = df - dq;
             const double ap = fma(ep, ep, eps4), am = fma(em, em, eps4);
@@ -885,23 +992,23 @@ __device__ __forceinline__ void sweep_line(const double *st, const double *aux, 
 
 // DIRS = 3: x and y sweeps (2-D grids, and the x-y pass of a 3-D grid with
 // NOUT = 0); DIRS = 2: the z pass of a 3-D grid (tile's second dimension = z).
-template <int NOUT, int DIRS>
-__global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
+template <class M, int NOUT, int DIRS>
+__global__ void __launch_bounds__(M::NTHR, M::MINB) k_flux_sweep(Grid g, Phys ph, FluxArgs a) {
     using namespace swp;
-    constexpr int NC = sf::NC, NW = sf::NW;
+    constexpr int NC = M::NC, NW = M::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *st = reinterpret_cast<double *>(smem_raw);
-    double *aux = reinterpret_cast<double *>(smem_raw + OFF_AUX);
+    double *aux = reinterpret_cast<double *>(smem_raw + off_aux<M>());
     const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
     const long long base = (long long)blockIdx.z * g.zoff;
     const int tid = threadIdx.x;
 
     // 1. one thread per staged cell (boundary conditions by index map; halo
-    // rows of a slab): its conserved variables and velocity, and its
-    // auxiliaries J, Z = rho h W^2, p + (E^2 + B^2)/2; an interior cell's
-    // primitives go to the warm-start array of the step's last pass
+    // rows of a slab): the staged planes and auxiliaries of the model; an
+    // interior cell's primitives go to the warm-start array of the step's
+    // last pass
     const bool halo_tile = (g.hlo && j0 < 2) || (g.hhi && j0 + S - 2 > g.ny);
-    for (int e = tid; e < S * S; e += NTHR) {
+    for (int e = tid; e < S * S; e += M::NTHR) {
         const int sy = e / S, sx = e - sy * S;
         const int gi = map_index(i0 + sx - 2, g.nx, g.bcx);
         int hr = 0;
@@ -918,23 +1025,12 @@ __global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, Fl
 #pragma unroll
             for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
         }
-        const int idx = sy * SP + sx;
-#pragma unroll
-        for (int v = 0; v < NST; ++v) st[v * SN + idx] = x[v];
-        const double *q = x, *w = x + NC;
-        double J[3];
-        sf::current(q, w, ph.sigma, J);
-        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
-                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
-        aux[0 * SN + idx] = J[0];
-        aux[1 * SN + idx] = J[1];
-        aux[2 * SN + idx] = J[2];
-        aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
-        aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
+        M::stage(x, ph, st, aux, sy * SP + sx);
         if constexpr (NOUT > 0) {
             const int gix = i0 + sx - 2, gjy = j0 + sy - 2;
             if (a.wcarry && sx >= 2 && sx < T + 2 && sy >= 2 && sy < T + 2 && gix < g.nx && gjy < g.ny) {
                 const long long gc = base + (long long)gjy * g.row + gix;
+                const double *w = x + NC;
 #pragma unroll
                 for (int v = 0; v < NW; ++v) a.wcarry[(long long)v * g.plane + gc] = w[v];
             }
@@ -949,39 +1045,34 @@ __global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, Fl
         constexpr bool PART = decltype(part_c)::value;
         const int gi = i0 + tx, gj = j0 + ty;
         if (gi >= g.nx || gj >= g.ny) return;
-        const long long o = (long long)c * g.plane + base + (long long)gj * g.row + gi;
+        const long long cell = base + (long long)gj * g.row + gi;
+        const long long o = (long long)c * g.plane + cell;
         if constexpr (NOUT == 0) {
             a.lout[o] = L;
         } else {
-            const int own = (ty + 2) * SP + tx + 2;
-            // nonzero source entries (Eq. resistive RMHD): E: -J, psi: varrho - kappa psi, phi: -kappa phi
-            const bool src = (c >= sf::EX && c <= sf::EZ) || c == sf::PSI || c == sf::PHI;
             double sv = 0.0;
-            if (c >= sf::EX && c <= sf::EZ) sv = -aux[(c - sf::EX) * SN + own];
-            else if (c == sf::PSI) sv = fma(-ph.kappa, st[sf::PSI * SN + own], st[sf::RHOE * SN + own]);
-            else if (c == sf::PHI) sv = -ph.kappa * st[sf::PHI * SN + own];
+            const bool has_src = M::source(c, st, aux, a, g, (ty + 2) * SP + tx + 2, cell, ph, sv);
             const double Lv = a.lin ? L + a.lin[o] : L;
             double b = PART ? a.out[0][o] : a.base[0][o];
 #pragma unroll
             for (int k = 0; k < NOUT; ++k) {
                 if (k > 0 && a.base[k] != a.base[k - 1]) b = a.base[k][o];
                 const double v0 = fma(a.cL[k], Lv, b);
-                a.out[k][o] = src ? fma(a.cS[k], sv, v0) : v0;
+                a.out[k][o] = has_src ? fma(a.cS[k], sv, v0) : v0;
             }
         }
     };
     using Full = std::false_type;
     using Part = std::true_type;
     // 2-3. sweeps: thread = (reconstruction, line); a warp is two reconstructions
-    const int r = tid / (T * SEG), seg = (tid / T) % SEG, line = tid % T;
-    const int c0 = seg * (T / SEG);
+    const int r = tid / T, line = tid % T;
     if constexpr (DIRS == 3) {
         const double ix = g.rdx4, iy = g.rdy4;
         // The x part of L of interior cell (tx, ty), component c: in lout (x-y
         // pass of a 3-D grid), folded into the output (one-output passes:
         // out = base + c_L L_x), or in the scratch, plane c of ncell cells.
         auto cell_of = [&](int tx, int ty) { return base + (long long)(j0 + ty) * g.row + i0 + tx; };
-        swp::sweep_line<true>(st, aux, r, line, c0, 0, [&](int c, int tx, int ty, double d) {
+        swp::sweep_line<M, true>(st, aux, ph, r, line, 0, [&](int c, int tx, int ty, double d) {
             if (i0 + tx >= g.nx || j0 + ty >= g.ny) return;
             const long long cx = cell_of(tx, ty);
             if constexpr (NOUT == 0) a.lout[(long long)c * g.plane + cx] = d * ix;
@@ -991,7 +1082,7 @@ __global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, Fl
             } else a.lscr[(long long)c * g.ncell + cx] = d * ix;
         });
         __syncthreads();
-        swp::sweep_line<false>(st, aux, r, line, c0, 1, [&](int c, int tx, int ty, double d) {
+        swp::sweep_line<M, false>(st, aux, ph, r, line, 1, [&](int c, int tx, int ty, double d) {
             if (i0 + tx >= g.nx || j0 + ty >= g.ny) return;
             const long long cx = cell_of(tx, ty);
             if constexpr (NOUT == 0) a.lout[(long long)c * g.plane + cx] += d * iy;
@@ -1000,24 +1091,25 @@ __global__ void __launch_bounds__(swp::NTHR, 3) k_flux_sweep(Grid g, Phys ph, Fl
         });
     } else {
         const double iz = g.rdy4;
-        swp::sweep_line<false>(st, aux, r, line, c0, 2, [&](int c, int tx, int ty, double d) {
+        swp::sweep_line<M, false>(st, aux, ph, r, line, 2, [&](int c, int tx, int ty, double d) {
             emit(c, tx, ty, d * iz, Full{});
         });
     }
 }
 
-template <int NOUT, int DIRS>
+template <class M, int NOUT, int DIRS>
 static cudaError_t launch_sweep_t(const Grid &g, const Phys &ph, const FluxArgs &a, cudaStream_t s, int gz) {
-    static_assert(swp::TOTAL <= 75 * 1024, "three CTAs per SM");
+    constexpr size_t smem = swp::total<M>();
+    static_assert(smem * M::MINB + 1024 * M::MINB <= 228 * 1024, "CTAs per SM");
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux_sweep<NOUT, DIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)swp::TOTAL);
+        cudaError_t e = cudaFuncSetAttribute(k_flux_sweep<M, NOUT, DIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((g.nx + swp::T - 1) / swp::T, (g.ny + swp::T - 1) / swp::T, gz);
-    k_flux_sweep<NOUT, DIRS><<<grid, swp::NTHR, swp::TOTAL, s>>>(g, ph, a);
+    k_flux_sweep<M, NOUT, DIRS><<<grid, M::NTHR, smem, s>>>(g, ph, a);
     return cudaGetLastError();
 }
 
@@ -1036,9 +1128,10 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     axy.lout = lbuf;
     axy.lin = nullptr;
     axy.wcarry = nullptr;
-    // single fluid, FP64: the line-sweep kernel for both passes
-    constexpr bool SWEEP = std::is_same<M, SFModel>::value && std::is_same<FT, double>::value;
-    cudaError_t e = SWEEP ? launch_sweep_t<0, 3>(gxy, ph, axy, s, g.nz)
+    // FP64: the line-sweep kernel for both passes
+    constexpr bool SWEEP = std::is_same<FT, double>::value;
+    using SW = typename std::conditional<std::is_same<M, SFModel>::value, swp::SF, swp::TF>::type;
+    cudaError_t e = SWEEP ? launch_sweep_t<SW, 0, 3>(gxy, ph, axy, s, g.nz)
                           : launch_flux_t<M, 32, 8, G, FT, 0, 3>(gxy, ph, axy, s, g.nz);
     if (e != cudaSuccess) return e;
     Grid gz = g;
@@ -1052,9 +1145,9 @@ static cudaError_t launch_flux_3d_t(int nout, const Grid &g, const Phys &ph, con
     az.lout = nullptr;
     az.lin = lbuf;
     if constexpr (SWEEP) {
-        if (nout == 1) return launch_sweep_t<1, 2>(gz, ph, az, s, g.ny);
-        if (nout == 2) return launch_sweep_t<2, 2>(gz, ph, az, s, g.ny);
-        if (nout == 3) return launch_sweep_t<3, 2>(gz, ph, az, s, g.ny);
+        if (nout == 1) return launch_sweep_t<SW, 1, 2>(gz, ph, az, s, g.ny);
+        if (nout == 2) return launch_sweep_t<SW, 2, 2>(gz, ph, az, s, g.ny);
+        if (nout == 3) return launch_sweep_t<SW, 3, 2>(gz, ph, az, s, g.ny);
         return cudaErrorInvalidValue;
     }
     if (nout == 1) return launch_flux_t<M, 32, 8, G, FT, 1, 2>(gz, ph, az, s, g.ny);

@@ -94,22 +94,23 @@ __global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     restart_done(a.rlist);
 }
 
-// Two fluids: the 7 x 7 Jacobian and its inverse of each thread live in a
+// Two fluids: the 7 x 7 Jacobian of each thread and its LU factors live in a
 // strided slice of shared memory (not in local memory: the pivoted
-// Gauss-Jordan indexes them with run-time rows).
+// factorisation indexes it with run-time rows).
 static constexpr int kStageThreadsTF = 64;
 // 8 blocks per SM (at most 128 registers, a 32-byte spill): 16 warps per SM
 // instead of 8 hide the latency of the 7-unknown solve (measured 18% faster)
 template <bool STATS>
 __global__ void __launch_bounds__(kStageThreadsTF, 8) k_stage_tf(Grid g, Phys ph, StageArgs a, double cpsi) {
     using namespace tf;
-    __shared__ float sJ[49 * kStageThreadsTF], sM[49 * kStageThreadsTF];
-    const Mat Jm{sJ + threadIdx.x, kStageThreadsTF}, Minv{sM + threadIdx.x, kStageThreadsTF};
+    __shared__ float sJ[49 * kStageThreadsTF];
+    const Mat Jm{sJ + threadIdx.x, kStageThreadsTF};
     tf::StageConst k{a.adt, cpsi, a.maxpass > 0 ? a.maxpass : 8, a.hist};
     for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
          cell += (long long)gridDim.x * blockDim.x) {
         const int st =
-            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm, Minv);
+            stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm + cell, k, ph, a.q + cell, a.w + cell, Jm,
+                                      a.src ? a.src + cell : nullptr);
         record(a.status, st, cell);
     }
 }
@@ -187,9 +188,9 @@ __global__ void k_stage_batch_tf(Grid g, Phys ph, StageArgs a, BatchArgs b) {
         pr.sigma = b.sigma[run];
         pr.eta = b.eta[run];
         tf::StageConst k{b.adt[run], b.cpsi[run], a.maxpass > 0 ? a.maxpass : 8, a.hist};
-        float jl[49], ml[49];
+        float jl[49];
         const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, a.wwarm + cell, k, pr, a.q + cell, a.w + cell,
-                                                 tf::Mat{jl, 1}, tf::Mat{ml, 1});
+                                                 tf::Mat{jl, 1});
         record(a.status, st, cell);
     }
 }

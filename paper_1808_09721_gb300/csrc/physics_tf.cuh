@@ -10,8 +10,9 @@
 // tau, Dbar, B have none; psi and phi are linear. The unknowns are scaled
 // (Sbar, taubar divided by mu_ref = max |mu_s|) so that the FP32 Jacobian is
 // balanced. Same precision strategy as the single fluid: FP32 Newton with
-// dual-number Jacobian columns, then FP64 refinement passes with the FP32
-// inverse Jacobian, then consistent FP64 primitives.
+// dual-number Jacobian columns (solved by an in-place LU factorisation), then
+// FP64 refinement passes with the FP32 LU factors, then consistent FP64
+// primitives.
 #pragma once
 #include "device_math.cuh"
 #include "physics_sf.cuh"
@@ -209,7 +210,8 @@ __device__ __forceinline__ void split_x(const Cell<S> &c, const T x[7], T St2[2]
 
 template <class T, class S>
 __device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], const T St2[2][3], const T a[2],
-                                            const T p[2], T G[7], T v[2][3], T Z[2]) {
+                                            const T p[2], T G[7], T v[2][3], T Z[2], T *src = nullptr,
+                                            long long ps = 0) {
     T sq[2], Dsv[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -232,6 +234,14 @@ __device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], cons
         G[4 + i] = (x[4 + i] - c.rx[4 + i]) + c.adt * J[i];
     }
     G[3] = (x[3] - c.rx[3]) - k1 * tb;
+    if (src) {  // the source entries Sbar (3), taubar, E (3) = -J at this point (7 values, ps apart)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            src[i * ps] = Sb[i];
+            src[(4 + i) * ps] = -J[i];
+        }
+        src[3 * ps] = tb;
+    }
 }
 
 // Per-thread N x N scratch matrix: a strided slice of shared memory (element
@@ -242,31 +252,58 @@ struct Mat {
     __device__ __forceinline__ float &operator[](int k) const { return p[k * stride]; }
 };
 
-// In-place inverse of an n x n FP32 matrix (Gauss-Jordan, partial pivoting).
+// In-place LU factorisation with partial pivoting of an N x N FP32 matrix
+// (Doolittle: L unit lower, U upper in the same storage; each pivot row swap
+// is applied to the stored rows and its row index kept in 3 bits of piv; the
+// diagonal holds the reciprocals of U's pivots).
 template <int N>
-__device__ __forceinline__ bool invert(Mat m, Mat inv) {
+__device__ __forceinline__ bool lu_factor(Mat m, unsigned &piv) {
+    static_assert(N <= 8, "3 bits per pivot");
+    piv = 0u;
 #pragma unroll
-    for (int i = 0; i < N * N; ++i) inv[i] = (i % (N + 1) == 0) ? 1.f : 0.f;
     for (int c = 0; c < N; ++c) {
-        int piv = c;
+        int pr = c;
         float best = fabsf(m[c * N + c]);
+#pragma unroll
         for (int r = c + 1; r < N; ++r)
-            if (fabsf(m[r * N + c]) > best) { best = fabsf(m[r * N + c]); piv = r; }
+            if (fabsf(m[r * N + c]) > best) { best = fabsf(m[r * N + c]); pr = r; }
         if (!(best > 0.f) || !isfinite(best)) return false;
-        if (piv != c)
-            for (int k = 0; k < N; ++k) {
-                float t = m[c * N + k]; m[c * N + k] = m[piv * N + k]; m[piv * N + k] = t;
-                t = inv[c * N + k]; inv[c * N + k] = inv[piv * N + k]; inv[piv * N + k] = t;
-            }
-        float id = 1.f / m[c * N + c];
-        for (int k = 0; k < N; ++k) { m[c * N + k] *= id; inv[c * N + k] *= id; }
-        for (int r = 0; r < N; ++r) {
-            if (r == c) continue;
-            float f = m[r * N + c];
-            for (int k = 0; k < N; ++k) { m[r * N + k] -= f * m[c * N + k]; inv[r * N + k] -= f * inv[c * N + k]; }
+        piv |= (unsigned)pr << (3 * c);
+        if (pr != c)
+            for (int k = 0; k < N; ++k) { const float t = m[c * N + k]; m[c * N + k] = m[pr * N + k]; m[pr * N + k] = t; }
+        const float id = 1.f / m[c * N + c];
+        m[c * N + c] = id;
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            const float f = m[r * N + c] * id;
+            m[r * N + c] = f;
+#pragma unroll
+            for (int k = c + 1; k < N; ++k) m[r * N + k] -= f * m[c * N + k];
         }
     }
     return true;
+}
+
+// b <- A^{-1} b from lu_factor's storage.
+template <int N>
+__device__ __forceinline__ void lu_solve(Mat m, unsigned piv, float b[N]) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        const int pr = (piv >> (3 * c)) & 7;
+#pragma unroll
+        for (int r = c + 1; r < N; ++r)
+            if (r == pr) { const float t = b[c]; b[c] = b[r]; b[r] = t; }
+    }
+#pragma unroll
+    for (int i = 1; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) b[i] -= m[i * N + j] * b[j];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) b[i] -= m[i * N + j] * b[j];
+        b[i] *= m[i * N + i];
+    }
 }
 
 // Magnitude of the terms of the stage residual G at (x, v) in FP32: the
@@ -318,13 +355,15 @@ __device__ __forceinline__ void load_cell(Cell<double> &c, const double *rp, lon
 
 // Solve one implicit stage for one cell (two fluids). rp: the cell's explicit
 // part (18 FP64 variables, ps apart); wwarm: its warm-start primitives (10,
-// ps apart). Writes q (18, through qp) and w (10, through wp). Jm and Minv
-// are the caller's 7 x 7 FP32 scratch for the Jacobian and its inverse. The
+// ps apart). Writes q (18, through qp) and w (10, through wp), and, if srcp
+// is not null, the source entries Sbar (3), taubar, E (3) at the result (7,
+// ps apart; Appendix A). Jm is the caller's 7 x 7 FP32 scratch for the
+// Jacobian and its LU factors. The
 // FP64 cell data are built again after the FP32 Newton phase rather than held
 // in registers through it.
 template <int NREF, bool STATS = false>
 __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, const StageConst &k,
-                           const Phys &ph, double *qp, double *wp, Mat Jm, Mat Minv) {
+                           const Phys &ph, double *qp, double *wp, Mat Jm, double *srcp = nullptr) {
     const Split sp(ph.mu_e, ph.mu_p, ph.inv_dmu);
     const double gm1 = ph.gamma - 1.0, gam = ph.gamma;
 
@@ -363,6 +402,7 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
 
     float dpdx[2][7];
     bool have_jac = false;
+    unsigned piv = 0u;
     int nit = 0;
     for (int it = 0; it < 30; ++it) {
         nit = it + 1;
@@ -380,14 +420,13 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
             stage_resid(cf, xd, Std, ad, pd, Gd, vd, Zd);
             for (int i = 0; i < 7; ++i) Jm[i * 7 + kc] = Gd[i].d;
         }
-        if (!invert<7>(Jm, Minv)) return sf::ST_NEWTON;
+        if (!lu_factor<7>(Jm, piv)) return sf::ST_NEWTON;
         have_jac = true;
         float dx[7], dn = 0.f, xn = scale;
+        for (int i = 0; i < 7; ++i) dx[i] = G[i];
+        lu_solve<7>(Jm, piv, dx);
         for (int i = 0; i < 7; ++i) {
-            float s = 0.f;
-            for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * G[j];
-            dx[i] = s;
-            dn = fmaxf(dn, fabsf(s));
+            dn = fmaxf(dn, fabsf(dx[i]));
             xn = fmaxf(xn, fabsf(x[i]));
         }
         if (dn <= 2e-7f * xn) break;
@@ -436,18 +475,15 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
     for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
         split_x(c, xd, St64, a64, S264);
         for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
-        stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64);
+        // every pass writes the sources at its point: the last pass's stay
+        stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64, srcp, ps);
         gres = 0.0;
         for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
         if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
         if (pass == 7 || pass == k.maxpass - 1) break;
-        float Gf[7], dx[7];
-        for (int i = 0; i < 7; ++i) Gf[i] = f32_of(G64[i]);
-        for (int i = 0; i < 7; ++i) {
-            float s = 0.f;
-            for (int j = 0; j < 7; ++j) s += Minv[i * 7 + j] * Gf[j];
-            dx[i] = s;
-        }
+        float dx[7];
+        for (int i = 0; i < 7; ++i) dx[i] = f32_of(G64[i]);
+        lu_solve<7>(Jm, piv, dx);
         for (int s = 0; s < 2; ++s) {
             float dp = 0.f;
             for (int i = 0; i < 7; ++i) dp += dpdx[s][i] * dx[i];
