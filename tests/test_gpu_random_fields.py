@@ -50,6 +50,9 @@ CASES = [
     ("3d_outflow", (9, 10, 35), 0, WL.OUTFLOW),
     ("tf_2d_periodic", (24, 40), 1, WL.PERIODIC),
     ("tf_3d_periodic", (6, 10, 12), 1, WL.PERIODIC),
+    # ragged 16 x 16 tiles of the line-sweep kernel in both directions, outflow
+    ("tf_2d_outflow", (27, 35), 1, WL.OUTFLOW),
+    ("tf_3d_outflow", (7, 19, 17), 1, WL.OUTFLOW),
 ]
 
 
