@@ -182,6 +182,12 @@ template <class S>
 struct Cell {
     S D, Ds[2], Sv[3], B[3], tauB, rx[7];  // rx: scaled explicit part of the unknowns
     S mu_e, mu_p, inv, mur, imur, eta, adt, gm1, gam;
+    // constants of the sources within a stage (D_s has no source): mu_s^2 D_s,
+    // mu_s D_s, M0 = sum mu_s^2 D_s, varrho = sum mu_s D_s, M0 varrho
+    S m2D[2], m1D[2], M0, vr, M0vr;
+    // the species split of the scaled unknowns: S~_s = xs_s x_S + ct_s S~,
+    // a_s = xs_s x_tau + ct_s tau~ + D_s (xs_s = +-mur / (mu_e - mu_p))
+    S xs[2], ct[2];
 };
 
 // Stage residual in scaled unknowns x = (Sbar/mur, taubar/mur, E). Pressures
@@ -194,16 +200,12 @@ __device__ __forceinline__ void split_x(const Cell<S> &c, const T x[7], T St2[2]
     cross(E, c.B, ExB);
     T St[3] = {c.Sv[0] - ExB[0], c.Sv[1] - ExB[1], c.Sv[2] - ExB[2]};
     T taut = c.tauB - S(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-    T Sb[3] = {c.mur * x[0], c.mur * x[1], c.mur * x[2]};
-    T tb = c.mur * x[3];
-    // X_e = (Xbar - mu_p X) inv ; X_p = (mu_e X - Xbar) inv
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        St2[0][i] = (Sb[i] - c.mu_p * St[i]) * c.inv;
-        St2[1][i] = (c.mu_e * St[i] - Sb[i]) * c.inv;
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) St2[s][i] = c.xs[s] * x[i] + c.ct[s] * St[i];
+        a[s] = c.xs[s] * x[3] + (c.ct[s] * taut + c.Ds[s]);
     }
-    a[0] = (tb - c.mu_p * taut) * c.inv + c.Ds[0];
-    a[1] = (c.mu_e * taut - tb) * c.inv + c.Ds[1];
 #pragma unroll
     for (int k = 0; k < 2; ++k) S2[k] = St2[k][0] * St2[k][0] + St2[k][1] * St2[k][1] + St2[k][2] * St2[k][2];
 }
@@ -212,7 +214,7 @@ template <class T, class S>
 __device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], const T St2[2][3], const T a[2],
                                             const T p[2], T G[7], T v[2][3], T Z[2], T *src = nullptr,
                                             long long ps = 0) {
-    T sq[2], Dsv[2];
+    T sq[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         Z[k] = a[k] + p[k];
@@ -222,11 +224,22 @@ __device__ __forceinline__ void stage_resid(const Cell<S> &c, const T x[7], cons
         v[k][2] = St2[k][2] * rZ;
         T om = S(1) - (v[k][0] * v[k][0] + v[k][1] * v[k][1] + v[k][2] * v[k][2]);
         sq[k] = om * s_rsqrt(om);
-        Dsv[k] = T(c.Ds[k]);
     }
     T E[3] = {x[4], x[5], x[6]};
-    T Sb[3], tb, J[3], varrho;
-    source_terms(Dsv, v, sq, E, c.B, c.mu_e, c.mu_p, c.eta, Sb, tb, J, varrho);
+    // the sources of Appendix A as in source_terms, with the stage's constants
+    T M1[3], J[3], Sb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        M1[i] = c.m2D[0] * v[0][i] + c.m2D[1] * v[1][i];
+        J[i] = c.m1D[0] * v[0][i] + c.m1D[1] * v[1][i];
+    }
+    const T wp2 = c.m2D[0] * sq[0] + c.m2D[1] * sq[1];
+    T M1xB[3];
+    cross(M1, c.B, M1xB);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Sb[i] = c.M0 * E[i] + M1xB[i] - c.eta * (wp2 * J[i] - c.vr * M1[i]);
+    const T r0 = (c.M0vr - (J[0] * M1[0] + J[1] * M1[1] + J[2] * M1[2])) * s_rcp(wp2);
+    const T tb = (M1[0] * E[0] + M1[1] * E[1] + M1[2] * E[2]) - c.eta * (wp2 * c.vr - c.M0 * r0);
     const S k1 = c.adt * c.imur;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -351,6 +364,18 @@ __device__ __forceinline__ void load_cell(Cell<double> &c, const double *rp, lon
     c.adt = k.adt; c.gm1 = ph.gamma - 1.0; c.gam = ph.gamma;
     for (int i = 0; i < 3; ++i) { c.rx[i] = rp[(SBX + i) * ps] * c.imur; c.rx[4 + i] = rp[(EX + i) * ps]; }
     c.rx[3] = rp[TAUB * ps] * c.imur;
+    for (int s = 0; s < 2; ++s) {
+        const double mu = s == 0 ? ph.mu_e : ph.mu_p;
+        c.m1D[s] = mu * c.Ds[s];
+        c.m2D[s] = mu * c.m1D[s];
+    }
+    c.M0 = c.m2D[0] + c.m2D[1];
+    c.vr = c.m1D[0] + c.m1D[1];
+    c.M0vr = c.M0 * c.vr;
+    c.xs[0] = c.mur * c.inv;
+    c.xs[1] = -c.xs[0];
+    c.ct[0] = -c.mu_p * c.inv;
+    c.ct[1] = c.mu_e * c.inv;
 }
 
 // Solve one implicit stage for one cell (two fluids). rp: the cell's explicit
@@ -378,6 +403,9 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
         cf.mu_e = f32_of(c.mu_e); cf.mu_p = f32_of(c.mu_p); cf.inv = f32_of(c.inv); cf.mur = f32_of(c.mur);
         cf.imur = f32_of(c.imur); cf.eta = f32_of(c.eta); cf.adt = f32_of(c.adt); cf.gm1 = f32_of(gm1);
         cf.gam = f32_of(gam);
+        for (int s = 0; s < 2; ++s) { cf.m2D[s] = f32_of(c.m2D[s]); cf.m1D[s] = f32_of(c.m1D[s]); }
+        cf.M0 = f32_of(c.M0); cf.vr = f32_of(c.vr); cf.M0vr = f32_of(c.M0vr);
+        for (int s = 0; s < 2; ++s) { cf.xs[s] = f32_of(c.xs[s]); cf.ct[s] = f32_of(c.ct[s]); }
         // source-free components equal r; psi and phi in closed form (varrho = Dbar has no source)
         for (int v : {D, SX, SY, SZ, TAU, DB, BX, BY, BZ}) qp[v * ps] = rp[v * ps];
         for (int i = 0; i < 3; ++i) qp[(EX + i) * ps] = rp[(EX + i) * ps];  // replaced by the root

@@ -65,7 +65,20 @@ def test_adjoint_matches_autodiff_oracle(env, name, make, nsteps, ckpt, scheme):
     assert abs(gs - gso) <= 1e-9 * abs(gso) + 1e-12 * np.abs(go).max(), (name, gs, gso)
 
 
-@pytest.mark.parametrize("name,make,nsteps,ckpt,scheme", TINY, ids=IDS)
+# The dot-product identity compares the GPU's linearisation at its forward
+# run with the oracle's at its own; their roots agree to round-off times the
+# conditioning of the stage solves. For the stiff, under-resolved sheet above
+# (mu = -+1e3, sigma = 1e4, a tanh sheet of width 0.05 on 8 cells) the two
+# gradients agree entry by entry to ~1e-10 of max |g|, so a contraction with
+# random vectors differs by ~1e-12 whatever the adjoint does (measured 4.5e-13
+# to 9e-12 as the forward's rounding changes). The identity is checked at
+# 1e-12 on a conditioned sheet (width 0.25, mu = -+1e2; the stiff one stays
+# in the entrywise test).
+DOT = [c if c[0] != "tf_sheet_8x8" else
+       ("tf_sheet_8x8_resolved", lambda: WL.tf_sheet(n=8, seed=1, mu=1e2, width=0.25), 3, 2, 0) for c in TINY]
+
+
+@pytest.mark.parametrize("name,make,nsteps,ckpt,scheme", DOT, ids=[c[0] for c in DOT])
 def test_adjoint_dot_product(env, name, make, nsteps, ckpt, scheme):
     """<J v, w> = <v, J^T w>: GPU reverse mode against the oracle's forward-mode
     derivative along a random direction of the primitives and sigma."""
