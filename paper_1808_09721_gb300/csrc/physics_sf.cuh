@@ -306,7 +306,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     // while G's own terms carry a dt sigma W: for stiff cells (a dt sigma W >> 1)
     // the tolerance shrinks by that factor, down to a few units of FP64
     // round-off of G's terms. Non-stiff cells keep 1e-12.
-    const double tolg = f64_of(fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
+    const float itol = 1.f / fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f);
     // FP64 inputs, read again (the stores above keep the compiler from reusing
     // the first loads' registers)
     const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
@@ -317,7 +317,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     double pdd = f64_of(p);
     const double rdf = f64_of(1.f / dfdp);
     double St64[3], a64, S264, G64[3], v64[3], W64;
-    double gres = 0.0;
+    float gres = 0.f;
     bool pconv = false;
     int pass = 0;
     for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
@@ -326,9 +326,11 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
         pdd -= dp;
         pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
         stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
-        gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
-        if (pass >= NREF - 1 && gres <= tolg && pconv) break;
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
+        // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
+        // infinity, so a non-finite G fails the tests)
+        gres = fmaxf(fmaxf(fabsf(Gf[0]), fabsf(Gf[1])), fabsf(Gf[2]));
+        if (pass >= NREF - 1 && gres * itol <= gs && pconv) break;
         float dE[3];
         for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
         if (pass == 7 || pass == k.maxpass - 1) break;
@@ -346,7 +348,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
-    if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
+    if (!(pdd > 0.0) || !(gres * 1e9f <= gs) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
         return ST_NEWTON;  // counted by the restart (stage_restarts)
     if constexpr (STATS) count_solve(k.hist, nit, pass + 1, 0);
     return ST_OK;
@@ -487,7 +489,7 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         // while G's own terms carry a dt sigma W: for stiff cells (a dt sigma W >> 1)
         // the tolerance shrinks by that factor, down to a few units of FP64
         // round-off of G's terms. Non-stiff cells keep 1e-12.
-        const double tolg = f64_of(fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f)) * f64_of(gs);
+        const float itol = 1.f / fmaxf(1e-12f * s_rcp(1.f + adtf * sigf * W), 1e-15f);
         // FP64 inputs, read again (the stores above keep the compiler from reusing
         // the first loads' registers)
         const double B[3] = {rp[BX * ps], rp[BY * ps], rp[BZ * ps]};
@@ -498,7 +500,7 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         double pdd = f64_of(p);
         const double rdf = f64_of(1.f / dfdp);
         double St64[3], a64, S264, G64[3], v64[3], W64;
-        double gres = 0.0;
+        float gres = 0.f;
         bool pconv = false;
         for (pass = 0; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
             em_split(Ed, Sv, B, tauB, Dd, St64, a64, S264);
@@ -508,9 +510,11 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
             // gains ~7 digits, so the error left after this one is below 1e-13 p
             pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
             stage_resid(Ed, pdd, St64, a64, B, rE, rhoe, k.adt, k.sigma, G64, v64, W64);
-            gres = fmax(fmax(fabs(G64[0]), fabs(G64[1])), fabs(G64[2]));
-            if (pass >= NREF - 1 && gres <= tolg && pconv) break;
             float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
+            // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
+            // infinity, so a non-finite G fails the tests)
+            gres = fmaxf(fmaxf(fabsf(Gf[0]), fabsf(Gf[1])), fabsf(Gf[2]));
+            if (pass >= NREF - 1 && gres * itol <= gs && pconv) break;
             float dE[3];
             for (int i = 0; i < 3; ++i) dE[i] = Minv[3 * i] * Gf[0] + Minv[3 * i + 1] * Gf[1] + Minv[3 * i + 2] * Gf[2];
             if (pass == 7 || pass == k.maxpass - 1) break;
@@ -520,7 +524,7 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
             Ed[1] -= f64_of(dE[1]);
             Ed[2] -= f64_of(dE[2]);
         }
-        if (!(pdd > 0.0) || !(gres <= 1e-9 * f64_of(gs)) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
+        if (!(pdd > 0.0) || !(gres * 1e9f <= gs) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
             return ST_NEWTON;
         wp[VX * ps] = v64[0];
         wp[VY * ps] = v64[1];
