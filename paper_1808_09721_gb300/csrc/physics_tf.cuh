@@ -498,19 +498,22 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
     const double rdf[2] = {f64_of(1.f / dfdp[0]), f64_of(1.f / dfdp[1])};
     for (int i = 0; i < 7; ++i) xd[i] = f64_of(x[i]);
     double St64[2][3], a64[2], S264[2], G64[7], v64[2][3], Z64[2];
-    double gres = 0.0;
+    float gres = 0.f;  // |G| in FP32 (f32_of maps a NaN to an infinity)
     int pass = 0;
+#pragma unroll 1
     for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
         split_x(c, xd, St64, a64, S264);
         for (int s = 0; s < 2; ++s) pdd[s] -= sf::pres_resid(pdd[s], a64[s], S264[s], c.Ds[s], gm1, gam) * rdf[s];
         // every pass writes the sources at its point: the last pass's stay
         stage_resid(c, xd, St64, a64, pdd, G64, v64, Z64, srcp, ps);
-        gres = 0.0;
-        for (int i = 0; i < 7; ++i) gres = fmax(gres, fabs(G64[i]));
-        if (pass >= NREF - 1 && gres <= 1e-12 * f64_of(gs)) break;
-        if (pass == 7 || pass == k.maxpass - 1) break;
         float dx[7];
-        for (int i = 0; i < 7; ++i) dx[i] = f32_of(G64[i]);
+        gres = 0.f;
+        for (int i = 0; i < 7; ++i) {
+            dx[i] = f32_of(G64[i]);
+            gres = fmaxf(gres, fabsf(dx[i]));
+        }
+        if (pass >= NREF - 1 && gres * 1e12f <= gs) break;
+        if (pass == 7 || pass == k.maxpass - 1) break;
         lu_solve<7>(Jm, piv, dx);
         for (int s = 0; s < 2; ++s) {
             float dp = 0.f;
@@ -533,7 +536,7 @@ __device__ int stage_solve(const double *rp, long long ps, const double *wwarm, 
         qp[(EX + i) * ps] = xd[4 + i];
     }
     qp[TAUB * ps] = xd[3] * c.mur;
-    ok = ok && gres <= 1e-9 * f64_of(gs);
+    ok = ok && gres * 1e9f <= gs;
     if constexpr (STATS) sf::count_solve(k.hist, nit, pass + 1, ok ? 0 : 3);
     if (!ok) return sf::ST_NEWTON;
     return sf::ST_OK;
