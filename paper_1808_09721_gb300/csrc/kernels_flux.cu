@@ -788,13 +788,22 @@ struct SF {
         if (i == pdir) f += aux[4 * SN + idx];
         return f;
     }
-    // staged cell idx from its conserved variables and primitives x
-    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx) {
+    // staged cell idx from its conserved variables and primitives x; js: the
+    // cell's current as the stage kernel wrote it (3 values, ps apart), or
+    // null (halo rows of a slab), then it is formed here
+    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx,
+                                                 const double *js, long long ps) {
 #pragma unroll
         for (int v = 0; v < NST; ++v) st[v * SN + idx] = x[v];
         const double *q = x, *w = x + NC;
         double J[3];
-        sf::current(q, w, ph.sigma, J);
+        if (js) {
+            J[0] = js[0];
+            J[1] = js[ps];
+            J[2] = js[2 * ps];
+        } else {
+            sf::current(q, w, ph.sigma, J);
+        }
         const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
                             q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
         aux[0 * SN + idx] = J[0];
@@ -861,7 +870,8 @@ struct TF {
         return f;
     }
     // staged cell idx from its conserved variables and primitives x
-    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx) {
+    static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx,
+                                                 const double *, long long) {
         using namespace tf;
         const double *q = x, *w = x + NC;
 #pragma unroll
@@ -1014,6 +1024,7 @@ __global__ void __launch_bounds__(M::NTHR, M::MINB) k_flux_sweep(Grid g, Phys ph
         int hr = 0;
         const double *hb = halo_tile ? halo_of(g, j0 + sy - 2, &hr) : nullptr;
         double x[NC + NW];
+        const double *js = nullptr;
         if (hb) {
 #pragma unroll
             for (int v = 0; v < NC + NW; ++v) x[v] = hb[((long long)v * 2 + hr) * g.nx + gi];
@@ -1024,8 +1035,9 @@ __global__ void __launch_bounds__(M::NTHR, M::MINB) k_flux_sweep(Grid g, Phys ph
             for (int v = 0; v < NC; ++v) x[v] = a.q[(long long)v * g.plane + gc];
 #pragma unroll
             for (int v = 0; v < NW; ++v) x[NC + v] = a.w[(long long)v * g.plane + gc];
+            if (a.srcg) js = a.srcg + gc;
         }
-        M::stage(x, ph, st, aux, sy * SP + sx);
+        M::stage(x, ph, st, aux, sy * SP + sx, js, g.plane);
         if constexpr (NOUT > 0) {
             const int gix = i0 + sx - 2, gjy = j0 + sy - 2;
             if (a.wcarry && sx >= 2 && sx < T + 2 && sy >= 2 && sy < T + 2 && gix < g.nx && gjy < g.ny) {

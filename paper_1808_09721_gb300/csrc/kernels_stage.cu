@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kStageThreads, 5) k_stage_sf(Grid g, Phys ph, 
     }
     for (long long cell = c0; cell < g.ncell; cell += cs) {
         const double pw = a.wwarm[P * g.plane + cell];
-        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell);
+        const int st = stage_solve<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell,
+                                                 a.src ? a.src + cell : nullptr);
         defer_or_record(a, st, cell);
     }
 }
@@ -88,7 +89,9 @@ __global__ void k_restart_sf(Grid g, Phys ph, StageArgs a, double cpsi) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const long long cell = a.rlist[2 + e];
         const double pw = a.wwarm[P * g.plane + cell];
-        record(a.status, stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start),
+        record(a.status,
+               stage_restarts<kNRef, STATS>(a.r + cell, g.plane, pw, k, a.q + cell, a.w + cell, a.first_start,
+                                            a.src ? a.src + cell : nullptr),
                cell);
     }
     restart_done(a.rlist);

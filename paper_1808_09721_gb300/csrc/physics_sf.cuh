@@ -130,7 +130,7 @@ __device__ __forceinline__ void em_split_k(const double E[3], const double Sv[3]
 }
 __device__ __forceinline__ void stage_resid_k(const double E[3], double p, const double St[3], double a,
                                               const double B[3], const double rE[3], double arho, double asig,
-                                              double G[3], double v[3], double &W) {
+                                              double G[3], double v[3], double &W, double u[3]) {
     const double rZ = s_rcp(a + p);
     v[0] = St[0] * rZ;
     v[1] = St[1] * rZ;
@@ -142,8 +142,8 @@ __device__ __forceinline__ void stage_resid_k(const double E[3], double p, const
     const double vE = v[0] * E[0] + v[1] * E[1] + v[2] * E[2];
     const double aW = asig * W;
     for (int i = 0; i < 3; ++i) {
-        const double u = E[i] + vxB[i] - vE * v[i];
-        G[i] = fma(aW, u, fma(arho, v[i], E[i] - rE[i]));
+        u[i] = E[i] + vxB[i] - vE * v[i];
+        G[i] = fma(aW, u[i], fma(arho, v[i], E[i] - rE[i]));
     }
 }
 
@@ -228,7 +228,7 @@ __device__ __forceinline__ void count_solve(unsigned long long *hist, int nit, i
 // which keeps the register allocation of the common path unchanged.
 template <int NREF, bool STATS = false>
 __device__ __forceinline__ int stage_solve(const double *rp, long long ps, double p_warm, const StageConst &k,
-                                           double *qp, double *wp) {
+                                           double *qp, double *wp, double *jp = nullptr) {
     const double gm1 = k.gamma - 1.0, gam = k.gamma;
     double tauB;
     float Bf[3], Sf[3], rEf[3], tauBf, Df, rhoef;
@@ -349,7 +349,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     double Ed[3] = {f64_of(E[0]), f64_of(E[1]), f64_of(E[2])};
     double pdd = f64_of(p);
     const double rdf = f64_of(1.f / dfdp);
-    double St64[3], a64, S264, G64[3], v64[3], W64;
+    double St64[3], a64, S264, G64[3], v64[3], W64, u64[3];
     float gres = 0.f;
     bool pconv = false;
     int pass = 0;
@@ -358,7 +358,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
         const double dp = pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         pdd -= dp;
         pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
-        stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64);
+        stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
         // infinity, so a non-finite G fails the tests)
@@ -381,6 +381,10 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
+    if (jp) {  // Ohm's-law current at the result (as current() forms it), for the flux pass
+        const double Ws = W64 * k.sigma;
+        for (int i = 0; i < 3; ++i) jp[i * ps] = rhoe * v64[i] + Ws * u64[i];
+    }
     if (!(pdd > 0.0) || !(gres * 1e9f <= gs) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
         return ST_NEWTON;  // counted by the restart (stage_restarts)
     if constexpr (STATS) count_solve(k.hist, nit, pass + 1, 0);
@@ -392,7 +396,7 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
 // in a dt (START = 2). Used only after start 0 failed.
 template <int NREF, bool STATS, int START>
 __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, double p_warm, const StageConst &k,
-                                             double *qp, double *wp) {
+                                             double *qp, double *wp, double *jp = nullptr) {
     constexpr int start = START;
     const double gm1 = k.gamma - 1.0, gam = k.gamma;
     double tauB;
@@ -533,7 +537,7 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         double Ed[3] = {f64_of(E[0]), f64_of(E[1]), f64_of(E[2])};
         double pdd = f64_of(p);
         const double rdf = f64_of(1.f / dfdp);
-        double St64[3], a64, S264, G64[3], v64[3], W64;
+        double St64[3], a64, S264, G64[3], v64[3], W64, u64[3];
         float gres = 0.f;
         bool pconv = false;
         for (pass = 0; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
@@ -543,7 +547,7 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
             // the pressure step is at round-off: with the FP32 slope each step
             // gains ~7 digits, so the error left after this one is below 1e-13 p
             pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
-            stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64);
+            stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
             float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
             // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
             // infinity, so a non-finite G fails the tests)
@@ -568,6 +572,10 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         qp[EX * ps] = Ed[0];
         qp[EY * ps] = Ed[1];
         qp[EZ * ps] = Ed[2];
+        if (jp) {
+            const double Ws = W64 * k.sigma;
+            for (int i = 0; i < 3; ++i) jp[i * ps] = rhoe * v64[i] + Ws * u64[i];
+        }
         if constexpr (STATS) count_solve(k.hist, nit, pass + 1, start);
         return ST_OK;
     }
@@ -577,9 +585,9 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
 // counted as start 3.
 template <int NREF, bool STATS>
 __device__ int stage_restarts(const double *rp, long long ps, double p_warm, const StageConst &k, double *qp,
-                              double *wp, int first = 1) {
-    if (first <= 1 && stage_attempt<NREF, STATS, 1>(rp, ps, p_warm, k, qp, wp) == ST_OK) return ST_OK;
-    if (stage_attempt<NREF, STATS, 2>(rp, ps, p_warm, k, qp, wp) == ST_OK) return ST_OK;
+                              double *wp, int first = 1, double *jp = nullptr) {
+    if (first <= 1 && stage_attempt<NREF, STATS, 1>(rp, ps, p_warm, k, qp, wp, jp) == ST_OK) return ST_OK;
+    if (stage_attempt<NREF, STATS, 2>(rp, ps, p_warm, k, qp, wp, jp) == ST_OK) return ST_OK;
     if constexpr (STATS) count_solve(k.hist, 24, 8, 3);
     return ST_NEWTON;
 }

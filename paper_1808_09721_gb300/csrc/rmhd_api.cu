@@ -40,7 +40,7 @@ struct rmhd_ctx {
     double *Q, *W, *Q1, *W1, *R, *ACC, *stage_buf, *scratch, *diag;
     double *R3;    // SSP3(332): q^n + dt/4 L1 + (1/2 - gamma) dt Psi1 (null for SSP2)
     double *LBUF;  // 3-D grids: L_x + L_y of the current flux pass (null otherwise)
-    double *SRCG;  // two fluids: source planes handed from the FP64 stage kernel to the flux pass (null otherwise)
+    double *SRCG;  // planes handed from the FP64 stage kernel to the line-sweep flux pass (null in batches)
     int *status;       // device [2]
     unsigned long long *hist;  // device [44]: solver statistics (FP32 iterations, FP64 passes, starts)
     int *rlist;                // device [2 + rcap]: cells whose first stage-solve start failed
@@ -217,8 +217,10 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     if (cfg->scheme == RMHD_SSP3) { L.R3 = o; o += align256(nc * pl); }
     L.LBUF = 0;
     if (cfg->nz > 1) { L.LBUF = o; o += align256(nc * pl); }
-    L.SRCG = 0;  // two fluids: source planes of the stage state (7 used by the FP64 line-sweep pass)
-    if (cfg->model == RMHD_TWO_FLUID && nruns == 0) { L.SRCG = o; o += align256(9 * pl); }
+    // planes the FP64 line-sweep pass takes from the stage kernel: one fluid J
+    // (3), two fluids the source entries (7 used)
+    L.SRCG = 0;
+    if (nruns == 0) { L.SRCG = o; o += align256((cfg->model == RMHD_TWO_FLUID ? 9 : 3) * pl); }
     L.ACC = o; o += align256(nc * pl);
     L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));
@@ -741,9 +743,9 @@ static int toc(rmhd_ctx *c) {
 // Stage-solve arguments with the context's statistics and refinement settings.
 static StageArgs stage_args(const rmhd_ctx *c, const double *r, const double *wwarm, double *q, double *w,
                             double adt) {
-    // two fluids, FP64, 2-D and 3-D grids: the stage kernel hands the stage
-    // state's sources to the line-sweep flux pass
-    const bool tf_src = c->cfg.model == RMHD_TWO_FLUID && c->cfg.precision == RMHD_FP64 && c->g.ny > 1;
+    // FP64, 2-D and 3-D grids: the stage kernel hands the stage state's current
+    // (one fluid) or sources (two fluids) to the line-sweep flux pass
+    const bool tf_src = c->cfg.precision == RMHD_FP64 && c->g.ny > 1;
     StageArgs a{r, wwarm, q, w, c->status, adt, c->stats_on ? c->hist : nullptr, c->maxpass,
                 c->cfg.model == RMHD_RESISTIVE ? c->rlist : nullptr, c->rcap, c->first_start,
                 tf_src ? c->SRCG : nullptr};

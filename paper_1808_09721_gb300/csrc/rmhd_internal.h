@@ -53,8 +53,8 @@ struct FluxArgs {
     double *wcarry;         // if not null: the stage primitives are copied here (next warm start)
     double *lout;           // nout = 0 (x-y pass of a 3-D grid): L_x + L_y is written here, nothing else
     const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
-    double *srcg;           // two fluids, FP64, 2-D tiles: the stage state's source entries Sbar (3),
-                            // taubar, E (3), written by the stage kernel (7 planes)
+    double *srcg;           // FP64 line-sweep passes: planes written by the stage kernel at the stage
+                            // state: one fluid J (3), two fluids Sbar (3), taubar, E (3)
     double *lscr;           // single fluid, FP64, 2-D: the x part of L between the x and y sweeps
                             // (NC planes of ncell cells)
 };
@@ -76,8 +76,9 @@ struct StageArgs {
     int *rlist;
     int rcap;
     int first_start;  // tests of the restart path: 1 or 2 skips the earlier starts (0: all starts)
-    // two fluids: if not null, the source entries Sbar (3), taubar, E (3) of
-    // the stage state (7 planes), read by the FP64 line-sweep flux pass
+    // if not null, what the FP64 line-sweep flux pass takes from the stage
+    // solve: one fluid, the current J of the stage state (3 planes); two
+    // fluids, its source entries Sbar (3), taubar, E (3) (7 planes)
     double *src;
 };
 
