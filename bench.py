@@ -56,14 +56,16 @@ ALG_FP64_FLOPS_PER_CELL = {"flux1": 1918, "flux2": 1880, "tf_flux1": 2556, "tf_f
 # FP64 arithmetic instructions the kernels themselves issue (dadd, dmul, dfma;
 # one each) per interior cell on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
-FP64_INST_PER_CELL = {"stage": 177.0, "flux1": 718.5, "flux2": 704.5}
+FP64_INST_PER_CELL = {"stage": 180.0, "flux1": 684.1, "flux2": 670.1}
 # DRAM bytes (read + write) per cell and launch of the same kernels, from an
 # ncu capture of the 512x512 KHI step (dram__bytes_read.sum + write.sum): the
 # reads scale with the cells; at that size part of the writes is still in L2
 # when a kernel ends, so the full-size writes are somewhat higher.
-DRAM_BYTES_PER_CELL = {"stage": 121.5, "flux1": 431.5, "flux2": 315.9}
-# Algorithmic HBM bytes per cell for each kernel (read once + written once).
-BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5), "flux1": 8 * (19 + 14 + 28), "flux2": 8 * (19 + 14 + 19)}
+DRAM_BYTES_PER_CELL = {"stage": 123.9, "flux1": 466.4, "flux2": 344.0}
+# Algorithmic HBM bytes per cell for each kernel (read once + written once; the
+# stage also writes the current J of its result, which the flux passes read).
+BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5 + 3), "flux1": 8 * (19 + 3 + 14 + 28),
+                  "flux2": 8 * (19 + 3 + 14 + 19)}
 
 
 def _peaks():
