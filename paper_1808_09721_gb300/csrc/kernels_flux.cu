@@ -789,28 +789,29 @@ struct SF {
         return f;
     }
     // staged cell idx from its conserved variables and primitives x; js: the
-    // cell's current as the stage kernel wrote it (3 values, ps apart), or
-    // null (halo rows of a slab), then it is formed here
+    // cell's auxiliaries as the stage kernel wrote them at its result (J, Z,
+    // p + (E^2 + B^2)/2; 5 values, ps apart), or null (halo rows of a slab),
+    // then they are formed here
     static __device__ __forceinline__ void stage(const double *x, const Phys &ph, double *st, double *aux, int idx,
                                                  const double *js, long long ps) {
 #pragma unroll
         for (int v = 0; v < NST; ++v) st[v * SN + idx] = x[v];
         const double *q = x, *w = x + NC;
-        double J[3];
         if (js) {
-            J[0] = js[0];
-            J[1] = js[ps];
-            J[2] = js[2 * ps];
-        } else {
+#pragma unroll
+            for (int k = 0; k < NAUX; ++k) aux[k * SN + idx] = js[k * ps];
+        } else {  // the stage kernel's expressions, so that slab halo rows match bit for bit
+            double J[3];
             sf::current(q, w, ph.sigma, J);
+            const double tauB = q[sf::TAU] - 0.5 * (q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ]);
+            const double tD = tauB + q[sf::D];
+            const double a = tD - 0.5 * (q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ]);
+            aux[0 * SN + idx] = J[0];
+            aux[1 * SN + idx] = J[1];
+            aux[2 * SN + idx] = J[2];
+            aux[3 * SN + idx] = a + w[sf::P];                            // Z = tau~ + D + p
+            aux[4 * SN + idx] = w[sf::P] + ((q[sf::TAU] + q[sf::D]) - a);  // p + (E^2 + B^2)/2
         }
-        const double E2B2 = q[sf::EX] * q[sf::EX] + q[sf::EY] * q[sf::EY] + q[sf::EZ] * q[sf::EZ] +
-                            q[sf::BX] * q[sf::BX] + q[sf::BY] * q[sf::BY] + q[sf::BZ] * q[sf::BZ];
-        aux[0 * SN + idx] = J[0];
-        aux[1 * SN + idx] = J[1];
-        aux[2 * SN + idx] = J[2];
-        aux[3 * SN + idx] = fma(-0.5, E2B2, q[sf::TAU]) + q[sf::D] + w[sf::P];
-        aux[4 * SN + idx] = fma(0.5, E2B2, w[sf::P]);
     }
     // nonzero source entries: E: -J, psi: varrho - kappa psi, phi: -kappa phi
     static __device__ __forceinline__ bool source(int c, const double *st, const double *aux, const FluxArgs &,

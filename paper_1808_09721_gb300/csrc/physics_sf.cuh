@@ -381,9 +381,11 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     qp[EX * ps] = Ed[0];
     qp[EY * ps] = Ed[1];
     qp[EZ * ps] = Ed[2];
-    if (jp) {  // Ohm's-law current at the result (as current() forms it), for the flux pass
+    if (jp) {  // for the flux pass: Ohm's-law current (as current() forms it), Z, p + (E^2 + B^2)/2
         const double Ws = W64 * k.sigma;
         for (int i = 0; i < 3; ++i) jp[i * ps] = rhoe * v64[i] + Ws * u64[i];
+        jp[3 * ps] = a64 + pdd;                             // Z = tau~ + D + p
+        jp[4 * ps] = pdd + ((rp[TAU * ps] + Dd) - a64);     // (E^2 + B^2)/2 = tau + D - a
     }
     if (!(pdd > 0.0) || !(gres * 1e9f <= gs) || !pconv || !isfinite(Ed[0] + Ed[1] + Ed[2] + W64))
         return ST_NEWTON;  // counted by the restart (stage_restarts)
@@ -575,6 +577,8 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         if (jp) {
             const double Ws = W64 * k.sigma;
             for (int i = 0; i < 3; ++i) jp[i * ps] = rhoe * v64[i] + Ws * u64[i];
+            jp[3 * ps] = a64 + pdd;
+            jp[4 * ps] = pdd + ((rp[TAU * ps] + Dd) - a64);
         }
         if constexpr (STATS) count_solve(k.hist, nit, pass + 1, start);
         return ST_OK;

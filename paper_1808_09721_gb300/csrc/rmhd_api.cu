@@ -218,9 +218,9 @@ static Layout layout_g(const rmhd_config *cfg, const Grid &g, int nruns, long lo
     L.LBUF = 0;
     if (cfg->nz > 1) { L.LBUF = o; o += align256(nc * pl); }
     // planes the FP64 line-sweep pass takes from the stage kernel: one fluid J
-    // (3), two fluids the source entries (7 used)
+    // (3), Z and p + (E^2 + B^2)/2; two fluids the source entries (7 used)
     L.SRCG = 0;
-    if (nruns == 0) { L.SRCG = o; o += align256((cfg->model == RMHD_TWO_FLUID ? 9 : 3) * pl); }
+    if (nruns == 0) { L.SRCG = o; o += align256((cfg->model == RMHD_TWO_FLUID ? 9 : 5) * pl); }
     L.ACC = o; o += align256(nc * pl);
     L.stage = o; o += align256((size_t)std::max(nc, np) * g.ncell * sizeof(double));
     L.scratch = o; o += align256(reduce_scratch_doubles() * sizeof(double));

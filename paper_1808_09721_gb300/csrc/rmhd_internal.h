@@ -54,7 +54,7 @@ struct FluxArgs {
     double *lout;           // nout = 0 (x-y pass of a 3-D grid): L_x + L_y is written here, nothing else
     const double *lin;      // if not null: added to L before the combinations (z pass of a 3-D grid)
     double *srcg;           // FP64 line-sweep passes: planes written by the stage kernel at the stage
-                            // state: one fluid J (3), two fluids Sbar (3), taubar, E (3)
+                            // state: one fluid J (3), Z, p + (E^2+B^2)/2; two fluids Sbar (3), taubar, E (3)
     double *lscr;           // single fluid, FP64, 2-D: the x part of L between the x and y sweeps
                             // (NC planes of ncell cells)
 };
@@ -77,8 +77,9 @@ struct StageArgs {
     int rcap;
     int first_start;  // tests of the restart path: 1 or 2 skips the earlier starts (0: all starts)
     // if not null, what the FP64 line-sweep flux pass takes from the stage
-    // solve: one fluid, the current J of the stage state (3 planes); two
-    // fluids, its source entries Sbar (3), taubar, E (3) (7 planes)
+    // solve: one fluid, the current J, Z = rho h W^2 and p + (E^2 + B^2)/2 of
+    // the stage state (5 planes); two fluids, its source entries Sbar (3),
+    // taubar, E (3) (7 planes)
     double *src;
 };
 
