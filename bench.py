@@ -56,16 +56,16 @@ ALG_FP64_FLOPS_PER_CELL = {"flux1": 1918, "flux2": 1880, "tf_flux1": 2556, "tf_f
 # FP64 arithmetic instructions the kernels themselves issue (dadd, dmul, dfma;
 # one each) per interior cell on a 2-D grid, counted by ncu's
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma} on a 512x512 KHI step.
-FP64_INST_PER_CELL = {"stage": 180.0, "flux1": 684.1, "flux2": 670.1}
+FP64_INST_PER_CELL = {"stage": 184.0, "flux1": 668.5, "flux2": 654.5}
 # DRAM bytes (read + write) per cell and launch of the same kernels, from an
 # ncu capture of the 512x512 KHI step (dram__bytes_read.sum + write.sum): the
 # reads scale with the cells; at that size part of the writes is still in L2
 # when a kernel ends, so the full-size writes are somewhat higher.
-DRAM_BYTES_PER_CELL = {"stage": 123.9, "flux1": 466.4, "flux2": 344.0}
+DRAM_BYTES_PER_CELL = {"stage": 126.6, "flux1": 484.9, "flux2": 365.1}
 # Algorithmic HBM bytes per cell for each kernel (read once + written once; the
-# stage also writes the current J of its result, which the flux passes read).
-BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5 + 3), "flux1": 8 * (19 + 3 + 14 + 28),
-                  "flux2": 8 * (19 + 3 + 14 + 19)}
+# stage also writes J, Z and p + (E^2 + B^2)/2 of its result for the flux passes).
+BYTES_PER_CELL = {"stage": 8 * (14 + 1 + 14 + 5 + 5), "flux1": 8 * (19 + 5 + 14 + 28),
+                  "flux2": 8 * (19 + 5 + 14 + 19)}
 
 
 def _peaks():
