@@ -115,11 +115,13 @@ __device__ __forceinline__ void stage_resid(const T E[3], T p, const T St[3], T 
     }
 }
 
-// The stage residual of the FP64 passes, with the per-cell constants folded:
-// tD = tau - B^2/2 + D (a = tD - E^2/2), arho = a dt varrho, asig = a dt sigma,
-//   G = E - r_E + arho v + asig W [E + v x B - (v.E) v].
-__device__ __forceinline__ void em_split_k(const double E[3], const double Sv[3], const double B[3], double tD,
-                                           double St[3], double &a, double &S2) {
+// The EM split and the stage residual of the FP64 passes, with the per-cell
+// constants folded: tD = tau - B^2/2 + D (a = tD - E^2/2), arho = a dt varrho,
+// asig = a dt sigma,
+//   G = E - r_E + arho v + asig W u,  u = E + v x B - (v.E) v
+// (u is returned: the current at the result is varrho v + sigma W u).
+__device__ __forceinline__ void em_split_folded(const double E[3], const double Sv[3], const double B[3], double tD,
+                                                double St[3], double &a, double &S2) {
     double ExB[3];
     cross(E, B, ExB);
     St[0] = Sv[0] - ExB[0];
@@ -128,9 +130,9 @@ __device__ __forceinline__ void em_split_k(const double E[3], const double Sv[3]
     a = tD - 0.5 * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
     S2 = St[0] * St[0] + St[1] * St[1] + St[2] * St[2];
 }
-__device__ __forceinline__ void stage_resid_k(const double E[3], double p, const double St[3], double a,
-                                              const double B[3], const double rE[3], double arho, double asig,
-                                              double G[3], double v[3], double &W, double u[3]) {
+__device__ __forceinline__ void stage_resid_folded(const double E[3], double p, const double St[3], double a,
+                                                   const double B[3], const double rE[3], double arho, double asig,
+                                                   double G[3], double v[3], double &W, double u[3]) {
     const double rZ = s_rcp(a + p);
     v[0] = St[0] * rZ;
     v[1] = St[1] * rZ;
@@ -354,11 +356,11 @@ __device__ __forceinline__ int stage_solve(const double *rp, long long ps, doubl
     bool pconv = false;
     int pass = 0;
     for (; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
-        em_split_k(Ed, Sv, B, tD, St64, a64, S264);
+        em_split_folded(Ed, Sv, B, tD, St64, a64, S264);
         const double dp = pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
         pdd -= dp;
         pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
-        stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
+        stage_resid_folded(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
         float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
         // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
         // infinity, so a non-finite G fails the tests)
@@ -543,13 +545,13 @@ __device__ __forceinline__ int stage_attempt(const double *rp, long long ps, dou
         float gres = 0.f;
         bool pconv = false;
         for (pass = 0; pass < 8; ++pass) {  // constant trip count; the cap k.maxpass breaks below
-            em_split_k(Ed, Sv, B, tD, St64, a64, S264);
+            em_split_folded(Ed, Sv, B, tD, St64, a64, S264);
             const double dp = pres_resid(pdd, a64, S264, Dd, gm1, gam) * rdf;
             pdd -= dp;
             // the pressure step is at round-off: with the FP32 slope each step
             // gains ~7 digits, so the error left after this one is below 1e-13 p
             pconv = f32_of(fabs(dp)) <= 1e-6f * f32_of(pdd);
-            stage_resid_k(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
+            stage_resid_folded(Ed, pdd, St64, a64, B, rE, arho, asig, G64, v64, W64, u64);
             float Gf[3] = {f32_of(G64[0]), f32_of(G64[1]), f32_of(G64[2])};
             // |G| in FP32 from the copy the correction uses (f32_of maps a NaN to an
             // infinity, so a non-finite G fails the tests)
