@@ -121,3 +121,34 @@ def test_jvp_matches_c_oracle_differences():
     h = 1e-8
     fd = _richardson(lambda d: c_oracle(wl, wl.prims + d * vp, nsteps, wl.sigma + d * vs), h)
     assert np.abs(Jv - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+def c_oracle_3d(wl, prims, nsteps):
+    o = O.Sim(wl.model, wl.nx, wl.ny, wl.xlim, wl.ylim, wl.gamma, wl.sigma, wl.bc_x, wl.bc_y, mu_e=wl.mu_e,
+              mu_p=wl.mu_p, kappa=wl.kappa, nz=wl.nz, zlim=wl.zlim, bc_z=wl.bc_z)
+    o.set_prims(np.ascontiguousarray(prims))
+    o.step(wl.dt, nsteps)
+    return o.cons()
+
+
+def test_3d_forward_and_sampled_gradient():
+    """A 3-D grid (z fluxes, ghosts along z): the forward run against the C
+    oracle's 3-D step and 12 sampled gradient entries against its differences."""
+    wl = WL.random_smooth((4, 5, 6), seed=2, model=1, sigma=10.0, mu=20.0)
+    nsteps = 2
+    rng = np.random.default_rng(11)
+    lam = rng.normal(size=(18,) + wl.prims.shape[1:])
+    _, g, _, q = A.gradient(wl, nsteps, lam)
+    ref = c_oracle_3d(wl, wl.prims, nsteps)
+    err = parity_errors(1, q.reshape(18, -1, 1), ref.reshape(18, -1, 1))
+    assert np.all(err <= 1e-12), err
+
+    def Jd(idx, d):
+        p = wl.prims.copy()
+        p[idx] += d
+        return float((lam * c_oracle_3d(wl, p, nsteps)).sum())
+
+    for _ in range(12):
+        idx = tuple(int(rng.integers(0, n)) for n in wl.prims.shape)
+        h = 1e-6 * max(np.abs(wl.prims[idx[0]]).max(), 1e-2)
+        assert abs(g[idx] - _richardson(lambda d: Jd(idx, d), h)) <= 1e-6 * np.abs(g).max(), idx
