@@ -152,3 +152,34 @@ def test_3d_forward_and_sampled_gradient():
         idx = tuple(int(rng.integers(0, n)) for n in wl.prims.shape)
         h = 1e-6 * max(np.abs(wl.prims[idx[0]]).max(), 1e-2)
         assert abs(g[idx] - _richardson(lambda d: Jd(idx, d), h)) <= 1e-6 * np.abs(g).max(), idx
+
+
+@pytest.mark.parametrize("mistake", ["flux_sign", "split_swap", "source_eta"])
+def test_planted_mistakes_fail_the_forward_pin(monkeypatch, mistake):
+    """The forward pin catches plausible mistakes planted in the two-fluid
+    autodiff oracle: a sign flip in the momentum flux's EM stress, the two
+    species of the split swapped, eta = sigma instead of 1/sigma."""
+    import torch
+    wl = WL.random_smooth((5, 6), seed=3, model=1, sigma=10.0, mu=20.0)
+    good = A.forward(wl, 1)
+    if mistake == "flux_sign":
+        orig = A.flux
+
+        def flux(q, w, gamma, mu, j):
+            f = orig(q, w, gamma, mu, j)
+            E, B = q[A.E0:A.E0 + 3], q[A.B0:A.B0 + 3]
+            return f.index_add(0, torch.arange(A.S0, A.S0 + 3), 2.0 * (E * E[j] + B * B[j]))
+        monkeypatch.setattr(A, "flux", flux)
+    elif mistake == "split_swap":
+        orig = A.species_split
+        monkeypatch.setattr(A, "species_split", lambda q, mu: tuple(reversed(orig(q, mu))))
+    else:
+        orig = A.source
+        monkeypatch.setattr(A, "source", lambda q, w, sigma, kappa, mu: orig(q, w, 1.0 / sigma, kappa, mu))
+    try:
+        bad = A.forward(wl, 1)
+    except ArithmeticError:
+        return  # the planted mistake breaks the recovery or the stage solve outright
+    err = parity_errors(1, bad, c_oracle(wl, wl.prims, 1))
+    assert np.max(err) > 1e-6, (mistake, err)
+    assert np.max(parity_errors(1, good, c_oracle(wl, wl.prims, 1))) <= 1e-12
