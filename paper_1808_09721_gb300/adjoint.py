@@ -1,9 +1,10 @@
 """Gradients through SSP2(222) or SSP3(332) IMEX runs as a torch.autograd.Function.
 
 `ImexSteps.apply(prims0, sigma, workload, nsteps, ckpt_every, scheme)` advances the
-resistive model from the primitives `prims0` ([11][ny][nx] or [11][nz][ny][nx] float64 CUDA
-tensor) with conductivity `sigma` (0-d float64 tensor) and returns the final
-conserved state [14][ny][nx]. Its backward runs the library's discrete
+workload's model from the primitives `prims0` ([n_prim][ny][nx] or [n_prim][nz][ny][nx]
+float64 CUDA tensor; n_prim = 11 for one fluid, 16 for two fluids) with conductivity
+`sigma` (0-d float64 tensor) and returns the final conserved state ([14] or [18] planes).
+Its backward runs the library's discrete
 adjoint (rmhd_record / rmhd_adjoint_step): checkpoints every `ckpt_every`
 steps, recomputation per segment, implicit-function-theorem adjoints of the
 per-cell implicit solves. Any functional written with torch ops on the
